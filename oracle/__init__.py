@@ -1,0 +1,190 @@
+"""FP64 CPU oracle for chirplet matching pursuit (test infrastructure only).
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+import this package.  The product path never does, and this package never
+imports the CUDA implementation.  The arithmetic lives in ``act_oracle.c``
+(plain C, double precision); this module only builds it with gcc and
+marshals numpy arrays through ctypes.
+
+See ``act_oracle.c`` for the passages of the paper each function follows and
+for the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "act_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile act_oracle.c into liboracle.so (gcc, -O2, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.act_oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.act_oracle_max_threads.restype = ctypes.c_int
+        lib.act_oracle_range_count.argtypes = [ctypes.c_double] * 3
+        lib.act_oracle_range_count.restype = ctypes.c_int64
+        lib.act_oracle_atom_params.argtypes = [_dp, _i64p, ctypes.c_int64, _dp, _dp, _dp, _dp]
+        lib.act_oracle_atom_complex.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp]
+        lib.act_oracle_atom.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp]
+        lib.act_oracle_atom.restype = ctypes.c_int
+        lib.act_oracle_dictionary.argtypes = [_dp, _i64p, ctypes.c_int, ctypes.c_double, _dp, _u8p]
+        lib.act_oracle_dictionary.restype = ctypes.c_int64
+        lib.act_oracle_scores.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, _dp, _dp]
+        lib.act_oracle_scores_grid.argtypes = [_dp, _i64p, ctypes.c_int, ctypes.c_double, _dp, _dp]
+        lib.act_oracle_select.argtypes = [_dp, ctypes.c_int64, _i64p, _i64p]
+        lib.act_oracle_mp.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, _dp, ctypes.c_int, _i64p,
+                                      _dp, _dp, _dp]
+        lib.act_oracle_mp.restype = ctypes.c_int
+        lib.act_oracle_mp_grid.argtypes = [_dp, _i64p, ctypes.c_int, ctypes.c_double, _dp,
+                                           ctypes.c_int, _i64p, _dp, _dp, _dp, _dp]
+        lib.act_oracle_mp_grid.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a: np.ndarray):
+    return a.ctypes.data_as(_i64p)
+
+
+def _grid_arrays(grid) -> Tuple[np.ndarray, np.ndarray]:
+    axes = np.array([grid.tc.lo, grid.tc.step, grid.fc.lo, grid.fc.step, grid.logdt.lo,
+                     grid.logdt.step, grid.c.lo, grid.c.step], dtype=np.float64)
+    counts = np.array([grid.tc.count, grid.fc.count, grid.logdt.count, grid.c.count],
+                      dtype=np.int64)
+    return axes, counts
+
+
+def set_threads(n: int) -> None:
+    _load().act_oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().act_oracle_max_threads())
+
+
+def range_count(start: float, stop: float, step: float) -> int:
+    """Values in the half-open range [start, stop) with the given step (Table 2)."""
+    return int(_load().act_oracle_range_count(float(start), float(stop), float(step)))
+
+
+def atom_params(grid, flat: int) -> Tuple[float, float, float, float]:
+    axes, counts = _grid_arrays(grid)
+    out = [ctypes.c_double() for _ in range(4)]
+    _load().act_oracle_atom_params(_d(axes), _i(counts), int(flat), *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def atom_complex(tc, fc, logdt, c, fs, n_samples) -> np.ndarray:
+    """Eq. (1) with its prefactor, sampled at t = n / fs (complex128)."""
+    re = np.empty(n_samples)
+    im = np.empty(n_samples)
+    _load().act_oracle_atom_complex(tc, fc, logdt, c, fs, int(n_samples), _d(re), _d(im))
+    return re + 1j * im
+
+
+def atom(tc, fc, logdt, c, fs, n_samples) -> Tuple[np.ndarray, bool]:
+    """Unit-norm real dictionary atom; returns (g, degenerate)."""
+    g = np.empty(n_samples)
+    d = _load().act_oracle_atom(tc, fc, logdt, c, fs, int(n_samples), _d(g))
+    return g, bool(d)
+
+
+def dictionary(grid) -> Tuple[np.ndarray, np.ndarray]:
+    """D[K][n_samples] (float64) and the degenerate-atom mask."""
+    axes, counts = _grid_arrays(grid)
+    K = int(np.prod(counts))
+    D = np.empty((K, grid.n_samples))
+    deg = np.zeros(K, dtype=np.uint8)
+    _load().act_oracle_dictionary(_d(axes), _i(counts), int(grid.n_samples), float(grid.fs), _d(D),
+                                  deg.ctypes.data_as(_u8p))
+    return D, deg.astype(bool)
+
+
+def scores(D: np.ndarray, r: np.ndarray) -> np.ndarray:
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.empty(D.shape[0])
+    _load().act_oracle_scores(_d(D), D.shape[0], D.shape[1], _d(r), _d(out))
+    return out
+
+
+def scores_grid(grid, r: np.ndarray) -> np.ndarray:
+    axes, counts = _grid_arrays(grid)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.empty(int(np.prod(counts)))
+    _load().act_oracle_scores_grid(_d(axes), _i(counts), int(grid.n_samples), float(grid.fs), _d(r),
+                                   _d(out))
+    return out
+
+
+def select(sc: np.ndarray) -> Tuple[int, int]:
+    """(best, runner_up) under the selection rule (lowest index on ties)."""
+    sc = np.ascontiguousarray(sc, dtype=np.float64)
+    b = ctypes.c_int64()
+    s = ctypes.c_int64()
+    _load().act_oracle_select(_d(sc), sc.shape[0], ctypes.byref(b), ctypes.byref(s))
+    return int(b.value), int(s.value)
+
+
+def mp(D: np.ndarray, s: np.ndarray, P: int):
+    """MP over a stored dictionary -> (idx[P], coef[P], residual, energy[P+1])."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    idx = np.empty(P, dtype=np.int64)
+    coef = np.empty(P)
+    r = np.empty(D.shape[1])
+    en = np.empty(P + 1)
+    rc = _load().act_oracle_mp(_d(D), D.shape[0], D.shape[1], _d(s), int(P), _i(idx), _d(coef), _d(r),
+                               _d(en))
+    if rc != 0:
+        raise MemoryError("oracle MP allocation failed")
+    return idx, coef, r, en
+
+
+def mp_grid(grid, s: np.ndarray, P: int):
+    """MP with atoms regenerated from the grid at every order
+    -> (idx[P], coef[P], residual, energy[P+1], gap[P])."""
+    axes, counts = _grid_arrays(grid)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    idx = np.empty(P, dtype=np.int64)
+    coef = np.empty(P)
+    r = np.empty(grid.n_samples)
+    en = np.empty(P + 1)
+    gap = np.empty(P)
+    rc = _load().act_oracle_mp_grid(_d(axes), _i(counts), int(grid.n_samples), float(grid.fs), _d(s),
+                                    int(P), _i(idx), _d(coef), _d(r), _d(en), _d(gap))
+    if rc != 0:
+        raise MemoryError("oracle MP allocation failed")
+    return idx, coef, r, en, gap

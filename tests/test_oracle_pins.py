@@ -1,0 +1,267 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against something other than its own formulas:
+numbers printed in the paper (Table 2), closed forms of Eq. (1), library
+routines that reduce to a special case (scipy.signal.chirp, gausspulse,
+numpy least squares), textbook MP properties, and brute force on tiny grids.
+A plausible slip in the oracle (a dropped term, a wrong sign or unit, a
+transposed operand, a wrong tie rule) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import signal as sps
+
+import oracle
+from paper_2607_16629_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Table 2: grid sizes printed in the paper
+# ---------------------------------------------------------------------------
+def _table2():
+    rows = {}
+    with open(os.path.join(GOLDEN, "table2_ranges.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            sig, axis, a, b, step, total = line.split()
+            rows.setdefault(sig, {"total": int(total), "axes": {}})
+            rows[sig]["axes"][axis] = (float(a), float(b), float(step))
+    return rows
+
+
+@pytest.mark.parametrize("sig", ["EEG", "EMG", "Radar"])
+def test_table2_combination_counts(sig):
+    """Table 2 prints 185,600 / 113,778 / 520,128 combinations."""
+    row = _table2()[sig]
+    total = 1
+    for axis in ("tc", "fc", "logDt", "c"):
+        total *= oracle.range_count(*row["axes"][axis])
+    assert total == row["total"]
+
+
+def test_range_count_matches_numpy_arange():
+    for (a, b, s) in [(0, 256, 16), (-4, 0, 0.3), (20, 450, 10), (-10, 10, 0.75), (10, 8533, 100)]:
+        assert oracle.range_count(a, b, s) == len(np.arange(a, b, s))
+
+
+# ---------------------------------------------------------------------------
+# Eq. (1): the complex atom and its closed forms
+# ---------------------------------------------------------------------------
+def test_eq1_prefactor_gives_unit_energy():
+    """(sqrt(pi) Dt)^(-1/2) makes the integral of |g|^2 equal to 1; the
+    sampled sum times 1/fs matches it when the atom sits well inside the
+    window and spans many samples."""
+    fs = 256.0
+    for (tc, fc, ld, c) in [(256.0, 10.0, -2.5, 3.0), (300.0, 2.0, -2.8, -15.0),
+                            (200.0, 30.0, -3.0, 0.0)]:
+        g = oracle.atom_complex(tc, fc, ld, c, fs, 512)
+        assert abs(np.sum(np.abs(g) ** 2) / fs - 1.0) < 1e-9
+
+
+def test_eq1_envelope_falls_to_exp_minus_half_at_one_duration():
+    """|g(tc + Dt)| / |g(tc)| = exp(-1/2), with Dt = exp(logDt) seconds."""
+    fs = 200.0
+    k = 20  # samples
+    ld = math.log(k / fs)
+    g = oracle.atom_complex(100.0, 17.0, ld, 40.0, fs, 256)
+    assert abs(abs(g[100 + k]) / abs(g[100]) - math.exp(-0.5)) < 1e-13
+    assert abs(abs(g[100 - k]) / abs(g[100]) - math.exp(-0.5)) < 1e-13
+
+
+def test_eq1_instantaneous_frequency():
+    """The phase of Eq. (1) advances at fc + 2 c (t - tc) cycles/s."""
+    fs, tc, fc, c = 1000.0, 500.0, 50.0, 120.0
+    g = oracle.atom_complex(tc, fc, -1.0, c, fs, 1000)
+    ph = np.unwrap(np.angle(g))
+    n = np.arange(1000)
+    tau_mid = (n[:-1] + 0.5 - tc) / fs
+    f_inst = np.diff(ph) * fs / (2 * math.pi)
+    assert np.max(np.abs(f_inst - (fc + 2 * c * tau_mid))) < 1e-6
+
+
+def test_real_atom_is_normalised_real_part_of_eq1():
+    """The dictionary atom equals Re(Eq. 1) divided by its l2 norm."""
+    for (tc, fc, ld, c) in [(10.0, 3.0, -2.0, 5.0), (250.0, 31.0, -3.0, -8.0), (128.5, 0.5, -0.5, 1.3)]:
+        z = oracle.atom_complex(tc, fc, ld, c, 128.0, 256)
+        g, deg = oracle.atom(tc, fc, ld, c, 128.0, 256)
+        assert not deg
+        ref = z.real / np.linalg.norm(z.real)
+        assert np.max(np.abs(g - ref)) < 1e-13
+
+
+def test_atom_against_scipy_chirp_and_gausspulse():
+    """A Gaussian window (gausspulse's envelope) times a linear chirp
+    (scipy.signal.chirp, f0 = fc, f1 = fc + 2c at t1 = 1 s), normalised,
+    equals the oracle's atom: pins tc in samples, fc in Hz, c as written in
+    Eq. (1) and logDt as a natural log."""
+    fs, n = 256.0, 512
+    for (tc, fc, ld, c) in [(100.0, 12.5, -2.2, 7.0), (400.0, 3.0, -1.0, -19.0), (0.0, 30.0, -2.9, 0.0)]:
+        tau = (np.arange(n) - tc) / fs
+        dt = math.exp(ld)
+        bwr = -6.0
+        bw = math.sqrt(-4.0 * math.log(10 ** (bwr / 20.0)) / (2 * dt * dt)) / math.pi
+        _, env = sps.gausspulse(tau, fc=1.0, bw=bw, bwr=bwr, retenv=True)
+        carrier = sps.chirp(tau, f0=fc, t1=1.0, f1=fc + 2 * c, method="linear")
+        ref = env * carrier
+        ref /= np.linalg.norm(ref)
+        g, _ = oracle.atom(tc, fc, ld, c, fs, n)
+        assert np.max(np.abs(g - ref)) < 1e-12
+
+
+def test_atom_with_zero_chirp_is_gausspulse():
+    """c = 0 reduces Eq. (1)'s real part to scipy's Gaussian-modulated cosine."""
+    fs, n, tc, fc, ld = 500.0, 400, 210.0, 40.0, -3.5
+    dt = math.exp(ld)
+    tau = (np.arange(n) - tc) / fs
+    bwr = -6.0
+    bw = math.sqrt(-4.0 * math.log(10 ** (bwr / 20.0)) / (2 * dt * dt)) / (math.pi * fc)
+    ref = sps.gausspulse(tau, fc=fc, bw=bw, bwr=bwr)
+    ref /= np.linalg.norm(ref)
+    g, _ = oracle.atom(tc, fc, ld, 0.0, fs, n)
+    assert np.max(np.abs(g - ref)) < 1e-12
+
+
+def test_every_dictionary_atom_has_unit_norm():
+    grid = synth.scaled_grid(synth.grid_c1(), tc_count=8, fc_count=5)
+    D, deg = oracle.dictionary(grid)
+    assert not deg.any()
+    assert np.max(np.abs(np.linalg.norm(D, axis=1) - 1.0)) < 1e-14
+
+
+def test_dictionary_row_order_and_params():
+    """Row i of D is the atom of flat index i, c fastest, tc slowest."""
+    grid = synth.grid_small_test()
+    D, _ = oracle.dictionary(grid)
+    for i in [0, 1, 5, 17, grid.n_atoms - 1]:
+        p = oracle.atom_params(grid, i)
+        assert p == pytest.approx(grid.params_of(i), abs=0)
+        g, _ = oracle.atom(*p, grid.fs, grid.n_samples)
+        assert np.array_equal(D[i], g)
+    assert oracle.atom_params(grid, 1)[3] == grid.c.lo + grid.c.step
+    assert oracle.atom_params(grid, grid.c.count)[2] == grid.logdt.lo + grid.logdt.step
+
+
+def test_degenerate_atom_is_zero():
+    g, deg = oracle.atom(5000.0, 10.0, -6.0, 0.0, 100.0, 64)   # centre far outside the window
+    assert deg and not np.any(g)
+
+
+# ---------------------------------------------------------------------------
+# Matching pursuit (Eq. 4, Fig. 1)
+# ---------------------------------------------------------------------------
+def test_identity_dictionary_reduces_to_sorting_by_magnitude():
+    """With the canonical basis as dictionary, MP picks samples in order of
+    decreasing |x| (lowest index on ties) with coefficients equal to them."""
+    x = np.array([0.5, -3.0, 2.0, 0.0, 3.0, -1.0, 0.25, 2.0])
+    idx, coef, r, en = oracle.mp(np.eye(8), x, 6)
+    assert list(idx) == [1, 4, 2, 7, 5, 0]
+    assert list(coef) == [-3.0, 3.0, 2.0, 2.0, -1.0, 0.5]
+    assert list(r) == [0, 0, 0, 0, 0, 0, 0.25, 0]
+    assert en[-1] == 0.25 ** 2
+
+
+def test_lone_on_grid_atom_is_recovered_exactly():
+    grid = synth.grid_c1()
+    D, _ = oracle.dictionary(grid)
+    for j, a in [(1234, 1.7), (16383, -0.6), (0, 2.0)]:
+        idx, coef, r, en = oracle.mp(D, a * D[j], 1)
+        assert idx[0] == j
+        assert abs(coef[0] - a) <= 1e-12 * abs(a)
+        assert np.linalg.norm(r) <= 1e-12 * abs(a)
+
+
+def test_energy_identity_and_monotone_residual():
+    """|s|^2 = sum_i c_i^2 + |r_k|^2 at every k; |r_k| never grows."""
+    w = synth.workload_c1()
+    grid = synth.scaled_grid(w.grid, tc_count=16, fc_count=8)
+    D, _ = oracle.dictionary(grid)
+    s = w.signals[0]
+    idx, coef, r, en = oracle.mp(D, s, 12)
+    e0 = float(s @ s)
+    for k in range(13):
+        assert abs(e0 - (np.sum(coef[:k] ** 2) + en[k])) <= 1e-12 * e0
+    assert np.all(np.diff(en) <= 0.0)
+    assert abs(en[-1] - float(r @ r)) <= 1e-14 * e0
+
+
+def test_residual_orthogonal_to_chosen_atom():
+    w = synth.workload_c1()
+    grid = synth.scaled_grid(w.grid, tc_count=8, fc_count=8)
+    D, _ = oracle.dictionary(grid)
+    s = w.signals[0]
+    r = s.copy()
+    for _ in range(4):
+        idx, coef, r, _ = oracle.mp(D, r, 1)
+        assert abs(D[idx[0]] @ r) <= 1e-13 * np.linalg.norm(s)
+
+
+def test_brute_force_best_one_term_approximation():
+    """At every order the chosen atom and coefficient minimise |r - a g|^2
+    over all atoms and all real a (least squares per atom, numpy lstsq)."""
+    grid = synth.grid_small_test()
+    D, _ = oracle.dictionary(grid)
+    s = synth.random_signals(90, 1, grid.n_samples)[0]
+    r = s.copy()
+    for _ in range(6):
+        errs, coefs = [], []
+        for i in range(D.shape[0]):
+            a, res, *_ = np.linalg.lstsq(D[i][:, None], r, rcond=None)
+            coefs.append(a[0])
+            errs.append(float(np.sum((r - a[0] * D[i]) ** 2)))
+        best = int(np.argmin(errs))
+        idx, coef, r_next, _ = oracle.mp(D, r, 1)
+        assert idx[0] == best
+        assert abs(coef[0] - coefs[best]) <= 1e-12 * max(1.0, abs(coefs[best]))
+        r = r_next
+
+
+def test_grid_mode_matches_stored_mode():
+    """Regenerating atoms every order gives the same decomposition as the
+    stored dictionary."""
+    w = synth.workload_c1()
+    grid = synth.scaled_grid(w.grid, tc_count=16, fc_count=8)
+    D, _ = oracle.dictionary(grid)
+    s = w.signals[0]
+    a = oracle.mp(D, s, 5)
+    b = oracle.mp_grid(grid, s, 5)
+    assert np.array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-13)
+    np.testing.assert_allclose(a[2], b[2], atol=1e-13)
+    assert np.all(b[4] >= 0.0) and np.all(b[4] <= 1.0)
+
+
+def test_ties_go_to_lowest_index():
+    sc = np.array([0.1, -0.7, 0.7, 0.3, -0.7])
+    assert oracle.select(sc) == (1, 2)
+    D = np.array([[1.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    idx, coef, r, _ = oracle.mp(D, np.array([2.0, 0.0]), 1)
+    assert idx[0] == 0 and coef[0] == 2.0
+
+
+def test_zero_signal_picks_index_zero_with_zero_coefficient():
+    grid = synth.grid_small_test()
+    D, _ = oracle.dictionary(grid)
+    idx, coef, r, en = oracle.mp(D, np.zeros(grid.n_samples), 3)
+    assert list(idx) == [0, 0, 0] and not np.any(coef) and not np.any(r) and not np.any(en)
+
+
+def test_c1_recovers_planted_atoms():
+    """Three on-grid atoms plus white noise (sigma 0.05): the first three
+    orders find the planted atoms and leave about the noise energy."""
+    w = synth.workload_c1()
+    D, _ = oracle.dictionary(w.grid)
+    s = w.signals[0]
+    idx, coef, r, en = oracle.mp(D, s, w.n_atoms)
+    planted = {w.grid.flat_of(
+        round((tc - w.grid.tc.lo) / w.grid.tc.step), round((fc - w.grid.fc.lo) / w.grid.fc.step),
+        round((ld - w.grid.logdt.lo) / w.grid.logdt.step), round((c - w.grid.c.lo) / w.grid.c.step))
+        for (tc, fc, ld, c, a) in w.truth[0]}
+    assert set(int(i) for i in idx[:3]) == planted
+    noise_energy = w.grid.n_samples * 0.05 ** 2
+    assert 0.5 * noise_energy < en[3] < 1.5 * noise_energy
