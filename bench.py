@@ -1,0 +1,444 @@
+"""Benchmark of the residual-projection chirplet matching pursuit on GB300.
+
+Default workload (one step = one whole decomposition, all orders):
+  EEG-like window, N = 512 samples at fs = 256 Hz, 5 random chirplets plus
+  pink noise at 10 dB SNR, searched over the 128 tc x 64 fc x 8 logDt x
+  32 c = 2,097,152-atom grid (FP32 dictionary, 4.3 GB, resident in HBM),
+  20 matching-pursuit orders, FP32 GEMV search (one channel per GPU).
+With the tensor-core search built, the same line also reports the batched
+BF16 search of 64 such channels ("bf16_batched").
+
+Metric: chirplet projections/s = channels * atoms * orders / time, plus MP
+atoms/s = channels * orders / time.  The dictionary (4.3 GB) is larger than
+L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank decomposes its own channel (weak scaling, no
+collective on the data path); the timing is the max over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "chirplet projections/s and MP atoms/s: BF16-TC batched vs FP32 plain, % roofline"
+UNIT = "projections/s"
+WORKLOAD = "eeg_like_fp32_1ch_n512_fs256_grid128x64x8x32_k2097152_p20"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(summary_name, kernel_files):
+    """DRAM bytes per launch recorded in a committed ncu summary, or None if
+    absent or if the kernel sources changed since it was taken."""
+    path = os.path.join(PROFILES, summary_name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != _source_hash(kernel_files):
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm / CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def _oracle_sample(tc_cols: int, orders: int):
+    import oracle
+    from paper_2607_16629_gb300 import synth
+    full = synth.grid_eeg()
+    sub = synth.Grid(full.n_samples, full.fs, synth.Axis(full.tc.lo, full.tc.step, tc_cols), full.fc,
+                     full.logdt, full.c)
+    s, _ = synth.eeg_like_signal(2, 0)
+    D, _ = oracle.dictionary(sub)
+    t0 = time.perf_counter()
+    oracle.mp(D, s, orders)
+    dt = time.perf_counter() - t0
+    return sub.n_atoms * orders / dt, sub.n_atoms, dt
+
+
+def cpu_baseline(target_s: float = 12.0):
+    import oracle
+    cores = oracle.max_threads()
+    # calibrate on 2 tc columns (32,768 atoms), then size the sample
+    rate, _, _ = _oracle_sample(2, 2)
+    per_col = 16384 * 20 / rate
+    cols = int(max(2, min(128, target_s / per_col)))
+    rate, K, dt = _oracle_sample(cols, 20)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle MP, 20 orders over the first {cols} of 128 tc columns "
+                      f"({K} of 2,097,152 atoms), N=512; {dt:.1f} s timed; dictionary build excluded"}
+
+
+def run_reference(args):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return
+    import oracle
+    cores = oracle.max_threads()
+    cols = 4  # 65,536 atoms per step, 20 orders: a bounded sample of the workload
+    for _ in range(args.warmup):
+        _oracle_sample(cols, 20)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, K, dt = _oracle_sample(cols, 20)
+        rates.append(r)
+        times.append(dt)
+    value = float(np.sum([16384 * cols * 20 for _ in times]) / np.sum(times))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_atoms": 16384 * cols},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle MP, 20 orders over {16384 * cols} of 2,097,152 atoms "
+                                       f"per step, N=512, dictionary build excluded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_16629_gb300 import act, synth
+
+    rank, local_rank, world = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    grid = synth.grid_eeg()
+    P = 20
+    sig_np, _ = synth.eeg_like_signal(2, rank)  # rank r decomposes EEG-like channel r
+    K = grid.n_atoms
+    h = act.act_grid_create(grid, local_rank)
+    build_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    build_ev[0].record(stream)
+    act.act_dictionary_build(h, act.ACT_DICT_FP32, stream)
+    build_ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    build_ms = build_ev[0].elapsed_time(build_ev[1])
+
+    sig = torch.tensor(sig_np[None, :], dtype=torch.float32, device=dev)
+    atoms = torch.empty((1, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev)
+    coef = torch.empty((1, P), dtype=torch.float32, device=dev)
+    resid = torch.empty((1, grid.n_samples), dtype=torch.float32, device=dev)
+    energy = torch.empty((1, P + 1), dtype=torch.float64, device=dev)
+    act.act_set_profiling(h, True)
+
+    def step():
+        act.act_decompose(h, sig, 1, P, atoms, coef, resid, energy, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+    search_ms, search_n, kernels = act.act_profile_read(h)
+    st = act.act_grid_status(h, stream)
+    if st != act.ACT_OK:
+        raise RuntimeError(f"device status {act.status_name(st)}")
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = world * K * P * args.steps
+    value = units / (ms / 1e3)
+
+    # dominant kernel: the FP32 GEMV (events around each launch inside the graph)
+    peaks, peak_kind = _measured_peaks()
+    gemv_bytes = K * grid.n_samples * 4 + grid.n_samples * 4
+    avg_ms = search_ms / max(1, search_n)
+    achieved = gemv_bytes / (avg_ms / 1e3) / 1e9
+    traffic = _profile_traffic("gemv_argmax_eeg_k2097152_n512.md",
+                               ["paper_2607_16629_gb300/csrc/act_kernels.cu",
+                                "paper_2607_16629_gb300/csrc/act_device.cuh"])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_gemv<4,1> (FP32 GEMV + fused argmax)",
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": gemv_bytes, "avg_launch_ms": avg_ms}
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    hs = torch.tensor(sig_np[None, :], dtype=torch.float32).pin_memory()
+    ha = torch.empty((1, P, act.ATOM_BYTES), dtype=torch.uint8).pin_memory()
+    hc = torch.empty((1, P), dtype=torch.float32).pin_memory()
+    hr = torch.empty((1, grid.n_samples), dtype=torch.float32).pin_memory()
+    he = torch.empty((1, P + 1), dtype=torch.float64).pin_memory()
+    act.act_set_profiling(h, False)
+    for _ in range(3):
+        act.act_decompose(h, hs, 1, P, ha, hc, hr, he, stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        act.act_decompose(h, hs, 1, P, ha, hc, hr, he, stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * K * P * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": hs.numel() * 4,
+           "d2h_bytes_per_step": ha.numel() + hc.numel() * 4 + hr.numel() * 4 + he.numel() * 8}
+    act.act_destroy(h)
+
+    bf16 = None
+    if not args.no_bf16:
+        bf16 = bench_bf16(args, dev, stream, peaks, peak_kind)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "channels_per_gpu": 1, "n_samples": grid.n_samples,
+                           "fs_hz": grid.fs, "grid_atoms": K, "orders": P,
+                           "dictionary": "FP32 4.29 GB stored in HBM", "search": "FP32 GEMV + fused argmax",
+                           "l2": "inputs larger than L2 (4.3 GB dictionary streamed every order); no flush",
+                           "parallelism": f"{world} independent channel(s), one per GPU"},
+                "atoms_per_s": world * P * args.steps / (ms / 1e3),
+                "dictionary_build_ms": build_ms,
+                "roofline": roofline, "e2e": e2e, "gpu_launches": kernels * args.steps,
+                "clocks": clk.summary()}
+        if bf16 is not None:
+            line["bf16_batched"] = bf16
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bench_bf16(args, dev, stream, peaks, peak_kind):
+    """64 EEG-like channels, BF16 tensor-core search with FP32 rescore,
+    against the plain FP32 path run channel by channel."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    w = synth.workload_c3()
+    B, P, K, L = w.signals.shape[0], w.n_atoms, w.grid.n_atoms, w.grid.n_samples
+    h = act.act_grid_create(w.grid, dev.index)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_BF16, stream)
+    except act.ActError as e:
+        act.act_destroy(h)
+        return {"status": f"unavailable: {e}"}
+    sig = torch.tensor(w.signals, dtype=torch.float32, device=dev)
+    out = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+           torch.empty((B, P), dtype=torch.float32, device=dev),
+           torch.empty((B, L), dtype=torch.float32, device=dev),
+           torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
+    act.act_set_search(h, act.ACT_SEARCH_BF16)
+    act.act_set_profiling(h, True)
+    steps = max(3, args.steps // 2)
+    for _ in range(3):
+        act.act_decompose(h, sig, B, P, *out, stream)
+    torch.cuda.synchronize(dev)
+    c0, f0 = act.act_bf16_stats(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        act.act_decompose(h, sig, B, P, *out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    search_ms, search_n, kernels = act.act_profile_read(h)
+    c1, f1 = act.act_bf16_stats(h)
+    # plain FP32 comparator: the same 64 channels, one FP32 GEMV decomposition each
+    act.act_set_search(h, act.ACT_SEARCH_FP32)
+    act.act_set_profiling(h, False)
+    one = [o[:1].contiguous() for o in out]
+    act.act_decompose(h, sig[:1].contiguous(), 1, P, *one, stream)
+    torch.cuda.synchronize(dev)
+    f_e0, f_e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f_e0.record(stream)
+    for b in range(B):
+        act.act_decompose(h, sig[b:b + 1], 1, P, *one, stream)
+    f_e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp32_ms = f_e0.elapsed_time(f_e1)
+    act.act_destroy(h)
+    value = B * K * P * steps / (ms / 1e3)
+    avg = search_ms / max(1, search_n)
+    bytes_per = K * L * 2
+    flops_per = 2.0 * K * L * B
+    return {"workload": f"eeg_like_bf16_{B}ch_n512_grid128x64x8x32_k2097152_p20", "value": value, "unit": UNIT,
+            "atoms_per_s": B * P * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+            "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 rescore",
+            "roofline": {"bound": "hbm", "achieved": bytes_per / (avg / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": bytes_per / (avg / 1e3) / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": f"{peak_kind} hbm_gbs", "avg_search_ms": avg,
+                         "tensor_tflops": flops_per / (avg / 1e3) / 1e12,
+                         "tensor_frac_of_bf16_peak": flops_per / (avg / 1e3) / 1e12 / peaks["bf16_tflops"]},
+            "certified_orders": c1 - c0, "fallback_orders": f1 - f0,
+            "fp32_plain_per_channel": {"value": B * K * P / (fp32_ms / 1e3), "ms": fp32_ms},
+            "speedup_vs_fp32_plain": (B * K * P * steps / (ms / 1e3)) / (B * K * P / (fp32_ms / 1e3)),
+            "gpu_launches": kernels * steps}
+
+
+def run_profile_case(args):
+    """Small, self-checking cases for ncu captures: a few launches of one
+    search kernel on a dictionary larger than L2 but a few GB at most.
+      gemv_small: FP32 GEMV over 1,048,576 EEG-grid atoms (2.1 GB), 1 channel.
+      bf16_small: BF16 GEMM search over the same atoms, 64 channels."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    full = synth.grid_eeg()
+    grid = synth.Grid(full.n_samples, full.fs, synth.Axis(full.tc.lo, full.tc.step, 64), full.fc, full.logdt,
+                      full.c)
+    B = 1 if args.case == "gemv_small" else 64
+    sig = torch.tensor(np.stack([synth.eeg_like_signal(2, b)[0] for b in range(B)]), dtype=torch.float32,
+                       device="cuda")
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32 if B == 1 else act.ACT_DICT_BF16)
+        act.act_set_search(h, act.ACT_SEARCH_FP32 if B == 1 else act.ACT_SEARCH_BF16)
+        for _ in range(args.steps):
+            act.decompose(h, sig, 3)
+        torch.cuda.synchronize()
+        st = act.act_grid_status(h)
+        if st != act.ACT_OK:
+            raise RuntimeError(act.status_name(st))
+    finally:
+        act.act_destroy(h)
+    print(json.dumps({"case": args.case, "atoms": grid.n_atoms, "channels": B, "ok": True}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small"],
+                    help="small single-kernel cases for profiler captures (not bench lines)")
+    args = ap.parse_args()
+    if args.case != "default":
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * act.h -- C ABI of the GB300 residual-projection matching-pursuit library
+ * for Gaussian-chirplet dictionaries (Adaptive Chirplet Transform).
+ *
+ * The operation (Sec. III-A, Eq. (3)-(4), Fig. 1): given real signals s and a
+ * finite grid of chirplet parameters theta = (tc, fc, logDt, c), return P
+ * atoms theta_k with coefficients c_k and the residual r_P of the greedy
+ * decomposition
+ *     r_0 = s;  i* = argmax_i |<g_i, r_k>|;  c_k = <g*, r_k>;
+ *     r_{k+1} = r_k - c_k g*,
+ * where every g_i is the real part of Eq. (1) sampled on the window and
+ * scaled to unit l2 norm (Sec. III-A).  The projection of all atoms against
+ * the residual is the matrix product P = D X^T of Sec. IV-A; the BFGS
+ * refinement of Fig. 1 is not part of this library's search.
+ *
+ * Units: tc in samples (0 = first sample), tau = (n - tc) / fs seconds,
+ * fc in Hz, c in Hz/s multiplying tau^2 in the phase of Eq. (1) (the
+ * instantaneous frequency is fc + 2 c tau), Dt = exp(logDt) seconds.
+ * Flat atom index: ((i_tc * N_fc + i_fc) * N_logDt + i_logDt) * N_c + i_c.
+ * Ties in |score| go to the lowest flat index.
+ *
+ * Conventions for every call:
+ *   - no call throws; each returns an act_status;
+ *   - the library owns the grid, its dictionary and all work buffers; the
+ *     caller owns every signal and output buffer it passes in;
+ *   - input buffers are never modified;
+ *   - calls that take a cuda_stream (a cudaStream_t, NULL = legacy default
+ *     stream) enqueue their GPU work on it and return without waiting,
+ *     except where a host buffer forces a copy back (then they wait);
+ *   - a grid may be used by one host thread at a time.
+ */
+#ifndef ACT_H
+#define ACT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ACT_API __attribute__((visibility("default")))
+#else
+#define ACT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ACT_OK = 0,
+    ACT_ERR_INVALID_ARG = 1,    /* NULL pointer, bad size, bad grid */
+    ACT_ERR_OOM = 2,            /* device allocation failed (no CPU fallback) */
+    ACT_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    ACT_ERR_NONFINITE = 4,      /* an input signal held NaN or Inf */
+    ACT_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up */
+    ACT_ERR_NOT_BUILT = 6,      /* act_dictionary_build has not run */
+    ACT_ERR_UNSUPPORTED = 7     /* size or mode outside what this build handles */
+} act_status;
+
+/* One grid axis: value_i = lo + i * step, i = 0 .. count-1. */
+typedef struct {
+    double lo;
+    double step;
+    int32_t count;
+} act_axis;
+
+/* A dictionary grid (Sec. III-A, Table 2) on an n_samples window at fs Hz. */
+typedef struct {
+    int32_t n_samples; /* window length L, 1 .. 2048 */
+    double fs;         /* sample rate, Hz */
+    act_axis tc;       /* time centre, samples */
+    act_axis fc;       /* frequency centre, Hz */
+    act_axis logdt;    /* natural log of the duration in seconds */
+    act_axis c;        /* chirp rate, Hz/s */
+} act_grid_desc;
+
+/* How act_dictionary_build stores the dictionary.
+ *   ACT_DICT_FP32: D as FP32 [K][Lp] (Lp = L rounded up to 128), searched by
+ *                  the FP32 GEMV / multi-channel GEMV.
+ *   ACT_DICT_BF16: D as FP32 [K][Lp] plus BF16 [K][Lb] (Lb = L rounded up to
+ *                  64) for the tensor-core search; FP32 rows are used to
+ *                  rescore candidates and for the update.
+ *   ACT_DICT_AUTO: ACT_DICT_FP32.
+ *   ACT_DICT_RECOMPUTE: reserved (atoms recomputed inside the search). */
+typedef enum {
+    ACT_DICT_AUTO = 0,
+    ACT_DICT_FP32 = 1,
+    ACT_DICT_BF16 = 2,
+    ACT_DICT_RECOMPUTE = 3
+} act_dict_mode;
+
+/* Which search act_decompose runs.
+ *   ACT_SEARCH_FP32: FP32 GEMV with the argmax fused (CUDA cores).
+ *   ACT_SEARCH_BF16: BF16 tcgen05 GEMM with a fused per-channel top-8,
+ *                    FP32 rescore of the 8 candidates, and an FP32 full
+ *                    search for any channel whose candidate set cannot be
+ *                    certified to hold the FP32 argmax.
+ *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
+ *                    FP32 otherwise. */
+typedef enum {
+    ACT_SEARCH_AUTO = 0,
+    ACT_SEARCH_FP32 = 1,
+    ACT_SEARCH_BF16 = 2
+} act_search_mode;
+
+/* One selected atom: its grid parameters and flat index. */
+typedef struct {
+    double tc;
+    double fc;
+    double logdt;
+    double c;
+    int64_t flat_index;
+} act_atom;
+
+typedef struct act_grid act_grid; /* opaque, library-owned */
+
+/* Human-readable name of a status code (static string, never NULL). */
+ACT_API const char *act_status_string(act_status status);
+
+/* Detail of the last failing CUDA call made by this library on the calling
+ * host thread ("" when none); valid until the next call on that thread. */
+ACT_API const char *act_last_error_message(void);
+
+/* Fills *out from (start, stop, step) triples enumerated as half-open
+ * sequences start, start+step, ... < stop, which is how the ranges of
+ * Table 2 give their printed combination counts.  Host only, no GPU.
+ * Errors: ACT_ERR_INVALID_ARG for NULL pointers, step <= 0, an empty axis,
+ * n_samples outside 1..2048 or fs <= 0. */
+ACT_API act_status act_grid_from_ranges(int32_t n_samples, double fs, const double tc[3],
+                                const double fc[3], const double logdt[3], const double c[3],
+                                act_grid_desc *out);
+
+/* Creates a grid on CUDA device `device` (Sec. III-A).  Allocates nothing
+ * large: the dictionary is made by act_dictionary_build.  *out receives the
+ * handle.  Errors: ACT_ERR_INVALID_ARG (bad descriptor, more than 2^32-1
+ * atoms), ACT_ERR_CUDA (device not usable). */
+ACT_API act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid **out);
+
+/* Number of atoms K of the grid and the FP32 row stride Lp in floats. */
+ACT_API act_status act_grid_size(const act_grid *grid, int64_t *n_atoms, int32_t *row_stride);
+
+/* Generates every atom on the device (Eq. (1) real part, unit l2 norm,
+ * Sec. III-A) in the layout `mode` selects, replacing any earlier build.
+ * Enqueued on cuda_stream.  Errors: ACT_ERR_OOM when the dictionary does not
+ * fit (nothing is kept), ACT_ERR_UNSUPPORTED for ACT_DICT_RECOMPUTE. */
+ACT_API act_status act_dictionary_build(act_grid *grid, act_dict_mode mode, void *cuda_stream);
+
+/* Selects the search act_decompose runs (see act_search_mode). */
+ACT_API act_status act_set_search(act_grid *grid, act_search_mode mode);
+
+/* Residual-projection matching pursuit (Eq. (4), Fig. 1) of `channels`
+ * independent signals, n_atoms orders each, as one CUDA-graph launch.
+ *   signals       [channels][n_samples] float32, device or host memory;
+ *   atoms_out     [channels][n_atoms] act_atom, device or host, may be NULL;
+ *   coeffs_out    [channels][n_atoms] float32 c_k, device or host, may be NULL;
+ *   residuals_out [channels][n_samples] float32 r_P, device or host, may be NULL;
+ *   energy_out    [channels][n_atoms+1] float64 |r_k|^2 for k = 0..n_atoms
+ *                 (FP64 sums of the FP32 residual), device or host, may be NULL.
+ * Device/host is detected per pointer.  With only device buffers the call
+ * returns after enqueueing; with any host buffer it waits for the result.
+ * Errors: ACT_ERR_NOT_BUILT, ACT_ERR_INVALID_ARG (channels < 1,
+ * n_atoms < 1, NULL signals), ACT_ERR_OOM, ACT_ERR_CUDA.  A NaN/Inf in the
+ * signals or a device-side timeout is reported by act_grid_status. */
+ACT_API act_status act_decompose(act_grid *grid, const float *signals, int32_t channels, int32_t n_atoms,
+                         act_atom *atoms_out, float *coeffs_out, float *residuals_out,
+                         double *energy_out, void *cuda_stream);
+
+/* Projection P = D X^T of Sec. IV-A without the selection: scores
+ * [channels][K] float32 (device memory) of every atom against each of
+ * `channels` signals [channels][n_samples] (device memory), on the FP32
+ * dictionary.  Errors as act_decompose. */
+ACT_API act_status act_project(act_grid *grid, const float *signals, int32_t channels, float *scores,
+                       void *cuda_stream);
+
+/* Copies `count` FP32 dictionary rows starting at atom `first` into
+ * out[count][n_samples] (device or host memory); waits when out is host
+ * memory. */
+ACT_API act_status act_dictionary_rows(act_grid *grid, int64_t first, int64_t count, float *out,
+                               void *cuda_stream);
+
+/* Waits for cuda_stream and returns the first device-side error recorded
+ * by this grid's kernels since the last call (ACT_ERR_NONFINITE,
+ * ACT_ERR_DEVICE_TIMEOUT), then clears it; ACT_OK otherwise. */
+ACT_API act_status act_grid_status(act_grid *grid, void *cuda_stream);
+
+/* Kernel-level measurement hooks used by the benchmark.
+ * act_set_profiling(grid, 1) makes later act_decompose graphs record a CUDA
+ * event pair around every search-kernel launch (the GEMV, or the GEMM with
+ * its rescore); act_profile_read waits for the last act_decompose and
+ * returns the summed search-kernel milliseconds and launch count of that
+ * call.  *kernels receives the number of kernels one act_decompose launches. */
+ACT_API act_status act_set_profiling(act_grid *grid, int32_t enable);
+ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, int32_t *search_launches,
+                            int32_t *kernels);
+
+/* BF16 search statistics since the grid was created: orders whose top-8
+ * certificate held, and orders that fell back to the FP32 full search. */
+ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *certified, int64_t *fallbacks);
+
+/* Frees the grid, its dictionary and all work buffers (waits for the device). */
+ACT_API void act_destroy(act_grid *grid);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACT_H */

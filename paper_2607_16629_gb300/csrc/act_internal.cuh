@@ -1,0 +1,89 @@
+// Internal declarations shared by the translation units of libact
+// (kernels, launchers, device helpers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/act.h"
+
+namespace act {
+
+// Device-side status flags (one int per grid, OR-ed by kernels).
+enum : int {
+    kFlagNonFinite = 1,
+    kFlagTimeout = 2,
+};
+
+// Grid axes in the form kernels take by value.
+struct GridAxes {
+    double lo[4];    // tc, fc, logdt, c
+    double step[4];
+    int32_t count[4];
+    double fs;
+    int32_t L;       // samples per window
+};
+
+// Flat index -> parameters (tc slowest, c fastest).
+__host__ __device__ inline void decode_params(const GridAxes &ax, int64_t flat, double *p) {
+    int64_t ic = flat % ax.count[3];
+    int64_t rest = flat / ax.count[3];
+    int64_t il = rest % ax.count[2];
+    rest /= ax.count[2];
+    int64_t ifc = rest % ax.count[1];
+    int64_t itc = rest / ax.count[1];
+    p[0] = ax.lo[0] + (double)itc * ax.step[0];
+    p[1] = ax.lo[1] + (double)ifc * ax.step[1];
+    p[2] = ax.lo[2] + (double)il * ax.step[2];
+    p[3] = ax.lo[3] + (double)ic * ax.step[3];
+}
+
+// Packed selection key: |score| bits in the high word, (2^32-1 - index) in
+// the low word, so that an unsigned max picks the largest |score| and, among
+// equal scores, the lowest index.  0 means "nothing selected yet".
+__device__ inline unsigned long long pack_key(float abs_score, uint32_t idx) {
+    return ((unsigned long long)__float_as_uint(abs_score) << 32) |
+           (unsigned long long)(0xFFFFFFFFu - idx);
+}
+__host__ __device__ inline uint32_t key_index(unsigned long long key) {
+    return key ? 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull) : 0u;
+}
+
+constexpr int kGemvThreads = 256;
+constexpr int kUpdateThreads = 256;
+constexpr int kMaxSamples = 2048;
+constexpr int kRowAlign = 128;   // FP32 row stride granule (floats)
+constexpr int kBf16Align = 64;   // BF16 row stride granule (elements)
+
+// ---- launchers (act_kernels.cu) -------------------------------------------
+cudaError_t launch_gen_atoms(const GridAxes &ax, int64_t K, int Lp, float *d32, __nv_bfloat16 *d16,
+                             int Lb, unsigned long long *degenerate, int sm_count, cudaStream_t st);
+cudaError_t launch_init(const float *sig, int B, int L, int Lp, float *R, __nv_bfloat16 *R16, int Lb,
+                        unsigned long long *keys, double *energy, int P1, int *status, cudaStream_t st);
+cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B,
+                               const int *chlist, const int *count_dev, unsigned long long *keys,
+                               int *status, int grid_ctas, cudaStream_t st);
+cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, int B, float *scores,
+                           int *status, int grid_ctas, cudaStream_t st);
+cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
+                          unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
+                          float *coefs, double *energy, int *fb_count, cudaStream_t st);
+int gemv_ctas(int sm_count, int Lp);
+
+// ---- tensor-core search (act_gemm.cu) -------------------------------------
+struct Bf16Search;
+// Prepares the tensor-core search over the BF16 dictionary d16 [K][Lb]
+// (tensor map, partial top-k buffers).  Returns cudaErrorNotSupported when
+// the shape is outside what the kernel handles.
+cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int64_t K, int Lb, int sm_count);
+void bf16_search_free(Bf16Search *s);
+// One search order for B <= 128 channels: GEMM + fused top-k, merge and
+// FP32 rescore with certificate, FP32 fallback for uncertified channels.
+// Leaves the packed selection key of every channel in keys[].
+cudaError_t launch_bf16_search(Bf16Search *s, int B, const __nv_bfloat16 *R16, const float *D32, int Lp, int L,
+                               const float *R, unsigned long long *keys, int *fb_list, int *fb_count,
+                               long long *stats, int *status, cudaStream_t st);
+
+}  // namespace act
