@@ -93,6 +93,7 @@ struct act_grid {
     float *d32 = nullptr;
     __nv_bfloat16 *d16 = nullptr;
     unsigned long long *degenerate = nullptr;
+    unsigned int *eps_bits = nullptr;  // largest |bf16(g) - g| (float bits)
     // work buffers
     int cap_B = 0, cap_P = 0;
     float *sig = nullptr;
@@ -195,7 +196,7 @@ act_status record_decompose(act_grid *g, int B, int P, act_search_mode mode, Gra
         }
         if (bf16) {
             ACT_CK(launch_bf16_search(g->bf16, B, g->R16, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list,
-                                      g->fb_count, g->stats, g->status, st));
+                                      g->fb_count, g->stats, g->status, g->gemv_grid, st));
             kernels += 3;
         } else {
             ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, g->R, B, nullptr, nullptr, g->keys, g->status,
@@ -345,6 +346,7 @@ act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid *
     if (e == cudaSuccess) e = cudaMalloc(&g->stats, 2 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(g->stats, 0, 2 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&g->degenerate, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&g->eps_bits, sizeof(unsigned int));
     if (e != cudaSuccess) {
         note_error("act_grid_create", e);
         act_destroy(g);
@@ -392,9 +394,11 @@ act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stre
         }
     }
     ACT_CK(cudaMemsetAsync(g->degenerate, 0, sizeof(unsigned long long), st));
-    ACT_CK(launch_gen_atoms(g->ax, g->K, g->Lp, g->d32, g->d16, g->Lb, g->degenerate, g->sm_count, st));
+    ACT_CK(cudaMemsetAsync(g->eps_bits, 0, sizeof(unsigned int), st));
+    ACT_CK(launch_gen_atoms(g->ax, g->K, g->Lp, g->d32, g->d16, g->Lb, g->degenerate, g->eps_bits, g->sm_count,
+                            st));
     if (mode == ACT_DICT_BF16) {
-        cudaError_t pe = bf16_search_prepare(&g->bf16, g->d16, g->K, g->Lb, g->sm_count);
+        cudaError_t pe = bf16_search_prepare(&g->bf16, g->d16, g->K, g->Lb, g->sm_count, g->eps_bits);
         if (pe != cudaSuccess) {
             note_error("bf16_search_prepare", pe);
             free_dictionary(g);
@@ -529,6 +533,7 @@ void act_destroy(act_grid *g) {
     free_dev(g->fb_count);
     free_dev(g->stats);
     free_dev(g->degenerate);
+    free_dev(g->eps_bits);
     if (g->cap) cudaStreamDestroy(g->cap);
     delete g;
 }

@@ -26,6 +26,17 @@ struct GridAxes {
     int32_t L;       // samples per window
 };
 
+// value = lo + i * step with one rounding per operation (never fused), so
+// the device gives the same doubles as plain host arithmetic.
+__host__ __device__ inline double axis_value(double lo, double step, int64_t i) {
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(lo, __dmul_rn((double)i, step));
+#else
+    volatile double m = (double)i * step;
+    return lo + m;
+#endif
+}
+
 // Flat index -> parameters (tc slowest, c fastest).
 __host__ __device__ inline void decode_params(const GridAxes &ax, int64_t flat, double *p) {
     int64_t ic = flat % ax.count[3];
@@ -34,10 +45,10 @@ __host__ __device__ inline void decode_params(const GridAxes &ax, int64_t flat, 
     rest /= ax.count[2];
     int64_t ifc = rest % ax.count[1];
     int64_t itc = rest / ax.count[1];
-    p[0] = ax.lo[0] + (double)itc * ax.step[0];
-    p[1] = ax.lo[1] + (double)ifc * ax.step[1];
-    p[2] = ax.lo[2] + (double)il * ax.step[2];
-    p[3] = ax.lo[3] + (double)ic * ax.step[3];
+    p[0] = axis_value(ax.lo[0], ax.step[0], itc);
+    p[1] = axis_value(ax.lo[1], ax.step[1], ifc);
+    p[2] = axis_value(ax.lo[2], ax.step[2], il);
+    p[3] = axis_value(ax.lo[3], ax.step[3], ic);
 }
 
 // Packed selection key: |score| bits in the high word, (2^32-1 - index) in
@@ -59,7 +70,8 @@ constexpr int kBf16Align = 64;   // BF16 row stride granule (elements)
 
 // ---- launchers (act_kernels.cu) -------------------------------------------
 cudaError_t launch_gen_atoms(const GridAxes &ax, int64_t K, int Lp, float *d32, __nv_bfloat16 *d16,
-                             int Lb, unsigned long long *degenerate, int sm_count, cudaStream_t st);
+                             int Lb, unsigned long long *degenerate, unsigned int *eps_bits, int sm_count,
+                             cudaStream_t st);
 cudaError_t launch_init(const float *sig, int B, int L, int Lp, float *R, __nv_bfloat16 *R16, int Lb,
                         unsigned long long *keys, double *energy, int P1, int *status, cudaStream_t st);
 cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B,
@@ -77,13 +89,16 @@ struct Bf16Search;
 // Prepares the tensor-core search over the BF16 dictionary d16 [K][Lb]
 // (tensor map, partial top-k buffers).  Returns cudaErrorNotSupported when
 // the shape is outside what the kernel handles.
-cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int64_t K, int Lb, int sm_count);
+// eps_bits: device word holding (as float bits) the largest |bf16(g) - g|_2
+// over the dictionary, written by the atom generator.
+cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int64_t K, int Lb, int sm_count,
+                                unsigned int *eps_bits);
 void bf16_search_free(Bf16Search *s);
 // One search order for B <= 128 channels: GEMM + fused top-k, merge and
 // FP32 rescore with certificate, FP32 fallback for uncertified channels.
 // Leaves the packed selection key of every channel in keys[].
 cudaError_t launch_bf16_search(Bf16Search *s, int B, const __nv_bfloat16 *R16, const float *D32, int Lp, int L,
                                const float *R, unsigned long long *keys, int *fb_list, int *fb_count,
-                               long long *stats, int *status, cudaStream_t st);
+                               long long *stats, int *status, int gemv_grid, cudaStream_t st);
 
 }  // namespace act

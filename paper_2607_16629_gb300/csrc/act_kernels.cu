@@ -25,7 +25,8 @@ namespace act {
 template <int NV>
 __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int Lp, float *__restrict__ d32,
                                                     __nv_bfloat16 *__restrict__ d16, int Lb,
-                                                    unsigned long long *__restrict__ degenerate) {
+                                                    unsigned long long *__restrict__ degenerate,
+                                                    unsigned int *__restrict__ eps_bits) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int L
         if (!bad) scale = (float)(1.0 / sqrt(energy));
         if (bad && lane == 0 && degenerate) atomicAdd(degenerate, 1ull);
         float4 *row = reinterpret_cast<float4 *>(d32 + atom * (int64_t)Lp);
+        double err = 0.0;  // |bf16(g) - g|^2 of this atom (BF16 layout only)
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             float4 w = make_float4(u[j][0] * scale, u[j][1] * scale, u[j][2] * scale, u[j][3] * scale);
@@ -69,6 +71,9 @@ __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int L
                 if (n0 < Lb) {
                     __nv_bfloat162 lo = __floats2bfloat162_rn(w.x, w.y);
                     __nv_bfloat162 hi = __floats2bfloat162_rn(w.z, w.w);
+                    const float2 flo = __bfloat1622float2(lo), fhi = __bfloat1622float2(hi);
+                    err += (double)(flo.x - w.x) * (flo.x - w.x) + (double)(flo.y - w.y) * (flo.y - w.y) +
+                           (double)(fhi.x - w.z) * (fhi.x - w.z) + (double)(fhi.y - w.w) * (fhi.y - w.w);
                     uint2 packed;
                     packed.x = *reinterpret_cast<uint32_t *>(&lo);
                     packed.y = *reinterpret_cast<uint32_t *>(&hi);
@@ -76,23 +81,28 @@ __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int L
                 }
             }
         }
+        if (d16 && eps_bits) {
+            err = warp_sum(err);
+            // positive floats order like their bit patterns; round the norm up
+            if (lane == 0) atomicMax(eps_bits, __float_as_uint(__double2float_ru(sqrt(err) * (1.0 + 1e-6))));
+        }
     }
 }
 
 cudaError_t launch_gen_atoms(const GridAxes &ax, int64_t K, int Lp, float *d32, __nv_bfloat16 *d16, int Lb,
-                             unsigned long long *degenerate, int sm_count, cudaStream_t st) {
+                             unsigned long long *degenerate, unsigned int *eps_bits, int sm_count, cudaStream_t st) {
     const int nv = Lp / 128;
     int64_t blocks = (K + 7) / 8;
     const int64_t cap = (int64_t)sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     switch (nv) {
-        case 1: k_gen_atoms<1><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate); break;
-        case 2: k_gen_atoms<2><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate); break;
-        case 3: k_gen_atoms<3><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate); break;
-        case 4: k_gen_atoms<4><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate); break;
-        case 8: k_gen_atoms<8><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate); break;
-        case 16: k_gen_atoms<16><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate); break;
+        case 1: k_gen_atoms<1><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate, eps_bits); break;
+        case 2: k_gen_atoms<2><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate, eps_bits); break;
+        case 3: k_gen_atoms<3><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate, eps_bits); break;
+        case 4: k_gen_atoms<4><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate, eps_bits); break;
+        case 8: k_gen_atoms<8><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate, eps_bits); break;
+        case 16: k_gen_atoms<16><<<(int)blocks, 256, 0, st>>>(ax, K, Lp, d32, d16, Lb, degenerate, eps_bits); break;
         default: {
             // Row strides between the instantiated ones are rounded up by the host.
             return cudaErrorInvalidValue;

@@ -1,0 +1,172 @@
+"""GPU parity of the BF16 tensor-core search (tcgen05 GEMM + fused top-8,
+FP32 rescore with certificate, FP32 fallback) through the C ABI.
+
+The certificate makes the BF16 search return the atom the FP32 search would
+return (up to near-ties below 1e-5 relative), so the same order-by-order
+checks against the FP64 oracle apply as for the FP32 path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_16629_gb300 import act, synth
+from parity_helpers import check_lockstep
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    act.load_library()
+
+
+class Bf16Grid:
+    def __init__(self, grid):
+        self.grid = grid
+
+    def __enter__(self):
+        self.h = act.act_grid_create(self.grid, 0)
+        act.act_dictionary_build(self.h, act.ACT_DICT_BF16)
+        act.act_set_search(self.h, act.ACT_SEARCH_BF16)
+        return self.h
+
+    def __exit__(self, *a):
+        act.act_destroy(self.h)
+
+
+def run(h, sig, P, mode):
+    act.act_set_search(h, mode)
+    atoms, coef, resid, energy = act.decompose(h, torch.tensor(sig, dtype=torch.float32, device="cuda"), P)
+    torch.cuda.synchronize()
+    st = act.act_grid_status(h)
+    assert st == act.ACT_OK, act.status_name(st)
+    return (act.atom_indices(atoms).cpu().numpy(), coef.cpu().numpy(), resid.cpu().numpy(),
+            energy.cpu().numpy())
+
+
+def chain(h, sig, P):
+    """Residuals entering each order for all channels (one-order BF16 calls)."""
+    rs = [np.asarray(sig, dtype=np.float32)]
+    idx, coef = [], []
+    for _ in range(P):
+        i, c, r, _ = run(h, rs[-1], 1, act.ACT_SEARCH_BF16)
+        idx.append(i[:, 0])
+        coef.append(c[:, 0])
+        rs.append(r)
+    return rs, np.stack(idx, 1), np.stack(coef, 1)
+
+
+def lockstep_all(D, rs, idx, coef):
+    ties = 0
+    for b in range(idx.shape[0]):
+        ties += check_lockstep(lambda r: D @ r, [r[b] for r in rs], idx[b], coef[b])
+    return ties
+
+
+@pytest.mark.parametrize("name,grid,B,P", [
+    ("tiny_k36_l32", synth.grid_small_test(), 3, 4),
+    ("c1_k16384_l256", synth.grid_c1(), 16, 5),
+])
+def test_bf16_lockstep_small(name, grid, B, P):
+    sig = np.concatenate([synth.workload_c1(min(B, 4)).signals if grid.n_samples == 256 else
+                          synth.random_signals(61, min(B, 4), grid.n_samples),
+                          synth.random_signals(62, B - min(B, 4), grid.n_samples)])
+    D, _ = oracle.dictionary(grid)
+    with Bf16Grid(grid) as h:
+        c0, f0 = act.act_bf16_stats(h)
+        i_full, c_full, r_full, e_full = run(h, sig, P, act.ACT_SEARCH_BF16)
+        rs, idx, coef = chain(h, sig, P)
+        c1, f1 = act.act_bf16_stats(h)
+    assert np.array_equal(idx, i_full) and np.array_equal(coef, c_full)
+    assert np.array_equal(rs[-1], r_full)
+    assert (c1 - c0) + (f1 - f0) == 2 * B * P
+    lockstep_all(D, rs, idx, coef)
+
+
+def test_bf16_matches_fp32_search_eeg():
+    """64 EEG-like channels on a 131,072-atom EEG grid (512 tiles over the
+    persistent CTAs, both accumulator buffers in use): the BF16 search and
+    the FP32 search agree order by order, and both match the oracle."""
+    grid = synth.scaled_grid(synth.grid_eeg(), tc_count=32, fc_count=16)
+    sig = np.stack([synth.eeg_like_signal(3, b)[0] for b in range(64)])
+    D, _ = oracle.dictionary(grid)
+    P = 6
+    with Bf16Grid(grid) as h:
+        ib, cb, rb, eb = run(h, sig, P, act.ACT_SEARCH_BF16)
+        i32, c32, r32, e32 = run(h, sig, P, act.ACT_SEARCH_FP32)
+        rs, idx, coef = chain(h, sig, P)
+        cert, fb = act.act_bf16_stats(h)
+    same = np.all(ib == i32, axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.array_equal(cb[same], c32[same]) and np.array_equal(rb[same], r32[same])
+    lockstep_all(D, rs, idx, coef)
+    print(f"certified {cert} fallback {fb}")
+
+
+def test_bf16_zero_channel_falls_back():
+    """An all-zero channel cannot be certified (every score ties); it takes
+    the FP32 fallback and selects index 0 with coefficient 0, while the other
+    channels are unaffected."""
+    grid = synth.grid_c1()
+    sig = synth.workload_c1(3).signals.copy()
+    sig[1] = 0.0
+    with Bf16Grid(grid) as h:
+        c0, f0 = act.act_bf16_stats(h)
+        idx, coef, resid, energy = run(h, sig, 3, act.ACT_SEARCH_BF16)
+        c1, f1 = act.act_bf16_stats(h)
+        i32, c32, r32, e32 = run(h, sig, 3, act.ACT_SEARCH_FP32)
+    assert f1 - f0 >= 3
+    assert not idx[1].any() and not coef[1].any()
+    assert np.array_equal(idx, i32)
+
+
+@pytest.mark.parametrize("B", [1, 128])
+def test_bf16_channel_counts(B):
+    grid = synth.grid_c1()
+    sig = synth.random_signals(71, B, grid.n_samples)
+    with Bf16Grid(grid) as h:
+        ib, cb, rb, eb = run(h, sig, 2, act.ACT_SEARCH_BF16)
+        i32, c32, r32, e32 = run(h, sig, 2, act.ACT_SEARCH_FP32)
+    same = np.all(ib == i32, axis=1)
+    assert same.mean() >= 0.9
+    assert np.array_equal(cb[same], c32[same])
+
+
+def test_bf16_rejects_more_than_128_channels():
+    grid = synth.grid_small_test()
+    with Bf16Grid(grid) as h:
+        with pytest.raises(act.ActError) as e:
+            act.decompose(h, torch.zeros((129, grid.n_samples), device="cuda"), 1)
+        assert e.value.status == act.ACT_ERR_UNSUPPORTED
+
+
+def test_bf16_full_eeg_grid_64_channels():
+    """The 64-channel EEG-like workload on the full 2,097,152-atom grid in the
+    benchmark's launch configuration: first order of every channel checked
+    against the oracle on sampled atoms plus its selected atom, and the
+    whole run against the FP32 search."""
+    w = synth.workload_c3()
+    P = 4
+    with Bf16Grid(w.grid) as h:
+        ib, cb, rb, eb = run(h, w.signals, P, act.ACT_SEARCH_BF16)
+        i32, c32, r32, e32 = run(h, w.signals, P, act.ACT_SEARCH_FP32)
+        cert, fb = act.act_bf16_stats(h)
+    same = np.all(ib == i32, axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.array_equal(cb[same], c32[same])
+    rng = np.random.default_rng(3)
+    sample = rng.integers(0, w.grid.n_atoms, 2000)
+    for b in range(0, 64, 8):
+        s = w.signals[b].astype(np.float32).astype(np.float64)
+        g, _ = oracle.atom(*w.grid.params_of(int(ib[b, 0])), w.grid.fs, w.grid.n_samples)
+        best = abs(g @ s)
+        assert abs(cb[b, 0] - g @ s) <= 1e-5 * best
+        for i in sample[:200]:
+            gi, _ = oracle.atom(*w.grid.params_of(int(i)), w.grid.fs, w.grid.n_samples)
+            assert abs(gi @ s) <= best * (1 + 1e-5)
+    e0 = eb[:, 0]
+    for k in range(P + 1):
+        assert np.all(np.abs(e0 - (np.sum(cb[:, :k].astype(np.float64) ** 2, axis=1) + eb[:, k])) <= 1e-5 * e0)
+    print(f"certified {cert} fallback {fb}")
