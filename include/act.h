@@ -89,10 +89,12 @@ typedef enum {
 
 /* Which search act_decompose runs.
  *   ACT_SEARCH_FP32: FP32 GEMV with the argmax fused (CUDA cores).
- *   ACT_SEARCH_BF16: BF16 tcgen05 GEMM with a fused per-channel top-8,
- *                    FP32 rescore of the 8 candidates, and an FP32 full
- *                    search for any channel whose candidate set cannot be
- *                    certified to hold the FP32 argmax.
+ *   ACT_SEARCH_BF16: BF16 tcgen05 GEMM over all atoms (tensor cores, FP32
+ *                    accumulation) reduced to the largest |score| per
+ *                    256-atom tile; the tiles that an error bound cannot
+ *                    exclude are rescored in FP32, so the selection equals
+ *                    the FP32 search's bit for bit (channels <= 128,
+ *                    n_samples <= 512).
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
  *                    FP32 otherwise. */
 typedef enum {
@@ -191,9 +193,12 @@ ACT_API act_status act_set_profiling(act_grid *grid, int32_t enable);
 ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, int32_t *search_launches,
                             int32_t *kernels);
 
-/* BF16 search statistics since the grid was created: orders whose top-8
- * certificate held, and orders that fell back to the FP32 full search. */
-ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *certified, int64_t *fallbacks);
+/* BF16 search statistics since the grid was created: (channel, order)
+ * selections resolved by the FP32 rescan of the flagged tiles, the total
+ * number of 256-atom tiles rescanned for them, and selections that took the
+ * FP32 full search instead (more than 64 flagged tiles). */
+ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *resolved, int64_t *tiles_rescanned,
+                                  int64_t *fallbacks);
 
 /* Frees the grid, its dictionary and all work buffers (waits for the device). */
 ACT_API void act_destroy(act_grid *grid);

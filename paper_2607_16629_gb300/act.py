@@ -96,7 +96,8 @@ def load_library(path: str = LIB_PATH):
         lib.act_set_profiling.argtypes = [_P, ctypes.c_int32]
         lib.act_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32)]
-        lib.act_bf16_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        lib.act_bf16_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -227,10 +228,13 @@ def act_profile_read(grid: int):
 
 
 def act_bf16_stats(grid: int):
+    """(resolved, tiles_rescanned, fallbacks) counts of the BF16 search."""
     a = ctypes.c_int64()
+    r = ctypes.c_int64()
     b = ctypes.c_int64()
-    _check(load_library().act_bf16_stats(grid, ctypes.byref(a), ctypes.byref(b)), "act_bf16_stats")
-    return a.value, b.value
+    _check(load_library().act_bf16_stats(grid, ctypes.byref(a), ctypes.byref(r), ctypes.byref(b)),
+           "act_bf16_stats")
+    return a.value, r.value, b.value
 
 
 def act_destroy(grid: int) -> None:

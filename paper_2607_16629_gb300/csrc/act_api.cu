@@ -197,7 +197,7 @@ act_status record_decompose(act_grid *g, int B, int P, act_search_mode mode, Gra
         if (bf16) {
             ACT_CK(launch_bf16_search(g->bf16, B, g->R16, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list,
                                       g->fb_count, g->stats, g->status, g->gemv_grid, st));
-            kernels += 3;
+            kernels += 4;
         } else {
             ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, g->R, B, nullptr, nullptr, g->keys, g->status,
                                       g->gemv_grid, st));
@@ -341,10 +341,10 @@ act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid *
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&g->fb_count, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(g->fb_count, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&g->stats, 2 * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMemset(g->stats, 0, 2 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&g->fb_count, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->fb_count, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&g->stats, 3 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(g->stats, 0, 3 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&g->degenerate, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&g->eps_bits, sizeof(unsigned int));
     if (e != cudaSuccess) {
@@ -383,8 +383,12 @@ act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stre
         return ACT_ERR_OOM;
     }
     if (mode == ACT_DICT_BF16) {
-        const size_t b16 = sizeof(__nv_bfloat16) * (size_t)g->K * g->Lb;
+        // tile-major layout [K/256 tiles][Lb/64 chunks][256 atoms][64 samples],
+        // the last tile padded with zero atoms
+        const int64_t ntiles = (g->K + 255) / 256;
+        const size_t b16 = sizeof(__nv_bfloat16) * (size_t)ntiles * 256 * g->Lb;
         e = cudaMalloc(&g->d16, b16);
+        if (e == cudaSuccess) e = cudaMemset(g->d16, 0, b16);
         if (e != cudaSuccess) {
             cudaGetLastError();
             g->d16 = nullptr;
@@ -512,13 +516,14 @@ act_status act_profile_read(act_grid *g, double *search_ms, int32_t *search_laun
     return ACT_OK;
 }
 
-act_status act_bf16_stats(act_grid *g, int64_t *certified, int64_t *fallbacks) {
+act_status act_bf16_stats(act_grid *g, int64_t *resolved, int64_t *tiles_rescanned, int64_t *fallbacks) {
     if (!g) return ACT_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
-    long long h[2] = {0, 0};
+    long long h[3] = {0, 0, 0};
     ACT_CK(cudaMemcpy(h, g->stats, sizeof(h), cudaMemcpyDeviceToHost));
-    if (certified) *certified = h[0];
+    if (resolved) *resolved = h[0];
     if (fallbacks) *fallbacks = h[1];
+    if (tiles_rescanned) *tiles_rescanned = h[2];
     return ACT_OK;
 }
 

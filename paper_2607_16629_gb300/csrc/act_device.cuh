@@ -78,6 +78,27 @@ __device__ __forceinline__ float4 ldg_stream(const float4 *p) {
     return v;
 }
 
+// FP32 score of one dictionary row against a residual, both padded to
+// nv * 128 floats: lane l takes float4 l + 32 j, accumulating x/z and y/w in
+// two chains, then a butterfly sum.  The GEMV uses the same order, so every
+// kernel gets the same bits for the same (atom, residual).
+__device__ __forceinline__ float row_score(const float4 *__restrict__ row, const float4 *__restrict__ res, int nv,
+                                           int lane) {
+    float x0 = 0.f, x1 = 0.f;
+    for (int j = 0; j < nv; ++j) {
+        const float4 a = row[lane + 32 * j];
+        const float4 r = res[lane + 32 * j];
+        x0 = fmaf(a.x, r.x, x0);
+        x1 = fmaf(a.y, r.y, x1);
+        x0 = fmaf(a.z, r.z, x0);
+        x1 = fmaf(a.w, r.w, x1);
+    }
+    float s = x0 + x1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

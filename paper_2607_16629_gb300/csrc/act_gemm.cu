@@ -1,19 +1,24 @@
 // Tensor-core search of the batched projection P = D X^T (Sec. IV-A) for up
-// to 128 channels: a persistent tcgen05 GEMM over the BF16 dictionary with
-// the per-channel candidate selection fused into the epilogue, followed by a
-// merge / FP32 rescore / certificate kernel and, for any channel whose
-// candidate set cannot be shown to contain the FP32 argmax, the FP32 GEMV.
+// to 128 channels, exact with respect to the FP32 search:
+//  1. a persistent tcgen05 GEMM over the BF16 dictionary writes, per channel
+//     and per tile of 256 atoms, the largest BF16 |score| of the tile;
+//  2. a select kernel bounds the BF16 error (delta) and flags, per channel,
+//     every tile whose maximum lies within 2 delta + 2 eps_r of the channel's
+//     largest BF16 |score| -- the FP32 argmax is provably in one of them;
+//  3. the flagged tiles are scored in FP32 with the GEMV's own arithmetic
+//     and folded into the packed selection key (a channel with too many
+//     flagged tiles takes the FP32 full search instead).
 //
 // GEMM shape per tile: M = 128 channels (rows of the residual matrix, padded
 // with zero rows), N = 256 atoms, K = Lb samples.  The residual matrix (A,
 // <= 128 KB of BF16) is loaded once per CTA by TMA and stays in shared
-// memory; dictionary tiles (B, 256 atoms x 64 samples = 32 KB per stage) are
-// streamed by TMA through a ring of stages; FP32 accumulators live in tensor
-// memory (two 256-column buffers, so the epilogue of one tile overlaps the
-// MMAs of the next).  Warp roles: warp 0 issues TMA, warp 1 issues MMAs,
-// warp 2 owns the tensor-memory allocation, warps 4-7 read the accumulators
-// (thread = channel) and keep, per channel, the KT largest |scores| seen by
-// the CTA (ties to the lower atom index).
+// memory; dictionary tiles (B, 256 atoms x 64 samples = 32 KB per stage,
+// contiguous in the tile-major BF16 layout) are streamed by TMA through a
+// ring of stages; FP32 accumulators live in tensor memory (two 256-column
+// buffers, so the epilogue of one tile overlaps the MMAs of the next).  Warp
+// roles: warp 0 issues TMA, warp 1 issues MMAs, warp 2 owns the
+// tensor-memory allocation, warps 4-7 read the accumulators (thread =
+// channel) and reduce each tile to its largest |score|.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -33,8 +38,7 @@ constexpr int kBM = 128;           // channels per tile (MMA M)
 constexpr int kBN = 256;           // atoms per tile (MMA N)
 constexpr int kBK = 64;            // samples per stage (one 128-byte swizzle row)
 constexpr int kUmmaK = 16;         // K per tcgen05.mma (16-bit inputs)
-constexpr int kCand = 8;           // candidates rescored per channel
-constexpr int kTrack = kCand + 1;  // entries tracked per channel per CTA
+constexpr int kMaxRescan = 64;     // flagged tiles per channel before the FP32 full search
 constexpr int kGemmThreads = 256;
 constexpr int kAChunkBytes = kBM * kBK * 2;  // 16 KB
 constexpr int kStageBytes = kBN * kBK * 2;   // 32 KB
@@ -113,21 +117,6 @@ __device__ __forceinline__ void sleep_ns(unsigned long long ns) {
     }
 }
 
-// Keeps vals[] sorted in decreasing order; a new entry equal to an existing
-// one goes after it (entries arrive in increasing atom order).
-__device__ __forceinline__ void topk_insert(float (&vals)[kTrack], uint32_t (&ids)[kTrack], float v, uint32_t id) {
-#pragma unroll
-    for (int q = 0; q < kTrack; ++q) {
-        const bool gt = v > vals[q];
-        const float tv = vals[q];
-        const uint32_t ti = ids[q];
-        vals[q] = gt ? v : tv;
-        ids[q] = gt ? id : ti;
-        v = gt ? tv : v;
-        id = gt ? ti : id;
-    }
-}
-
 struct GemmSmem {
     uint64_t bar_a;
     uint64_t bar_full[8];
@@ -139,8 +128,8 @@ struct GemmSmem {
 };
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t K, int nkc,
-                int stages, float *__restrict__ part_val, uint32_t *__restrict__ part_idx, int *status) {
+    k_gemm_tilemax(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t K, int nkc,
+                   int stages, int B, float *__restrict__ tile_max, int *status) {
     extern __shared__ uint8_t dyn_raw[];
     __shared__ GemmSmem sm;
     const uint32_t dyn_base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
@@ -191,7 +180,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     break;
                 }
                 mbar_expect_tx(&sm.bar_full[s], kStageBytes);
-                tma_load_2d(b_smem + s * kStageBytes, &tmB, kc * kBK, (int)(tile * kBN), &sm.bar_full[s]);
+                tma_load_2d(b_smem + s * kStageBytes, &tmB, 0, (int)((tile * nkc + kc) * kBN), &sm.bar_full[s]);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -229,13 +218,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // ---------------- epilogue: thread = channel ----------------
         const int q = warp - 4;
         const int ch = q * 32 + lane;
-        float vals[kTrack];
-        uint32_t ids[kTrack];
-#pragma unroll
-        for (int i = 0; i < kTrack; ++i) {
-            vals[i] = -1.0f;
-            ids[i] = 0xFFFFFFFFu;
-        }
         uint32_t local = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
@@ -244,33 +226,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int64_t base = tile * kBN;
-            const bool full_tile = base + kBN <= K;
+            // atoms past K in the last tile are zero rows: they score 0
+            float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll 1
             for (int c = 0; c < kBN / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * kBN + c * 32, v);
-                const float thr0 = vals[kTrack - 1];
-                bool any = false;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) any |= fabsf(v[j]) > thr0;
-                if (any) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t atom = base + c * 32 + j;
-                        const float s = fabsf(v[j]);
-                        if (s > vals[kTrack - 1] && (full_tile || atom < K)) topk_insert(vals, ids, s, (uint32_t)atom);
-                    }
+                for (int j = 0; j < 32; j += 2) {
+                    m0 = fmaxf(m0, fabsf(v[j]));
+                    m1 = fmaxf(m1, fabsf(v[j + 1]));
                 }
             }
             tc_fence_before();
             mbar_arrive(&sm.bar_acc_empty[acc]);
-        }
-        const size_t off = ((size_t)blockIdx.x * kBM + ch) * kTrack;
-#pragma unroll
-        for (int i = 0; i < kTrack; ++i) {
-            part_val[off + i] = vals[i];
-            part_idx[off + i] = ids[i];
+            if (ch < B) tile_max[(size_t)ch * ntiles + tile] = fmaxf(m0, m1);
         }
     }
 
@@ -286,45 +256,36 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Merge of the per-CTA candidate lists, FP32 rescore and certificate.
+// Tile selection: which tiles can hold the FP32 argmax of channel b.
 // ---------------------------------------------------------------------------
-// For channel b the GEMM left, per CTA c, its kTrack largest BF16 |scores|
-// L_c (sorted).  The global top kTrack entries of the union all lie at or
-// above T = max_c L_c[kTrack-1]; those entries are gathered, the first kCand
-// become the candidates and the next one is U.  Every atom that is not a
-// candidate has a BF16 |score| <= U.  With
+// Let s_j be the exact <g_j, r>, f_j the FP32 score the GEMV computes and
+// h_j the tensor-core BF16 score.  With
 //   delta = eps_g (|r| + |dr|) + (1 + 1e-5) |dr| + L 2^-23 (1 + eps_g)(|r| + |dr|)
 // (eps_g = largest |bf16(g) - g| over the dictionary, dr = bf16(r) - r, the
-// last term bounds FP32 accumulation in the tensor core), every
-// non-candidate has an exact |<g, r>| <= U + delta.  The candidates are
-// rescored in FP32 (error <= eps_r = L 2^-23 |r|); if the best rescored
-// |score| - eps_r exceeds U + delta, the argmax of the exact scores is among
-// the candidates and the best FP32 candidate is selected (near-ties within
-// 1e-5 relative are settled by an FP64 rescore).  Otherwise the channel is
-// queued for the FP32 full search.
-constexpr int kGather = 1024;
-
-__global__ void __launch_bounds__(256) k_rescore(int G, const float *__restrict__ part_val,
-                                                 const uint32_t *__restrict__ part_idx, const float *__restrict__ D32,
-                                                 int Lp, int L, const float *__restrict__ R,
-                                                 const unsigned int *__restrict__ eps_bits,
-                                                 unsigned long long *__restrict__ keys, int *__restrict__ fb_list,
-                                                 int *__restrict__ fb_count, long long *__restrict__ stats) {
-    __shared__ float g_val[kGather];
-    __shared__ uint32_t g_idx[kGather];
-    __shared__ int g_n;
-    __shared__ float sh_f[32];
+// last term bounds FP32 accumulation in the tensor core) and
+// eps_r = L 2^-23 |r| (FP32 accumulation of the GEMV), |h_j - s_j| <= delta
+// and |f_j - s_j| <= eps_r.  If j* maximises |f| and jb maximises |h|:
+//   |h_j*| >= |f_j*| - eps_r - delta >= |f_jb| - eps_r - delta
+//          >= |h_jb| - 2 delta - 2 eps_r,
+// so j* lies in a tile whose largest |h| is >= bmax - 2 delta - 2 eps_r.
+// Those tiles are queued for the FP32 rescan (keys[b] cleared); a channel
+// with more than kMaxRescan of them is queued for the FP32 full search.
+__global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__restrict__ tile_max, int Lp, int L,
+                                                const float *__restrict__ R,
+                                                const unsigned int *__restrict__ eps_bits,
+                                                unsigned long long *__restrict__ keys, int *__restrict__ fb_list,
+                                                int *__restrict__ counters, int *__restrict__ pairs,
+                                                long long *__restrict__ stats) {
     __shared__ double sh_d[32];
-    __shared__ uint32_t c_idx[kCand];
-    __shared__ float c_fp[kCand];
-    __shared__ int n_cand;
-    __shared__ float U_sh;
-
+    __shared__ float sh_f[32];
+    __shared__ int n_sh;
+    __shared__ int list[kMaxRescan];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
     const float *r = R + (size_t)b * Lp;
+    const float *tm = tile_max + (size_t)b * ntiles;
 
-    // |r|^2 and |bf16(r) - r|^2
     double e = 0.0, de = 0.0;
     for (int n = threadIdx.x; n < L; n += blockDim.x) {
         const float x = r[n];
@@ -334,142 +295,104 @@ __global__ void __launch_bounds__(256) k_rescore(int G, const float *__restrict_
     }
     const double rn = sqrt(block_sum(e, sh_d));
     const double drn = sqrt(block_sum(de, sh_d));
+    const double eps_g = (double)__uint_as_float(*eps_bits);
+    const double rr = rn + drn;
+    const double ulp = 1.1920928955078125e-07;  // 2^-23
+    const double delta = eps_g * rr + (1.0 + 1e-5) * drn + (double)L * ulp * (1.0 + eps_g) * rr;
+    const double eps_r = (double)L * ulp * rn;
 
-    // threshold T
-    float t = -1.0f;
-    for (int c = threadIdx.x; c < G; c += blockDim.x)
-        t = fmaxf(t, part_val[((size_t)c * kBM + b) * kTrack + kTrack - 1]);
-    for (int off = 16; off > 0; off >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, off));
-    if (lane == 0) sh_f[warp] = t;
-    if (threadIdx.x == 0) g_n = 0;
+    float m = 0.0f;
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) m = fmaxf(m, tm[t]);
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) sh_f[warp] = m;
+    if (threadIdx.x == 0) n_sh = 0;
     __syncthreads();
-    float T = sh_f[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) T = fmaxf(T, sh_f[w]);
+    float bmax = sh_f[0];
+    for (int w = 1; w < nwarps; ++w) bmax = fmaxf(bmax, sh_f[w]);
+    const double thr = (double)bmax - 2.0 * delta - 2.0 * eps_r;
 
-    // gather every tracked entry >= T (each list is sorted, so a prefix)
-    for (int c = threadIdx.x; c < G; c += blockDim.x) {
-        const size_t base = ((size_t)c * kBM + b) * kTrack;
-        for (int i = 0; i < kTrack; ++i) {
-            const float v = part_val[base + i];
-            if (v < T || v < 0.0f) break;
-            const int pos = atomicAdd(&g_n, 1);
-            if (pos < kGather) {
-                g_val[pos] = v;
-                g_idx[pos] = part_idx[base + i];
-            }
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        if ((double)tm[t] >= thr) {
+            const int pos = atomicAdd(&n_sh, 1);
+            if (pos < kMaxRescan) list[pos] = (int)t;
         }
     }
     __syncthreads();
-    const int n_all = g_n;
-    const bool overflow = n_all > kGather;
-    const int n = overflow ? kGather : n_all;
+    const int n = n_sh;
+    if (n > kMaxRescan) {
+        if (threadIdx.x == 0) {
+            keys[b] = 0ull;
+            fb_list[atomicAdd(&counters[0], 1)] = b;
+            atomicAdd((unsigned long long *)&stats[1], 1ull);
+        }
+        return;
+    }
+    __shared__ int base_sh;
+    if (threadIdx.x == 0) {
+        keys[b] = 0ull;
+        base_sh = atomicAdd(&counters[1], n);
+        atomicAdd((unsigned long long *)&stats[0], 1ull);
+        atomicAdd((unsigned long long *)&stats[2], (unsigned long long)n);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        pairs[2 * (base_sh + i)] = b;
+        pairs[2 * (base_sh + i) + 1] = list[i];
+    }
+}
 
-    // warp 0: the kCand + 1 best entries (|score| desc, index asc), in rounds
-    if (warp == 0) {
-        int taken = 0;
-        float U = -1.0f;
-        for (int round = 0; round <= kCand; ++round) {
-            float bv = -2.0f;
-            uint32_t bi = 0xFFFFFFFFu;
-            int bp = -1;
-            for (int i = lane; i < n; i += 32) {
-                const float v = g_val[i];
-                const uint32_t id = g_idx[i];
-                if (v > bv || (v == bv && id < bi)) {
-                    bv = v;
-                    bi = id;
-                    bp = i;
-                }
+// FP32 rescan of the flagged (channel, tile) pairs: every atom of the tile is
+// scored exactly as the GEMV scores it and folded into keys[b] with the
+// packed atomicMax (largest |score|, then lowest index).  One block per pair.
+__global__ void __launch_bounds__(256) k_rescan(const float *__restrict__ D32, int64_t K, int Lp,
+                                                const float *__restrict__ R, const int *__restrict__ pairs,
+                                                const int *__restrict__ counters,
+                                                unsigned long long *__restrict__ keys) {
+    __shared__ float red_s[8];
+    __shared__ uint32_t red_i[8];
+    const int n_items = counters[1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nv = Lp / 128;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const int b = pairs[2 * w];
+        const int64_t tile = pairs[2 * w + 1];
+        const float4 *res = reinterpret_cast<const float4 *>(R + (size_t)b * Lp);
+        float best = -1.0f;
+        uint32_t bidx = 0u;
+        const int64_t row0 = tile * kBN + warp * 32;
+        // four rows in flight per step; rows past K (last tile) are skipped
+        for (int i = 0; i < 32; i += 4) {
+            float sc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t row = row0 + i + u;
+                sc[u] = row < K ? fabsf(row_score(reinterpret_cast<const float4 *>(D32 + (size_t)row * Lp), res, nv,
+                                                  lane))
+                                : -1.0f;
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-                const uint32_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                const int op = __shfl_xor_sync(0xffffffffu, bp, off);
-                if (ov > bv || (ov == bv && oi < bi)) {
-                    bv = ov;
-                    bi = oi;
-                    bp = op;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (sc[u] > best) {
+                    best = sc[u];
+                    bidx = (uint32_t)(row0 + i + u);
                 }
-            }
-            if (bp < 0 || bv < 0.0f) break;
-            if (round < kCand) {
-                if (lane == 0) {
-                    c_idx[taken] = bi;
-                    g_val[bp] = -2.0f;
-                }
-                ++taken;
-            } else {
-                U = bv;
-            }
-            __syncwarp();
         }
         if (lane == 0) {
-            n_cand = taken;
-            U_sh = U;
+            red_s[warp] = best;
+            red_i[warp] = bidx;
         }
-    }
-    __syncthreads();
-    const int nc = n_cand;
-
-    // FP32 rescore, one warp per candidate
-    for (int i = warp; i < nc; i += (int)(blockDim.x >> 5)) {
-        const float *g = D32 + (size_t)c_idx[i] * Lp;
-        float s = 0.0f;
-        for (int k = lane; k < L; k += 32) s = fmaf(g[k], r[k], s);
-        s = warp_sum(s);
-        if (lane == 0) c_fp[i] = s;
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-        // best and runner-up FP32 candidate
-        int best = -1, second = -1;
-        for (int i = 0; i < nc; ++i) {
-            const float a = fabsf(c_fp[i]);
-            if (best < 0 || a > fabsf(c_fp[best]) || (a == fabsf(c_fp[best]) && c_idx[i] < c_idx[best])) {
-                second = best;
-                best = i;
-            } else if (second < 0 || a > fabsf(c_fp[second]) ||
-                       (a == fabsf(c_fp[second]) && c_idx[i] < c_idx[second])) {
-                second = i;
-            }
-        }
-        // near-tie: settle among the candidates within 1e-5 of the best in FP64
-        if (best >= 0 && second >= 0 && fabsf(c_fp[best]) - fabsf(c_fp[second]) <= 1e-5f * fabsf(c_fp[best])) {
-            const float lim = fabsf(c_fp[best]) * (1.0f - 1e-5f);
-            double bv = -1.0;
-            int bsel = best;
-            for (int i = 0; i < nc; ++i) {
-                if (fabsf(c_fp[i]) < lim) continue;
-                const float *g = D32 + (size_t)c_idx[i] * Lp;
-                double s = 0.0;
-                for (int k = lane; k < L; k += 32) s = fma((double)g[k], (double)r[k], s);
-                s = fabs(warp_sum(s));
-                if (s > bv || (s == bv && c_idx[i] < c_idx[bsel])) {
-                    bv = s;
-                    bsel = i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float bs = -1.0f;
+            uint32_t bi = 0u;
+            for (int q = 0; q < 8; ++q)
+                if (red_s[q] > bs || (red_s[q] == bs && red_i[q] < bi)) {
+                    bs = red_s[q];
+                    bi = red_i[q];
                 }
-            }
-            best = bsel;
+            if (bs >= 0.0f) atomicMax(keys + b, pack_key(bs, bi));
         }
-        if (lane == 0) {
-            const double eps_g = (double)__uint_as_float(*eps_bits);
-            const double rr = rn + drn;
-            const double delta = eps_g * rr + (1.0 + 1e-5) * drn + (double)L * 1.1920928955078125e-07 * (1.0 + eps_g) * rr;
-            const double eps_r = (double)L * 1.1920928955078125e-07 * rn;
-            const double U = (double)U_sh;
-            bool ok = !overflow && best >= 0;
-            if (ok && U >= 0.0) ok = (double)fabsf(c_fp[best]) - eps_r > U + delta;
-            if (ok) {
-                keys[b] = pack_key(fabsf(c_fp[best]), c_idx[best]);
-                atomicAdd((unsigned long long *)&stats[0], 1ull);
-            } else {
-                keys[b] = 0ull;
-                const int pos = atomicAdd(fb_count, 1);
-                fb_list[pos] = b;
-                atomicAdd((unsigned long long *)&stats[1], 1ull);
-            }
-        }
+        __syncthreads();
     }
 }
 
@@ -508,13 +431,14 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, ui
 struct Bf16Search {
     CUtensorMap mapB;
     int64_t K = 0;
+    int64_t ntiles = 0;
     int Lb = 0;
     int nkc = 0;
     int stages = 0;
     int grid = 0;
     size_t smem = 0;
-    float *part_val = nullptr;
-    uint32_t *part_idx = nullptr;
+    float *tile_max = nullptr;         // [kBM][ntiles]
+    int *pairs = nullptr;              // [kBM * kMaxRescan][2]
     unsigned int *eps_bits = nullptr;  // owned by the caller (dictionary build)
 };
 
@@ -522,29 +446,32 @@ cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int6
                                 unsigned int *eps_bits) {
     *out = nullptr;
     if (Lb % kBK != 0 || Lb > 512 || Lb < kBK) return cudaErrorNotSupported;
+    const int64_t ntiles = (K + kBN - 1) / kBN;
+    if (ntiles * (Lb / kBK) * kBN >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
     Bf16Search *s = new (std::nothrow) Bf16Search();
     if (!s) return cudaErrorMemoryAllocation;
     s->K = K;
+    s->ntiles = ntiles;
     s->Lb = Lb;
     s->nkc = Lb / kBK;
     const int avail = kMaxDynSmem - 1024 - s->nkc * kAChunkBytes;
     s->stages = avail / kStageBytes;
-    if (s->stages > 6) s->stages = 6;
+    if (s->stages > 8) s->stages = 8;
     if (s->stages < 2) {
         delete s;
         return cudaErrorNotSupported;
     }
     s->smem = 1024 + (size_t)s->nkc * kAChunkBytes + (size_t)s->stages * kStageBytes;
-    const int64_t ntiles = (K + kBN - 1) / kBN;
     s->grid = (int)(ntiles < sm_count ? ntiles : sm_count);
     s->eps_bits = eps_bits;
-    if (!make_map(&s->mapB, d16, (uint64_t)Lb, (uint64_t)K, kBN)) {
+    // the tile-major BF16 dictionary seen as [ntiles * nkc * 256 rows][64]
+    if (!make_map(&s->mapB, d16, (uint64_t)kBK, (uint64_t)ntiles * s->nkc * kBN, kBN)) {
         delete s;
         return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
-    if (e == cudaSuccess) e = cudaMalloc(&s->part_val, sizeof(float) * (size_t)s->grid * kBM * kTrack);
-    if (e == cudaSuccess) e = cudaMalloc(&s->part_idx, sizeof(uint32_t) * (size_t)s->grid * kBM * kTrack);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tilemax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)kBM * ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pairs, sizeof(int) * 2 * kBM * kMaxRescan);
     if (e != cudaSuccess) {
         bf16_search_free(s);
         return e;
@@ -555,8 +482,8 @@ cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int6
 
 void bf16_search_free(Bf16Search *s) {
     if (!s) return;
-    if (s->part_val) cudaFree(s->part_val);
-    if (s->part_idx) cudaFree(s->part_idx);
+    if (s->tile_max) cudaFree(s->tile_max);
+    if (s->pairs) cudaFree(s->pairs);
     delete s;
 }
 
@@ -566,15 +493,18 @@ cudaError_t launch_bf16_search(Bf16Search *s, int B, const __nv_bfloat16 *R16, c
     if (!s || B < 1 || B > kBM) return cudaErrorInvalidValue;
     CUtensorMap mapA;
     if (!make_map(&mapA, R16, (uint64_t)s->Lb, (uint64_t)kBM, kBM)) return cudaErrorInvalidValue;
-    k_gemm_topk<<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB, s->K, s->nkc, s->stages, s->part_val,
-                                                        s->part_idx, status);
+    k_gemm_tilemax<<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB, s->K, s->nkc, s->stages, B, s->tile_max,
+                                                           status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_rescore<<<B, 256, 0, st>>>(s->grid, s->part_val, s->part_idx, D32, Lp, L, R, s->eps_bits, keys, fb_list,
-                                 fb_count, stats);
+    k_select<<<B, 256, 0, st>>>(s->ntiles, s->tile_max, Lp, L, R, s->eps_bits, keys, fb_list, fb_count, s->pairs,
+                                stats);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // FP32 full search for the channels the certificate did not cover
+    k_rescan<<<2 * s->grid, 256, 0, st>>>(D32, s->K, Lp, R, s->pairs, fb_count, keys);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // FP32 full search for the channels with too many flagged tiles
     return launch_gemv_argmax(D32, s->K, Lp, R, B, fb_list, fb_count, keys, status, gemv_grid, st);
 }
 

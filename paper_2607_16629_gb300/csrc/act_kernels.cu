@@ -16,7 +16,10 @@ namespace act {
 // Atom generation
 // ---------------------------------------------------------------------------
 // One warp per atom.  Lane l owns samples 4*(l + 32 j) + e, e = 0..3, so the
-// FP32 row is written with 128-bit stores.  The phase of Eq. (1), in cycles,
+// FP32 row is written with 128-bit stores.  The BF16 copy is written
+// tile-major, [atom / 256][sample / 64][atom % 256][sample % 64], so that one
+// 256-atom x 64-sample operand tile of the tensor-core search is a single
+// contiguous 32 KB block.  The phase of Eq. (1), in cycles,
 // phi = c tau^2 + fc tau with tau = (n - tc) / fs, is evaluated in FP64 and
 // reduced to [-1/2, 1/2] before the FP32 cospi; the Gaussian exponent is
 // formed in FP64 and exponentiated in FP32; the squared norm is summed in
@@ -77,7 +80,9 @@ __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int L
                     uint2 packed;
                     packed.x = *reinterpret_cast<uint32_t *>(&lo);
                     packed.y = *reinterpret_cast<uint32_t *>(&hi);
-                    *reinterpret_cast<uint2 *>(d16 + atom * (int64_t)Lb + n0) = packed;
+                    // tile-major: [atom / 256][n0 / 64][atom % 256][n0 % 64]
+                    const int64_t off = (((atom >> 8) * (Lb >> 6) + (n0 >> 6)) * 256 + (atom & 255)) * 64 + (n0 & 63);
+                    *reinterpret_cast<uint2 *>(d16 + off) = packed;
                 }
             }
         }
@@ -429,7 +434,10 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const float *__restri
         coefs[(int64_t)b * P + k] = c;
         energy[(int64_t)b * (P + 1) + k + 1] = tot;
         keys[b] = 0ull;
-        if (fb_count && b == 0) *fb_count = 0;
+        if (fb_count && b == 0) {
+            fb_count[0] = 0;  // channels queued for the FP32 full search
+            fb_count[1] = 0;  // (channel, CTA) pairs queued for an FP32 rescan
+        }
     }
 }
 

@@ -332,4 +332,6 @@ def workload_c5(channels: int = 32) -> Workload:
 
 def random_signals(config: int, channels: int, n_samples: int, scale: float = 1.0) -> np.ndarray:
     """Plain white Gaussian signals (for edge-case and stress tests)."""
+    if channels == 0:
+        return np.zeros((0, n_samples))
     return np.stack([scale * white_noise(rng_for(config, ch), n_samples) for ch in range(channels)])
