@@ -200,6 +200,37 @@ ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, int32_t *
 ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *resolved, int64_t *tiles_rescanned,
                                   int64_t *fallbacks);
 
+/* act_search_noalloc -- the FP32 search (one projection + argmax step) for
+ * callers that cannot allocate device memory.  The paper has no counterpart:
+ * it exists because some callers may not call cudaMalloc -- code inside a
+ * CUDA stream capture in global mode (an allocation there is illegal), a
+ * latency-bound streaming loop that cannot take the device synchronisation
+ * an allocation implies, or a process whose device memory is fully reserved
+ * by another allocator.  It allocates nothing and uses no grid object.
+ *
+ * For each channel b it returns the atom i maximising |<D_i, r_b>| (lowest
+ * index on ties) and that |score|, computed exactly as act_decompose's FP32
+ * search computes them.
+ *   dictionary  device, [n_atoms][row_stride] float32, caller-owned, rows
+ *               zero beyond the window; 16-byte aligned;
+ *   row_stride  128, 256, 384, 512, 1024 or 2048 floats;
+ *   residuals   device, [channels][row_stride] float32, 16-byte aligned;
+ *   channels    1 .. 256 (larger counts return ACT_ERR_UNSUPPORTED);
+ *   best_index  device, [channels] int64 (-1 if a bounded device-side wait
+ *               gave up or no finite score exists);
+ *   best_score  device, [channels] float32 |score|.
+ * Scratch: a fixed 2056-byte device array inside the library (one key per
+ * channel plus a status word), held by every GPU that loads the library
+ * until exit.  The first call on a device looks up that array's address with
+ * cudaGetSymbolAddress while the device is current; make that first call
+ * before any stream capture.  Every call clears and reuses the same array,
+ * so calls whose GPU work overlaps (different streams, or different host
+ * threads on one device) race and must be serialised by the caller.
+ * Enqueued on cuda_stream; nothing is waited for. */
+ACT_API act_status act_search_noalloc(const float *dictionary, int64_t n_atoms, int32_t row_stride,
+                                      const float *residuals, int32_t channels, int64_t *best_index,
+                                      float *best_score, void *cuda_stream);
+
 /* Frees the grid, its dictionary and all work buffers (waits for the device). */
 ACT_API void act_destroy(act_grid *grid);
 

@@ -33,7 +33,7 @@ EXPORTS = (
     "act_status_string", "act_last_error_message", "act_grid_from_ranges", "act_grid_create",
     "act_grid_size", "act_dictionary_build", "act_set_search", "act_decompose", "act_project",
     "act_dictionary_rows", "act_grid_status", "act_set_profiling", "act_profile_read",
-    "act_bf16_stats", "act_destroy",
+    "act_bf16_stats", "act_destroy", "act_search_noalloc",
 )
 
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
                                          ctypes.POINTER(ctypes.c_int32)]
         lib.act_bf16_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]
+        lib.act_search_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -235,6 +236,15 @@ def act_bf16_stats(grid: int):
     _check(load_library().act_bf16_stats(grid, ctypes.byref(a), ctypes.byref(r), ctypes.byref(b)),
            "act_bf16_stats")
     return a.value, r.value, b.value
+
+
+def act_search_noalloc(dictionary, n_atoms: int, row_stride: int, residuals, channels: int, best_index,
+                       best_score, stream=None) -> None:
+    """FP32 search over a caller-owned dictionary without any allocation
+    (see include/act.h)."""
+    _check(load_library().act_search_noalloc(_ptr(dictionary), int(n_atoms), int(row_stride), _ptr(residuals),
+                                             int(channels), _ptr(best_index), _ptr(best_score), _stream(stream)),
+           "act_search_noalloc")
 
 
 def act_destroy(grid: int) -> None:

@@ -1,0 +1,71 @@
+"""act_search_noalloc, the search entry point for callers that cannot
+allocate device memory (inside a stream capture in global mode, in a
+latency-bound loop, or with all device memory reserved elsewhere).
+
+Its selections and scores must equal those of the allocating entry points
+(act_decompose's one-order FP32 search for the index, act_project for the
+score) within the tolerance the parity tests use, on two calls in a row --
+the second with smaller scores, so that a scratch array left uncleared by the
+first call would show.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2607_16629_gb300 import act, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    act.load_library()
+
+
+def test_noalloc_search_matches_allocating_entry_points():
+    grid = synth.scaled_grid(synth.grid_eeg(), tc_count=16, fc_count=16)   # 65,536 atoms, N = 512
+    B, L = 6, grid.n_samples
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        K, Lp = act.act_grid_size(h)
+        # the caller's own dictionary copy, rows padded with zeros to the stride
+        rows = torch.empty((K, L), dtype=torch.float32, device="cuda")
+        act.act_dictionary_rows(h, 0, K, rows)
+        dictionary = torch.zeros((K, Lp), dtype=torch.float32, device="cuda")
+        dictionary[:, :L] = rows
+        for call, scale in enumerate((10.0, 1.0)):
+            sig = torch.tensor(scale * synth.random_signals(91 + call, B, L), dtype=torch.float32, device="cuda")
+            res = torch.zeros((B, Lp), dtype=torch.float32, device="cuda")
+            res[:, :L] = sig
+            best_index = torch.full((B,), -7, dtype=torch.int64, device="cuda")
+            best_score = torch.zeros((B,), dtype=torch.float32, device="cuda")
+            act.act_search_noalloc(dictionary, K, Lp, res, B, best_index, best_score)
+            # the allocating paths on the same inputs
+            atoms, coef, _, _ = act.decompose(h, sig, 1)
+            scores = torch.empty((B, K), dtype=torch.float32, device="cuda")
+            act.act_project(h, sig, B, scores)
+            torch.cuda.synchronize()
+            assert act.act_grid_status(h) == act.ACT_OK
+            ref_index = act.atom_indices(atoms)[:, 0]
+            assert torch.equal(best_index, ref_index), (call, best_index, ref_index)
+            ref_score = scores.abs().gather(1, ref_index[:, None])[:, 0]
+            assert torch.all((best_score - ref_score).abs() <= 1e-5 * ref_score), call
+            # the argmax of the projection agrees too
+            assert torch.equal(scores.abs().argmax(dim=1), ref_index)
+    finally:
+        act.act_destroy(h)
+
+
+def test_noalloc_rejects_oversize_requests():
+    d = torch.zeros((4, 128), dtype=torch.float32, device="cuda")
+    r = torch.zeros((257, 128), dtype=torch.float32, device="cuda")
+    i = torch.zeros(257, dtype=torch.int64, device="cuda")
+    s = torch.zeros(257, dtype=torch.float32, device="cuda")
+    with pytest.raises(act.ActError) as e:
+        act.act_search_noalloc(d, 4, 128, r, 257, i, s)
+    assert e.value.status == act.ACT_ERR_UNSUPPORTED
+    with pytest.raises(act.ActError) as e:
+        act.act_search_noalloc(d, 4, 100, r, 1, i, s)
+    assert e.value.status == act.ACT_ERR_UNSUPPORTED
