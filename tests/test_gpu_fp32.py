@@ -271,3 +271,21 @@ def test_full_eeg_grid_lockstep_first_orders():
     for k in range(P + 1):
         assert abs(e0 - (np.sum(coef[0, :k].astype(np.float64) ** 2) + energy[0, k])) <= 1e-5 * e0
     assert np.all(np.diff(energy[0]) <= 1e-7 * e0)
+
+
+def test_degenerate_atoms_match_oracle():
+    """Atoms centred far outside the window (tc = 5000 samples, Dt well under a
+    sample) underflow to zero on both sides and are never selected."""
+    grid = synth.Grid(64, 100.0, synth.Axis(20.0, 4980.0, 2), synth.Axis(10.0, 5.0, 2),
+                      synth.Axis(-6.0, 0.5, 2), synth.Axis(0.0, 1.0, 2))
+    D, deg = oracle.dictionary(grid)
+    assert deg.sum() == 8 and not deg[:8].any()
+    s = synth.random_signals(33, 1, grid.n_samples)[0]
+    with Grid(grid) as h:
+        G = _rows(h, grid, 0, grid.n_atoms)
+        idx, _, coef, _, _ = gpu_decompose(h, s[None, :], 3)
+    assert not G[deg].any()
+    assert np.max(np.abs(G - D)) <= ATOM_ATOL
+    assert not deg[idx[0]].any()
+    o_idx, o_coef, _, _ = oracle.mp(D, s.astype(np.float32).astype(np.float64), 3)
+    assert np.array_equal(idx[0], o_idx)
