@@ -226,6 +226,8 @@ def run_ours(args):
     build_ms = build_ev[0].elapsed_time(build_ev[1])
 
     sig = torch.tensor(sig_np[None, :], dtype=torch.float32, device=dev)
+    act.act_autotune(h, sig, 1, stream)
+    gemv_ctas, _, _ = act.act_get_tuning(h)
     atoms = torch.empty((1, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev)
     coef = torch.empty((1, P), dtype=torch.float32, device=dev)
     resid = torch.empty((1, grid.n_samples), dtype=torch.float32, device=dev)
@@ -281,7 +283,7 @@ def run_ours(args):
                                 "paper_2607_16629_gb300/csrc/act_device.cuh"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_gemv<4,1> (FP32 GEMV + fused argmax)",
+                "kernel": "k_gemv<4,1> (FP32 GEMV + fused argmax)", "autotuned_gemv_ctas": gemv_ctas,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": gemv_bytes, "avg_launch_ms": avg_ms,
                 "launches_timed": search_n,
@@ -355,6 +357,8 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
            torch.empty((B, L), dtype=torch.float32, device=dev),
            torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
     act.act_set_search(h, act.ACT_SEARCH_BF16)
+    tune_ms = act.act_autotune(h, sig, B, stream)
+    gemv_ctas, tile_atoms, stages_used = act.act_get_tuning(h)
     steps = max(3, args.steps // 2)
     for _ in range(3):
         act.act_decompose(h, sig, B, P, *out, stream)
@@ -379,9 +383,11 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
         search_ms += a
         gemm_ms += g_ms
         search_n += n_i
-    # plain FP32 comparator: the same 64 channels, one FP32 GEMV decomposition each
+    # plain FP32 comparator: the same 64 channels, one FP32 GEMV decomposition each,
+    # with the GEMV tuned for one channel
     act.act_set_search(h, act.ACT_SEARCH_FP32)
     act.act_set_profiling(h, False)
+    act.act_autotune(h, sig[:1].contiguous(), 1, stream)
     one = [o[:1].contiguous() for o in out]
     act.act_decompose(h, sig[:1].contiguous(), 1, P, *one, stream)
     torch.cuda.synchronize(dev)
@@ -412,6 +418,7 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
                          "tensor_peak_source": f"{peak_kind} bf16_tflops_sustained",
                          "avg_search_ms_per_order": avg,
                          "search_frac_of_hbm_roofline": bytes_per / (avg / 1e3) / 1e9 / peaks["hbm_gbs"]},
+            "autotuned": {"tile_atoms": tile_atoms, "stages": stages_used, "search_ms_per_order": tune_ms},
             "orders_resolved_by_tile_rescan": c1 - c0, "tiles_rescanned": s1 - s0,
             "orders_full_fp32_fallback": f1 - f0,
             "fp32_plain_per_channel": {"value": B * K * P / (fp32_ms / 1e3), "ms": fp32_ms},

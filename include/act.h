@@ -183,15 +183,44 @@ ACT_API act_status act_dictionary_rows(act_grid *grid, int64_t first, int64_t co
  * ACT_ERR_DEVICE_TIMEOUT), then clears it; ACT_OK otherwise. */
 ACT_API act_status act_grid_status(act_grid *grid, void *cuda_stream);
 
+/* Autotuner: times one search order of every candidate launch configuration
+ * on this grid's dictionary with the caller's `channels` signals
+ * [channels][n_samples] (device or host memory) as residuals, keeps the
+ * fastest, and returns its time per order in *best_ms (may be NULL).
+ * Candidates: resident CTAs per SM of the FP32 GEMV (1..4, as occupancy
+ * allows) and, when the grid holds a BF16 dictionary and channels <= 128,
+ * tile width (128 or 256 atoms) x pipeline depth (2 .. what fits in shared
+ * memory) of the tensor-core GEMM, each timed with its tile selection and
+ * rescan.  Results never depend on the configuration, only the speed does.
+ * Waits for the device.  Later act_decompose calls use the chosen
+ * configuration. */
+ACT_API act_status act_autotune(act_grid *grid, const float *signals, int32_t channels, void *cuda_stream,
+                                double *best_ms);
+
+/* The configuration in use: FP32 GEMV grid size in CTAs, tensor-core tile
+ * width in atoms and pipeline stages (0 and 0 without a BF16 dictionary). */
+ACT_API act_status act_get_tuning(const act_grid *grid, int32_t *gemv_ctas, int32_t *bf16_tile_atoms,
+                                  int32_t *bf16_stages);
+
+/* Sets the configuration by hand: gemv_ctas > 0 sets the FP32 GEMV grid
+ * (at most the resident limit); bf16_tile_atoms (128 or 256) > 0 sets the
+ * tensor-core tile width with bf16_stages pipeline stages (<= 0: the most
+ * that fit).  Out-of-range values return ACT_ERR_INVALID_ARG. */
+ACT_API act_status act_set_tuning(act_grid *grid, int32_t gemv_ctas, int32_t bf16_tile_atoms,
+                                  int32_t bf16_stages);
+
 /* Kernel-level measurement hooks used by the benchmark.
- * act_set_profiling(grid, 1) makes later act_decompose graphs record a CUDA
- * event pair around every search-kernel launch (the GEMV, or the GEMM with
- * its rescore); act_profile_read waits for the last act_decompose and
- * returns the summed search-kernel milliseconds and launch count of that
- * call.  *kernels receives the number of kernels one act_decompose launches. */
+ * act_set_profiling(grid, 1) makes later act_decompose graphs record CUDA
+ * events around every search of every order: before it, after its dominant
+ * kernel (the FP32 GEMV, or the tensor-core GEMM) and after the whole search
+ * (GEMM + tile selection + rescan + fallback).  act_profile_read waits for
+ * the last act_decompose and returns, summed over its orders, the whole
+ * search time (*search_ms) and the dominant kernel's time (*core_ms), the
+ * number of orders timed, and in *kernels the number of kernels one
+ * act_decompose launches. */
 ACT_API act_status act_set_profiling(act_grid *grid, int32_t enable);
-ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, int32_t *search_launches,
-                            int32_t *kernels);
+ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, double *core_ms,
+                                    int32_t *search_launches, int32_t *kernels);
 
 /* BF16 search statistics since the grid was created: (channel, order)
  * selections resolved by the FP32 rescan of the flagged tiles, the total

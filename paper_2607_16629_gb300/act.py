@@ -33,7 +33,7 @@ EXPORTS = (
     "act_status_string", "act_last_error_message", "act_grid_from_ranges", "act_grid_create",
     "act_grid_size", "act_dictionary_build", "act_set_search", "act_decompose", "act_project",
     "act_dictionary_rows", "act_grid_status", "act_set_profiling", "act_profile_read",
-    "act_bf16_stats", "act_destroy", "act_search_noalloc",
+    "act_bf16_stats", "act_destroy", "act_search_noalloc", "act_autotune", "act_get_tuning", "act_set_tuning",
 )
 
 
@@ -94,11 +94,15 @@ def load_library(path: str = LIB_PATH):
         lib.act_dictionary_rows.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]
         lib.act_grid_status.argtypes = [_P, _P]
         lib.act_set_profiling.argtypes = [_P, ctypes.c_int32]
-        lib.act_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
-                                         ctypes.POINTER(ctypes.c_int32)]
+        lib.act_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         lib.act_bf16_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]
         lib.act_search_noalloc.argtypes = [_P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P]
+        lib.act_autotune.argtypes = [_P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]
+        lib.act_get_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]
+        lib.act_set_tuning.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -220,12 +224,14 @@ def act_set_profiling(grid: int, enable: bool) -> None:
 
 
 def act_profile_read(grid: int):
+    """(search_ms, core_ms, orders, kernels_per_call) of the last act_decompose."""
     ms = ctypes.c_double()
+    core = ctypes.c_double()
     n = ctypes.c_int32()
     k = ctypes.c_int32()
-    _check(load_library().act_profile_read(grid, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)),
-           "act_profile_read")
-    return ms.value, n.value, k.value
+    _check(load_library().act_profile_read(grid, ctypes.byref(ms), ctypes.byref(core), ctypes.byref(n),
+                                           ctypes.byref(k)), "act_profile_read")
+    return ms.value, core.value, n.value, k.value
 
 
 def act_bf16_stats(grid: int):
@@ -245,6 +251,29 @@ def act_search_noalloc(dictionary, n_atoms: int, row_stride: int, residuals, cha
     _check(load_library().act_search_noalloc(_ptr(dictionary), int(n_atoms), int(row_stride), _ptr(residuals),
                                              int(channels), _ptr(best_index), _ptr(best_score), _stream(stream)),
            "act_search_noalloc")
+
+
+def act_autotune(grid: int, signals, channels: int, stream=None) -> float:
+    """Picks the fastest launch configuration for these signals; returns ms per order."""
+    ms = ctypes.c_double()
+    _check(load_library().act_autotune(grid, _ptr(signals), int(channels), _stream(stream), ctypes.byref(ms)),
+           "act_autotune")
+    return ms.value
+
+
+def act_get_tuning(grid: int):
+    """(gemv_ctas, bf16_tile_atoms, bf16_stages) in use."""
+    a = ctypes.c_int32()
+    b = ctypes.c_int32()
+    c = ctypes.c_int32()
+    _check(load_library().act_get_tuning(grid, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "act_get_tuning")
+    return a.value, b.value, c.value
+
+
+def act_set_tuning(grid: int, gemv_ctas: int = 0, bf16_tile_atoms: int = 0, bf16_stages: int = 0) -> None:
+    _check(load_library().act_set_tuning(grid, int(gemv_ctas), int(bf16_tile_atoms), int(bf16_stages)),
+           "act_set_tuning")
 
 
 def act_destroy(grid: int) -> None:

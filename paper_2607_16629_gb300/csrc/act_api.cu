@@ -186,24 +186,29 @@ act_status record_decompose(act_grid *g, int B, int P, act_search_mode mode, Gra
     ACT_CK(launch_init(g->sig, B, g->L, g->Lp, g->R, R16, g->Lb, g->keys, g->energy, P + 1, g->status, st));
     ++kernels;
     for (int k = 0; k < P; ++k) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        // profiling: events before the search, after its dominant kernel
+        // (GEMV or GEMM) and after the whole search
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
         if (g->profiling) {
-            ACT_CK(cudaEventCreate(&e0));
-            ge.events.push_back(e0);
-            ACT_CK(cudaEventCreate(&e1));
-            ge.events.push_back(e1);
-            ACT_CK(cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
+            for (int i = 0; i < 3; ++i) {
+                ACT_CK(cudaEventCreate(&ev[i]));
+                ge.events.push_back(ev[i]);
+            }
+            ACT_CK(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
         }
         if (bf16) {
-            ACT_CK(launch_bf16_search(g->bf16, B, g->R16, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list,
-                                      g->fb_count, g->stats, g->status, g->gemv_grid, st));
+            ACT_CK(launch_bf16_gemm(g->bf16, B, g->R16, g->status, st));
+            if (g->profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+            ACT_CK(launch_bf16_resolve(g->bf16, B, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list, g->fb_count,
+                                       g->stats, g->status, g->gemv_grid, st));
             kernels += 4;
         } else {
             ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, g->R, B, nullptr, nullptr, g->keys, g->status,
                                       g->gemv_grid, st));
+            if (g->profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         }
-        if (g->profiling) ACT_CK(cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+        if (g->profiling) ACT_CK(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
         ACT_CK(launch_update(g->d32, g->Lp, g->L, g->R, R16, g->Lb, B, g->keys, g->ax, k, P, g->atoms, g->coefs,
                              g->energy, bf16 ? g->fb_count : nullptr, st));
         ++kernels;
@@ -492,26 +497,149 @@ act_status act_grid_status(act_grid *g, void *cuda_stream) {
     return ACT_OK;
 }
 
+act_status act_autotune(act_grid *g, const float *signals, int32_t channels, void *cuda_stream, double *best_ms) {
+    if (!g || !signals || channels < 1) return ACT_ERR_INVALID_ARG;
+    if (g->built < 0) return ACT_ERR_NOT_BUILT;
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool bf16 = g->bf16 != nullptr && channels <= 128;
+    act_status s = ensure_work(g, channels, 1);
+    if (s != ACT_OK) return s;
+    ACT_CK(cudaMemcpyAsync(g->sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
+    ACT_CK(launch_init(g->sig, channels, g->L, g->Lp, g->R, g->R16, g->Lb, g->keys, nullptr, 1, g->status, st));
+    cudaEvent_t e0, e1;
+    ACT_CK(cudaEventCreate(&e0));
+    ACT_CK(cudaEventCreate(&e1));
+    const int reps = 3;
+    // one search order of the current configuration, `reps` times, in ms per order
+    auto time_search = [&](bool use_bf16, double *ms) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {  // pass 0 warms up
+            e = cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                if (use_bf16) {
+                    e = cudaMemsetAsync(g->fb_count, 0, 2 * sizeof(int), st);
+                    if (e == cudaSuccess) e = launch_bf16_gemm(g->bf16, channels, g->R16, g->status, st);
+                    if (e == cudaSuccess)
+                        e = launch_bf16_resolve(g->bf16, channels, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list,
+                                                g->fb_count, g->stats, g->status, g->gemv_grid, st);
+                } else {
+                    e = launch_gemv_argmax(g->d32, g->K, g->Lp, g->R, channels, nullptr, nullptr, g->keys,
+                                           g->status, g->gemv_grid, st);
+                }
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        }
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        *ms = t / reps;
+        return e;
+    };
+    cudaError_t err = cudaSuccess;
+    // FP32 GEMV: resident CTAs per SM
+    double best32 = 1e30;
+    int best_grid = g->gemv_grid;
+    const int max_per_sm = gemv_max_ctas_per_sm(g->Lp);
+    for (int per_sm = 1; per_sm <= max_per_sm && err == cudaSuccess; ++per_sm) {
+        g->gemv_grid = g->sm_count * per_sm;
+        double ms = 0.0;
+        err = time_search(false, &ms);
+        if (err == cudaSuccess && ms < best32) {
+            best32 = ms;
+            best_grid = g->gemv_grid;
+        }
+    }
+    g->gemv_grid = best_grid;
+    // tensor-core search: tile width x pipeline depth
+    double best16 = 1e30;
+    if (bf16 && err == cudaSuccess) {
+        int best_bn = 256, best_st = 0;
+        const int widths[2] = {128, 256};
+        for (int wi = 0; wi < 2 && err == cudaSuccess; ++wi) {
+            const int ms_max = bf16_search_max_stages(g->bf16, widths[wi]);
+            for (int stg = 2; stg <= ms_max && err == cudaSuccess; ++stg) {
+                err = bf16_search_configure(g->bf16, widths[wi], stg);
+                double ms = 0.0;
+                if (err == cudaSuccess) err = time_search(true, &ms);
+                if (err == cudaSuccess && ms < best16) {
+                    best16 = ms;
+                    best_bn = widths[wi];
+                    best_st = stg;
+                }
+            }
+        }
+        if (err == cudaSuccess) err = bf16_search_configure(g->bf16, best_bn, best_st);
+    }
+    // leave clean state: keys and counters zero, no stale graphs
+    if (err == cudaSuccess) err = cudaMemsetAsync(g->keys, 0, sizeof(unsigned long long) * (size_t)channels, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(g->fb_count, 0, 2 * sizeof(int), st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) {
+        note_error("act_autotune", err);
+        return ACT_ERR_CUDA;
+    }
+    drop_graphs(g);
+    if (best_ms) *best_ms = effective_search(g) == ACT_SEARCH_BF16 && bf16 ? best16 : best32;
+    return ACT_OK;
+}
+
+act_status act_get_tuning(const act_grid *g, int32_t *gemv_ctas_out, int32_t *bf16_tile_atoms,
+                          int32_t *bf16_stages) {
+    if (!g) return ACT_ERR_INVALID_ARG;
+    int bn = 0, stg = 0;
+    if (g->bf16) bf16_search_get_config(g->bf16, &bn, &stg, nullptr);
+    if (gemv_ctas_out) *gemv_ctas_out = g->gemv_grid;
+    if (bf16_tile_atoms) *bf16_tile_atoms = bn;
+    if (bf16_stages) *bf16_stages = stg;
+    return ACT_OK;
+}
+
+act_status act_set_tuning(act_grid *g, int32_t gemv_ctas_in, int32_t bf16_tile_atoms, int32_t bf16_stages) {
+    if (!g) return ACT_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (gemv_ctas_in > 0) {
+        if (gemv_ctas_in > g->sm_count * gemv_max_ctas_per_sm(g->Lp)) return ACT_ERR_INVALID_ARG;
+        g->gemv_grid = gemv_ctas_in;
+    }
+    if (bf16_tile_atoms > 0) {
+        if (!g->bf16) return ACT_ERR_NOT_BUILT;
+        cudaError_t e = bf16_search_configure(g->bf16, bf16_tile_atoms, bf16_stages);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ACT_ERR_INVALID_ARG;
+        }
+    }
+    drop_graphs(g);
+    return ACT_OK;
+}
+
 act_status act_set_profiling(act_grid *g, int32_t enable) {
     if (!g) return ACT_ERR_INVALID_ARG;
     g->profiling = enable != 0;
     return ACT_OK;
 }
 
-act_status act_profile_read(act_grid *g, double *search_ms, int32_t *search_launches, int32_t *kernels) {
+act_status act_profile_read(act_grid *g, double *search_ms, double *core_ms, int32_t *search_launches,
+                            int32_t *kernels) {
     if (!g) return ACT_ERR_INVALID_ARG;
     if (!g->last) return ACT_ERR_NOT_BUILT;
     DeviceGuard dg(g->device);
-    double total = 0.0;
+    double total = 0.0, core = 0.0;
     const auto &ev = g->last->events;
-    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
-        ACT_CK(cudaEventSynchronize(ev[i + 1]));
-        float ms = 0.f;
-        ACT_CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-        total += ms;
+    for (size_t i = 0; i + 2 < ev.size(); i += 3) {
+        ACT_CK(cudaEventSynchronize(ev[i + 2]));
+        float a = 0.f, b = 0.f;
+        ACT_CK(cudaEventElapsedTime(&a, ev[i], ev[i + 2]));
+        ACT_CK(cudaEventElapsedTime(&b, ev[i], ev[i + 1]));
+        total += a;
+        core += b;
     }
     if (search_ms) *search_ms = total;
-    if (search_launches) *search_launches = (int32_t)(ev.size() / 2);
+    if (core_ms) *core_ms = core;
+    if (search_launches) *search_launches = (int32_t)(ev.size() / 3);
     if (kernels) *kernels = g->last->kernels;
     return ACT_OK;
 }

@@ -1,7 +1,7 @@
 // Tensor-core search of the batched projection P = D X^T (Sec. IV-A) for up
 // to 128 channels, exact with respect to the FP32 search:
 //  1. a persistent tcgen05 GEMM over the BF16 dictionary writes, per channel
-//     and per tile of 256 atoms, the largest BF16 |score| of the tile;
+//     and per tile of BN atoms, the largest BF16 |score| of the tile;
 //  2. a select kernel bounds the BF16 error (delta) and flags, per channel,
 //     every tile whose maximum lies within 2 delta + 2 eps_r of the channel's
 //     largest BF16 |score| -- the FP32 argmax is provably in one of them;
@@ -10,15 +10,17 @@
 //     flagged tiles takes the FP32 full search instead).
 //
 // GEMM shape per tile: M = 128 channels (rows of the residual matrix, padded
-// with zero rows), N = 256 atoms, K = Lb samples.  The residual matrix (A,
+// with zero rows), N = BN atoms (128 or 256, picked by the autotuner),
+// K = Lb samples.  For windows up to 512 samples the residual matrix (A,
 // <= 128 KB of BF16) is loaded once per CTA by TMA and stays in shared
-// memory; dictionary tiles (B, 256 atoms x 64 samples = 32 KB per stage,
-// contiguous in the tile-major BF16 layout) are streamed by TMA through a
-// ring of stages; FP32 accumulators live in tensor memory (two 256-column
-// buffers, so the epilogue of one tile overlaps the MMAs of the next).  Warp
-// roles: warp 0 issues TMA, warp 1 issues MMAs, warp 2 owns the
-// tensor-memory allocation, warps 4-7 read the accumulators (thread =
-// channel) and reduce each tile to its largest |score|.
+// memory; longer windows stream its 16 KB chunks with the dictionary chunks.
+// Dictionary chunks (B, BN atoms x 64 samples, contiguous in the tile-major
+// BF16 layout) are streamed by TMA through a ring of stages; FP32
+// accumulators live in tensor memory (two BN-column buffers, so the epilogue
+// of one tile overlaps the MMAs of the next).  Warp roles: warp 0 issues
+// TMA, warp 1 issues MMAs, warp 2 owns the tensor-memory allocation, warps
+// 4-7 read the accumulators (thread = channel) and reduce each tile to its
+// largest |score|.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -35,23 +37,27 @@ namespace act {
 namespace {
 
 constexpr int kBM = 128;           // channels per tile (MMA M)
-constexpr int kBN = 256;           // atoms per tile (MMA N)
 constexpr int kBK = 64;            // samples per stage (one 128-byte swizzle row)
+constexpr int kBlockRows = 256;    // atoms per block of the tile-major BF16 layout
 constexpr int kUmmaK = 16;         // K per tcgen05.mma (16-bit inputs)
 constexpr int kMaxRescan = 64;     // flagged tiles per channel before the FP32 full search
 constexpr int kGemmThreads = 256;
 constexpr int kAChunkBytes = kBM * kBK * 2;  // 16 KB
-constexpr int kStageBytes = kBN * kBK * 2;   // 32 KB
 constexpr int kMaxDynSmem = 232448;
-constexpr uint32_t kTmemCols = 512;          // 2 accumulators x 256 FP32 columns
+constexpr int kMaxStages = 8;
 
-// Instruction descriptor of tcgen05.mma.kind::f16: D = F32, A = B = BF16,
-// both K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4)                     // D format F32
-                            | (1u << 7)                   // A format BF16
-                            | (1u << 10)                  // B format BF16
-                            | ((uint32_t)(kBN >> 3) << 17)  // N / 8
-                            | ((uint32_t)(kBM >> 4) << 24); // M / 16
+template <int BN>
+struct TileCfg {
+    static constexpr int kStageBytes = BN * kBK * 2;  // one dictionary chunk
+    static constexpr uint32_t kTmemCols = 2 * BN;     // two accumulators (a power of two >= 32)
+    // Instruction descriptor of tcgen05.mma.kind::f16: D = F32, A = B = BF16,
+    // both K-major, N = BN, M = 128.
+    static constexpr uint32_t kIdesc = (1u << 4)                      // D format F32
+                                       | (1u << 7)                    // A format BF16
+                                       | (1u << 10)                   // B format BF16
+                                       | ((uint32_t)(BN >> 3) << 17)  // N / 8
+                                       | ((uint32_t)(kBM >> 4) << 24);  // M / 16
+};
 
 // Shared-memory matrix descriptor for a K-major operand written by TMA with
 // 128-byte swizzling: rows of 128 bytes, 8-row groups 1024 bytes apart.
@@ -81,12 +87,13 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -119,25 +126,34 @@ __device__ __forceinline__ void sleep_ns(unsigned long long ns) {
 
 struct GemmSmem {
     uint64_t bar_a;
-    uint64_t bar_full[8];
-    uint64_t bar_empty[8];
+    uint64_t bar_full[kMaxStages];
+    uint64_t bar_empty[kMaxStages];
     uint64_t bar_acc_full[2];
     uint64_t bar_acc_empty[2];
     uint32_t tmem_base;
     int abort;
 };
 
+// a_stream = 0: the whole residual matrix (nkc chunks of 16 KB) is loaded
+// once and stays resident; stages hold dictionary chunks only.
+// a_stream = 1 (windows longer than 512 samples): every stage holds a
+// dictionary chunk followed by the matching residual chunk (16 KB, re-read
+// from L2 for every tile).
+template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_tilemax(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t K, int nkc,
-                   int stages, int B, float *__restrict__ tile_max, int *status) {
+                   int stages, int a_stream, int B, float *__restrict__ tile_max, int *status) {
+    using Cfg = TileCfg<BN>;
     extern __shared__ uint8_t dyn_raw[];
     __shared__ GemmSmem sm;
     const uint32_t dyn_base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
     const uint32_t a_smem = dyn_base;
-    const uint32_t b_smem = dyn_base + (uint32_t)nkc * kAChunkBytes;
+    const uint32_t b_smem = a_stream ? dyn_base : dyn_base + (uint32_t)nkc * kAChunkBytes;
+    const uint32_t stage_bytes =
+        a_stream ? (uint32_t)(Cfg::kStageBytes + kAChunkBytes) : (uint32_t)Cfg::kStageBytes;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (K + kBN - 1) / kBN;
+    const int64_t ntiles = (K + BN - 1) / BN;
 
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar_a, 1);
@@ -154,7 +170,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
-                     "r"(kTmemCols)
+                     "r"(Cfg::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -168,10 +184,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // ---------------- TMA producer ----------------
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-        mbar_expect_tx(&sm.bar_a, (uint32_t)(nkc * kAChunkBytes));
-        for (int kc = 0; kc < nkc; ++kc) tma_load_2d(a_smem + kc * kAChunkBytes, &tmA, kc * kBK, 0, &sm.bar_a);
+        if (!a_stream) {
+            mbar_expect_tx(&sm.bar_a, (uint32_t)(nkc * kAChunkBytes));
+            for (int kc = 0; kc < nkc; ++kc) tma_load_2d(a_smem + kc * kAChunkBytes, &tmA, kc * kBK, 0, &sm.bar_a);
+        }
         uint32_t it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+            // row of this tile's first chunk in the tile-major layout viewed as [rows][64]
+            const int64_t atom0 = tile * BN;
+            const int64_t blk = atom0 / kBlockRows, sub = atom0 % kBlockRows;
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
@@ -179,13 +200,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     *abort_flag = 1;
                     break;
                 }
-                mbar_expect_tx(&sm.bar_full[s], kStageBytes);
-                tma_load_2d(b_smem + s * kStageBytes, &tmB, 0, (int)((tile * nkc + kc) * kBN), &sm.bar_full[s]);
+                mbar_expect_tx(&sm.bar_full[s], stage_bytes);
+                tma_load_2d(b_smem + s * stage_bytes, &tmB, 0, (int)((blk * nkc + kc) * kBlockRows + sub),
+                            &sm.bar_full[s]);
+                if (a_stream)
+                    tma_load_2d(b_smem + s * stage_bytes + Cfg::kStageBytes, &tmA, kc * kBK, 0, &sm.bar_full[s]);
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        if (!mbar_wait(&sm.bar_a, 0)) *abort_flag = 1;
+        if (!a_stream && !mbar_wait(&sm.bar_a, 0)) *abort_flag = 1;
         tc_fence_after();
         uint32_t it = 0, local = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++local) {
@@ -195,7 +219,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t d_tmem = tmem + acc * kBN;
+            const uint32_t d_tmem = tmem + acc * BN;
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
@@ -204,11 +228,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = a_smem + kc * kAChunkBytes;
-                const uint32_t b0 = b_smem + s * kStageBytes;
+                const uint32_t b0 = b_smem + s * stage_bytes;
+                const uint32_t a0 = a_stream ? b0 + Cfg::kStageBytes : a_smem + kc * kAChunkBytes;
 #pragma unroll
                 for (int k = 0; k < kBK / kUmmaK; ++k)
-                    tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2),
+                    tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2), Cfg::kIdesc,
                            (kc | k) != 0 ? 1u : 0u);
                 tc_commit(&sm.bar_empty[s]);
             }
@@ -229,9 +253,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             // atoms past K in the last tile are zero rows: they score 0
             float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll 1
-            for (int c = 0; c < kBN / 32; ++c) {
+            for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * kBN + c * 32, v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c * 32, v);
 #pragma unroll
                 for (int j = 0; j < 32; j += 2) {
                     m0 = fmaxf(m0, fabsf(v[j]));
@@ -251,7 +275,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
     tc_fence_after();
     if (warp == 2) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kTmemCols)
+                     : "memory");
     }
 }
 
@@ -279,6 +304,7 @@ __global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__r
     __shared__ double sh_d[32];
     __shared__ float sh_f[32];
     __shared__ int n_sh;
+    __shared__ int base_sh;
     __shared__ int list[kMaxRescan];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -327,7 +353,6 @@ __global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__r
         }
         return;
     }
-    __shared__ int base_sh;
     if (threadIdx.x == 0) {
         keys[b] = 0ull;
         base_sh = atomicAdd(&counters[1], n);
@@ -341,10 +366,11 @@ __global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__r
     }
 }
 
-// FP32 rescan of the flagged (channel, tile) pairs: every atom of the tile is
-// scored exactly as the GEMV scores it and folded into keys[b] with the
-// packed atomicMax (largest |score|, then lowest index).  One block per pair.
-__global__ void __launch_bounds__(256) k_rescan(const float *__restrict__ D32, int64_t K, int Lp,
+// FP32 rescan of the flagged (channel, tile) pairs: every atom of the tile
+// (tile_atoms of them) is scored exactly as the GEMV scores it and folded
+// into keys[b] with the packed atomicMax (largest |score|, then lowest
+// index).  One block of 8 warps per pair.
+__global__ void __launch_bounds__(256) k_rescan(const float *__restrict__ D32, int64_t K, int Lp, int tile_atoms,
                                                 const float *__restrict__ R, const int *__restrict__ pairs,
                                                 const int *__restrict__ counters,
                                                 unsigned long long *__restrict__ keys) {
@@ -353,15 +379,16 @@ __global__ void __launch_bounds__(256) k_rescan(const float *__restrict__ D32, i
     const int n_items = counters[1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nv = Lp / 128;
+    const int rows_per_warp = tile_atoms / 8;
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
         const int b = pairs[2 * w];
         const int64_t tile = pairs[2 * w + 1];
         const float4 *res = reinterpret_cast<const float4 *>(R + (size_t)b * Lp);
         float best = -1.0f;
         uint32_t bidx = 0u;
-        const int64_t row0 = tile * kBN + warp * 32;
+        const int64_t row0 = tile * tile_atoms + warp * rows_per_warp;
         // four rows in flight per step; rows past K (last tile) are skipped
-        for (int i = 0; i < 32; i += 4) {
+        for (int i = 0; i < rows_per_warp; i += 4) {
             float sc[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -426,51 +453,85 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, ui
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Largest number of stages that fits the shared memory for a tile width.
+int max_stages(int bn, int nkc, bool a_stream) {
+    const int chunk = bn * kBK * 2;
+    int st = a_stream ? (kMaxDynSmem - 1024) / (chunk + kAChunkBytes)
+                      : (kMaxDynSmem - 1024 - nkc * kAChunkBytes) / chunk;
+    return st > kMaxStages ? kMaxStages : st;
+}
+
 }  // namespace
 
 struct Bf16Search {
-    CUtensorMap mapB;
+    CUtensorMap mapB[2];  // box heights 128 and 256
     int64_t K = 0;
-    int64_t ntiles = 0;
     int Lb = 0;
     int nkc = 0;
+    int a_stream = 0;
+    int sm_count = 0;
+    // current configuration
+    int bn = 256;
     int stages = 0;
     int grid = 0;
+    int64_t ntiles = 0;
     size_t smem = 0;
-    float *tile_max = nullptr;         // [kBM][ntiles]
+    float *tile_max = nullptr;         // [kBM][ntiles at BN = 128]
     int *pairs = nullptr;              // [kBM * kMaxRescan][2]
     unsigned int *eps_bits = nullptr;  // owned by the caller (dictionary build)
 };
 
+cudaError_t bf16_search_configure(Bf16Search *s, int bn, int stages) {
+    if (!s || (bn != 128 && bn != 256)) return cudaErrorInvalidValue;
+    const int ms = max_stages(bn, s->nkc, s->a_stream != 0);
+    if (stages <= 0) stages = ms;
+    if (stages < 2 || stages > ms) return cudaErrorInvalidValue;
+    const size_t chunk = (size_t)bn * kBK * 2;
+    const size_t smem = s->a_stream ? 1024 + (size_t)stages * (chunk + kAChunkBytes)
+                                    : 1024 + (size_t)s->nkc * kAChunkBytes + (size_t)stages * chunk;
+    cudaError_t e =
+        bn == 256 ? cudaFuncSetAttribute(k_gemm_tilemax<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                  : cudaFuncSetAttribute(k_gemm_tilemax<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    s->bn = bn;
+    s->stages = stages;
+    s->smem = smem;
+    s->ntiles = (s->K + bn - 1) / bn;
+    s->grid = (int)(s->ntiles < s->sm_count ? s->ntiles : s->sm_count);
+    return cudaSuccess;
+}
+
+void bf16_search_get_config(const Bf16Search *s, int *bn, int *stages, int *max_stages_out) {
+    if (bn) *bn = s->bn;
+    if (stages) *stages = s->stages;
+    if (max_stages_out) *max_stages_out = max_stages(s->bn, s->nkc, s->a_stream != 0);
+}
+
+int bf16_search_max_stages(const Bf16Search *s, int bn) { return max_stages(bn, s->nkc, s->a_stream != 0); }
+
 cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int64_t K, int Lb, int sm_count,
                                 unsigned int *eps_bits) {
     *out = nullptr;
-    if (Lb % kBK != 0 || Lb > 512 || Lb < kBK) return cudaErrorNotSupported;
-    const int64_t ntiles = (K + kBN - 1) / kBN;
-    if (ntiles * (Lb / kBK) * kBN >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
+    if (Lb % kBK != 0 || Lb > kMaxSamples || Lb < kBK) return cudaErrorNotSupported;
+    const int64_t nblocks = (K + kBlockRows - 1) / kBlockRows;
+    if (nblocks * (Lb / kBK) * kBlockRows >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
     Bf16Search *s = new (std::nothrow) Bf16Search();
     if (!s) return cudaErrorMemoryAllocation;
     s->K = K;
-    s->ntiles = ntiles;
     s->Lb = Lb;
     s->nkc = Lb / kBK;
-    const int avail = kMaxDynSmem - 1024 - s->nkc * kAChunkBytes;
-    s->stages = avail / kStageBytes;
-    if (s->stages > 8) s->stages = 8;
-    if (s->stages < 2) {
-        delete s;
-        return cudaErrorNotSupported;
-    }
-    s->smem = 1024 + (size_t)s->nkc * kAChunkBytes + (size_t)s->stages * kStageBytes;
-    s->grid = (int)(ntiles < sm_count ? ntiles : sm_count);
+    s->a_stream = s->nkc > 8 ? 1 : 0;  // a resident residual matrix must leave room for >= 3 stages
+    s->sm_count = sm_count;
     s->eps_bits = eps_bits;
-    // the tile-major BF16 dictionary seen as [ntiles * nkc * 256 rows][64]
-    if (!make_map(&s->mapB, d16, (uint64_t)kBK, (uint64_t)ntiles * s->nkc * kBN, kBN)) {
+    // the tile-major BF16 dictionary seen as [blocks * nkc * 256 rows][64]
+    const uint64_t rows = (uint64_t)nblocks * s->nkc * kBlockRows;
+    if (!make_map(&s->mapB[0], d16, (uint64_t)kBK, rows, 128) ||
+        !make_map(&s->mapB[1], d16, (uint64_t)kBK, rows, 256)) {
         delete s;
         return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tilemax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
-    if (e == cudaSuccess) e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)kBM * ntiles);
+    cudaError_t e = bf16_search_configure(s, 256, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)kBM * ((K + 127) / 128));
     if (e == cudaSuccess) e = cudaMalloc(&s->pairs, sizeof(int) * 2 * kBM * kMaxRescan);
     if (e != cudaSuccess) {
         bf16_search_free(s);
@@ -487,21 +548,28 @@ void bf16_search_free(Bf16Search *s) {
     delete s;
 }
 
-cudaError_t launch_bf16_search(Bf16Search *s, int B, const __nv_bfloat16 *R16, const float *D32, int Lp, int L,
-                               const float *R, unsigned long long *keys, int *fb_list, int *fb_count,
-                               long long *stats, int *status, int gemv_grid, cudaStream_t st) {
+cudaError_t launch_bf16_gemm(Bf16Search *s, int B, const __nv_bfloat16 *R16, int *status, cudaStream_t st) {
     if (!s || B < 1 || B > kBM) return cudaErrorInvalidValue;
     CUtensorMap mapA;
     if (!make_map(&mapA, R16, (uint64_t)s->Lb, (uint64_t)kBM, kBM)) return cudaErrorInvalidValue;
-    k_gemm_tilemax<<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB, s->K, s->nkc, s->stages, B, s->tile_max,
-                                                           status);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (s->bn == 256)
+        k_gemm_tilemax<256><<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB[1], s->K, s->nkc, s->stages,
+                                                                    s->a_stream, B, s->tile_max, status);
+    else
+        k_gemm_tilemax<128><<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB[0], s->K, s->nkc, s->stages,
+                                                                    s->a_stream, B, s->tile_max, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bf16_resolve(Bf16Search *s, int B, const float *D32, int Lp, int L, const float *R,
+                                unsigned long long *keys, int *fb_list, int *fb_count, long long *stats, int *status,
+                                int gemv_grid, cudaStream_t st) {
+    if (!s || B < 1 || B > kBM) return cudaErrorInvalidValue;
     k_select<<<B, 256, 0, st>>>(s->ntiles, s->tile_max, Lp, L, R, s->eps_bits, keys, fb_list, fb_count, s->pairs,
                                 stats);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_rescan<<<2 * s->grid, 256, 0, st>>>(D32, s->K, Lp, R, s->pairs, fb_count, keys);
+    k_rescan<<<2 * s->sm_count, 256, 0, st>>>(D32, s->K, Lp, s->bn, R, s->pairs, fb_count, keys);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // FP32 full search for the channels with too many flagged tiles

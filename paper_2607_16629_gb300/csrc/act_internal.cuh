@@ -82,7 +82,8 @@ cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, in
 cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
                           float *coefs, double *energy, int *fb_count, cudaStream_t st);
-int gemv_ctas(int sm_count, int Lp);
+int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
+int gemv_max_ctas_per_sm(int Lp);
 
 // ---- tensor-core search (act_gemm.cu) -------------------------------------
 struct Bf16Search;
@@ -94,11 +95,18 @@ struct Bf16Search;
 cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int64_t K, int Lb, int sm_count,
                                 unsigned int *eps_bits);
 void bf16_search_free(Bf16Search *s);
-// One search order for B <= 128 channels: GEMM + fused top-k, merge and
-// FP32 rescore with certificate, FP32 fallback for uncertified channels.
-// Leaves the packed selection key of every channel in keys[].
-cudaError_t launch_bf16_search(Bf16Search *s, int B, const __nv_bfloat16 *R16, const float *D32, int Lp, int L,
-                               const float *R, unsigned long long *keys, int *fb_list, int *fb_count,
-                               long long *stats, int *status, int gemv_grid, cudaStream_t st);
+// Tile width (128 or 256 atoms) and pipeline depth of the GEMM; stages <= 0
+// picks the deepest that fits.  Invalid combinations are rejected.
+cudaError_t bf16_search_configure(Bf16Search *s, int bn, int stages);
+void bf16_search_get_config(const Bf16Search *s, int *bn, int *stages, int *max_stages);
+int bf16_search_max_stages(const Bf16Search *s, int bn);
+// One search order for B <= 128 channels, in two launches sequences:
+// the tensor-core GEMM writing per-tile maxima, then tile selection, FP32
+// rescan of the flagged tiles and the FP32 full search for channels with too
+// many of them.  Leaves the packed selection key of every channel in keys[].
+cudaError_t launch_bf16_gemm(Bf16Search *s, int B, const __nv_bfloat16 *R16, int *status, cudaStream_t st);
+cudaError_t launch_bf16_resolve(Bf16Search *s, int B, const float *D32, int Lp, int L, const float *R,
+                                unsigned long long *keys, int *fb_list, int *fb_count, long long *stats, int *status,
+                                int gemv_grid, cudaStream_t st);
 
 }  // namespace act

@@ -359,7 +359,9 @@ static cudaError_t gemv_dispatch(const float *D, int64_t K, int Lp, const float 
 #undef ACT_GEMV_CASE
 }
 
-int gemv_ctas(int sm_count, int Lp) {
+int gemv_ctas(int sm_count, int Lp) { return sm_count * gemv_max_ctas_per_sm(Lp); }
+
+int gemv_max_ctas_per_sm(int Lp) {
     int per_sm = 0;
     const int nv = Lp / 128;
     cudaError_t e = cudaErrorInvalidValue;
@@ -375,7 +377,7 @@ int gemv_ctas(int sm_count, int Lp) {
     }
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     if (per_sm > 4) per_sm = 4;
-    return sm_count * per_sm;
+    return per_sm;
 }
 
 cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,

@@ -173,3 +173,50 @@ def test_bf16_full_eeg_grid_64_channels():
     for k in range(P + 1):
         assert np.all(np.abs(e0 - (np.sum(cb[:, :k].astype(np.float64) ** 2, axis=1) + eb[:, k])) <= 1e-5 * e0)
     print(f"resolved {cert} tiles {rescan} fallback {fb}")
+
+
+@pytest.mark.parametrize("L,fs", [(600, 500.0), (1024, 1000.0), (2048, 500.0)])
+def test_bf16_long_windows_stream_the_residual(L, fs):
+    """Windows longer than 512 samples stream the residual chunks with the
+    dictionary chunks instead of keeping them resident; the selection still
+    equals the FP32 search's on every output."""
+    grid = synth.Grid(L, fs, synth.Axis(0.0, L / 16.0, 16), synth.Axis.linspace(20.0, 200.0, 12),
+                      synth.Axis.linspace(-4.0, -1.5, 4), synth.Axis.linspace(-100.0, 100.0, 8))
+    sig = np.stack([synth.emg_like_signal(b, L, fs)[0] for b in range(12)])
+    with Bf16Grid(grid) as h:
+        ib, cb, rb, eb = run(h, sig, 4, act.ACT_SEARCH_BF16)
+        i32, c32, r32, e32 = run(h, sig, 4, act.ACT_SEARCH_FP32)
+    for x, y in zip((ib, cb, rb, eb), (i32, c32, r32, e32)):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("tile,stages", [(128, 2), (128, 0), (256, 2)])
+def test_bf16_tile_widths_and_depths(tile, stages):
+    """Every tensor-core configuration the autotuner may pick (tile width x
+    pipeline depth) returns the FP32 search's results bit for bit."""
+    grid = synth.scaled_grid(synth.grid_eeg(), tc_count=16, fc_count=16)
+    sig = np.stack([synth.eeg_like_signal(3, b)[0] for b in range(20)])
+    with Bf16Grid(grid) as h:
+        act.act_set_tuning(h, 0, tile, stages)
+        g, bn, st = act.act_get_tuning(h)
+        assert bn == tile and (stages == 0 or st == stages)
+        ib, cb, rb, eb = run(h, sig, 4, act.ACT_SEARCH_BF16)
+        i32, c32, r32, e32 = run(h, sig, 4, act.ACT_SEARCH_FP32)
+    for x, y in zip((ib, cb, rb, eb), (i32, c32, r32, e32)):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_keeps_results():
+    grid = synth.scaled_grid(synth.grid_eeg(), tc_count=16, fc_count=16)
+    sig = np.stack([synth.eeg_like_signal(3, b)[0] for b in range(20)])
+    with Bf16Grid(grid) as h:
+        before = run(h, sig, 3, act.ACT_SEARCH_BF16)
+        ms = act.act_autotune(h, torch.tensor(sig, dtype=torch.float32, device="cuda"), 20)
+        assert ms > 0
+        g, bn, st = act.act_get_tuning(h)
+        assert bn in (128, 256) and st >= 2 and g > 0
+        after = run(h, sig, 3, act.ACT_SEARCH_BF16)
+        with pytest.raises(act.ActError):
+            act.act_set_tuning(h, 0, 64, 0)
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
