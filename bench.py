@@ -314,6 +314,9 @@ def run_ours(args):
     bf16 = None
     if not args.no_bf16:
         bf16 = bench_bf16(args, dev, stream, peaks, peak_kind)
+    ragged = None
+    if not args.no_ragged:
+        ragged = bench_ragged(args, dev, stream, peaks, peak_kind)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -330,6 +333,8 @@ def run_ours(args):
                 "clocks": clk.summary()}
         if bf16 is not None:
             line["bf16_batched"] = bf16
+        if ragged is not None:
+            line["ragged_uneven_batch"] = ragged
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -426,6 +431,69 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
             "gpu_launches": kernels * steps}
 
 
+def bench_ragged(args, dev, stream, peaks, peak_kind):
+    """Uneven batch: 256 EMG-like signals, N uniform in {256, 512, 1024, 2048}
+    at fs = 500 Hz, each over the 256 x 96 x 8 x 24 = 4,718,592-atom grid of
+    its length (four stored BF16 + FP32 dictionaries, 108 GB), 30 orders, BF16
+    search, all length groups in one CUDA graph."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    sigs, grids_py, P = synth.workload_c4()
+    lengths = sorted({int(len(x)) for x in sigs})
+    offsets = np.concatenate([[0], np.cumsum([len(x) for x in sigs])]).astype(np.int64)
+    handles = {}
+    t0 = time.perf_counter()
+    try:
+        for L in lengths:
+            h = act.act_grid_create(synth.grid_emg(L), dev.index)
+            handles[L] = h
+            act.act_dictionary_build(h, act.ACT_DICT_BF16, stream)
+        torch.cuda.synchronize(dev)
+        build_s = time.perf_counter() - t0
+        flat = torch.tensor(np.concatenate(sigs).astype(np.float32), device=dev)
+        for L in lengths:  # tune each length group on its own channels
+            idx = [i for i, x in enumerate(sigs) if len(x) == L]
+            grp = torch.tensor(np.stack([sigs[i] for i in idx]).astype(np.float32), device=dev)
+            act.act_autotune(handles[L], grp, len(idx), stream)
+        plan = act.act_ragged_plan_create([handles[L] for L in lengths], offsets, P)
+        try:
+            C = len(sigs)
+            out = [torch.empty((C, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+                   torch.empty((C, P), dtype=torch.float32, device=dev),
+                   torch.empty((int(offsets[-1]),), dtype=torch.float32, device=dev),
+                   torch.empty((C, P + 1), dtype=torch.float64, device=dev)]
+            act.act_ragged_decompose(plan, flat, *out, stream)
+            torch.cuda.synchronize(dev)
+            steps = max(2, args.steps // 10)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                act.act_ragged_decompose(plan, flat, *out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            for L in lengths:
+                st = act.act_grid_status(handles[L], stream)
+                if st != act.ACT_OK:
+                    raise RuntimeError(act.status_name(st))
+            groups, kernels = act.act_ragged_plan_info(plan)
+        finally:
+            act.act_ragged_plan_destroy(plan)
+        K = synth.grid_emg(256).n_atoms
+        bf16_bytes = sum(K * L * 2 for L in lengths)
+        counts = {L: sum(1 for x in sigs if len(x) == L) for L in lengths}
+        return {"workload": "emg_like_ragged_256ch_n256-2048_fs500_grid256x96x8x24_k4718592_p30",
+                "value": C * K * P * steps / (ms / 1e3), "unit": UNIT, "atoms_per_s": C * P * steps / (ms / 1e3),
+                "ms_per_step": ms / steps, "steps": steps, "channels_per_length": counts,
+                "dictionary_build_s": build_s, "length_groups": groups, "gpu_launches": kernels * steps,
+                "hbm_frac_of_bf16_dictionary_stream": bf16_bytes * P / (ms / steps / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 tile rescan"}
+    finally:
+        for h in handles.values():
+            act.act_destroy(h)
+
+
 def run_profile_case(args):
     """Small, self-checking cases for ncu captures: a few launches of one
     search kernel on a dictionary larger than L2 but a few GB at most.
@@ -463,6 +531,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()

@@ -229,6 +229,41 @@ ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, double *c
 ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *resolved, int64_t *tiles_rescanned,
                                   int64_t *fallbacks);
 
+/* Uneven batches (channels of different window lengths).
+ *
+ * act_ragged_plan_create prepares the decomposition of `channels` signals
+ * laid end to end, channel c occupying samples offsets[c] .. offsets[c+1]-1
+ * (offsets: host memory, [channels+1], offsets[0] = 0).  Each channel is
+ * decomposed over the grid in grids[0 .. n_grids-1] whose n_samples equals
+ * its length (one grid per length; every grid built on the same device).
+ * Each length group uses its grid's search (ACT_SEARCH_BF16 needs at most
+ * 128 channels in the group, else the group uses FP32).  The whole batch --
+ * gathers, every group's n_atoms orders, scatters -- is captured once as one
+ * CUDA graph whose length groups are independent branches.  The plan owns
+ * its work buffers; it shares each grid's dictionary and search scratch, so
+ * it must not run concurrently with other calls on those grids, and it must
+ * be destroyed before they are.  Rebuilding a grid's dictionary or changing
+ * its tuning makes the plan stale (act_ragged_decompose then returns
+ * ACT_ERR_NOT_BUILT).  Errors: ACT_ERR_INVALID_ARG (bad offsets, a length
+ * with no grid, two grids of one length), ACT_ERR_NOT_BUILT, ACT_ERR_OOM. */
+typedef struct act_ragged_plan act_ragged_plan;
+ACT_API act_status act_ragged_plan_create(act_grid *const *grids, int32_t n_grids, const int64_t *offsets,
+                                          int32_t channels, int32_t n_atoms, act_ragged_plan **out);
+
+/* Runs the plan on signals (concatenated, [offsets[channels]] float32,
+ * device or host).  Outputs as act_decompose, in the callers' channel order:
+ * atoms_out and coeffs_out [channels][n_atoms], energy_out
+ * [channels][n_atoms+1], residuals_out concatenated like the signals; any may
+ * be NULL.  Waits only when a host buffer is involved. */
+ACT_API act_status act_ragged_decompose(act_ragged_plan *plan, const float *signals, act_atom *atoms_out,
+                                        float *coeffs_out, float *residuals_out, double *energy_out,
+                                        void *cuda_stream);
+
+/* Number of non-empty length groups, and kernels one act_ragged_decompose launches. */
+ACT_API act_status act_ragged_plan_info(const act_ragged_plan *plan, int32_t *groups, int32_t *kernels);
+
+ACT_API void act_ragged_plan_destroy(act_ragged_plan *plan);
+
 /* act_search_noalloc -- the FP32 search (one projection + argmax step) for
  * callers that cannot allocate device memory.  The paper has no counterpart:
  * it exists because some callers may not call cudaMalloc -- code inside a

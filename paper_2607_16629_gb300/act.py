@@ -34,6 +34,7 @@ EXPORTS = (
     "act_grid_size", "act_dictionary_build", "act_set_search", "act_decompose", "act_project",
     "act_dictionary_rows", "act_grid_status", "act_set_profiling", "act_profile_read",
     "act_bf16_stats", "act_destroy", "act_search_noalloc", "act_autotune", "act_get_tuning", "act_set_tuning",
+    "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
 )
 
 
@@ -103,10 +104,17 @@ def load_library(path: str = LIB_PATH):
         lib.act_get_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]
         lib.act_set_tuning.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        lib.act_ragged_plan_create.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(_P)]
+        lib.act_ragged_decompose.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        lib.act_ragged_plan_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        lib.act_ragged_plan_destroy.argtypes = [_P]
+        lib.act_ragged_plan_destroy.restype = None
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
-            if name not in ("act_status_string", "act_last_error_message", "act_destroy"):
+            if name not in ("act_status_string", "act_last_error_message", "act_destroy",
+                            "act_ragged_plan_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -274,6 +282,37 @@ def act_get_tuning(grid: int):
 def act_set_tuning(grid: int, gemv_ctas: int = 0, bf16_tile_atoms: int = 0, bf16_stages: int = 0) -> None:
     _check(load_library().act_set_tuning(grid, int(gemv_ctas), int(bf16_tile_atoms), int(bf16_stages)),
            "act_set_tuning")
+
+
+def act_ragged_plan_create(grids, offsets, n_atoms: int) -> int:
+    """Plan for channels of uneven length: grids (handles, one per length),
+    offsets (host int64 sequence of channels+1 sample offsets)."""
+    import numpy as np
+    hs = (_P * len(grids))(*grids)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    h = _P()
+    _check(load_library().act_ragged_plan_create(ctypes.cast(hs, _P), len(grids), off.ctypes.data, len(off) - 1,
+                                                 int(n_atoms), ctypes.byref(h)), "act_ragged_plan_create")
+    return h.value
+
+
+def act_ragged_decompose(plan: int, signals, atoms_out=None, coeffs_out=None, residuals_out=None, energy_out=None,
+                         stream=None) -> None:
+    _check(load_library().act_ragged_decompose(plan, _ptr(signals), _ptr(atoms_out), _ptr(coeffs_out),
+                                               _ptr(residuals_out), _ptr(energy_out), _stream(stream)),
+           "act_ragged_decompose")
+
+
+def act_ragged_plan_info(plan: int):
+    g = ctypes.c_int32()
+    k = ctypes.c_int32()
+    _check(load_library().act_ragged_plan_info(plan, ctypes.byref(g), ctypes.byref(k)), "act_ragged_plan_info")
+    return g.value, k.value
+
+
+def act_ragged_plan_destroy(plan: int) -> None:
+    if plan:
+        load_library().act_ragged_plan_destroy(plan)
 
 
 def act_destroy(grid: int) -> None:

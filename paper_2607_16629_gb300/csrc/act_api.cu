@@ -81,6 +81,21 @@ void free_dev(T *&p) {
 
 }  // namespace
 
+// Per-decomposition device buffers: a grid owns one set, a ragged plan one
+// per length group.
+struct WorkBuffers {
+    int cap_B = 0, cap_P = 0;
+    float *sig = nullptr;             // [B][L] staged input signals
+    float *R = nullptr;               // [B][Lp] FP32 residuals
+    __nv_bfloat16 *R16 = nullptr;     // [ceil(B/128)*128][Lb] BF16 residuals
+    unsigned long long *keys = nullptr;
+    act_atom *atoms = nullptr;        // [B][P]
+    float *coefs = nullptr;           // [B][P]
+    double *energy = nullptr;         // [B][P+1]
+    int *fb_list = nullptr;           // [B] channels queued for the FP32 full search
+    int *fb_count = nullptr;          // [2] full-search and rescan queue lengths
+};
+
 struct act_grid {
     act_grid_desc desc;
     GridAxes ax;
@@ -94,18 +109,8 @@ struct act_grid {
     __nv_bfloat16 *d16 = nullptr;
     unsigned long long *degenerate = nullptr;
     unsigned int *eps_bits = nullptr;  // largest |bf16(g) - g| (float bits)
-    // work buffers
-    int cap_B = 0, cap_P = 0;
-    float *sig = nullptr;
-    float *R = nullptr;
-    __nv_bfloat16 *R16 = nullptr;
-    unsigned long long *keys = nullptr;
-    act_atom *atoms = nullptr;
-    float *coefs = nullptr;
-    double *energy = nullptr;
+    WorkBuffers w;
     int *status = nullptr;
-    int *fb_list = nullptr;
-    int *fb_count = nullptr;
     long long *stats = nullptr;
     Bf16Search *bf16 = nullptr;
     int gemv_grid = 0;
@@ -113,6 +118,7 @@ struct act_grid {
     bool profiling = false;
     std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
     GraphEntry *last = nullptr;
+    uint64_t generation = 0;  // bumped whenever the dictionary or the launch configuration changes
 };
 
 namespace {
@@ -127,16 +133,17 @@ void drop_graphs(act_grid *g) {
     g->last = nullptr;
 }
 
-void free_work(act_grid *g) {
-    free_dev(g->sig);
-    free_dev(g->R);
-    free_dev(g->R16);
-    free_dev(g->keys);
-    free_dev(g->atoms);
-    free_dev(g->coefs);
-    free_dev(g->energy);
-    free_dev(g->fb_list);
-    g->cap_B = g->cap_P = 0;
+void free_work(WorkBuffers &w) {
+    free_dev(w.sig);
+    free_dev(w.R);
+    free_dev(w.R16);
+    free_dev(w.keys);
+    free_dev(w.atoms);
+    free_dev(w.coefs);
+    free_dev(w.energy);
+    free_dev(w.fb_list);
+    free_dev(w.fb_count);
+    w.cap_B = w.cap_P = 0;
 }
 
 void free_dictionary(act_grid *g) {
@@ -147,28 +154,37 @@ void free_dictionary(act_grid *g) {
     g->built = -1;
 }
 
-// Work buffers for B channels and P orders.  The BF16 residual copy always
-// has at least 128 rows (the tensor-core tile height), padded with zeros.
-act_status ensure_work(act_grid *g, int B, int P) {
-    if (B <= g->cap_B && P <= g->cap_P) return ACT_OK;
-    drop_graphs(g);
-    const int nB = B > g->cap_B ? B : g->cap_B;
-    const int nP = P > g->cap_P ? P : g->cap_P;
-    free_work(g);
-    const int rows16 = round_up(nB, 128);
-    ACT_CK(cudaMalloc(&g->sig, sizeof(float) * (size_t)nB * g->L));
-    ACT_CK(cudaMalloc(&g->R, sizeof(float) * (size_t)nB * g->Lp));
-    ACT_CK(cudaMalloc(&g->R16, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb));
-    ACT_CK(cudaMemset(g->R16, 0, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb));
-    ACT_CK(cudaMalloc(&g->keys, sizeof(unsigned long long) * (size_t)nB));
-    ACT_CK(cudaMemset(g->keys, 0, sizeof(unsigned long long) * (size_t)nB));
-    ACT_CK(cudaMalloc(&g->atoms, sizeof(act_atom) * (size_t)nB * nP));
-    ACT_CK(cudaMalloc(&g->coefs, sizeof(float) * (size_t)nB * nP));
-    ACT_CK(cudaMalloc(&g->energy, sizeof(double) * (size_t)nB * (nP + 1)));
-    ACT_CK(cudaMalloc(&g->fb_list, sizeof(int) * (size_t)nB));
-    g->cap_B = nB;
-    g->cap_P = nP;
+// Work buffers for B channels and P orders on a grid of window L.  The BF16
+// residual copy always has a multiple of 128 rows (the tensor-core tile
+// height), padded with zeros.
+act_status alloc_work(const act_grid *g, WorkBuffers &w, int B, int P) {
+    const int rows16 = round_up(B, 128);
+    ACT_CK(cudaMalloc(&w.sig, sizeof(float) * (size_t)B * g->L));
+    ACT_CK(cudaMalloc(&w.R, sizeof(float) * (size_t)B * g->Lp));
+    ACT_CK(cudaMalloc(&w.R16, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb));
+    ACT_CK(cudaMemset(w.R16, 0, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb));
+    ACT_CK(cudaMalloc(&w.keys, sizeof(unsigned long long) * (size_t)B));
+    ACT_CK(cudaMemset(w.keys, 0, sizeof(unsigned long long) * (size_t)B));
+    ACT_CK(cudaMalloc(&w.atoms, sizeof(act_atom) * (size_t)B * P));
+    ACT_CK(cudaMalloc(&w.coefs, sizeof(float) * (size_t)B * P));
+    ACT_CK(cudaMalloc(&w.energy, sizeof(double) * (size_t)B * (P + 1)));
+    ACT_CK(cudaMalloc(&w.fb_list, sizeof(int) * (size_t)B));
+    ACT_CK(cudaMalloc(&w.fb_count, 2 * sizeof(int)));
+    ACT_CK(cudaMemset(w.fb_count, 0, 2 * sizeof(int)));
+    w.cap_B = B;
+    w.cap_P = P;
     return ACT_OK;
+}
+
+act_status ensure_work(act_grid *g, int B, int P) {
+    if (B <= g->w.cap_B && P <= g->w.cap_P) return ACT_OK;
+    drop_graphs(g);
+    const int nB = B > g->w.cap_B ? B : g->w.cap_B;
+    const int nP = P > g->w.cap_P ? P : g->w.cap_P;
+    free_work(g->w);
+    act_status s = alloc_work(g, g->w, nB, nP);
+    if (s != ACT_OK) free_work(g->w);
+    return s;
 }
 
 act_search_mode effective_search(const act_grid *g) {
@@ -177,19 +193,19 @@ act_search_mode effective_search(const act_grid *g) {
     return g->built == ACT_DICT_BF16 ? ACT_SEARCH_BF16 : ACT_SEARCH_FP32;
 }
 
-// Records the whole decomposition (init + P orders) on the capture stream.
-act_status record_decompose(act_grid *g, int B, int P, act_search_mode mode, GraphEntry &ge) {
-    cudaStream_t st = g->cap;
+// Records the whole decomposition (init + P orders) on stream st (being captured).
+act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_search_mode mode, GraphEntry &ge,
+                            cudaStream_t st, bool profiling) {
     const bool bf16 = mode == ACT_SEARCH_BF16;
-    __nv_bfloat16 *R16 = bf16 ? g->R16 : nullptr;
+    __nv_bfloat16 *R16 = bf16 ? w.R16 : nullptr;
     int kernels = 0;
-    ACT_CK(launch_init(g->sig, B, g->L, g->Lp, g->R, R16, g->Lb, g->keys, g->energy, P + 1, g->status, st));
+    ACT_CK(launch_init(w.sig, B, g->L, g->Lp, w.R, R16, g->Lb, w.keys, w.energy, P + 1, g->status, st));
     ++kernels;
     for (int k = 0; k < P; ++k) {
         // profiling: events before the search, after its dominant kernel
         // (GEMV or GEMM) and after the whole search
         cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-        if (g->profiling) {
+        if (profiling) {
             for (int i = 0; i < 3; ++i) {
                 ACT_CK(cudaEventCreate(&ev[i]));
                 ge.events.push_back(ev[i]);
@@ -197,20 +213,20 @@ act_status record_decompose(act_grid *g, int B, int P, act_search_mode mode, Gra
             ACT_CK(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
         }
         if (bf16) {
-            ACT_CK(launch_bf16_gemm(g->bf16, B, g->R16, g->status, st));
-            if (g->profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
-            ACT_CK(launch_bf16_resolve(g->bf16, B, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list, g->fb_count,
+            ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
+            if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+            ACT_CK(launch_bf16_resolve(g->bf16, B, g->d32, g->Lp, g->L, w.R, w.keys, w.fb_list, w.fb_count,
                                        g->stats, g->status, g->gemv_grid, st));
             kernels += 4;
         } else {
-            ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, g->R, B, nullptr, nullptr, g->keys, g->status,
+            ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
                                       g->gemv_grid, st));
-            if (g->profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+            if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         }
-        if (g->profiling) ACT_CK(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
-        ACT_CK(launch_update(g->d32, g->Lp, g->L, g->R, R16, g->Lb, B, g->keys, g->ax, k, P, g->atoms, g->coefs,
-                             g->energy, bf16 ? g->fb_count : nullptr, st));
+        if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
+        ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
+                             w.energy, bf16 ? w.fb_count : nullptr, st));
         ++kernels;
     }
     ge.kernels = kernels;
@@ -226,7 +242,7 @@ act_status get_graph(act_grid *g, int B, int P, act_search_mode mode, GraphEntry
     }
     GraphEntry ge;
     ACT_CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
-    act_status s = record_decompose(g, B, P, mode, ge);
+    act_status s = record_decompose(g, g->w, B, P, mode, ge, g->cap, g->profiling);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
     if (s != ACT_OK) {
@@ -346,8 +362,6 @@ act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid *
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&g->fb_count, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(g->fb_count, 0, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->stats, 3 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(g->stats, 0, 3 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&g->degenerate, sizeof(unsigned long long));
@@ -378,6 +392,7 @@ act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stre
     cudaStream_t st = (cudaStream_t)cuda_stream;
     ACT_CK(cudaStreamSynchronize(st));
     drop_graphs(g);
+    ++g->generation;  // ragged plans built on the old dictionary are stale
     free_dictionary(g);
     const size_t b32 = sizeof(float) * (size_t)g->K * g->Lp;
     cudaError_t e = cudaMalloc(&g->d32, b32);
@@ -439,21 +454,21 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
     act_status s = ensure_work(g, channels, n_atoms);
     if (s != ACT_OK) return s;
     bool host_seen = !is_device_ptr(signals);
-    ACT_CK(cudaMemcpyAsync(g->sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
+    ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     GraphEntry *ge = nullptr;
     s = get_graph(g, channels, n_atoms, mode, &ge);
     if (s != ACT_OK) return s;
     ACT_CK(cudaGraphLaunch(ge->exec, st));
     g->last = ge;
     const size_t BP = (size_t)channels * n_atoms;
-    if ((s = copy_out(atoms_out, g->atoms, sizeof(act_atom) * BP, st, &host_seen)) != ACT_OK) return s;
-    if ((s = copy_out(coeffs_out, g->coefs, sizeof(float) * BP, st, &host_seen)) != ACT_OK) return s;
-    if ((s = copy_out(energy_out, g->energy, sizeof(double) * (size_t)channels * (n_atoms + 1), st,
+    if ((s = copy_out(atoms_out, g->w.atoms, sizeof(act_atom) * BP, st, &host_seen)) != ACT_OK) return s;
+    if ((s = copy_out(coeffs_out, g->w.coefs, sizeof(float) * BP, st, &host_seen)) != ACT_OK) return s;
+    if ((s = copy_out(energy_out, g->w.energy, sizeof(double) * (size_t)channels * (n_atoms + 1), st,
                       &host_seen)) != ACT_OK)
         return s;
     if (residuals_out) {
         if (!is_device_ptr(residuals_out)) host_seen = true;
-        ACT_CK(cudaMemcpy2DAsync(residuals_out, sizeof(float) * g->L, g->R, sizeof(float) * g->Lp,
+        ACT_CK(cudaMemcpy2DAsync(residuals_out, sizeof(float) * g->L, g->w.R, sizeof(float) * g->Lp,
                                  sizeof(float) * g->L, channels, cudaMemcpyDefault, st));
     }
     if (host_seen) ACT_CK(cudaStreamSynchronize(st));
@@ -467,9 +482,9 @@ act_status act_project(act_grid *g, const float *signals, int32_t channels, floa
     cudaStream_t st = (cudaStream_t)cuda_stream;
     act_status s = ensure_work(g, channels, 1);
     if (s != ACT_OK) return s;
-    ACT_CK(cudaMemcpyAsync(g->sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
-    ACT_CK(launch_init(g->sig, channels, g->L, g->Lp, g->R, nullptr, g->Lb, nullptr, nullptr, 1, g->status, st));
-    ACT_CK(launch_project(g->d32, g->K, g->Lp, g->R, channels, scores, g->status, g->gemv_grid, st));
+    ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
+    ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, nullptr, g->Lb, nullptr, nullptr, 1, g->status, st));
+    ACT_CK(launch_project(g->d32, g->K, g->Lp, g->w.R, channels, scores, g->status, g->gemv_grid, st));
     return ACT_OK;
 }
 
@@ -505,8 +520,8 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
     const bool bf16 = g->bf16 != nullptr && channels <= 128;
     act_status s = ensure_work(g, channels, 1);
     if (s != ACT_OK) return s;
-    ACT_CK(cudaMemcpyAsync(g->sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
-    ACT_CK(launch_init(g->sig, channels, g->L, g->Lp, g->R, g->R16, g->Lb, g->keys, nullptr, 1, g->status, st));
+    ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
+    ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, g->w.R16, g->Lb, g->w.keys, nullptr, 1, g->status, st));
     cudaEvent_t e0, e1;
     ACT_CK(cudaEventCreate(&e0));
     ACT_CK(cudaEventCreate(&e1));
@@ -518,13 +533,13 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
             e = cudaEventRecord(e0, st);
             for (int r = 0; r < reps && e == cudaSuccess; ++r) {
                 if (use_bf16) {
-                    e = cudaMemsetAsync(g->fb_count, 0, 2 * sizeof(int), st);
-                    if (e == cudaSuccess) e = launch_bf16_gemm(g->bf16, channels, g->R16, g->status, st);
+                    e = cudaMemsetAsync(g->w.fb_count, 0, 2 * sizeof(int), st);
+                    if (e == cudaSuccess) e = launch_bf16_gemm(g->bf16, channels, g->w.R16, g->status, st);
                     if (e == cudaSuccess)
-                        e = launch_bf16_resolve(g->bf16, channels, g->d32, g->Lp, g->L, g->R, g->keys, g->fb_list,
-                                                g->fb_count, g->stats, g->status, g->gemv_grid, st);
+                        e = launch_bf16_resolve(g->bf16, channels, g->d32, g->Lp, g->L, g->w.R, g->w.keys, g->w.fb_list,
+                                                g->w.fb_count, g->stats, g->status, g->gemv_grid, st);
                 } else {
-                    e = launch_gemv_argmax(g->d32, g->K, g->Lp, g->R, channels, nullptr, nullptr, g->keys,
+                    e = launch_gemv_argmax(g->d32, g->K, g->Lp, g->w.R, channels, nullptr, nullptr, g->w.keys,
                                            g->status, g->gemv_grid, st);
                 }
             }
@@ -572,8 +587,8 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
         if (err == cudaSuccess) err = bf16_search_configure(g->bf16, best_bn, best_st);
     }
     // leave clean state: keys and counters zero, no stale graphs
-    if (err == cudaSuccess) err = cudaMemsetAsync(g->keys, 0, sizeof(unsigned long long) * (size_t)channels, st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(g->fb_count, 0, 2 * sizeof(int), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(g->w.keys, 0, sizeof(unsigned long long) * (size_t)channels, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(g->w.fb_count, 0, 2 * sizeof(int), st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -582,6 +597,7 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
         return ACT_ERR_CUDA;
     }
     drop_graphs(g);
+    ++g->generation;
     if (best_ms) *best_ms = effective_search(g) == ACT_SEARCH_BF16 && bf16 ? best16 : best32;
     return ACT_OK;
 }
@@ -613,6 +629,7 @@ act_status act_set_tuning(act_grid *g, int32_t gemv_ctas_in, int32_t bf16_tile_a
         }
     }
     drop_graphs(g);
+    ++g->generation;
     return ACT_OK;
 }
 
@@ -655,15 +672,204 @@ act_status act_bf16_stats(act_grid *g, int64_t *resolved, int64_t *tiles_rescann
     return ACT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Uneven batches
+// ---------------------------------------------------------------------------
+struct act_ragged_plan {
+    struct Group {
+        act_grid *g = nullptr;
+        uint64_t generation = 0;
+        act_search_mode mode = ACT_SEARCH_FP32;
+        std::vector<int> chan;       // caller channel ids of this group
+        int64_t *src_off = nullptr;  // [B] sample offsets in the concatenated signals
+        int *d_chan = nullptr;       // [B]
+        WorkBuffers w;
+        cudaStream_t st = nullptr;
+        cudaEvent_t join = nullptr;
+    };
+    int device = 0;
+    int channels = 0;
+    int P = 0;
+    int64_t total = 0;
+    std::vector<Group> groups;
+    float *d_sig = nullptr;       // [total] staged concatenated signals
+    float *d_resid = nullptr;     // [total] concatenated residuals
+    act_atom *d_atoms = nullptr;  // [channels][P]
+    float *d_coefs = nullptr;     // [channels][P]
+    double *d_energy = nullptr;   // [channels][P+1]
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+};
+
+static void ragged_free(act_ragged_plan *p) {
+    if (!p) return;
+    DeviceGuard dg(p->device);
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto &gr : p->groups) {
+        free_dev(gr.src_off);
+        free_dev(gr.d_chan);
+        free_work(gr.w);
+        if (gr.st) cudaStreamDestroy(gr.st);
+        if (gr.join) cudaEventDestroy(gr.join);
+    }
+    free_dev(p->d_sig);
+    free_dev(p->d_resid);
+    free_dev(p->d_atoms);
+    free_dev(p->d_coefs);
+    free_dev(p->d_energy);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    delete p;
+}
+
+static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32_t n_grids, const int64_t *offsets) {
+    // group channels by window length
+    std::map<int, int> group_of_len;
+    for (int i = 0; i < n_grids; ++i) {
+        act_grid *g = grids[i];
+        if (!g || g->built < 0) return ACT_ERR_NOT_BUILT;
+        if (g->device != p->device) return ACT_ERR_INVALID_ARG;
+        if (group_of_len.count(g->L)) return ACT_ERR_INVALID_ARG;  // one grid per window length
+        group_of_len[g->L] = (int)p->groups.size();
+        act_ragged_plan::Group gr;
+        gr.g = g;
+        gr.generation = g->generation;
+        p->groups.push_back(gr);
+    }
+    for (int c = 0; c < p->channels; ++c) {
+        const int64_t len = offsets[c + 1] - offsets[c];
+        auto it = group_of_len.find((int)len);
+        if (len < 1 || it == group_of_len.end()) return ACT_ERR_INVALID_ARG;
+        p->groups[it->second].chan.push_back(c);
+    }
+    p->total = offsets[p->channels];
+    ACT_CK(cudaMalloc(&p->d_sig, sizeof(float) * (size_t)p->total));
+    ACT_CK(cudaMalloc(&p->d_resid, sizeof(float) * (size_t)p->total));
+    ACT_CK(cudaMalloc(&p->d_atoms, sizeof(act_atom) * (size_t)p->channels * p->P));
+    ACT_CK(cudaMalloc(&p->d_coefs, sizeof(float) * (size_t)p->channels * p->P));
+    ACT_CK(cudaMalloc(&p->d_energy, sizeof(double) * (size_t)p->channels * (p->P + 1)));
+    ACT_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    ACT_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    for (auto &gr : p->groups) {
+        const int B = (int)gr.chan.size();
+        if (B == 0) continue;
+        act_grid *g = gr.g;
+        gr.mode = effective_search(g);
+        if (gr.mode == ACT_SEARCH_BF16 && (!g->bf16 || B > 128)) gr.mode = ACT_SEARCH_FP32;
+        act_status s = alloc_work(g, gr.w, B, p->P);
+        if (s != ACT_OK) return s;
+        std::vector<int64_t> off(B);
+        for (int i = 0; i < B; ++i) off[i] = offsets[gr.chan[i]];
+        ACT_CK(cudaMalloc(&gr.src_off, sizeof(int64_t) * B));
+        ACT_CK(cudaMemcpy(gr.src_off, off.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice));
+        ACT_CK(cudaMalloc(&gr.d_chan, sizeof(int) * B));
+        ACT_CK(cudaMemcpy(gr.d_chan, gr.chan.data(), sizeof(int) * B, cudaMemcpyHostToDevice));
+        ACT_CK(cudaStreamCreateWithFlags(&gr.st, cudaStreamNonBlocking));
+        ACT_CK(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
+    }
+    // one graph: fork, then per length group gather -> MP loop -> scatter on
+    // its own branch, then join
+    ACT_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    act_status s = ACT_OK;
+    cudaError_t e = cudaEventRecord(p->fork, p->cap);
+    for (auto &gr : p->groups) {
+        const int B = (int)gr.chan.size();
+        if (B == 0 || e != cudaSuccess || s != ACT_OK) continue;
+        act_grid *g = gr.g;
+        e = cudaStreamWaitEvent(gr.st, p->fork, 0);
+        if (e == cudaSuccess) e = launch_ragged_gather(p->d_sig, gr.src_off, B, g->L, gr.w.sig, gr.st);
+        GraphEntry ge;
+        if (e == cudaSuccess) s = record_decompose(g, gr.w, B, p->P, gr.mode, ge, gr.st, false);
+        p->kernels += ge.kernels + 2;
+        if (e == cudaSuccess && s == ACT_OK)
+            e = launch_ragged_scatter(B, p->P, g->L, g->Lp, gr.d_chan, gr.src_off, gr.w.atoms, gr.w.coefs,
+                                      gr.w.energy, gr.w.R, p->d_atoms, p->d_coefs, p->d_energy, p->d_resid, gr.st);
+        if (e == cudaSuccess && s == ACT_OK) e = cudaEventRecord(gr.join, gr.st);
+        if (e == cudaSuccess && s == ACT_OK) e = cudaStreamWaitEvent(p->cap, gr.join, 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+    if (s != ACT_OK || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (s != ACT_OK) return s;
+        note_error("ragged capture", e != cudaSuccess ? e : e2);
+        return ACT_ERR_CUDA;
+    }
+    p->graph = graph;
+    ACT_CK(cudaGraphInstantiate(&p->exec, graph, 0));
+    return ACT_OK;
+}
+
+act_status act_ragged_plan_create(act_grid *const *grids, int32_t n_grids, const int64_t *offsets, int32_t channels,
+                                  int32_t n_atoms, act_ragged_plan **out) {
+    if (!grids || n_grids < 1 || !offsets || channels < 1 || n_atoms < 1 || !out) return ACT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (offsets[0] != 0) return ACT_ERR_INVALID_ARG;
+    for (int c = 0; c < channels; ++c)
+        if (offsets[c + 1] <= offsets[c]) return ACT_ERR_INVALID_ARG;
+    if (!grids[0]) return ACT_ERR_INVALID_ARG;
+    DeviceGuard dg(grids[0]->device);
+    act_ragged_plan *p = new (std::nothrow) act_ragged_plan();
+    if (!p) return ACT_ERR_OOM;
+    p->device = grids[0]->device;
+    p->channels = channels;
+    p->P = n_atoms;
+    act_status s = ragged_build(p, grids, n_grids, offsets);
+    if (s != ACT_OK) {
+        ragged_free(p);
+        return s;
+    }
+    *out = p;
+    return ACT_OK;
+}
+
+act_status act_ragged_decompose(act_ragged_plan *p, const float *signals, act_atom *atoms_out, float *coeffs_out,
+                                float *residuals_out, double *energy_out, void *cuda_stream) {
+    if (!p || !signals) return ACT_ERR_INVALID_ARG;
+    for (auto &gr : p->groups)
+        if (gr.g->generation != gr.generation || gr.g->built < 0) return ACT_ERR_NOT_BUILT;  // stale plan
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    bool host_seen = !is_device_ptr(signals);
+    ACT_CK(cudaMemcpyAsync(p->d_sig, signals, sizeof(float) * (size_t)p->total, cudaMemcpyDefault, st));
+    ACT_CK(cudaGraphLaunch(p->exec, st));
+    const size_t BP = (size_t)p->channels * p->P;
+    act_status s;
+    if ((s = copy_out(atoms_out, p->d_atoms, sizeof(act_atom) * BP, st, &host_seen)) != ACT_OK) return s;
+    if ((s = copy_out(coeffs_out, p->d_coefs, sizeof(float) * BP, st, &host_seen)) != ACT_OK) return s;
+    if ((s = copy_out(energy_out, p->d_energy, sizeof(double) * (size_t)p->channels * (p->P + 1), st,
+                      &host_seen)) != ACT_OK)
+        return s;
+    if ((s = copy_out(residuals_out, p->d_resid, sizeof(float) * (size_t)p->total, st, &host_seen)) != ACT_OK)
+        return s;
+    if (host_seen) ACT_CK(cudaStreamSynchronize(st));
+    return ACT_OK;
+}
+
+act_status act_ragged_plan_info(const act_ragged_plan *p, int32_t *groups, int32_t *kernels) {
+    if (!p) return ACT_ERR_INVALID_ARG;
+    int n = 0;
+    for (auto &gr : p->groups) n += gr.chan.empty() ? 0 : 1;
+    if (groups) *groups = n;
+    if (kernels) *kernels = p->kernels;
+    return ACT_OK;
+}
+
+void act_ragged_plan_destroy(act_ragged_plan *p) { ragged_free(p); }
+
 void act_destroy(act_grid *g) {
     if (!g) return;
     DeviceGuard dg(g->device);
     cudaDeviceSynchronize();
     drop_graphs(g);
     free_dictionary(g);
-    free_work(g);
+    free_work(g->w);
     free_dev(g->status);
-    free_dev(g->fb_count);
     free_dev(g->stats);
     free_dev(g->degenerate);
     free_dev(g->eps_bits);

@@ -453,12 +453,31 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, ui
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Dynamic shared memory the GEMM may use: the opt-in limit minus its static
+// shared memory (barriers), less 1 KB of slack for 1024-byte alignment.
+constexpr int kStaticSmemReserve = 512;
+constexpr int kSmemBudget = kMaxDynSmem - kStaticSmemReserve - 1024;
+
 // Largest number of stages that fits the shared memory for a tile width.
 int max_stages(int bn, int nkc, bool a_stream) {
     const int chunk = bn * kBK * 2;
-    int st = a_stream ? (kMaxDynSmem - 1024) / (chunk + kAChunkBytes)
-                      : (kMaxDynSmem - 1024 - nkc * kAChunkBytes) / chunk;
+    int st = a_stream ? kSmemBudget / (chunk + kAChunkBytes) : (kSmemBudget - nkc * kAChunkBytes) / chunk;
     return st > kMaxStages ? kMaxStages : st;
+}
+
+// Raises the kernel's dynamic shared-memory limit to everything the device
+// allows next to its static shared memory (the limit is per kernel function
+// and shared by every grid in the process).
+cudaError_t allow_max_smem(const void *func, size_t needed) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    const int limit = optin - (int)fa.sharedSizeBytes;
+    if ((size_t)limit < needed) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
 }
 
 }  // namespace
@@ -489,9 +508,8 @@ cudaError_t bf16_search_configure(Bf16Search *s, int bn, int stages) {
     const size_t chunk = (size_t)bn * kBK * 2;
     const size_t smem = s->a_stream ? 1024 + (size_t)stages * (chunk + kAChunkBytes)
                                     : 1024 + (size_t)s->nkc * kAChunkBytes + (size_t)stages * chunk;
-    cudaError_t e =
-        bn == 256 ? cudaFuncSetAttribute(k_gemm_tilemax<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                  : cudaFuncSetAttribute(k_gemm_tilemax<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = bn == 256 ? allow_max_smem((const void *)k_gemm_tilemax<256>, smem)
+                              : allow_max_smem((const void *)k_gemm_tilemax<128>, smem);
     if (e != cudaSuccess) return e;
     s->bn = bn;
     s->stages = stages;

@@ -82,6 +82,11 @@ cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, in
 cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
                           float *coefs, double *energy, int *fb_count, cudaStream_t st);
+cudaError_t launch_ragged_gather(const float *src, const int64_t *src_off, int B, int L, float *dst, cudaStream_t st);
+cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, const int64_t *dst_off,
+                                  const act_atom *atoms, const float *coefs, const double *energy, const float *R,
+                                  act_atom *out_atoms, float *out_coefs, double *out_energy, float *out_resid,
+                                  cudaStream_t st);
 int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
 int gemv_max_ctas_per_sm(int Lp);
 

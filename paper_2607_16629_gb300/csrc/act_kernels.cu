@@ -452,3 +452,52 @@ cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat
 }
 
 }  // namespace act
+
+namespace act {
+
+// ---------------------------------------------------------------------------
+// Uneven batches: one length group's signals are gathered from the
+// concatenated input, and its outputs scattered back to the callers' channel
+// order (one block per channel of the group).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ragged_gather(const float *__restrict__ src,
+                                                       const int64_t *__restrict__ src_off, int L,
+                                                       float *__restrict__ dst) {
+    const int b = blockIdx.x;
+    const float *s = src + src_off[b];
+    for (int n = threadIdx.x; n < L; n += blockDim.x) dst[(int64_t)b * L + n] = s[n];
+}
+
+__global__ void __launch_bounds__(256) k_ragged_scatter(int P, int L, int Lp, const int *__restrict__ chan,
+                                                        const int64_t *__restrict__ dst_off,
+                                                        const act_atom *__restrict__ atoms,
+                                                        const float *__restrict__ coefs,
+                                                        const double *__restrict__ energy,
+                                                        const float *__restrict__ R, act_atom *__restrict__ out_atoms,
+                                                        float *__restrict__ out_coefs, double *__restrict__ out_energy,
+                                                        float *__restrict__ out_resid) {
+    const int b = blockIdx.x;
+    const int64_t c = chan[b];
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        out_atoms[c * P + k] = atoms[(int64_t)b * P + k];
+        out_coefs[c * P + k] = coefs[(int64_t)b * P + k];
+    }
+    for (int k = threadIdx.x; k <= P; k += blockDim.x) out_energy[c * (P + 1) + k] = energy[(int64_t)b * (P + 1) + k];
+    for (int n = threadIdx.x; n < L; n += blockDim.x) out_resid[dst_off[b] + n] = R[(int64_t)b * Lp + n];
+}
+
+cudaError_t launch_ragged_gather(const float *src, const int64_t *src_off, int B, int L, float *dst, cudaStream_t st) {
+    k_ragged_gather<<<B, 256, 0, st>>>(src, src_off, L, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, const int64_t *dst_off,
+                                  const act_atom *atoms, const float *coefs, const double *energy, const float *R,
+                                  act_atom *out_atoms, float *out_coefs, double *out_energy, float *out_resid,
+                                  cudaStream_t st) {
+    k_ragged_scatter<<<B, 256, 0, st>>>(P, L, Lp, chan, dst_off, atoms, coefs, energy, R, out_atoms, out_coefs,
+                                        out_energy, out_resid);
+    return cudaGetLastError();
+}
+
+}  // namespace act

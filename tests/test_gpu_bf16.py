@@ -220,3 +220,17 @@ def test_autotune_keeps_results():
             act.act_set_tuning(h, 0, 64, 0)
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
+
+
+def test_two_bf16_grids_with_different_windows_coexist():
+    """Two BF16 grids with different shared-memory configurations (resident
+    and streamed residual) can be used alternately."""
+    ga = synth.scaled_grid(synth.grid_emg(256), tc_count=16, fc_count=8, logdt_count=4, c_count=8)
+    gb = synth.scaled_grid(synth.grid_emg(2048), tc_count=16, fc_count=8, logdt_count=4, c_count=8)
+    with Bf16Grid(ga) as ha, Bf16Grid(gb) as hb:
+        for h, g, seed in ((ha, ga, 0), (hb, gb, 1), (ha, ga, 2)):
+            sig = np.stack([synth.emg_like_signal(seed * 10 + b, g.n_samples)[0] for b in range(5)])
+            x = run(h, sig, 3, act.ACT_SEARCH_BF16)
+            y = run(h, sig, 3, act.ACT_SEARCH_FP32)
+            for u, v in zip(x, y):
+                assert np.array_equal(u, v)
