@@ -68,6 +68,13 @@ def _load():
         lib.act_oracle_mp_grid.argtypes = [_dp, _i64p, ctypes.c_int, ctypes.c_double, _dp,
                                            ctypes.c_int, _i64p, _dp, _dp, _dp, _dp]
         lib.act_oracle_mp_grid.restype = ctypes.c_int
+        lib.act_oracle_score_grad.argtypes = [_dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+        lib.act_oracle_score_grad.restype = ctypes.c_int
+        lib.act_oracle_refine.argtypes = [_dp, ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
+        lib.act_oracle_refine.restype = ctypes.c_double
+        lib.act_oracle_mp_refine.argtypes = [_dp, _i64p, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int,
+                                             ctypes.c_int, _i64p, _dp, _dp, _dp, _dp]
+        lib.act_oracle_mp_refine.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -190,3 +197,50 @@ def mp_grid(grid, s: np.ndarray, P: int):
     if rc != 0:
         raise MemoryError("oracle MP allocation failed")
     return idx, coef, r, en, gap
+
+
+def score_grad(theta, fs, r):
+    """(s, ds/dtheta[4]) of the unit-norm real chirplet at continuous theta."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    sc = ctypes.c_double()
+    g = np.empty(4)
+    _load().act_oracle_score_grad(_d(th), float(fs), int(r.shape[0]), _d(r), ctypes.byref(sc), _d(g))
+    return sc.value, g
+
+
+def refine(theta, fs, r, steps, w, lo, hi):
+    """BFGS refinement of theta from the grid start (returns (theta*, J*))."""
+    th = np.array(theta, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    J = _load().act_oracle_refine(_d(th), float(fs), int(r.shape[0]), _d(r), int(steps),
+                                  _d(np.ascontiguousarray(w, dtype=np.float64)),
+                                  _d(np.ascontiguousarray(lo, dtype=np.float64)),
+                                  _d(np.ascontiguousarray(hi, dtype=np.float64)))
+    return th, J
+
+
+def refine_box(grid):
+    """(scales, lo, hi) the refinement uses for a grid: the grid steps and
+    the grid box widened by one step on each side."""
+    axes = [grid.tc, grid.fc, grid.logdt, grid.c]
+    w = np.array([a.step for a in axes])
+    lo = np.array([a.lo - a.step for a in axes])
+    hi = np.array([a.lo + a.count * a.step for a in axes])
+    return w, lo, hi
+
+
+def mp_refine(grid, s, P, steps):
+    """MP with off-grid refinement -> (idx[P], coef[P], theta[P][4], residual, energy[P+1])."""
+    axes, counts = _grid_arrays(grid)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    idx = np.empty(P, dtype=np.int64)
+    coef = np.empty(P)
+    th = np.empty((P, 4))
+    r = np.empty(grid.n_samples)
+    en = np.empty(P + 1)
+    rc = _load().act_oracle_mp_refine(_d(axes), _i(counts), int(grid.n_samples), float(grid.fs), _d(s), int(P),
+                                      int(steps), _i(idx), _d(coef), _d(th), _d(r), _d(en))
+    if rc != 0:
+        raise MemoryError("oracle MP allocation failed")
+    return idx, coef, th, r, en

@@ -15,7 +15,12 @@
  *     ranges of Table 2 are half-open (start, stop, step) sequences.
  *   - Eq. (4) and Fig. 1: r_0 = s; at every order k pick
  *     i* = argmax_i |<g_i, r_k>|, take c_k = <g*, r_k>, set
- *     r_{k+1} = r_k - c_k g*  (BFGS refinement is not part of this path).
+ *     r_{k+1} = r_k - c_k g*.
+ *   - Fig. 1's refinement step theta* = argmax_theta |<g(theta), r_k>| by
+ *     BFGS from the grid winner (Sec. III-A): the analytic gradient of the
+ *     score and a plain BFGS with Armijo backtracking in grid-step-scaled
+ *     coordinates (act_oracle_score_grad, act_oracle_refine,
+ *     act_oracle_mp_refine).
  *   - Eq. (5): the normalised residue |r_k|^2 / |s|^2 is derived from the
  *     recorded residual energies.
  *
@@ -274,6 +279,201 @@ int act_oracle_mp_grid(const double *axes, const int64_t *counts, int n_samples,
         act_oracle_atom_params(axes, counts, best, &tc, &fc, &ld, &c);
         act_oracle_atom(tc, fc, ld, c, fs, n_samples, g);
         idx[k] = best;
+        coef[k] = mp_update(g, r, n_samples);
+        if (energy) energy[k + 1] = dot(r, r, n_samples);
+    }
+    free(scores);
+    free(g);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Off-grid refinement (Fig. 1: theta* = argmax_theta |<g(theta), r_k>|,  */
+/* started from the grid winner)                                           */
+/* ---------------------------------------------------------------------- */
+
+/* s(theta) = <r, g(theta)> for the unit-norm real atom of Eq. (1) at
+ * continuous theta = (tc, fc, logDt, c), and its gradient.  With
+ * u = E cos(phi), E = exp(-x^2/2), x = tau/Dt, phi = 2 pi (c tau^2 + fc tau),
+ * tau = (n - tc)/fs and g = u/|u|:
+ *   ds/dtheta_i = <r, du_i>/|u| - s <u, du_i>/|u|^2, where
+ *   du/dtc    = (E x/Dt cos(phi) + E sin(phi) 2 pi (2 c tau + fc)) / fs,
+ *   du/dfc    = -E sin(phi) 2 pi tau,
+ *   du/dlogDt = E x^2 cos(phi),
+ *   du/dc     = -E sin(phi) 2 pi tau^2.
+ * Returns 1 for a degenerate atom (score and gradient 0). grad may be NULL. */
+int act_oracle_score_grad(const double *theta, double fs, int n_samples, const double *r, double *score,
+                          double *grad) {
+    const double tc = theta[0], fc = theta[1], ld = theta[2], c = theta[3];
+    const double dt = exp(ld);
+    double ru = 0.0, uu = 0.0, rd[4] = {0, 0, 0, 0}, ud[4] = {0, 0, 0, 0};
+    for (int n = 0; n < n_samples; ++n) {
+        const double tau = ((double)n - tc) / fs;
+        const double x = tau / dt;
+        const double E = exp(-0.5 * x * x);
+        const double phi = 2.0 * ORACLE_PI * (c * tau * tau + fc * tau);
+        const double C = cos(phi), S = sin(phi);
+        const double u = E * C;
+        double du[4];
+        du[0] = (E * x / dt * C + E * S * 2.0 * ORACLE_PI * (2.0 * c * tau + fc)) / fs;
+        du[1] = -E * S * 2.0 * ORACLE_PI * tau;
+        du[2] = E * x * x * C;
+        du[3] = -E * S * 2.0 * ORACLE_PI * tau * tau;
+        ru += r[n] * u;
+        uu += u * u;
+        for (int i = 0; i < 4; ++i) {
+            rd[i] += r[n] * du[i];
+            ud[i] += u * du[i];
+        }
+    }
+    if (!(uu >= 1e-300) || !isfinite(uu)) {
+        *score = 0.0;
+        if (grad)
+            for (int i = 0; i < 4; ++i) grad[i] = 0.0;
+        return 1;
+    }
+    const double nu = sqrt(uu);
+    const double s = ru / nu;
+    *score = s;
+    if (grad)
+        for (int i = 0; i < 4; ++i) grad[i] = rd[i] / nu - s * ud[i] / uu;
+    return 0;
+}
+
+/* Refinement by BFGS on f(z) = -|s(theta)|, theta = w (.) z (coordinates
+ * scaled by w, the grid steps), from theta (updated in place), `steps`
+ * iterations of:
+ *   p = -H grad f              (H: inverse-Hessian estimate, starts at I;
+ *                               reset to I when p is not a descent direction)
+ *   alpha = min(1, 1/(2|p|))   (a first step of at most half a grid step)
+ *   halve alpha (up to 20 times) until the Armijo condition
+ *     f(z + alpha p) <= f(z) + 1e-4 alpha <grad f, p> holds
+ *   z' = clamp(z + alpha p);  s = z' - z;  y = grad f(z') - grad f(z)
+ *   if <y, s> > 0:  H = (I - s y^T / <y,s>) H (I - y s^T / <y,s>) + s s^T / <y,s>
+ * stopping early when no step is accepted.  lo/hi[4] clamp theta.
+ * Returns the final |s|. */
+static void scaled_eval(const double *z, const double *w, double fs, int n, const double *r, double *f, double *gz,
+                        double *th_out) {
+    double th[4], s, g[4];
+    for (int i = 0; i < 4; ++i) th[i] = z[i] * w[i];
+    act_oracle_score_grad(th, fs, n, r, &s, g);
+    const double sg = s < 0.0 ? -1.0 : 1.0;
+    *f = -fabs(s);
+    for (int i = 0; i < 4; ++i) gz[i] = -sg * g[i] * w[i];
+    if (th_out)
+        for (int i = 0; i < 4; ++i) th_out[i] = th[i];
+}
+
+double act_oracle_refine(double *theta, double fs, int n_samples, const double *r, int steps, const double *w,
+                         const double *lo, const double *hi) {
+    double z[4], gz[4], f, H[16];
+    for (int i = 0; i < 4; ++i) z[i] = theta[i] / w[i];
+    scaled_eval(z, w, fs, n_samples, r, &f, gz, NULL);
+    for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    for (int it = 0; it < steps; ++it) {
+        double p[4], gp = 0.0, pn = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            p[i] = 0.0;
+            for (int j = 0; j < 4; ++j) p[i] -= H[4 * i + j] * gz[j];
+            gp += gz[i] * p[i];
+        }
+        if (!(gp < 0.0)) {
+            for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
+            gp = 0.0;
+            for (int i = 0; i < 4; ++i) {
+                p[i] = -gz[i];
+                gp += gz[i] * p[i];
+            }
+            if (!(gp < 0.0)) break;  /* zero gradient */
+        }
+        for (int i = 0; i < 4; ++i) pn += p[i] * p[i];
+        pn = sqrt(pn);
+        double alpha = pn > 0.5 ? 0.5 / pn : 1.0;
+        double z2[4], f2 = 0.0, g2[4];
+        int ok = 0;
+        for (int ls = 0; ls < 20; ++ls) {
+            for (int i = 0; i < 4; ++i) {
+                double v = (z[i] + alpha * p[i]) * w[i];
+                if (v < lo[i]) v = lo[i];
+                if (v > hi[i]) v = hi[i];
+                z2[i] = v / w[i];
+            }
+            scaled_eval(z2, w, fs, n_samples, r, &f2, g2, NULL);
+            if (f2 <= f + 1e-4 * alpha * gp) {
+                ok = 1;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!ok) break;
+        double sv[4], yv[4], ys = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            sv[i] = z2[i] - z[i];
+            yv[i] = g2[i] - gz[i];
+            ys += yv[i] * sv[i];
+        }
+        if (ys > 1e-300) {
+            /* H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T */
+            const double rho = 1.0 / ys;
+            double A[16], T[16];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) A[4 * i + j] = (i == j ? 1.0 : 0.0) - rho * sv[i] * yv[j];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 4; ++k) acc += A[4 * i + k] * H[4 * k + j];
+                    T[4 * i + j] = acc;
+                }
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 4; ++k) acc += T[4 * i + k] * A[4 * j + k];
+                    H[4 * i + j] = acc + rho * sv[i] * sv[j];
+                }
+        }
+        for (int i = 0; i < 4; ++i) {
+            z[i] = z2[i];
+            gz[i] = g2[i];
+        }
+        f = f2;
+    }
+    for (int i = 0; i < 4; ++i) theta[i] = z[i] * w[i];
+    return -f;
+}
+
+/* MP over a grid where every order's grid winner is refined off the grid
+ * (act_oracle_refine with the grid steps as scales and the grid box
+ * widened by one step) and the refined atom is subtracted.  Outputs as
+ * act_oracle_mp_grid plus theta_out[P][4] (refined parameters). */
+int act_oracle_mp_refine(const double *axes, const int64_t *counts, int n_samples, double fs, const double *s,
+                         int P, int steps, int64_t *idx, double *coef, double *theta_out, double *r,
+                         double *energy) {
+    int64_t K = grid_size(counts);
+    double *scores = (double *)malloc(sizeof(double) * (size_t)K);
+    double *g = (double *)malloc(sizeof(double) * (size_t)n_samples);
+    if (!scores || !g) {
+        free(scores);
+        free(g);
+        return -1;
+    }
+    double w[4], lo[4], hi[4];
+    for (int i = 0; i < 4; ++i) {
+        w[i] = axes[2 * i + 1];
+        lo[i] = axes[2 * i] - w[i];
+        hi[i] = axes[2 * i] + (double)counts[i] * w[i];
+    }
+    memcpy(r, s, sizeof(double) * (size_t)n_samples);
+    if (energy) energy[0] = dot(r, r, n_samples);
+    for (int k = 0; k < P; ++k) {
+        int64_t best, second;
+        act_oracle_scores_grid(axes, counts, n_samples, fs, r, scores);
+        act_oracle_select(scores, K, &best, &second);
+        double th[4];
+        act_oracle_atom_params(axes, counts, best, &th[0], &th[1], &th[2], &th[3]);
+        act_oracle_refine(th, fs, n_samples, r, steps, w, lo, hi);
+        act_oracle_atom(th[0], th[1], th[2], th[3], fs, n_samples, g);
+        idx[k] = best;
+        for (int i = 0; i < 4; ++i) theta_out[4 * k + i] = th[i];
         coef[k] = mp_update(g, r, n_samples);
         if (energy) energy[k + 1] = dot(r, r, n_samples);
     }
