@@ -183,6 +183,32 @@ ACT_API act_status act_dictionary_rows(act_grid *grid, int64_t first, int64_t co
  * ACT_ERR_DEVICE_TIMEOUT), then clears it; ACT_OK otherwise. */
 ACT_API act_status act_grid_status(act_grid *grid, void *cuda_stream);
 
+/* Off-grid refinement (Fig. 1: theta* = argmax_theta |<g(theta), r_k>|,
+ * started from the grid winner; the paper runs BFGS on the CPU for it).
+ * With steps > 0, every order's grid selection is followed on the GPU by
+ * `steps` BFGS iterations per channel on -|<g(theta), r_k>| in coordinates
+ * scaled by the grid steps (first step at most half a grid step, Armijo
+ * backtracking, parameters kept inside the grid box widened by one step),
+ * and the refined atom g(theta*), generated on the fly and unit-normalised,
+ * is the one subtracted.  The act_atom records then hold theta* and the grid
+ * winner's flat index.  0 (the default) keeps the grid-only search.
+ * Changing the setting makes ragged plans built on this grid stale. */
+ACT_API act_status act_set_refinement(act_grid *grid, int32_t steps);
+
+/* Score and adjoint of continuous-parameter chirplets: for each channel b,
+ * s_b = <r_b, g(theta_b)> with g the unit-norm real atom of Eq. (1), its
+ * gradient ds_b/dtheta_b (tc, fc, logDt, c), and ds_b/dr_b = g(theta_b).
+ *   theta      device, [channels][4] float64 (tc in samples, fc Hz, logDt,
+ *              c Hz/s);
+ *   residuals  device, [channels][n_samples] float32;
+ *   score      device, [channels] float32;
+ *   grad_theta device, [channels][4] float64, may be NULL;
+ *   atoms      device, [channels][n_samples] float32 (g(theta_b)), may be NULL.
+ * n_samples 1..2048.  Enqueued on cuda_stream. */
+ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double *theta,
+                                      const float *residuals, int32_t channels, float *score,
+                                      double *grad_theta, float *atoms, void *cuda_stream);
+
 /* Autotuner: times one search order of every candidate launch configuration
  * on this grid's dictionary with the caller's `channels` signals
  * [channels][n_samples] (device or host memory) as residuals, keeps the

@@ -224,10 +224,14 @@ def refine_box(grid):
     """(scales, lo, hi) the refinement uses for a grid: the grid steps and
     the grid box widened by one step on each side."""
     axes = [grid.tc, grid.fc, grid.logdt, grid.c]
-    w = np.array([a.step for a in axes])
-    lo = np.array([a.lo - a.step for a in axes])
-    hi = np.array([a.lo + a.count * a.step for a in axes])
-    return w, lo, hi
+    w, lo, hi = [], [], []
+    for a in axes:
+        st = abs(a.step)
+        first, last = a.lo, a.lo + (a.count - 1) * a.step
+        w.append(st if st > 0 else 1.0)
+        lo.append(min(first, last) - st if st > 0 else first)
+        hi.append(max(first, last) + st if st > 0 else first)
+    return np.array(w), np.array(lo), np.array(hi)
 
 
 def mp_refine(grid, s, P, steps):

@@ -456,11 +456,15 @@ int act_oracle_mp_refine(const double *axes, const int64_t *counts, int n_sample
         free(g);
         return -1;
     }
+    /* scales: the grid steps; box: the grid range widened by one step (an
+     * axis with a zero step is held fixed) */
     double w[4], lo[4], hi[4];
     for (int i = 0; i < 4; ++i) {
-        w[i] = axes[2 * i + 1];
-        lo[i] = axes[2 * i] - w[i];
-        hi[i] = axes[2 * i] + (double)counts[i] * w[i];
+        const double st = fabs(axes[2 * i + 1]);
+        const double first = axes[2 * i], last = axes[2 * i] + (double)(counts[i] - 1) * axes[2 * i + 1];
+        w[i] = st > 0.0 ? st : 1.0;
+        lo[i] = st > 0.0 ? fmin(first, last) - st : first;
+        hi[i] = st > 0.0 ? fmax(first, last) + st : first;
     }
     memcpy(r, s, sizeof(double) * (size_t)n_samples);
     if (energy) energy[0] = dot(r, r, n_samples);

@@ -35,6 +35,7 @@ EXPORTS = (
     "act_dictionary_rows", "act_grid_status", "act_set_profiling", "act_profile_read",
     "act_bf16_stats", "act_destroy", "act_search_noalloc", "act_autotune", "act_get_tuning", "act_set_tuning",
     "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
+    "act_set_refinement", "act_chirplet_score",
 )
 
 
@@ -110,6 +111,8 @@ def load_library(path: str = LIB_PATH):
         lib.act_ragged_plan_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         lib.act_ragged_plan_destroy.argtypes = [_P]
         lib.act_ragged_plan_destroy.restype = None
+        lib.act_set_refinement.argtypes = [_P, ctypes.c_int32]
+        lib.act_chirplet_score.argtypes = [ctypes.c_int32, ctypes.c_double, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -313,6 +316,17 @@ def act_ragged_plan_info(plan: int):
 def act_ragged_plan_destroy(plan: int) -> None:
     if plan:
         load_library().act_ragged_plan_destroy(plan)
+
+
+def act_set_refinement(grid: int, steps: int) -> None:
+    _check(load_library().act_set_refinement(grid, int(steps)), "act_set_refinement")
+
+
+def act_chirplet_score(n_samples: int, fs: float, theta, residuals, channels: int, score, grad_theta=None,
+                       atoms=None, stream=None) -> None:
+    _check(load_library().act_chirplet_score(int(n_samples), float(fs), _ptr(theta), _ptr(residuals), int(channels),
+                                             _ptr(score), _ptr(grad_theta), _ptr(atoms), _stream(stream)),
+           "act_chirplet_score")
 
 
 def act_destroy(grid: int) -> None:

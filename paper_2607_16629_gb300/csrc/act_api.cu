@@ -94,6 +94,7 @@ struct WorkBuffers {
     double *energy = nullptr;         // [B][P+1]
     int *fb_list = nullptr;           // [B] channels queued for the FP32 full search
     int *fb_count = nullptr;          // [2] full-search and rescan queue lengths
+    double *theta = nullptr;          // [B][4] refined parameters of the current order
 };
 
 struct act_grid {
@@ -114,9 +115,10 @@ struct act_grid {
     long long *stats = nullptr;
     Bf16Search *bf16 = nullptr;
     int gemv_grid = 0;
+    int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
     cudaStream_t cap = nullptr;
     bool profiling = false;
-    std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
+    std::map<std::tuple<int, int, int, int, int>, GraphEntry> graphs;
     GraphEntry *last = nullptr;
     uint64_t generation = 0;  // bumped whenever the dictionary or the launch configuration changes
 };
@@ -143,6 +145,7 @@ void free_work(WorkBuffers &w) {
     free_dev(w.energy);
     free_dev(w.fb_list);
     free_dev(w.fb_count);
+    free_dev(w.theta);
     w.cap_B = w.cap_P = 0;
 }
 
@@ -171,6 +174,7 @@ act_status alloc_work(const act_grid *g, WorkBuffers &w, int B, int P) {
     ACT_CK(cudaMalloc(&w.fb_list, sizeof(int) * (size_t)B));
     ACT_CK(cudaMalloc(&w.fb_count, 2 * sizeof(int)));
     ACT_CK(cudaMemset(w.fb_count, 0, 2 * sizeof(int)));
+    ACT_CK(cudaMalloc(&w.theta, sizeof(double) * 4 * (size_t)B));
     w.cap_B = B;
     w.cap_P = P;
     return ACT_OK;
@@ -225,16 +229,23 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             kernels += 1;
         }
         if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
-        ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
-                             w.energy, bf16 ? w.fb_count : nullptr, st));
-        ++kernels;
+        if (g->refine_steps > 0) {
+            ACT_CK(launch_refine(g->ax, g->refine_steps, g->Lp, w.R, w.keys, B, w.theta, st));
+            ACT_CK(launch_update_refined(g->Lp, w.R, R16, g->Lb, B, w.keys, g->ax, w.theta, k, P, w.atoms, w.coefs,
+                                         w.energy, bf16 ? w.fb_count : nullptr, st));
+            kernels += 2;
+        } else {
+            ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
+                                 w.energy, bf16 ? w.fb_count : nullptr, st));
+            ++kernels;
+        }
     }
     ge.kernels = kernels;
     return ACT_OK;
 }
 
 act_status get_graph(act_grid *g, int B, int P, act_search_mode mode, GraphEntry **out) {
-    auto key = std::make_tuple(B, P, (int)mode, g->profiling ? 1 : 0);
+    auto key = std::make_tuple(B, P, (int)mode, g->profiling ? 1 : 0, g->refine_steps);
     auto it = g->graphs.find(key);
     if (it != g->graphs.end()) {
         *out = &it->second;
@@ -630,6 +641,24 @@ act_status act_set_tuning(act_grid *g, int32_t gemv_ctas_in, int32_t bf16_tile_a
     }
     drop_graphs(g);
     ++g->generation;
+    return ACT_OK;
+}
+
+act_status act_set_refinement(act_grid *g, int32_t steps) {
+    if (!g || steps < 0 || steps > 1000) return ACT_ERR_INVALID_ARG;
+    if (steps != g->refine_steps) {
+        g->refine_steps = steps;
+        ++g->generation;
+    }
+    return ACT_OK;
+}
+
+act_status act_chirplet_score(int32_t n_samples, double fs, const double *theta, const float *residuals,
+                              int32_t channels, float *score, double *grad_theta, float *atoms, void *cuda_stream) {
+    if (!theta || !residuals || !score || channels < 1 || n_samples < 1 || n_samples > kMaxSamples || !(fs > 0.0))
+        return ACT_ERR_INVALID_ARG;
+    ACT_CK(launch_chirplet_score(n_samples, fs, theta, residuals, channels, score, grad_theta, atoms,
+                                 (cudaStream_t)cuda_stream));
     return ACT_OK;
 }
 

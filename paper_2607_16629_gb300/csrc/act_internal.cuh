@@ -90,6 +90,15 @@ cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, 
 int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
 int gemv_max_ctas_per_sm(int Lp);
 
+// ---- off-grid refinement (act_refine.cu) ----------------------------------
+cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, float *score,
+                                  double *grad, float *atoms, cudaStream_t st);
+cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys, int B,
+                          double *theta_out, cudaStream_t st);
+cudaError_t launch_update_refined(int Lp, float *R, __nv_bfloat16 *R16, int Lb, int B, unsigned long long *keys,
+                                  const GridAxes &ax, const double *theta, int k, int P, act_atom *atoms, float *coefs,
+                                  double *energy, int *fb_count, cudaStream_t st);
+
 // ---- tensor-core search (act_gemm.cu) -------------------------------------
 struct Bf16Search;
 // Prepares the tensor-core search over the BF16 dictionary d16 [K][Lb]

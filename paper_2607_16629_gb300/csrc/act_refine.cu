@@ -1,0 +1,438 @@
+// Off-grid refinement of each order's selected chirplet (Fig. 1:
+// theta* = argmax_theta |<g(theta), r_k>| started from the grid winner) and
+// the adjoint of the chirplet score used for it.
+//
+// Score and adjoint.  For the unit-norm real atom of Eq. (1) at continuous
+// theta = (tc, fc, logDt, c), with u = E cos(phi), E = exp(-x^2/2),
+// x = tau/Dt, phi = 2 pi (c tau^2 + fc tau), tau = (n - tc)/fs, g = u/|u|:
+//   s = <r, u>/|u|,  ds/dr = g,
+//   ds/dtheta_i = <r, du_i>/|u| - s <u, du_i>/|u|^2 with
+//   du/dtc = (E x/Dt cos(phi) + E sin(phi) 2 pi (2 c tau + fc)) / fs,
+//   du/dfc = -E sin(phi) 2 pi tau,  du/dlogDt = E x^2 cos(phi),
+//   du/dc  = -E sin(phi) 2 pi tau^2.
+// Samples are evaluated as the dictionary generator does (phase formed in
+// FP64 and range-reduced before FP32 cospi/sinpi, Gaussian argument in
+// FP64).  The standalone score kernel accumulates all ten sums in FP64; the
+// refinement keeps FP64 for the two sums that define the objective and FP32
+// for the eight gradient sums (FP64 throughput is low on this GPU).
+//
+// Refinement.  BFGS on f(z) = -|s(w (.) z)| in coordinates scaled by the
+// grid steps w, one block per channel: p = -H grad f (H reset to I when p
+// is not a descent direction), a first step of at most half a grid step,
+// Armijo backtracking (c1 = 1e-4, up to 20 halvings, evaluated 8 at a time
+// by the 8 warps), the standard BFGS inverse update when <y, s> > 0,
+// parameters clamped to the grid box widened by one step; it stops early
+// when no step is accepted.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "act_device.cuh"
+#include "act_internal.cuh"
+
+namespace act {
+
+namespace {
+
+constexpr int kRefineThreads = 256;
+constexpr double kTwoPi = 6.283185307179586;
+
+struct EvalOut {
+    double s;
+    double g[4];
+    double nu;  // |u|
+};
+
+// The ten sums of one evaluation, reduced over the block; every thread
+// receives the score and gradient.  sh must hold 10 * 32 doubles.
+__device__ EvalOut eval_score(const double *th, const float *__restrict__ r, int L, double inv_fs, double *sh) {
+    const double tc = th[0], fc = th[1], inv_dt = exp(-th[2]), c = th[3];
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // ru, uu, rd[4], ud[4]
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(c, tau, fc) * tau;
+        ph -= rint(ph);
+        const float C = cospif(2.0f * (float)ph);
+        const float S = sinpif(2.0f * (float)ph);
+        const float x = (float)(tau * inv_dt);
+        const float E = expf(-0.5f * x * x);
+        const float u = E * C;
+        const float ES = E * S;
+        const float du0 = (float)(((double)(E * x * C) * inv_dt + (double)ES * kTwoPi * (2.0 * c * tau + fc)) * inv_fs);
+        const float du1 = (float)(-(double)ES * kTwoPi * tau);
+        const float du2 = E * x * x * C;
+        const float du3 = (float)(-(double)ES * kTwoPi * tau * tau);
+        const double rv = (double)r[n];
+        acc[0] = fma(rv, (double)u, acc[0]);
+        acc[1] = fma((double)u, (double)u, acc[1]);
+        acc[2] = fma(rv, (double)du0, acc[2]);
+        acc[3] = fma(rv, (double)du1, acc[3]);
+        acc[4] = fma(rv, (double)du2, acc[4]);
+        acc[5] = fma(rv, (double)du3, acc[5]);
+        acc[6] = fma((double)u, (double)du0, acc[6]);
+        acc[7] = fma((double)u, (double)du1, acc[7]);
+        acc[8] = fma((double)u, (double)du2, acc[8]);
+        acc[9] = fma((double)u, (double)du3, acc[9]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        acc[i] = warp_sum(acc[i]);
+        if (lane == 0) sh[i * 32 + wid] = acc[i];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) {
+            double t = lane < nw ? sh[i * 32 + lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) sh[i * 32] = t;
+        }
+    }
+    __syncthreads();
+    double tot[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) tot[i] = sh[i * 32];
+    __syncthreads();
+    EvalOut o;
+    if (!(tot[1] > 0.0) || !isfinite(tot[1])) {
+        o.s = 0.0;
+        o.nu = 0.0;
+        for (int i = 0; i < 4; ++i) o.g[i] = 0.0;
+        return o;
+    }
+    o.nu = sqrt(tot[1]);
+    o.s = tot[0] / o.nu;
+    for (int i = 0; i < 4; ++i) o.g[i] = tot[2 + i] / o.nu - o.s * tot[6 + i] / tot[1];
+    return o;
+}
+
+// Writes g(theta) = u/|u| for one channel (block), FP32.
+__device__ void write_atom(const double *th, double nu, int L, double inv_fs, float *__restrict__ out) {
+    const double tc = th[0], fc = th[1], inv_dt = exp(-th[2]), c = th[3];
+    const float scale = nu > 0.0 ? (float)(1.0 / nu) : 0.0f;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(c, tau, fc) * tau;
+        ph -= rint(ph);
+        const float x = (float)(tau * inv_dt);
+        out[n] = expf(-0.5f * x * x) * cospif(2.0f * (float)ph) * scale;
+    }
+}
+
+// Standalone score + adjoint: one block per channel.
+__global__ void __launch_bounds__(kRefineThreads) k_chirplet_score(int L, double inv_fs, const double *__restrict__ theta,
+                                                                  const float *__restrict__ R, float *__restrict__ score,
+                                                                  double *__restrict__ grad, float *__restrict__ atoms) {
+    __shared__ double sh[10 * 32];
+    __shared__ double th[4];
+    const int b = blockIdx.x;
+    if (threadIdx.x < 4) th[threadIdx.x] = theta[4 * b + threadIdx.x];
+    __syncthreads();
+    const EvalOut o = eval_score(th, R + (size_t)b * L, L, inv_fs, sh);
+    if (threadIdx.x == 0) {
+        score[b] = (float)o.s;
+        if (grad)
+            for (int i = 0; i < 4; ++i) grad[4 * b + i] = o.g[i];
+    }
+    if (atoms) write_atom(th, o.nu, L, inv_fs, atoms + (size_t)b * L);
+}
+
+struct RefineBox {
+    double w[4], lo[4], hi[4];
+};
+
+// Score and gradient of one warp's candidate (lane-strided samples, warp
+// reductions only): same arithmetic per sample as eval_score.
+__device__ EvalOut eval_warp(const double *th, const float *__restrict__ r, int L, double inv_fs) {
+    const int lane = threadIdx.x & 31;
+    const double tc = th[0], fc = th[1], inv_dt = exp(-th[2]), c = th[3];
+    const float inv_dt_f = (float)inv_dt, inv_fs_f = (float)inv_fs, two_pi = (float)kTwoPi;
+    const float c_f = (float)c, fc_f = (float)fc;
+    double ru = 0.0, uu = 0.0;                    // the objective: FP64 sums
+    float rd[4] = {0, 0, 0, 0}, ud[4] = {0, 0, 0, 0};  // its gradient: FP32 sums
+    for (int n = lane; n < L; n += 32) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(c, tau, fc) * tau;
+        ph -= rint(ph);
+        const float t = (float)tau;
+        const float C = cospif(2.0f * (float)ph);
+        const float S = sinpif(2.0f * (float)ph);
+        const float x = t * inv_dt_f;
+        const float E = expf(-0.5f * x * x);
+        const float u = E * C;
+        const float ES = E * S;
+        const float du0 = (E * x * C * inv_dt_f + ES * two_pi * fmaf(2.0f * c_f, t, fc_f)) * inv_fs_f;
+        const float du1 = -ES * two_pi * t;
+        const float du2 = E * x * x * C;
+        const float du3 = -ES * two_pi * t * t;
+        const float rv = r[n];
+        ru = fma((double)rv, (double)u, ru);
+        uu = fma((double)u, (double)u, uu);
+        rd[0] = fmaf(rv, du0, rd[0]);
+        rd[1] = fmaf(rv, du1, rd[1]);
+        rd[2] = fmaf(rv, du2, rd[2]);
+        rd[3] = fmaf(rv, du3, rd[3]);
+        ud[0] = fmaf(u, du0, ud[0]);
+        ud[1] = fmaf(u, du1, ud[1]);
+        ud[2] = fmaf(u, du2, ud[2]);
+        ud[3] = fmaf(u, du3, ud[3]);
+    }
+    ru = warp_sum(ru);
+    uu = warp_sum(uu);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        rd[i] = warp_sum(rd[i]);
+        ud[i] = warp_sum(ud[i]);
+    }
+    EvalOut o;
+    if (!(uu > 0.0) || !isfinite(uu)) {
+        o.s = 0.0;
+        o.nu = 0.0;
+        for (int i = 0; i < 4; ++i) o.g[i] = 0.0;
+        return o;
+    }
+    o.nu = sqrt(uu);
+    o.s = ru / o.nu;
+    for (int i = 0; i < 4; ++i) o.g[i] = (double)rd[i] / o.nu - o.s * (double)ud[i] / uu;
+    return o;
+}
+
+constexpr int kLineSearch = 20;  // Armijo halvings per iteration
+
+// BFGS refinement of channel b's grid winner; theta_out[b][4].  The 8 warps
+// of the block evaluate 8 consecutive step sizes alpha0 2^-j at once; the
+// first (largest) that satisfies the Armijo condition is taken, which is
+// what sequential backtracking would take.
+__global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBox box, int steps, int Lp,
+                                                          const float *__restrict__ R,
+                                                          const unsigned long long *__restrict__ keys,
+                                                          double *__restrict__ theta_out) {
+    constexpr int kWarps = kRefineThreads / 32;
+    __shared__ double z[4], gz[4], H[16], p[4];
+    __shared__ double cz[kWarps][4], cg[kWarps][4], cf[kWarps], ca[kWarps];
+    __shared__ double f, gp, alpha0;
+    __shared__ int state;  // -1: stop; otherwise the accepted warp (or kWarps: none yet)
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float *r = R + (size_t)b * Lp;
+    const int L = ax.L;
+    const double inv_fs = 1.0 / ax.fs;
+
+    if (threadIdx.x == 0) {
+        double p0[4];
+        decode_params(ax, (int64_t)key_index(keys[b]), p0);
+        for (int i = 0; i < 4; ++i) z[i] = p0[i] / box.w[i];
+        for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double th[4];
+        for (int i = 0; i < 4; ++i) th[i] = z[i] * box.w[i];
+        const EvalOut o = eval_warp(th, r, L, inv_fs);
+        if (lane == 0) {
+            const double sg = o.s < 0.0 ? -1.0 : 1.0;
+            f = -fabs(o.s);
+            for (int i = 0; i < 4; ++i) gz[i] = -sg * o.g[i] * box.w[i];
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < steps; ++it) {
+        if (threadIdx.x == 0) {
+            double g_p = 0.0, pn = 0.0;
+            for (int i = 0; i < 4; ++i) {
+                double v = 0.0;
+                for (int j = 0; j < 4; ++j) v -= H[4 * i + j] * gz[j];
+                p[i] = v;
+                g_p += gz[i] * v;
+            }
+            if (!(g_p < 0.0)) {
+                for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
+                g_p = 0.0;
+                for (int i = 0; i < 4; ++i) {
+                    p[i] = -gz[i];
+                    g_p += gz[i] * p[i];
+                }
+            }
+            for (int i = 0; i < 4; ++i) pn += p[i] * p[i];
+            pn = sqrt(pn);
+            gp = g_p;
+            alpha0 = pn > 0.5 ? 0.5 / pn : 1.0;
+            state = (g_p < 0.0) ? kWarps : -1;
+        }
+        __syncthreads();
+        if (state < 0) break;
+        for (int round = 0; round * kWarps < kLineSearch; ++round) {
+            const int j = round * kWarps + warp;
+            if (j < kLineSearch) {
+                const double a = alpha0 * ldexp(1.0, -j);
+                double th[4], zz[4];
+                for (int i = 0; i < 4; ++i) {
+                    double v = (z[i] + a * p[i]) * box.w[i];
+                    v = v < box.lo[i] ? box.lo[i] : (v > box.hi[i] ? box.hi[i] : v);
+                    zz[i] = v / box.w[i];
+                    th[i] = v;
+                }
+                const EvalOut o = eval_warp(th, r, L, inv_fs);
+                if (lane == 0) {
+                    const double sg = o.s < 0.0 ? -1.0 : 1.0;
+                    cf[warp] = -fabs(o.s);
+                    ca[warp] = a;
+                    for (int i = 0; i < 4; ++i) {
+                        cz[warp][i] = zz[i];
+                        cg[warp][i] = -sg * o.g[i] * box.w[i];
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int q = 0; q < kWarps && round * kWarps + q < kLineSearch; ++q)
+                    if (cf[q] <= f + 1e-4 * ca[q] * gp) {
+                        state = q;
+                        break;
+                    }
+            }
+            __syncthreads();
+            if (state < kWarps) break;
+        }
+        if (state >= kWarps) break;  // no acceptable step
+        if (threadIdx.x == 0) {
+            const int q = state;
+            double sv[4], yv[4], ys = 0.0;
+            for (int i = 0; i < 4; ++i) {
+                sv[i] = cz[q][i] - z[i];
+                yv[i] = cg[q][i] - gz[i];
+                ys += yv[i] * sv[i];
+            }
+            if (ys > 1e-300) {
+                const double rho = 1.0 / ys;
+                double A[16], T[16];
+                for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) A[4 * i + j] = (i == j ? 1.0 : 0.0) - rho * sv[i] * yv[j];
+                for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) {
+                        double a = 0.0;
+                        for (int k = 0; k < 4; ++k) a += A[4 * i + k] * H[4 * k + j];
+                        T[4 * i + j] = a;
+                    }
+                for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) {
+                        double a = 0.0;
+                        for (int k = 0; k < 4; ++k) a += T[4 * i + k] * A[4 * j + k];
+                        H[4 * i + j] = a + rho * sv[i] * sv[j];
+                    }
+            }
+            for (int i = 0; i < 4; ++i) {
+                z[i] = cz[q][i];
+                gz[i] = cg[q][i];
+            }
+            f = cf[q];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = z[threadIdx.x] * box.w[threadIdx.x];
+}
+
+// Coefficient and residual update with the refined atom g(theta*) generated
+// on the fly (Eq. (4)); the record keeps the grid winner's flat index.
+__global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float *__restrict__ R,
+                                                                  __nv_bfloat16 *__restrict__ R16, int Lb,
+                                                                  unsigned long long *__restrict__ keys, GridAxes ax,
+                                                                  const double *__restrict__ theta, int k, int P,
+                                                                  act_atom *__restrict__ atoms,
+                                                                  float *__restrict__ coefs,
+                                                                  double *__restrict__ energy, int *fb_count) {
+    __shared__ float shf[32];
+    __shared__ double shd[32];
+    const int b = blockIdx.x;
+    const int L = ax.L;
+    const double inv_fs = 1.0 / ax.fs;
+    const double tc = theta[4 * b], fc = theta[4 * b + 1], ld = theta[4 * b + 2], cc = theta[4 * b + 3];
+    const double inv_dt = exp(-ld);
+    float *r = R + (size_t)b * Lp;
+    // |u|^2 in FP64, then g = u / |u| recomputed per sample
+    double e = 0.0;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(cc, tau, fc) * tau;
+        ph -= rint(ph);
+        const float x = (float)(tau * inv_dt);
+        const float u = expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
+        e = fma((double)u, (double)u, e);
+    }
+    const double uu = block_sum(e, shd);
+    const float scale = (uu > 0.0 && isfinite(uu)) ? (float)(1.0 / sqrt(uu)) : 0.0f;
+    float part = 0.0f;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(cc, tau, fc) * tau;
+        ph -= rint(ph);
+        const float x = (float)(tau * inv_dt);
+        const float g = expf(-0.5f * x * x) * cospif(2.0f * (float)ph) * scale;
+        part = fmaf(g, r[n], part);
+    }
+    const float c = block_sum(part, shf);
+    double e2 = 0.0;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(cc, tau, fc) * tau;
+        ph -= rint(ph);
+        const float x = (float)(tau * inv_dt);
+        const float g = expf(-0.5f * x * x) * cospif(2.0f * (float)ph) * scale;
+        const float v = fmaf(-c, g, r[n]);
+        r[n] = v;
+        e2 = fma((double)v, (double)v, e2);
+        if (R16) R16[(size_t)b * Lb + n] = __float2bfloat16_rn(v);
+    }
+    const double tot = block_sum(e2, shd);
+    if (threadIdx.x == 0) {
+        act_atom a;
+        a.tc = tc;
+        a.fc = fc;
+        a.logdt = ld;
+        a.c = cc;
+        a.flat_index = (int64_t)key_index(keys[b]);
+        atoms[(size_t)b * P + k] = a;
+        coefs[(size_t)b * P + k] = c;
+        energy[(size_t)b * (P + 1) + k + 1] = tot;
+        keys[b] = 0ull;
+        if (fb_count && b == 0) {
+            fb_count[0] = 0;
+            fb_count[1] = 0;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, float *score,
+                                  double *grad, float *atoms, cudaStream_t st) {
+    k_chirplet_score<<<B, kRefineThreads, 0, st>>>(L, 1.0 / fs, theta, R, score, grad, atoms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys, int B,
+                          double *theta_out, cudaStream_t st) {
+    RefineBox box;
+    for (int i = 0; i < 4; ++i) {
+        // scale = grid step; box = grid range widened by one step (an axis
+        // with a zero step is held fixed)
+        const double st = fabs(ax.step[i]);
+        const double first = ax.lo[i], last = ax.lo[i] + (double)(ax.count[i] - 1) * ax.step[i];
+        box.w[i] = st > 0.0 ? st : 1.0;
+        box.lo[i] = st > 0.0 ? fmin(first, last) - st : first;
+        box.hi[i] = st > 0.0 ? fmax(first, last) + st : first;
+    }
+    k_refine<<<B, kRefineThreads, 0, st>>>(ax, box, steps, Lp, R, keys, theta_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_refined(int Lp, float *R, __nv_bfloat16 *R16, int Lb, int B, unsigned long long *keys,
+                                  const GridAxes &ax, const double *theta, int k, int P, act_atom *atoms, float *coefs,
+                                  double *energy, int *fb_count, cudaStream_t st) {
+    k_update_refined<<<B, kRefineThreads, 0, st>>>(Lp, R, R16, Lb, keys, ax, theta, k, P, atoms, coefs, energy,
+                                                   fb_count);
+    return cudaGetLastError();
+}
+
+}  // namespace act
