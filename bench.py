@@ -279,7 +279,7 @@ def run_ours(args):
     avg_ms = search_ms / max(1, search_n)
     achieved = gemv_bytes / (avg_ms / 1e3) / 1e9
     traffic = _profile_traffic("gemv_argmax_eeg_k2097152_n512.md",
-                               ["paper_2607_16629_gb300/csrc/act_kernels.cu",
+                               ["paper_2607_16629_gb300/csrc/act_gemv.cu",
                                 "paper_2607_16629_gb300/csrc/act_device.cuh"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
