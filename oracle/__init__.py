@@ -26,6 +26,15 @@ _lock = threading.Lock()
 _lib = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
+
+
+class LemParams(ctypes.Structure):
+    """Settings of the hierarchical search (Sec. VII-A): LHS samples of the
+    coarse level, candidates kept per level, refinement levels, the step of
+    each level per axis (tc, fc, logDt, c) and the neighbourhood half-width
+    in steps per axis."""
+    _fields_ = [("n_coarse", ctypes.c_int), ("top_k", ctypes.c_int), ("levels", ctypes.c_int),
+                ("steps", (ctypes.c_double * 4) * 3), ("radius", ctypes.c_int * 4)]
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 
@@ -75,6 +84,16 @@ def _load():
         lib.act_oracle_mp_refine.argtypes = [_dp, _i64p, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int,
                                              ctypes.c_int, _i64p, _dp, _dp, _dp, _dp]
         lib.act_oracle_mp_refine.restype = ctypes.c_int
+        lib.act_oracle_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.act_oracle_splitmix64_at.restype = ctypes.c_uint64
+        lib.act_oracle_lhs.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _dp]
+        lib.act_oracle_lem_select.argtypes = [ctypes.POINTER(LemParams), _dp, _dp, ctypes.c_double, ctypes.c_int,
+                                              _dp, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        lib.act_oracle_lem_select.restype = ctypes.c_int
+        lib.act_oracle_mp_lem.argtypes = [ctypes.POINTER(LemParams), _dp, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                          ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.c_int, _dp, _dp, _dp, _dp]
+        lib.act_oracle_mp_lem.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -248,3 +267,57 @@ def mp_refine(grid, s, P, steps):
     if rc != 0:
         raise MemoryError("oracle MP allocation failed")
     return idx, coef, th, r, en
+
+
+def lem_params(n_coarse, top_k, levels, steps, radius) -> LemParams:
+    p = LemParams()
+    p.n_coarse, p.top_k, p.levels = int(n_coarse), int(top_k), int(levels)
+    for l in range(3):
+        for a in range(4):
+            p.steps[l][a] = float(steps[min(l, len(steps) - 1)][a])
+    for a in range(4):
+        p.radius[a] = int(radius[a])
+    return p
+
+
+def splitmix64_at(seed: int, n: int) -> int:
+    """The n-th output of SplitMix64 seeded with `seed`."""
+    return int(_load().act_oracle_splitmix64_at(int(seed), int(n)))
+
+
+def lhs(lo, hi, n, seed, channel, order) -> np.ndarray:
+    out = np.empty((n, 4))
+    _load().act_oracle_lhs(_d(np.ascontiguousarray(lo, dtype=np.float64)),
+                           _d(np.ascontiguousarray(hi, dtype=np.float64)), int(n), int(seed), int(channel),
+                           int(order), _d(out))
+    return out
+
+
+def lem_select(params: LemParams, lo, hi, fs, r, seed, channel, order):
+    """Hierarchical selection before BFGS -> (theta[4], score)."""
+    th = np.empty(4)
+    sc = np.empty(1)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    rc = _load().act_oracle_lem_select(ctypes.byref(params), _d(np.ascontiguousarray(lo, dtype=np.float64)),
+                                       _d(np.ascontiguousarray(hi, dtype=np.float64)), float(fs), int(r.shape[0]),
+                                       _d(r), int(seed), int(channel), int(order), _d(th), _d(sc))
+    if rc != 0:
+        raise MemoryError("oracle LEM allocation failed")
+    return th, float(sc[0])
+
+
+def mp_lem(params: LemParams, lo, hi, scale, box_lo, box_hi, fs, s, P, steps, seed, channel):
+    """MP with hierarchical selection (+ BFGS) -> (theta[P][4], coef[P], residual, energy[P+1])."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    L = s.shape[0]
+    th = np.empty((P, 4))
+    coef = np.empty(P)
+    r = np.empty(L)
+    en = np.empty(P + 1)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    rc = _load().act_oracle_mp_lem(ctypes.byref(params), f(lo), f(hi), f(scale), f(box_lo), f(box_hi), float(fs),
+                                   int(L), _d(s), int(P), int(steps), int(seed), int(channel), _d(th), _d(coef),
+                                   _d(r), _d(en))
+    if rc != 0:
+        raise MemoryError("oracle LEM allocation failed")
+    return th, coef, r, en

@@ -485,3 +485,178 @@ int act_oracle_mp_refine(const double *axes, const int64_t *counts, int n_sample
     free(g);
     return 0;
 }
+
+/* ---------------------------------------------------------------------- */
+/* LEM-inspired hierarchical search (Sec. VII-A, Fig. 7)                   */
+/* ---------------------------------------------------------------------- */
+
+/* The n-th output (n = 0, 1, ...) of SplitMix64 seeded with `seed`
+ * (Steele, Lea and Flood, 2014): state advances by 0x9E3779B97F4A7C15 and
+ * each output is the published mix of the state. */
+uint64_t act_oracle_splitmix64_at(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Counter of one random draw: channel < 2^16, order < 2^12, axis < 4,
+ * kind 0 (stratum key) or 1 (offset in the stratum), sample i < 2^20. */
+static uint64_t lem_counter(int channel, int order, int axis, int kind, int i) {
+    return (((((((uint64_t)channel << 12) | (uint64_t)order) << 2 | (uint64_t)axis) << 1) | (uint64_t)kind) << 20) |
+           (uint64_t)i;
+}
+
+typedef struct {
+    int n_coarse;          /* LHS samples of the coarse level */
+    int top_k;             /* candidates kept per level */
+    int levels;            /* refinement levels after the coarse level (<= 2) */
+    double steps[3][4];    /* step of each level, (tc, fc, logDt, c) */
+    int radius[4];         /* neighbourhood half-width in steps, per axis */
+} act_oracle_lem;
+
+/* Latin hypercube sample of n points in the box [lo, hi]: on every axis the
+ * n strata of width (hi - lo)/n are each used exactly once, in a random
+ * order (the ranks of SplitMix64 keys), and each point sits at a uniform
+ * random offset inside its stratum:
+ *   theta[i][a] = lo[a] + ((rank_a(i) + u) / n) * (hi[a] - lo[a]). */
+void act_oracle_lhs(const double *lo, const double *hi, int n, uint64_t seed, int channel, int order,
+                    double *theta) {
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    for (int a = 0; a < 4; ++a) {
+        for (int i = 0; i < n; ++i) key[i] = act_oracle_splitmix64_at(seed, lem_counter(channel, order, a, 0, i));
+        for (int i = 0; i < n; ++i) {
+            int rank = 0;  /* number of keys below key[i] (keys are distinct) */
+            for (int j = 0; j < n; ++j) rank += key[j] < key[i];
+            const uint64_t h = act_oracle_splitmix64_at(seed, lem_counter(channel, order, a, 1, i));
+            const double u = (double)(h >> 11) * 0x1.0p-53;
+            const double t = ((double)rank + u) / (double)n;
+            theta[4 * i + a] = lo[a] + t * (hi[a] - lo[a]);
+        }
+    }
+    free(key);
+}
+
+static double lem_score(const double *th, double fs, int L, const double *r, double *g) {
+    act_oracle_atom(th[0], th[1], th[2], th[3], fs, L, g);
+    return dot(g, r, L);
+}
+
+/* The k best candidates by |score| (lowest candidate index on ties),
+ * skipping candidates whose parameters equal an already kept one. */
+static int lem_topk(const double *cand, const double *score, int n, int k, double *kept, double *kept_score) {
+    int m = 0;
+    for (int round = 0; round < k; ++round) {
+        int best = -1;
+        for (int i = 0; i < n; ++i) {
+            int dup = 0;
+            for (int q = 0; q < m && !dup; ++q)
+                dup = cand[4 * i] == kept[4 * q] && cand[4 * i + 1] == kept[4 * q + 1] &&
+                      cand[4 * i + 2] == kept[4 * q + 2] && cand[4 * i + 3] == kept[4 * q + 3];
+            if (dup) continue;
+            if (best < 0 || fabs(score[i]) > fabs(score[best])) best = i;
+        }
+        if (best < 0) break;
+        for (int a = 0; a < 4; ++a) kept[4 * m + a] = cand[4 * best + a];
+        kept_score[m] = score[best];
+        ++m;
+    }
+    return m;
+}
+
+/* Local neighbourhood dictionary of one level around the kept candidates:
+ * for every parent (in kept order) and every offset o in
+ * [-R_tc..R_tc] x [-R_fc..R_fc] x [-R_ld..R_ld] x [-R_c..R_c]
+ * (c fastest), theta = clamp(parent + o * step, lo, hi).  Returns the
+ * number of candidates written. */
+static int lem_neighbours(const double *kept, int m, const double *step, const int *R, const double *lo,
+                          const double *hi, double *cand) {
+    int n = 0;
+    for (int j = 0; j < m; ++j)
+        for (int o0 = -R[0]; o0 <= R[0]; ++o0)
+            for (int o1 = -R[1]; o1 <= R[1]; ++o1)
+                for (int o2 = -R[2]; o2 <= R[2]; ++o2)
+                    for (int o3 = -R[3]; o3 <= R[3]; ++o3) {
+                        const int o[4] = {o0, o1, o2, o3};
+                        for (int a = 0; a < 4; ++a) {
+                            double v = kept[4 * j + a] + (double)o[a] * step[a];
+                            if (v < lo[a]) v = lo[a];
+                            if (v > hi[a]) v = hi[a];
+                            cand[4 * n + a] = v;
+                        }
+                        ++n;
+                    }
+    return n;
+}
+
+/* One hierarchical selection (Fig. 7 up to, not including, BFGS): LHS over
+ * the box, projections onto r, keep top_k; then for each refinement level
+ * build the neighbourhood dictionaries of the kept candidates with that
+ * level's steps, project, pool and keep top_k.  Writes the best
+ * candidate's parameters and score; returns 0 (or -1 on allocation
+ * failure). */
+int act_oracle_lem_select(const act_oracle_lem *p, const double *lo, const double *hi, double fs, int L,
+                          const double *r, uint64_t seed, int channel, int order, double *theta_out,
+                          double *score_out) {
+    int per_parent = 1;
+    for (int a = 0; a < 4; ++a) per_parent *= 2 * p->radius[a] + 1;
+    int cap = p->n_coarse > p->top_k * per_parent ? p->n_coarse : p->top_k * per_parent;
+    double *cand = (double *)malloc(sizeof(double) * 4 * (size_t)cap);
+    double *score = (double *)malloc(sizeof(double) * (size_t)cap);
+    double *g = (double *)malloc(sizeof(double) * (size_t)L);
+    double *kept = (double *)malloc(sizeof(double) * 4 * (size_t)p->top_k);
+    double *kept_score = (double *)malloc(sizeof(double) * (size_t)p->top_k);
+    if (!cand || !score || !g || !kept || !kept_score) {
+        free(cand);
+        free(score);
+        free(g);
+        free(kept);
+        free(kept_score);
+        return -1;
+    }
+    act_oracle_lhs(lo, hi, p->n_coarse, seed, channel, order, cand);
+    for (int i = 0; i < p->n_coarse; ++i) score[i] = lem_score(cand + 4 * i, fs, L, r, g);
+    int m = lem_topk(cand, score, p->n_coarse, p->top_k, kept, kept_score);
+    for (int lev = 1; lev <= p->levels; ++lev) {
+        const int n = lem_neighbours(kept, m, p->steps[lev], p->radius, lo, hi, cand);
+        for (int i = 0; i < n; ++i) score[i] = lem_score(cand + 4 * i, fs, L, r, g);
+        m = lem_topk(cand, score, n, p->top_k, kept, kept_score);
+    }
+    for (int a = 0; a < 4; ++a) theta_out[a] = kept[a];
+    *score_out = kept_score[0];
+    free(cand);
+    free(score);
+    free(g);
+    free(kept);
+    free(kept_score);
+    return 0;
+}
+
+/* MP whose every order is selected by the hierarchical search (no stored
+ * dictionary), optionally refined by `steps` BFGS iterations (scales: the
+ * level-0 LEM steps... see act_oracle_refine), then subtracted.
+ * lo/hi: the parameter box; scale[4]: BFGS coordinate scales; box_lo/hi:
+ * the BFGS clamp box.  Outputs theta_out[P][4], coef[P], r, energy[P+1]. */
+int act_oracle_mp_lem(const act_oracle_lem *p, const double *lo, const double *hi, const double *scale,
+                      const double *box_lo, const double *box_hi, double fs, int L, const double *s, int P,
+                      int steps, uint64_t seed, int channel, double *theta_out, double *coef, double *r,
+                      double *energy) {
+    double *g = (double *)malloc(sizeof(double) * (size_t)L);
+    if (!g) return -1;
+    memcpy(r, s, sizeof(double) * (size_t)L);
+    if (energy) energy[0] = dot(r, r, L);
+    for (int k = 0; k < P; ++k) {
+        double th[4], sc;
+        if (act_oracle_lem_select(p, lo, hi, fs, L, r, seed, channel, k, th, &sc) != 0) {
+            free(g);
+            return -1;
+        }
+        if (steps > 0) act_oracle_refine(th, fs, L, r, steps, scale, box_lo, box_hi);
+        act_oracle_atom(th[0], th[1], th[2], th[3], fs, L, g);
+        for (int a = 0; a < 4; ++a) theta_out[4 * k + a] = th[a];
+        coef[k] = mp_update(g, r, L);
+        if (energy) energy[k + 1] = dot(r, r, L);
+    }
+    free(g);
+    return 0;
+}

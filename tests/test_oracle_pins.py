@@ -356,3 +356,55 @@ def test_refined_mp_keeps_the_mp_identities():
         assert coef[k] ** 2 >= grid_gain * (1 - 1e-12)
         gk, _ = oracle.atom(*th[k], grid.fs, grid.n_samples)
         rr = rr - coef[k] * gk
+
+
+# ---------------------------------------------------------------------------
+# Hierarchical (LEM-inspired) search, Sec. VII-A
+# ---------------------------------------------------------------------------
+def test_splitmix64_matches_published_outputs():
+    with open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for n, v in rows:
+        assert oracle.splitmix64_at(0, int(n)) == int(v, 16)
+
+
+def test_lhs_uses_every_stratum_once_per_axis():
+    lo = np.array([0.0, 0.5, -3.0, -20.0])
+    hi = np.array([508.0, 32.0, -0.5, 20.0])
+    n = 300
+    pts = oracle.lhs(lo, hi, n, seed=123, channel=3, order=7)
+    for a in range(4):
+        strata = np.floor((pts[:, a] - lo[a]) / (hi[a] - lo[a]) * n).astype(int)
+        assert sorted(strata) == list(range(n))
+        assert np.all(pts[:, a] >= lo[a]) and np.all(pts[:, a] <= hi[a])
+    other = oracle.lhs(lo, hi, n, seed=123, channel=3, order=8)
+    assert not np.array_equal(pts, other)
+    assert np.array_equal(pts, oracle.lhs(lo, hi, n, seed=123, channel=3, order=7))
+
+
+def _lem_box(grid):
+    axes = [grid.tc, grid.fc, grid.logdt, grid.c]
+    lo = np.array([min(a.lo, a.lo + (a.count - 1) * a.step) for a in axes])
+    hi = np.array([max(a.lo, a.lo + (a.count - 1) * a.step) for a in axes])
+    return lo, hi
+
+
+def test_lem_levels_never_lose_score_and_find_a_lone_atom():
+    """Each refinement level contains its parents (offset 0), so the best
+    |score| never drops; on a lone atom whose parameters lie on the last
+    level's lattice around a coarse candidate the search recovers it."""
+    grid = synth.grid_eeg()
+    lo, hi = _lem_box(grid)
+    true = (300.0, 12.0, -1.5, 5.0)
+    x, _ = oracle.atom(*true, grid.fs, grid.n_samples)
+    x = x + 0.01 * synth.random_signals(5, 1, grid.n_samples)[0]
+    steps = [(64, 2, 2, 5), (32, 1, 1, 2.5), (16, 0.5, 0.5, 0.5)]
+    best = []
+    for levels in (0, 1, 2):
+        p = oracle.lem_params(1024, 4, levels, steps, (2, 2, 1, 2))
+        th, sc = oracle.lem_select(p, lo, hi, grid.fs, x, 9, 0, 0)
+        best.append(abs(sc))
+        g, _ = oracle.atom(*th, grid.fs, grid.n_samples)
+        assert abs(sc - g @ x) <= 1e-12
+    assert best[0] <= best[1] <= best[2]
+    assert best[2] > 0.9
