@@ -320,6 +320,9 @@ def run_ours(args):
     refine = None
     if not args.no_refine:
         refine = bench_refine(args, dev, stream, peaks, peak_kind)
+    lem = None
+    if not args.no_lem:
+        lem = bench_lem(args, dev, stream, peaks, peak_kind)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -340,6 +343,8 @@ def run_ours(args):
             line["ragged_uneven_batch"] = ragged
         if refine is not None:
             line["offgrid_refinement"] = refine
+        if lem is not None:
+            line["hierarchical_lem"] = lem
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -549,6 +554,58 @@ def bench_refine(args, dev, stream, peaks, peak_kind):
         act.act_destroy(h)
 
 
+def bench_lem(args, dev, stream, peaks, peak_kind):
+    """Hierarchical (LEM-inspired) search without a dictionary against the
+    dense search, on 64 EEG-like channels (N = 512, fs = 256 Hz) over the
+    2,097,152-atom grid's box, 20 orders, each selection refined by 20 BFGS
+    iterations: time, device memory and normalised residue (the trade-off of
+    the paper's Table 7)."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    w = synth.workload_c3()
+    B, P, L = w.signals.shape[0], w.n_atoms, w.grid.n_samples
+    sig = torch.tensor(w.signals, dtype=torch.float32, device=dev)
+    out = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+           torch.empty((B, P), dtype=torch.float32, device=dev),
+           torch.empty((B, L), dtype=torch.float32, device=dev),
+           torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
+    res = {}
+    for name in ("lem", "dense_bf16"):
+        torch.cuda.synchronize(dev)
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        h = act.act_grid_create(w.grid, dev.index)
+        try:
+            if name == "lem":
+                act.act_set_search(h, act.ACT_SEARCH_LEM)
+            else:
+                act.act_dictionary_build(h, act.ACT_DICT_BF16, stream)
+                act.act_set_search(h, act.ACT_SEARCH_BF16)
+            act.act_set_refinement(h, 20)
+            act.act_decompose(h, sig, B, P, *out, stream)
+            torch.cuda.synchronize(dev)
+            used = free0 - torch.cuda.mem_get_info(dev)[0]
+            n = max(2, args.steps // 10)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                act.act_decompose(h, sig, B, P, *out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            st = act.act_grid_status(h, stream)
+            if st != act.ACT_OK:
+                raise RuntimeError(act.status_name(st))
+            en = out[3].cpu().numpy()
+            res[name] = {"ms_per_step": e0.elapsed_time(e1) / n, "device_bytes": int(used),
+                         "mean_normalised_residue": float(np.mean(en[:, -1] / en[:, 0]))}
+        finally:
+            act.act_destroy(h)
+    return {"workload": "eeg_like_64ch_n512_box128x64x8x32_p20_bfgs20", "lem": res["lem"],
+            "dense_bf16": res["dense_bf16"],
+            "lem_settings": "paper EEG settings: top_k 4, 2 levels, steps (64,2,2,5)/(32,1,1,2.5)/(16,.5,.5,.5), "
+                            "radius (2,2,1,2), 2048 LHS samples"}
+
+
 def run_profile_case(args):
     """Small, self-checking cases for ncu captures: a few launches of one
     search kernel on a dictionary larger than L2 but a few GB at most.
@@ -588,6 +645,7 @@ def main():
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-lem", action="store_true")
     ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()
