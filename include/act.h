@@ -95,13 +95,36 @@ typedef enum {
  *                    exclude are rescored in FP32, so the selection equals
  *                    the FP32 search's bit for bit (channels <= 128,
  *                    n_samples <= 512).
+ *   ACT_SEARCH_LEM:  the hierarchical search of act_lem_params (no
+ *                    dictionary needed; act_atom.flat_index is -1).
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
  *                    FP32 otherwise. */
 typedef enum {
     ACT_SEARCH_AUTO = 0,
     ACT_SEARCH_FP32 = 1,
-    ACT_SEARCH_BF16 = 2
+    ACT_SEARCH_BF16 = 2,
+    ACT_SEARCH_LEM = 3
 } act_search_mode;
+
+/* Settings of the LEM-inspired hierarchical search (Sec. VII-A, Fig. 7),
+ * which needs no stored dictionary: per order, a Latin hypercube sample of
+ * n_coarse parameter vectors over the grid's box (0: as many as the coarse
+ * grid of steps[0] would hold, at most 16384), the top_k by |<g, r_k>| kept;
+ * then for each of `levels` refinement levels (0..2) the neighbourhood
+ * dictionary of every kept candidate -- offsets of -radius..radius steps of
+ * that level's steps per axis, clamped to the box -- pooled and reranked to
+ * a new top_k (1..16); the best candidate starts the BFGS refinement
+ * (act_set_refinement; 0 iterations keeps it as is).  Axes in the order
+ * (tc [samples], fc [Hz], logDt, c [Hz/s]).  The draws come from SplitMix64
+ * seeded with `seed` (counter = channel, order, axis, draw). */
+typedef struct {
+    int32_t n_coarse;
+    int32_t top_k;
+    int32_t levels;
+    double steps[3][4];
+    int32_t radius[4];
+    uint64_t seed;
+} act_lem_params;
 
 /* One selected atom: its grid parameters and flat index. */
 typedef struct {
@@ -144,6 +167,14 @@ ACT_API act_status act_grid_size(const act_grid *grid, int64_t *n_atoms, int32_t
  * Enqueued on cuda_stream.  Errors: ACT_ERR_OOM when the dictionary does not
  * fit (nothing is kept), ACT_ERR_UNSUPPORTED for ACT_DICT_RECOMPUTE. */
 ACT_API act_status act_dictionary_build(act_grid *grid, act_dict_mode mode, void *cuda_stream);
+
+/* Sets the hierarchical search (ACT_SEARCH_LEM).  A new grid starts with the
+ * settings the paper reports for EEG: top_k 4, 2 levels, steps
+ * (64, 2, 2, 5), (32, 1, 1, 2.5), (16, 0.5, 0.5, 0.5), radius (2, 2, 1, 2),
+ * n_coarse 0, seed 0.  Errors: ACT_ERR_INVALID_ARG (non-positive steps,
+ * top_k or levels out of range), ACT_ERR_UNSUPPORTED (more than 16384 coarse
+ * samples).  Makes ragged plans built on this grid stale. */
+ACT_API act_status act_set_lem(act_grid *grid, const act_lem_params *params);
 
 /* Selects the search act_decompose runs (see act_search_mode). */
 ACT_API act_status act_set_search(act_grid *grid, act_search_mode mode);

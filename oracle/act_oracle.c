@@ -352,23 +352,22 @@ int act_oracle_score_grad(const double *theta, double fs, int n_samples, const d
  *   if <y, s> > 0:  H = (I - s y^T / <y,s>) H (I - y s^T / <y,s>) + s s^T / <y,s>
  * stopping early when no step is accepted.  lo/hi[4] clamp theta.
  * Returns the final |s|. */
-static void scaled_eval(const double *z, const double *w, double fs, int n, const double *r, double *f, double *gz,
-                        double *th_out) {
-    double th[4], s, g[4];
-    for (int i = 0; i < 4; ++i) th[i] = z[i] * w[i];
+static void scaled_eval(const double *th, const double *w, double fs, int n, const double *r, double *f,
+                        double *gz) {
+    double s, g[4];
     act_oracle_score_grad(th, fs, n, r, &s, g);
     const double sg = s < 0.0 ? -1.0 : 1.0;
     *f = -fabs(s);
     for (int i = 0; i < 4; ++i) gz[i] = -sg * g[i] * w[i];
-    if (th_out)
-        for (int i = 0; i < 4; ++i) th_out[i] = th[i];
 }
 
 double act_oracle_refine(double *theta, double fs, int n_samples, const double *r, int steps, const double *w,
                          const double *lo, const double *hi) {
+    /* z: scaled coordinates; theta itself is kept alongside, so a start
+     * that is never improved is returned bit for bit */
     double z[4], gz[4], f, H[16];
     for (int i = 0; i < 4; ++i) z[i] = theta[i] / w[i];
-    scaled_eval(z, w, fs, n_samples, r, &f, gz, NULL);
+    scaled_eval(theta, w, fs, n_samples, r, &f, gz);
     for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
     for (int it = 0; it < steps; ++it) {
         double p[4], gp = 0.0, pn = 0.0;
@@ -389,16 +388,17 @@ double act_oracle_refine(double *theta, double fs, int n_samples, const double *
         for (int i = 0; i < 4; ++i) pn += p[i] * p[i];
         pn = sqrt(pn);
         double alpha = pn > 0.5 ? 0.5 / pn : 1.0;
-        double z2[4], f2 = 0.0, g2[4];
+        double z2[4], t2[4], f2 = 0.0, g2[4];
         int ok = 0;
         for (int ls = 0; ls < 20; ++ls) {
             for (int i = 0; i < 4; ++i) {
                 double v = (z[i] + alpha * p[i]) * w[i];
                 if (v < lo[i]) v = lo[i];
                 if (v > hi[i]) v = hi[i];
+                t2[i] = v;
                 z2[i] = v / w[i];
             }
-            scaled_eval(z2, w, fs, n_samples, r, &f2, g2, NULL);
+            scaled_eval(t2, w, fs, n_samples, r, &f2, g2);
             if (f2 <= f + 1e-4 * alpha * gp) {
                 ok = 1;
                 break;
@@ -433,11 +433,11 @@ double act_oracle_refine(double *theta, double fs, int n_samples, const double *
         }
         for (int i = 0; i < 4; ++i) {
             z[i] = z2[i];
+            theta[i] = t2[i];
             gz[i] = g2[i];
         }
         f = f2;
     }
-    for (int i = 0; i < 4; ++i) theta[i] = z[i] * w[i];
     return -f;
 }
 

@@ -26,7 +26,7 @@ ACT_ERR_NOT_BUILT = 6
 ACT_ERR_UNSUPPORTED = 7
 
 ACT_DICT_AUTO, ACT_DICT_FP32, ACT_DICT_BF16, ACT_DICT_RECOMPUTE = 0, 1, 2, 3
-ACT_SEARCH_AUTO, ACT_SEARCH_FP32, ACT_SEARCH_BF16 = 0, 1, 2
+ACT_SEARCH_AUTO, ACT_SEARCH_FP32, ACT_SEARCH_BF16, ACT_SEARCH_LEM = 0, 1, 2, 3
 
 # Every symbol include/act.h declares (checked by the CPU tests).
 EXPORTS = (
@@ -35,7 +35,7 @@ EXPORTS = (
     "act_dictionary_rows", "act_grid_status", "act_set_profiling", "act_profile_read",
     "act_bf16_stats", "act_destroy", "act_search_noalloc", "act_autotune", "act_get_tuning", "act_set_tuning",
     "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
-    "act_set_refinement", "act_chirplet_score",
+    "act_set_refinement", "act_chirplet_score", "act_set_lem",
 )
 
 
@@ -54,6 +54,11 @@ class act_atom(ctypes.Structure):
 
 
 ATOM_BYTES = ctypes.sizeof(act_atom)  # 40
+
+
+class act_lem_params(ctypes.Structure):
+    _fields_ = [("n_coarse", ctypes.c_int32), ("top_k", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("steps", (ctypes.c_double * 4) * 3), ("radius", ctypes.c_int32 * 4), ("seed", ctypes.c_uint64)]
 
 
 class ActError(RuntimeError):
@@ -113,6 +118,7 @@ def load_library(path: str = LIB_PATH):
         lib.act_ragged_plan_destroy.restype = None
         lib.act_set_refinement.argtypes = [_P, ctypes.c_int32]
         lib.act_chirplet_score.argtypes = [ctypes.c_int32, ctypes.c_double, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
+        lib.act_set_lem.argtypes = [_P, ctypes.POINTER(act_lem_params)]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -327,6 +333,19 @@ def act_chirplet_score(n_samples: int, fs: float, theta, residuals, channels: in
     _check(load_library().act_chirplet_score(int(n_samples), float(fs), _ptr(theta), _ptr(residuals), int(channels),
                                              _ptr(score), _ptr(grad_theta), _ptr(atoms), _stream(stream)),
            "act_chirplet_score")
+
+
+def act_set_lem(grid: int, n_coarse: int = 0, top_k: int = 4, levels: int = 2,
+                steps=((64, 2, 2, 5), (32, 1, 1, 2.5), (16, 0.5, 0.5, 0.5)), radius=(2, 2, 1, 2),
+                seed: int = 0) -> None:
+    p = act_lem_params()
+    p.n_coarse, p.top_k, p.levels, p.seed = int(n_coarse), int(top_k), int(levels), int(seed)
+    for l in range(3):
+        for a in range(4):
+            p.steps[l][a] = float(steps[min(l, len(steps) - 1)][a])
+    for a in range(4):
+        p.radius[a] = int(radius[a])
+    _check(load_library().act_set_lem(grid, ctypes.byref(p)), "act_set_lem")
 
 
 def act_destroy(grid: int) -> None:

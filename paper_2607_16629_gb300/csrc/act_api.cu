@@ -95,6 +95,8 @@ struct WorkBuffers {
     int *fb_list = nullptr;           // [B] channels queued for the FP32 full search
     int *fb_count = nullptr;          // [2] full-search and rescan queue lengths
     double *theta = nullptr;          // [B][4] refined parameters of the current order
+    LemBuffers lem;                   // hierarchical-search candidates (allocated on first use)
+    int lem_B = 0;
 };
 
 struct act_grid {
@@ -116,6 +118,7 @@ struct act_grid {
     Bf16Search *bf16 = nullptr;
     int gemv_grid = 0;
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
+    LemConfig lem;         // hierarchical search settings
     cudaStream_t cap = nullptr;
     bool profiling = false;
     std::map<std::tuple<int, int, int, int, int>, GraphEntry> graphs;
@@ -146,6 +149,14 @@ void free_work(WorkBuffers &w) {
     free_dev(w.fb_list);
     free_dev(w.fb_count);
     free_dev(w.theta);
+    free_dev(w.lem.cand);
+    free_dev(w.lem.score);
+    free_dev(w.lem.kept);
+    free_dev(w.lem.kept_score);
+    free_dev(w.lem.ncand);
+    free_dev(w.lem.nkept);
+    w.lem.cap = 0;
+    w.lem_B = 0;
     w.cap_B = w.cap_P = 0;
 }
 
@@ -191,7 +202,70 @@ act_status ensure_work(act_grid *g, int B, int P) {
     return s;
 }
 
+int lem_capacity(const LemConfig &c) {
+    int per = 1;
+    for (int a = 0; a < 4; ++a) per *= 2 * c.level[1].radius[a] + 1;
+    int per2 = 1;
+    for (int a = 0; a < 4; ++a) per2 *= 2 * c.level[2].radius[a] + 1;
+    int cap = c.n_coarse;
+    if (c.levels >= 1 && c.top_k * per > cap) cap = c.top_k * per;
+    if (c.levels >= 2 && c.top_k * per2 > cap) cap = c.top_k * per2;
+    return cap;
+}
+
+act_status ensure_lem(const act_grid *g, WorkBuffers &w, int B) {
+    const int cap = lem_capacity(g->lem);
+    if (w.lem.cap >= cap && w.lem_B >= B && w.lem.cand) return ACT_OK;
+    free_dev(w.lem.cand);
+    free_dev(w.lem.score);
+    free_dev(w.lem.kept);
+    free_dev(w.lem.kept_score);
+    free_dev(w.lem.ncand);
+    free_dev(w.lem.nkept);
+    const int k = g->lem.top_k;
+    ACT_CK(cudaMalloc(&w.lem.cand, sizeof(double) * 4 * (size_t)B * cap));
+    ACT_CK(cudaMalloc(&w.lem.score, sizeof(double) * (size_t)B * cap));
+    ACT_CK(cudaMalloc(&w.lem.kept, sizeof(double) * 4 * (size_t)B * k));
+    ACT_CK(cudaMalloc(&w.lem.kept_score, sizeof(double) * (size_t)B * k));
+    ACT_CK(cudaMalloc(&w.lem.ncand, sizeof(int) * (size_t)B));
+    ACT_CK(cudaMalloc(&w.lem.nkept, sizeof(int) * (size_t)B));
+    w.lem.cap = cap;
+    w.lem_B = B;
+    return ACT_OK;
+}
+
+// Hierarchical-search settings from the public struct; the box is the
+// grid's range on every axis.
+act_status lem_configure(act_grid *g, const act_lem_params *p) {
+    LemConfig c;
+    if (p->top_k < 1 || p->top_k > 16 || p->levels < 0 || p->levels > 2) return ACT_ERR_INVALID_ARG;
+    const act_axis *axes[4] = {&g->desc.tc, &g->desc.fc, &g->desc.logdt, &g->desc.c};
+    double n_est = 1.0;
+    for (int a = 0; a < 4; ++a) {
+        const double first = axes[a]->lo, last = axes[a]->lo + (double)(axes[a]->count - 1) * axes[a]->step;
+        c.box.lo[a] = fmin(first, last);
+        c.box.hi[a] = fmax(first, last);
+        for (int l = 0; l < 3; ++l) {
+            if (!(p->steps[l][a] > 0.0) || !isfinite(p->steps[l][a])) return ACT_ERR_INVALID_ARG;
+            c.level[l].step[a] = p->steps[l][a];
+            c.level[l].radius[a] = p->radius[a];
+        }
+        if (p->radius[a] < 0 || p->radius[a] > 8) return ACT_ERR_INVALID_ARG;
+        const double cnt = ceil((c.box.hi[a] - c.box.lo[a]) / p->steps[0][a]);
+        n_est *= cnt > 1.0 ? cnt : 1.0;
+    }
+    c.n_coarse = p->n_coarse > 0 ? p->n_coarse : (n_est > 16384.0 ? 16384 : (int)n_est);
+    if (c.n_coarse < 1 || c.n_coarse > 16384) return ACT_ERR_UNSUPPORTED;
+    c.top_k = p->top_k;
+    c.levels = p->levels;
+    c.seed = p->seed;
+    if (lem_capacity(c) > (1 << 20)) return ACT_ERR_UNSUPPORTED;
+    g->lem = c;
+    return ACT_OK;
+}
+
 act_search_mode effective_search(const act_grid *g) {
+    if (g->search == ACT_SEARCH_LEM) return ACT_SEARCH_LEM;
     if (g->search == ACT_SEARCH_FP32) return ACT_SEARCH_FP32;
     if (g->search == ACT_SEARCH_BF16) return ACT_SEARCH_BF16;
     return g->built == ACT_DICT_BF16 ? ACT_SEARCH_BF16 : ACT_SEARCH_FP32;
@@ -216,7 +290,11 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             }
             ACT_CK(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
         }
-        if (bf16) {
+        if (mode == ACT_SEARCH_LEM) {
+            ACT_CK(launch_lem_select(g->lem, B, k, w.R, g->Lp, g->L, g->desc.fs, w.lem, st));
+            if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+            kernels += lem_kernels(g->lem);
+        } else if (bf16) {
             ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             ACT_CK(launch_bf16_resolve(g->bf16, B, g->d32, g->Lp, g->L, w.R, w.keys, w.fb_list, w.fb_count,
@@ -229,8 +307,15 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             kernels += 1;
         }
         if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
-        if (g->refine_steps > 0) {
-            ACT_CK(launch_refine(g->ax, g->refine_steps, g->Lp, w.R, w.keys, B, w.theta, st));
+        if (mode == ACT_SEARCH_LEM) {
+            // the best hierarchical candidate starts the (optional) BFGS refinement
+            ACT_CK(launch_refine(g->ax, g->refine_steps, g->Lp, w.R, nullptr, w.lem.kept, 4 * g->lem.top_k, B,
+                                 w.theta, st));
+            ACT_CK(launch_update_refined(g->Lp, w.R, nullptr, g->Lb, B, nullptr, g->ax, w.theta, k, P, w.atoms,
+                                         w.coefs, w.energy, nullptr, st));
+            kernels += 2;
+        } else if (g->refine_steps > 0) {
+            ACT_CK(launch_refine(g->ax, g->refine_steps, g->Lp, w.R, w.keys, nullptr, 0, B, w.theta, st));
             ACT_CK(launch_update_refined(g->Lp, w.R, R16, g->Lb, B, w.keys, g->ax, w.theta, k, P, w.atoms, w.coefs,
                                          w.energy, bf16 ? w.fb_count : nullptr, st));
             kernels += 2;
@@ -383,6 +468,21 @@ act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid *
         return e == cudaErrorMemoryAllocation ? ACT_ERR_OOM : ACT_ERR_CUDA;
     }
     g->gemv_grid = gemv_ctas(g->sm_count, g->Lp);
+    act_lem_params lp;
+    memset(&lp, 0, sizeof(lp));
+    lp.top_k = 4;
+    lp.levels = 2;
+    const double paper_steps[3][4] = {{64, 2, 2, 5}, {32, 1, 1, 2.5}, {16, 0.5, 0.5, 0.5}};
+    for (int l = 0; l < 3; ++l)
+        for (int a = 0; a < 4; ++a) lp.steps[l][a] = paper_steps[l][a];
+    lp.radius[0] = 2;
+    lp.radius[1] = 2;
+    lp.radius[2] = 1;
+    lp.radius[3] = 2;
+    if (lem_configure(g, &lp) != ACT_OK) {  // a grid whose box needs more coarse samples: cap them
+        lp.n_coarse = 16384;
+        lem_configure(g, &lp);
+    }
     *out = g;
     return ACT_OK;
 }
@@ -444,8 +544,17 @@ act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stre
     return ACT_OK;
 }
 
+act_status act_set_lem(act_grid *g, const act_lem_params *params) {
+    if (!g || !params) return ACT_ERR_INVALID_ARG;
+    act_status s = lem_configure(g, params);
+    if (s != ACT_OK) return s;
+    drop_graphs(g);
+    ++g->generation;
+    return ACT_OK;
+}
+
 act_status act_set_search(act_grid *g, act_search_mode mode) {
-    if (!g || (int)mode < 0 || (int)mode > 2) return ACT_ERR_INVALID_ARG;
+    if (!g || (int)mode < 0 || (int)mode > 3) return ACT_ERR_INVALID_ARG;
     g->search = mode;
     return ACT_OK;
 }
@@ -454,16 +563,18 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
                          act_atom *atoms_out, float *coeffs_out, float *residuals_out, double *energy_out,
                          void *cuda_stream) {
     if (!g || !signals || channels < 1 || n_atoms < 1) return ACT_ERR_INVALID_ARG;
-    if (g->built < 0) return ACT_ERR_NOT_BUILT;
+    const act_search_mode mode = effective_search(g);
+    if (g->built < 0 && mode != ACT_SEARCH_LEM) return ACT_ERR_NOT_BUILT;
+    if (mode == ACT_SEARCH_LEM && n_atoms > 4096) return ACT_ERR_UNSUPPORTED;  // draw counter holds 12 bits of order
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const act_search_mode mode = effective_search(g);
     if (mode == ACT_SEARCH_BF16) {
         if (!g->bf16 || !g->d16) return ACT_ERR_NOT_BUILT;
         if (channels > 128) return ACT_ERR_UNSUPPORTED;
     }
     act_status s = ensure_work(g, channels, n_atoms);
     if (s != ACT_OK) return s;
+    if (mode == ACT_SEARCH_LEM && (s = ensure_lem(g, g->w, channels)) != ACT_OK) return s;
     bool host_seen = !is_device_ptr(signals);
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     GraphEntry *ge = nullptr;
@@ -761,7 +872,7 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
     std::map<int, int> group_of_len;
     for (int i = 0; i < n_grids; ++i) {
         act_grid *g = grids[i];
-        if (!g || g->built < 0) return ACT_ERR_NOT_BUILT;
+        if (!g || (g->built < 0 && effective_search(g) != ACT_SEARCH_LEM)) return ACT_ERR_NOT_BUILT;
         if (g->device != p->device) return ACT_ERR_INVALID_ARG;
         if (group_of_len.count(g->L)) return ACT_ERR_INVALID_ARG;  // one grid per window length
         group_of_len[g->L] = (int)p->groups.size();
@@ -792,6 +903,7 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
         if (gr.mode == ACT_SEARCH_BF16 && (!g->bf16 || B > 128)) gr.mode = ACT_SEARCH_FP32;
         act_status s = alloc_work(g, gr.w, B, p->P);
         if (s != ACT_OK) return s;
+        if (gr.mode == ACT_SEARCH_LEM && (s = ensure_lem(g, gr.w, B)) != ACT_OK) return s;
         std::vector<int64_t> off(B);
         for (int i = 0; i < B; ++i) off[i] = offsets[gr.chan[i]];
         ACT_CK(cudaMalloc(&gr.src_off, sizeof(int64_t) * B));
@@ -861,7 +973,8 @@ act_status act_ragged_decompose(act_ragged_plan *p, const float *signals, act_at
                                 float *residuals_out, double *energy_out, void *cuda_stream) {
     if (!p || !signals) return ACT_ERR_INVALID_ARG;
     for (auto &gr : p->groups)
-        if (gr.g->generation != gr.generation || gr.g->built < 0) return ACT_ERR_NOT_BUILT;  // stale plan
+        if (gr.g->generation != gr.generation || (gr.g->built < 0 && gr.mode != ACT_SEARCH_LEM))
+            return ACT_ERR_NOT_BUILT;  // stale plan
     DeviceGuard dg(p->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     bool host_seen = !is_device_ptr(signals);

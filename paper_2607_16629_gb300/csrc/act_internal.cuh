@@ -90,11 +90,42 @@ cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, 
 int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
 int gemv_max_ctas_per_sm(int Lp);
 
+// ---- hierarchical search (act_lem.cu) -------------------------------------
+struct LemBox {
+    double lo[4], hi[4];
+};
+struct LemLevel {
+    double step[4];
+    int radius[4];
+};
+struct LemConfig {
+    int n_coarse = 0;  // LHS samples of the coarse level
+    int top_k = 4;
+    int levels = 2;
+    LemBox box;
+    LemLevel level[3];
+    uint64_t seed = 0;
+};
+struct LemBuffers {
+    int cap = 0;                  // candidates per channel
+    double *cand = nullptr;       // [B][cap][4]
+    double *score = nullptr;      // [B][cap]
+    double *kept = nullptr;       // [B][top_k][4]
+    double *kept_score = nullptr; // [B][top_k]
+    int *ncand = nullptr;         // [B]
+    int *nkept = nullptr;         // [B]
+};
+cudaError_t launch_lem_select(const LemConfig &cfg, int B, int order, const float *R, int Lp, int L, double fs,
+                              const LemBuffers &lb, cudaStream_t st);
+int lem_kernels(const LemConfig &cfg);
+
 // ---- off-grid refinement (act_refine.cu) ----------------------------------
 cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, float *score,
                                   double *grad, float *atoms, cudaStream_t st);
-cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys, int B,
-                          double *theta_out, cudaStream_t st);
+// Start: theta_in[b * theta_in_stride ..] when theta_in is given, else the
+// grid winner decoded from keys[b].
+cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys,
+                          const double *theta_in, int theta_in_stride, int B, double *theta_out, cudaStream_t st);
 cudaError_t launch_update_refined(int Lp, float *R, __nv_bfloat16 *R16, int Lb, int B, unsigned long long *keys,
                                   const GridAxes &ax, const double *theta, int k, int P, act_atom *atoms, float *coefs,
                                   double *energy, int *fb_count, cudaStream_t st);

@@ -1,0 +1,250 @@
+// LEM-inspired hierarchical coarse-to-fine search (Sec. VII-A, Fig. 7), with
+// no stored dictionary: per channel and order,
+//   1. a Latin hypercube sample of n_coarse parameter vectors over the grid's
+//      box (strata ranked by SplitMix64 keys, uniform offsets inside them);
+//   2. every candidate atom generated on the fly and projected onto the
+//      residual; the top_k by |score| kept (lowest candidate index on ties,
+//      duplicate parameter vectors skipped);
+//   3. per refinement level, the local neighbourhood dictionary of each kept
+//      candidate (offsets -R..R steps of that level per axis, clamped to the
+//      box), all candidates pooled, projected and reranked to a new top_k;
+//   4. the best candidate then starts the BFGS refinement (act_refine.cu).
+// The random draws come from SplitMix64 (Steele, Lea and Flood, 2014): draw
+// n of a stream seeded s is mix(s + (n + 1) 0x9E3779B97F4A7C15), with n
+// packing (channel, order, axis, kind, sample).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "act_device.cuh"
+#include "act_internal.cuh"
+
+namespace act {
+
+namespace {
+
+constexpr int kLemThreads = 256;
+
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t lem_counter(int channel, int order, int axis, int kind, int i) {
+    return (((((((uint64_t)channel << 12) | (uint64_t)order) << 2 | (uint64_t)axis) << 1) | (uint64_t)kind) << 20) |
+           (uint64_t)i;
+}
+
+// 1. Latin hypercube: one block per channel; keys sorted in shared memory
+// (bitonic sort over npow2 >= n entries, padding keys sort last).
+__global__ void __launch_bounds__(kLemThreads) k_lem_lhs(int n, int npow2, LemBox box, uint64_t seed, int order,
+                                                        int cap, double *__restrict__ cand, int *__restrict__ ncand) {
+    extern __shared__ uint8_t sm_raw[];
+    uint64_t *key = reinterpret_cast<uint64_t *>(sm_raw);
+    uint32_t *idx = reinterpret_cast<uint32_t *>(key + npow2);
+    const int b = blockIdx.x;
+    double *out = cand + (size_t)b * cap * 4;
+    for (int a = 0; a < 4; ++a) {
+        for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+            key[i] = i < n ? splitmix64_at(seed, lem_counter(b, order, a, 0, i)) : ~0ull;
+            idx[i] = (uint32_t)i;
+        }
+        __syncthreads();
+        for (int size = 2; size <= npow2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const bool up = (i & size) == 0;
+                        const uint64_t ki = key[i], kj = key[j];
+                        if ((ki > kj) == up) {
+                            key[i] = kj;
+                            key[j] = ki;
+                            const uint32_t t = idx[i];
+                            idx[i] = idx[j];
+                            idx[j] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // sorted position p is the stratum (rank) of sample idx[p]
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int i = (int)idx[p];
+            const uint64_t h = splitmix64_at(seed, lem_counter(b, order, a, 1, i));
+            const double u = (double)(h >> 11) * 0x1.0p-53;
+            const double t = __ddiv_rn(__dadd_rn((double)p, u), (double)n);
+            out[4 * i + a] = __dadd_rn(box.lo[a], __dmul_rn(t, __dadd_rn(box.hi[a], -box.lo[a])));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ncand[b] = n;
+}
+
+// 2. Scores s = <r, u>/|u| of every candidate of every channel, one warp per
+// candidate (samples as the dictionary generator evaluates them, FP64 sums).
+__global__ void __launch_bounds__(kLemThreads) k_lem_score(int cap, const double *__restrict__ cand,
+                                                          const int *__restrict__ ncand, const float *__restrict__ R,
+                                                          int Lp, int L, double inv_fs, double *__restrict__ score) {
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kLemThreads / 32) + (threadIdx.x >> 5);
+    if (i >= ncand[b]) return;
+    const double *th = cand + ((size_t)b * cap + i) * 4;
+    const double tc = th[0], fc = th[1], inv_dt = exp(-th[2]), c = th[3];
+    const float *r = R + (size_t)b * Lp;
+    double ru = 0.0, uu = 0.0;
+    for (int n = lane; n < L; n += 32) {
+        const double tau = ((double)n - tc) * inv_fs;
+        double ph = fma(c, tau, fc) * tau;
+        ph -= rint(ph);
+        const float x = (float)(tau * inv_dt);
+        const float u = expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
+        ru = fma((double)r[n], (double)u, ru);
+        uu = fma((double)u, (double)u, uu);
+    }
+    ru = warp_sum(ru);
+    uu = warp_sum(uu);
+    if (lane == 0) score[(size_t)b * cap + i] = (uu > 0.0 && isfinite(uu)) ? ru / sqrt(uu) : 0.0;
+}
+
+// 3. Top-k by |score| with duplicates skipped: one block per channel, k
+// rounds of a block-wide arg-max (largest |score|, then lowest index).
+__global__ void __launch_bounds__(kLemThreads) k_lem_topk(int cap, int k, const double *__restrict__ cand,
+                                                         const int *__restrict__ ncand,
+                                                         const double *__restrict__ score, double *__restrict__ kept,
+                                                         double *__restrict__ kept_score, int *__restrict__ nkept) {
+    __shared__ double kt[16][4];
+    __shared__ double bv_s[kLemThreads / 32];
+    __shared__ int bi_s[kLemThreads / 32];
+    __shared__ int m_sh;
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = ncand[b];
+    const double *cb = cand + (size_t)b * cap * 4;
+    const double *sb = score + (size_t)b * cap;
+    if (threadIdx.x == 0) m_sh = 0;
+    __syncthreads();
+    for (int round = 0; round < k; ++round) {
+        const int m = m_sh;
+        double bv = -1.0;
+        int bi = -1;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            bool dup = false;
+            for (int q = 0; q < m && !dup; ++q)
+                dup = cb[4 * i] == kt[q][0] && cb[4 * i + 1] == kt[q][1] && cb[4 * i + 2] == kt[q][2] &&
+                      cb[4 * i + 3] == kt[q][3];
+            const double v = fabs(sb[i]);
+            if (!dup && v == v && v > bv) {  // strided ascending: the first index wins ties
+                bv = v;
+                bi = i;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            bv_s[warp] = bv;
+            bi_s[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = -1.0;
+            int id = -1;
+            for (int w = 0; w < kLemThreads / 32; ++w)
+                if (bv_s[w] > v || (bv_s[w] == v && bi_s[w] >= 0 && (id < 0 || bi_s[w] < id))) {
+                    v = bv_s[w];
+                    id = bi_s[w];
+                }
+            if (id >= 0) {
+                for (int a = 0; a < 4; ++a) kt[m][a] = cb[4 * id + a];
+                kept_score[(size_t)b * k + m] = sb[id];
+                for (int a = 0; a < 4; ++a) kept[((size_t)b * k + m) * 4 + a] = cb[4 * id + a];
+                m_sh = m + 1;
+            }
+        }
+        __syncthreads();
+        if (m_sh == m) break;  // nothing left
+    }
+    if (threadIdx.x == 0) nkept[b] = m_sh;
+}
+
+// 4. Neighbourhood dictionaries of the kept candidates for one level.
+__global__ void __launch_bounds__(kLemThreads) k_lem_neigh(int cap, int k, LemBox box, LemLevel lev,
+                                                          const double *__restrict__ kept,
+                                                          const int *__restrict__ nkept, double *__restrict__ cand,
+                                                          int *__restrict__ ncand) {
+    const int b = blockIdx.x;
+    const int m = nkept[b];
+    int w[4], per = 1;
+    for (int a = 0; a < 4; ++a) {
+        w[a] = 2 * lev.radius[a] + 1;
+        per *= w[a];
+    }
+    const int total = m * per;
+    double *out = cand + (size_t)b * cap * 4;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int j = t / per;
+        int rest = t % per;
+        int o[4];
+        for (int a = 3; a >= 0; --a) {
+            o[a] = rest % w[a] - lev.radius[a];
+            rest /= w[a];
+        }
+        for (int a = 0; a < 4; ++a) {
+            double v = __dadd_rn(kept[((size_t)b * k + j) * 4 + a], __dmul_rn((double)o[a], lev.step[a]));
+            v = v < box.lo[a] ? box.lo[a] : (v > box.hi[a] ? box.hi[a] : v);
+            out[4 * t + a] = v;
+        }
+    }
+    if (threadIdx.x == 0) ncand[b] = total;
+}
+
+}  // namespace
+
+cudaError_t launch_lem_select(const LemConfig &cfg, int B, int order, const float *R, int Lp, int L, double fs,
+                              const LemBuffers &lb, cudaStream_t st) {
+    int npow2 = 1;
+    while (npow2 < cfg.n_coarse) npow2 <<= 1;
+    const size_t smem = (size_t)npow2 * (sizeof(uint64_t) + sizeof(uint32_t));
+    if (smem > 48 * 1024) {
+        cudaError_t ea = cudaFuncSetAttribute(k_lem_lhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea != cudaSuccess) return ea;
+    }
+    k_lem_lhs<<<B, kLemThreads, smem, st>>>(cfg.n_coarse, npow2, cfg.box, cfg.seed, order, lb.cap, lb.cand, lb.ncand);
+    cudaError_t e = cudaGetLastError();
+    const int per_block = kLemThreads / 32;
+    const double inv_fs = 1.0 / fs;
+    int n = cfg.n_coarse;
+    for (int lev = 0; lev <= cfg.levels && e == cudaSuccess; ++lev) {
+        if (lev > 0) {
+            k_lem_neigh<<<B, kLemThreads, 0, st>>>(lb.cap, cfg.top_k, cfg.box, cfg.level[lev], lb.kept, lb.nkept,
+                                                   lb.cand, lb.ncand);
+            e = cudaGetLastError();
+            int per = 1;
+            for (int a = 0; a < 4; ++a) per *= 2 * cfg.level[lev].radius[a] + 1;
+            n = cfg.top_k * per;
+        }
+        if (e != cudaSuccess) break;
+        dim3 grid((n + per_block - 1) / per_block, B);
+        k_lem_score<<<grid, kLemThreads, 0, st>>>(lb.cap, lb.cand, lb.ncand, R, Lp, L, inv_fs, lb.score);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        k_lem_topk<<<B, kLemThreads, 0, st>>>(lb.cap, cfg.top_k, lb.cand, lb.ncand, lb.score, lb.kept, lb.kept_score,
+                                              lb.nkept);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+int lem_kernels(const LemConfig &cfg) { return 1 + 2 + 3 * cfg.levels; }
+
+}  // namespace act

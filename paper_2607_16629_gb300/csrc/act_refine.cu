@@ -207,10 +207,11 @@ constexpr int kLineSearch = 20;  // Armijo halvings per iteration
 __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBox box, int steps, int Lp,
                                                           const float *__restrict__ R,
                                                           const unsigned long long *__restrict__ keys,
+                                                          const double *__restrict__ theta_in, int theta_in_stride,
                                                           double *__restrict__ theta_out) {
     constexpr int kWarps = kRefineThreads / 32;
-    __shared__ double z[4], gz[4], H[16], p[4];
-    __shared__ double cz[kWarps][4], cg[kWarps][4], cf[kWarps], ca[kWarps];
+    __shared__ double z[4], gz[4], H[16], p[4], th_cur[4];
+    __shared__ double cz[kWarps][4], cth[kWarps][4], cg[kWarps][4], cf[kWarps], ca[kWarps];
     __shared__ double f, gp, alpha0;
     __shared__ int state;  // -1: stop; otherwise the accepted warp (or kWarps: none yet)
     const int b = blockIdx.x;
@@ -221,14 +222,21 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
 
     if (threadIdx.x == 0) {
         double p0[4];
-        decode_params(ax, (int64_t)key_index(keys[b]), p0);
-        for (int i = 0; i < 4; ++i) z[i] = p0[i] / box.w[i];
+        if (theta_in) {
+            for (int i = 0; i < 4; ++i) p0[i] = theta_in[(size_t)b * theta_in_stride + i];
+        } else {
+            decode_params(ax, (int64_t)key_index(keys[b]), p0);
+        }
+        for (int i = 0; i < 4; ++i) {
+            z[i] = p0[i] / box.w[i];
+            th_cur[i] = p0[i];  // the parameters themselves: returned unchanged if no step is taken
+        }
         for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
     }
     __syncthreads();
     if (warp == 0) {
         double th[4];
-        for (int i = 0; i < 4; ++i) th[i] = z[i] * box.w[i];
+        for (int i = 0; i < 4; ++i) th[i] = th_cur[i];
         const EvalOut o = eval_warp(th, r, L, inv_fs);
         if (lane == 0) {
             const double sg = o.s < 0.0 ? -1.0 : 1.0;
@@ -280,6 +288,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
                     ca[warp] = a;
                     for (int i = 0; i < 4; ++i) {
                         cz[warp][i] = zz[i];
+                        cth[warp][i] = th[i];
                         cg[warp][i] = -sg * o.g[i] * box.w[i];
                     }
                 }
@@ -324,17 +333,19 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
             }
             for (int i = 0; i < 4; ++i) {
                 z[i] = cz[q][i];
+                th_cur[i] = cth[q][i];
                 gz[i] = cg[q][i];
             }
             f = cf[q];
         }
         __syncthreads();
     }
-    if (threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = z[threadIdx.x] * box.w[threadIdx.x];
+    if (threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = th_cur[threadIdx.x];
 }
 
 // Coefficient and residual update with the refined atom g(theta*) generated
-// on the fly (Eq. (4)); the record keeps the grid winner's flat index.
+// on the fly (Eq. (4)); the record keeps the grid winner's flat index (-1
+// when the selection did not come from the grid).
 __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float *__restrict__ R,
                                                                   __nv_bfloat16 *__restrict__ R16, int Lb,
                                                                   unsigned long long *__restrict__ keys, GridAxes ax,
@@ -391,11 +402,11 @@ __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float
         a.fc = fc;
         a.logdt = ld;
         a.c = cc;
-        a.flat_index = (int64_t)key_index(keys[b]);
+        a.flat_index = keys ? (int64_t)key_index(keys[b]) : -1;  // -1: not a grid atom
         atoms[(size_t)b * P + k] = a;
         coefs[(size_t)b * P + k] = c;
         energy[(size_t)b * (P + 1) + k + 1] = tot;
-        keys[b] = 0ull;
+        if (keys) keys[b] = 0ull;
         if (fb_count && b == 0) {
             fb_count[0] = 0;
             fb_count[1] = 0;
@@ -411,8 +422,8 @@ cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const f
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys, int B,
-                          double *theta_out, cudaStream_t st) {
+cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys,
+                          const double *theta_in, int theta_in_stride, int B, double *theta_out, cudaStream_t st) {
     RefineBox box;
     for (int i = 0; i < 4; ++i) {
         // scale = grid step; box = grid range widened by one step (an axis
@@ -423,7 +434,7 @@ cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R,
         box.lo[i] = st > 0.0 ? fmin(first, last) - st : first;
         box.hi[i] = st > 0.0 ? fmax(first, last) + st : first;
     }
-    k_refine<<<B, kRefineThreads, 0, st>>>(ax, box, steps, Lp, R, keys, theta_out);
+    k_refine<<<B, kRefineThreads, 0, st>>>(ax, box, steps, Lp, R, keys, theta_in, theta_in_stride, theta_out);
     return cudaGetLastError();
 }
 
