@@ -79,7 +79,17 @@ typedef struct {
  *                  64) for the tensor-core search; FP32 rows are used to
  *                  rescore candidates and for the update.
  *   ACT_DICT_AUTO: ACT_DICT_FP32.
- *   ACT_DICT_RECOMPUTE: reserved (atoms recomputed inside the search). */
+ *   ACT_DICT_RECOMPUTE: no atom rows are stored.  The real atom of Eq. (1)
+ *                  depends on n and tc only through n - tc, so on a grid
+ *                  whose time centres are whole samples (tc.lo and tc.step
+ *                  integers, step >= 1) every atom is a window of one
+ *                  template per (fc, logDt, c).  The build stores those
+ *                  templates (FP32, the lags the window can see) and one FP32
+ *                  scale 1/|u| per atom; the search (ACT_SEARCH_SHIFT) forms
+ *                  every atom's samples in-kernel from its template and scores
+ *                  all time centres of a template as one cross-correlation.
+ *                  Memory: about (N_fc N_logDt N_c)(S + 1)(ceil(L/S) + N_tc)
+ *                  x 4 bytes instead of K x L x 4 (S = tc.step). */
 typedef enum {
     ACT_DICT_AUTO = 0,
     ACT_DICT_FP32 = 1,
@@ -97,13 +107,17 @@ typedef enum {
  *                    n_samples <= 512).
  *   ACT_SEARCH_LEM:  the hierarchical search of act_lem_params (no
  *                    dictionary needed; act_atom.flat_index is -1).
+ *   ACT_SEARCH_SHIFT: the template search over an ACT_DICT_RECOMPUTE build
+ *                    (FP32 CUDA cores, every atom scored, the selected atom
+ *                    regenerated for the update).
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
- *                    FP32 otherwise. */
+ *                    SHIFT with ACT_DICT_RECOMPUTE, FP32 otherwise. */
 typedef enum {
     ACT_SEARCH_AUTO = 0,
     ACT_SEARCH_FP32 = 1,
     ACT_SEARCH_BF16 = 2,
-    ACT_SEARCH_LEM = 3
+    ACT_SEARCH_LEM = 3,
+    ACT_SEARCH_SHIFT = 4
 } act_search_mode;
 
 /* Settings of the LEM-inspired hierarchical search (Sec. VII-A, Fig. 7),
@@ -165,7 +179,8 @@ ACT_API act_status act_grid_size(const act_grid *grid, int64_t *n_atoms, int32_t
 /* Generates every atom on the device (Eq. (1) real part, unit l2 norm,
  * Sec. III-A) in the layout `mode` selects, replacing any earlier build.
  * Enqueued on cuda_stream.  Errors: ACT_ERR_OOM when the dictionary does not
- * fit (nothing is kept), ACT_ERR_UNSUPPORTED for ACT_DICT_RECOMPUTE. */
+ * fit (nothing is kept), ACT_ERR_UNSUPPORTED for ACT_DICT_RECOMPUTE on a grid
+ * whose time centres are not whole samples. */
 ACT_API act_status act_dictionary_build(act_grid *grid, act_dict_mode mode, void *cuda_stream);
 
 /* Sets the hierarchical search (ACT_SEARCH_LEM).  A new grid starts with the
@@ -199,13 +214,14 @@ ACT_API act_status act_decompose(act_grid *grid, const float *signals, int32_t c
 /* Projection P = D X^T of Sec. IV-A without the selection: scores
  * [channels][K] float32 (device memory) of every atom against each of
  * `channels` signals [channels][n_samples] (device memory), on the FP32
- * dictionary.  Errors as act_decompose. */
+ * dictionary or, for an ACT_DICT_RECOMPUTE build, by the template search.
+ * Errors as act_decompose. */
 ACT_API act_status act_project(act_grid *grid, const float *signals, int32_t channels, float *scores,
                        void *cuda_stream);
 
 /* Copies `count` FP32 dictionary rows starting at atom `first` into
  * out[count][n_samples] (device or host memory); waits when out is host
- * memory. */
+ * memory.  ACT_ERR_UNSUPPORTED for an ACT_DICT_RECOMPUTE build (no rows). */
 ACT_API act_status act_dictionary_rows(act_grid *grid, int64_t first, int64_t count, float *out,
                                void *cuda_stream);
 
@@ -248,7 +264,9 @@ ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double
  * allows) and, when the grid holds a BF16 dictionary and channels <= 128,
  * tile width (128 or 256 atoms) x pipeline depth (2 .. what fits in shared
  * memory) of the tensor-core GEMM, each timed with its tile selection and
- * rescan.  Results never depend on the configuration, only the speed does.
+ * rescan; with an ACT_DICT_RECOMPUTE build, every valid (lags per thread,
+ * warps) pair of the template search instead (act_set_shift_tuning).
+ * Results never depend on the configuration, only the speed does.
  * Waits for the device.  Later act_decompose calls use the chosen
  * configuration. */
 ACT_API act_status act_autotune(act_grid *grid, const float *signals, int32_t channels, void *cuda_stream,
@@ -265,6 +283,17 @@ ACT_API act_status act_get_tuning(const act_grid *grid, int32_t *gemv_ctas, int3
  * that fit).  Out-of-range values return ACT_ERR_INVALID_ARG. */
 ACT_API act_status act_set_tuning(act_grid *grid, int32_t gemv_ctas, int32_t bf16_tile_atoms,
                                   int32_t bf16_stages);
+
+/* Launch configuration of the template search (ACT_DICT_RECOMPUTE builds):
+ * lags_per_thread (8, 16 or 32) time centres per thread, `warps` (1..8)
+ * warps per CTA, whose product must divide the tc count rounded up to 32;
+ * the grid is one persistent wave (*ctas CTAs).  act_autotune on such a
+ * build times every valid pair and keeps the fastest.  Errors:
+ * ACT_ERR_NOT_BUILT without a template dictionary, ACT_ERR_INVALID_ARG for
+ * an invalid pair.  Setting makes ragged plans built on this grid stale. */
+ACT_API act_status act_set_shift_tuning(act_grid *grid, int32_t lags_per_thread, int32_t warps);
+ACT_API act_status act_get_shift_tuning(const act_grid *grid, int32_t *lags_per_thread, int32_t *warps,
+                                        int32_t *ctas);
 
 /* Kernel-level measurement hooks used by the benchmark.
  * act_set_profiling(grid, 1) makes later act_decompose graphs record CUDA

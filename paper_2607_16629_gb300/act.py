@@ -26,7 +26,7 @@ ACT_ERR_NOT_BUILT = 6
 ACT_ERR_UNSUPPORTED = 7
 
 ACT_DICT_AUTO, ACT_DICT_FP32, ACT_DICT_BF16, ACT_DICT_RECOMPUTE = 0, 1, 2, 3
-ACT_SEARCH_AUTO, ACT_SEARCH_FP32, ACT_SEARCH_BF16, ACT_SEARCH_LEM = 0, 1, 2, 3
+ACT_SEARCH_AUTO, ACT_SEARCH_FP32, ACT_SEARCH_BF16, ACT_SEARCH_LEM, ACT_SEARCH_SHIFT = 0, 1, 2, 3, 4
 
 # Every symbol include/act.h declares (checked by the CPU tests).
 EXPORTS = (
@@ -35,7 +35,7 @@ EXPORTS = (
     "act_dictionary_rows", "act_grid_status", "act_set_profiling", "act_profile_read",
     "act_bf16_stats", "act_destroy", "act_search_noalloc", "act_autotune", "act_get_tuning", "act_set_tuning",
     "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
-    "act_set_refinement", "act_chirplet_score", "act_set_lem",
+    "act_set_refinement", "act_chirplet_score", "act_set_lem", "act_set_shift_tuning", "act_get_shift_tuning",
 )
 
 
@@ -119,6 +119,9 @@ def load_library(path: str = LIB_PATH):
         lib.act_set_refinement.argtypes = [_P, ctypes.c_int32]
         lib.act_chirplet_score.argtypes = [ctypes.c_int32, ctypes.c_double, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
         lib.act_set_lem.argtypes = [_P, ctypes.POINTER(act_lem_params)]
+        lib.act_set_shift_tuning.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
+        lib.act_get_shift_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -291,6 +294,20 @@ def act_get_tuning(grid: int):
 def act_set_tuning(grid: int, gemv_ctas: int = 0, bf16_tile_atoms: int = 0, bf16_stages: int = 0) -> None:
     _check(load_library().act_set_tuning(grid, int(gemv_ctas), int(bf16_tile_atoms), int(bf16_stages)),
            "act_set_tuning")
+
+
+def act_set_shift_tuning(grid: int, lags_per_thread: int, warps: int) -> None:
+    _check(load_library().act_set_shift_tuning(grid, int(lags_per_thread), int(warps)), "act_set_shift_tuning")
+
+
+def act_get_shift_tuning(grid: int):
+    """(lags_per_thread, warps, ctas) of the template search."""
+    a = ctypes.c_int32()
+    b = ctypes.c_int32()
+    c = ctypes.c_int32()
+    _check(load_library().act_get_shift_tuning(grid, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "act_get_shift_tuning")
+    return a.value, b.value, c.value
 
 
 def act_ragged_plan_create(grids, offsets, n_atoms: int) -> int:

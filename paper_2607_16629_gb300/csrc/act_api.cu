@@ -116,6 +116,7 @@ struct act_grid {
     int *status = nullptr;
     long long *stats = nullptr;
     Bf16Search *bf16 = nullptr;
+    ShiftPlan shift;       // template dictionary (ACT_DICT_RECOMPUTE)
     int gemv_grid = 0;
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
     LemConfig lem;         // hierarchical search settings
@@ -165,6 +166,9 @@ void free_dictionary(act_grid *g) {
     g->bf16 = nullptr;
     free_dev(g->d32);
     free_dev(g->d16);
+    free_dev(g->shift.tpl);
+    free_dev(g->shift.scale);
+    g->shift = ShiftPlan();
     g->built = -1;
 }
 
@@ -265,10 +269,21 @@ act_status lem_configure(act_grid *g, const act_lem_params *p) {
 }
 
 act_search_mode effective_search(const act_grid *g) {
-    if (g->search == ACT_SEARCH_LEM) return ACT_SEARCH_LEM;
-    if (g->search == ACT_SEARCH_FP32) return ACT_SEARCH_FP32;
-    if (g->search == ACT_SEARCH_BF16) return ACT_SEARCH_BF16;
-    return g->built == ACT_DICT_BF16 ? ACT_SEARCH_BF16 : ACT_SEARCH_FP32;
+    if (g->search != ACT_SEARCH_AUTO) return g->search;
+    if (g->built == ACT_DICT_BF16) return ACT_SEARCH_BF16;
+    if (g->built == ACT_DICT_RECOMPUTE) return ACT_SEARCH_SHIFT;
+    return ACT_SEARCH_FP32;
+}
+
+// Whether the grid holds what `mode` searches.
+bool search_available(const act_grid *g, act_search_mode mode) {
+    switch (mode) {
+        case ACT_SEARCH_LEM: return true;
+        case ACT_SEARCH_FP32: return g->d32 != nullptr;
+        case ACT_SEARCH_BF16: return g->bf16 != nullptr && g->d16 != nullptr;
+        case ACT_SEARCH_SHIFT: return g->shift.tpl != nullptr;
+        default: return false;
+    }
 }
 
 // Records the whole decomposition (init + P orders) on stream st (being captured).
@@ -294,6 +309,10 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             ACT_CK(launch_lem_select(g->lem, B, k, w.R, g->Lp, g->L, g->desc.fs, w.lem, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += lem_kernels(g->lem);
+        } else if (mode == ACT_SEARCH_SHIFT) {
+            ACT_CK(launch_shift_search(g->shift, w.R, g->Lp, g->L, B, w.keys, nullptr, g->status, st));
+            if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+            kernels += 1;
         } else if (bf16) {
             ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
@@ -319,6 +338,11 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             ACT_CK(launch_update_refined(g->Lp, w.R, R16, g->Lb, B, w.keys, g->ax, w.theta, k, P, w.atoms, w.coefs,
                                          w.energy, bf16 ? w.fb_count : nullptr, st));
             kernels += 2;
+        } else if (mode == ACT_SEARCH_SHIFT) {
+            // no stored rows: the selected grid atom is generated for the update
+            ACT_CK(launch_update_refined(g->Lp, w.R, nullptr, g->Lb, B, w.keys, g->ax, nullptr, k, P, w.atoms,
+                                         w.coefs, w.energy, nullptr, st));
+            ++kernels;
         } else {
             ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
                                  w.energy, bf16 ? w.fb_count : nullptr, st));
@@ -494,17 +518,40 @@ act_status act_grid_size(const act_grid *g, int64_t *n_atoms, int32_t *row_strid
     return ACT_OK;
 }
 
+// Template dictionary: per (fc, logDt, c) the samples the window can see,
+// and one FP32 scale per atom.
+static act_status build_templates(act_grid *g, cudaStream_t st) {
+    ShiftPlan sp;
+    if (shift_plan(sp, g->ax) != cudaSuccess) return ACT_ERR_UNSUPPORTED;
+    if (shift_default_config(sp, g->sm_count) != cudaSuccess) return ACT_ERR_UNSUPPORTED;
+    const size_t bt = sizeof(float) * (size_t)sp.TB * sp.Sa * sp.rows * 32;
+    const size_t bs = sizeof(float) * (size_t)sp.TB * sp.NtcP * 32;
+    cudaError_t e = cudaMalloc(&sp.tpl, bt);
+    if (e == cudaSuccess) e = cudaMalloc(&sp.scale, bs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_dev(sp.tpl);
+        note_error("template dictionary", e);
+        return ACT_ERR_OOM;
+    }
+    g->shift = sp;
+    ACT_CK(cudaMemsetAsync(g->degenerate, 0, sizeof(unsigned long long), st));
+    ACT_CK(launch_shift_build(g->shift, g->ax, g->degenerate, g->sm_count, st));
+    g->built = ACT_DICT_RECOMPUTE;
+    return ACT_OK;
+}
+
 act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stream) {
     if (!g) return ACT_ERR_INVALID_ARG;
-    if (mode == ACT_DICT_RECOMPUTE) return ACT_ERR_UNSUPPORTED;
     if (mode == ACT_DICT_AUTO) mode = ACT_DICT_FP32;
-    if (mode != ACT_DICT_FP32 && mode != ACT_DICT_BF16) return ACT_ERR_INVALID_ARG;
+    if (mode != ACT_DICT_FP32 && mode != ACT_DICT_BF16 && mode != ACT_DICT_RECOMPUTE) return ACT_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     ACT_CK(cudaStreamSynchronize(st));
     drop_graphs(g);
     ++g->generation;  // ragged plans built on the old dictionary are stale
     free_dictionary(g);
+    if (mode == ACT_DICT_RECOMPUTE) return build_templates(g, st);
     const size_t b32 = sizeof(float) * (size_t)g->K * g->Lp;
     cudaError_t e = cudaMalloc(&g->d32, b32);
     if (e != cudaSuccess) {
@@ -554,7 +601,7 @@ act_status act_set_lem(act_grid *g, const act_lem_params *params) {
 }
 
 act_status act_set_search(act_grid *g, act_search_mode mode) {
-    if (!g || (int)mode < 0 || (int)mode > 3) return ACT_ERR_INVALID_ARG;
+    if (!g || (int)mode < 0 || (int)mode > 4) return ACT_ERR_INVALID_ARG;
     g->search = mode;
     return ACT_OK;
 }
@@ -564,14 +611,11 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
                          void *cuda_stream) {
     if (!g || !signals || channels < 1 || n_atoms < 1) return ACT_ERR_INVALID_ARG;
     const act_search_mode mode = effective_search(g);
-    if (g->built < 0 && mode != ACT_SEARCH_LEM) return ACT_ERR_NOT_BUILT;
+    if (!search_available(g, mode)) return ACT_ERR_NOT_BUILT;
     if (mode == ACT_SEARCH_LEM && n_atoms > 4096) return ACT_ERR_UNSUPPORTED;  // draw counter holds 12 bits of order
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (mode == ACT_SEARCH_BF16) {
-        if (!g->bf16 || !g->d16) return ACT_ERR_NOT_BUILT;
-        if (channels > 128) return ACT_ERR_UNSUPPORTED;
-    }
+    if (mode == ACT_SEARCH_BF16 && channels > 128) return ACT_ERR_UNSUPPORTED;
     act_status s = ensure_work(g, channels, n_atoms);
     if (s != ACT_OK) return s;
     if (mode == ACT_SEARCH_LEM && (s = ensure_lem(g, g->w, channels)) != ACT_OK) return s;
@@ -606,13 +650,18 @@ act_status act_project(act_grid *g, const float *signals, int32_t channels, floa
     if (s != ACT_OK) return s;
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, nullptr, g->Lb, nullptr, nullptr, 1, g->status, st));
-    ACT_CK(launch_project(g->d32, g->K, g->Lp, g->w.R, channels, scores, g->status, g->gemv_grid, st));
+    if (g->built == ACT_DICT_RECOMPUTE) {
+        ACT_CK(launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, nullptr, scores, g->status, st));
+    } else {
+        ACT_CK(launch_project(g->d32, g->K, g->Lp, g->w.R, channels, scores, g->status, g->gemv_grid, st));
+    }
     return ACT_OK;
 }
 
 act_status act_dictionary_rows(act_grid *g, int64_t first, int64_t count, float *out, void *cuda_stream) {
     if (!g || !out || first < 0 || count < 0 || first + count > g->K) return ACT_ERR_INVALID_ARG;
     if (g->built < 0) return ACT_ERR_NOT_BUILT;
+    if (!g->d32) return ACT_ERR_UNSUPPORTED;  // template dictionary: no rows
     if (count == 0) return ACT_OK;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -634,11 +683,71 @@ act_status act_grid_status(act_grid *g, void *cuda_stream) {
     return ACT_OK;
 }
 
+// Template search: every valid (lags per thread, warps per CTA) pair.
+static act_status autotune_shift(act_grid *g, int channels, cudaStream_t st, double *best_ms) {
+    cudaEvent_t e0, e1;
+    ACT_CK(cudaEventCreate(&e0));
+    ACT_CK(cudaEventCreate(&e1));
+    const int reps = 3;
+    const ShiftPlan keep = g->shift;
+    double best = 1e30;
+    int bJ = keep.J, bW = keep.W;
+    cudaError_t err = cudaSuccess;
+    static const int Js[] = {8, 16, 32};
+    for (int J : Js) {
+        for (int W = 1; W <= 8 && err == cudaSuccess; ++W) {
+            if (!shift_config_valid(g->shift, J, W)) continue;
+            if (shift_configure(g->shift, J, W, g->sm_count) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            for (int pass = 0; pass < 2 && err == cudaSuccess; ++pass) {  // pass 0 warms up
+                err = cudaEventRecord(e0, st);
+                for (int r = 0; r < reps && err == cudaSuccess; ++r)
+                    err = launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, g->w.keys, nullptr, g->status,
+                                              st);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            }
+            float t = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+            if (err == cudaSuccess && t / reps < best) {
+                best = t / reps;
+                bJ = J;
+                bW = W;
+            }
+        }
+    }
+    if (err == cudaSuccess) err = shift_configure(g->shift, bJ, bW, g->sm_count);
+    if (err == cudaSuccess) err = cudaMemsetAsync(g->w.keys, 0, sizeof(unsigned long long) * (size_t)channels, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) {
+        g->shift.J = keep.J;
+        shift_configure(g->shift, keep.J, keep.W, g->sm_count);
+        note_error("act_autotune", err);
+        return ACT_ERR_CUDA;
+    }
+    drop_graphs(g);
+    ++g->generation;
+    if (best_ms) *best_ms = best;
+    return ACT_OK;
+}
+
 act_status act_autotune(act_grid *g, const float *signals, int32_t channels, void *cuda_stream, double *best_ms) {
     if (!g || !signals || channels < 1) return ACT_ERR_INVALID_ARG;
     if (g->built < 0) return ACT_ERR_NOT_BUILT;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (g->built == ACT_DICT_RECOMPUTE) {
+        act_status s = ensure_work(g, channels, 1);
+        if (s != ACT_OK) return s;
+        ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
+        ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, nullptr, g->Lb, g->w.keys, nullptr, 1, g->status,
+                           st));
+        return autotune_shift(g, channels, st, best_ms);
+    }
     const bool bf16 = g->bf16 != nullptr && channels <= 128;
     act_status s = ensure_work(g, channels, 1);
     if (s != ACT_OK) return s;
@@ -749,6 +858,29 @@ act_status act_set_tuning(act_grid *g, int32_t gemv_ctas_in, int32_t bf16_tile_a
             cudaGetLastError();
             return ACT_ERR_INVALID_ARG;
         }
+    }
+    drop_graphs(g);
+    ++g->generation;
+    return ACT_OK;
+}
+
+act_status act_get_shift_tuning(const act_grid *g, int32_t *lags_per_thread, int32_t *warps, int32_t *ctas) {
+    if (!g) return ACT_ERR_INVALID_ARG;
+    if (!g->shift.tpl) return ACT_ERR_NOT_BUILT;
+    if (lags_per_thread) *lags_per_thread = g->shift.J;
+    if (warps) *warps = g->shift.W;
+    if (ctas) *ctas = g->shift.ctas;
+    return ACT_OK;
+}
+
+act_status act_set_shift_tuning(act_grid *g, int32_t lags_per_thread, int32_t warps) {
+    if (!g) return ACT_ERR_INVALID_ARG;
+    if (!g->shift.tpl) return ACT_ERR_NOT_BUILT;
+    DeviceGuard dg(g->device);
+    if (!shift_config_valid(g->shift, lags_per_thread, warps)) return ACT_ERR_INVALID_ARG;
+    if (shift_configure(g->shift, lags_per_thread, warps, g->sm_count) != cudaSuccess) {
+        cudaGetLastError();
+        return ACT_ERR_INVALID_ARG;
     }
     drop_graphs(g);
     ++g->generation;
@@ -901,6 +1033,7 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
         act_grid *g = gr.g;
         gr.mode = effective_search(g);
         if (gr.mode == ACT_SEARCH_BF16 && (!g->bf16 || B > 128)) gr.mode = ACT_SEARCH_FP32;
+        if (!search_available(g, gr.mode)) return ACT_ERR_NOT_BUILT;
         act_status s = alloc_work(g, gr.w, B, p->P);
         if (s != ACT_OK) return s;
         if (gr.mode == ACT_SEARCH_LEM && (s = ensure_lem(g, gr.w, B)) != ACT_OK) return s;

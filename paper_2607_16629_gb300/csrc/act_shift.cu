@@ -1,0 +1,412 @@
+// Template ("shift-correlation") dictionary and search.
+//
+// The real atom of Eq. (1) depends on the sample index n and the time centre
+// tc only through m = n - tc.  On a grid whose tc values are whole samples,
+// tc_j = tc0 + S j, every atom is therefore a window of one template
+// u_t(m) per (fc, logDt, c) triple t, and the scores of all atoms that share
+// t are a cross-correlation:
+//     <r, u_{t, tc_j}> = sum_n r[n] u_t(n - tc0 - S j).
+// Nothing of size K x L is stored: the templates (samples of u_t over the
+// lags the window can see) and one FP32 scale 1/|u_{t,tc_j}| per atom are
+// built once; the search forms every atom's samples in-kernel from its
+// template held in shared memory.
+//
+// Polyphase form.  Writing n = a + S p (a = 0..Sa-1, Sa = min(S, L): a
+// phase a >= L holds no sample) and k = p - j,
+//     s_j = sum_a sum_p r_a[p] v_a[p - j],  r_a[p] = r[a + S p],
+//                                           v_a[k] = u_t(a - tc0 + S k),
+// one 1-D correlation per phase a with unit stride in p and j.
+//
+// Layouts (FP32):
+//   templates [TB][Sa][rows][32]: block tb holds templates 32 tb .. 32 tb + 31
+//     (lane = template), row rho holds k = rho - (NtcP - 1); rows =
+//     NtcP + P - 1, NtcP = Ntc rounded up to 32, P = ceil(L / S) rounded up
+//     to 8.  Zero for padding templates.
+//   scales [TB][NtcP][32]: 1/|u| in FP32 from an FP64 sum over the window,
+//     0 for a degenerate atom, a padding template or a padding lag.
+// The flat index of (lag j, template t) is j T + t, the order of the grid.
+//
+// Search: persistent CTAs of W warps take units (channel b, lag group g of
+// W J lags, template block tb).  Per unit and phase, one bulk copy brings
+// the Kc = W J + P - 1 template rows the group needs into shared memory
+// (two stages: the next copy is in flight while the current one is used).
+// Warp w computes lags g W J + w J + q, q < J, for the block's 32 templates:
+// each thread keeps J accumulators and a J-entry register window of its
+// template that slides by one row per p, so every p costs one shared load of
+// the template, one broadcast load of r_a[p] and J FMAs.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "act_device.cuh"
+#include "act_internal.cuh"
+
+namespace act {
+
+namespace {
+
+constexpr int kShiftMaxThreads = 256;
+
+struct ShiftArgs {
+    const float *tpl;
+    const float *scale;
+    const float *R;
+    int Lp, L, B;
+    int S, Sa, P, T, TB, NtcP, Ntc, rows;
+    int W, G, Kc;
+    int64_t K;
+    unsigned long long *keys;
+    float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
+    int *status;
+};
+
+// Template value u_t(m), computed exactly as the dictionary generator
+// computes sample n of an atom with n - tc = m.
+__device__ __forceinline__ float template_sample(double m, double inv_fs, double fc, double inv_dt, double chirp) {
+    const double tau = m * inv_fs;
+    double ph = fma(chirp, tau, fc) * tau;
+    ph -= rint(ph);
+    const float x = (float)(tau * inv_dt);
+    return expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
+}
+
+// One thread per stored template value.
+__global__ void __launch_bounds__(256) k_shift_templates(GridAxes ax, int S, int Sa, int tc0, int NtcP, int rows,
+                                                         int T, int64_t total, float *__restrict__ tpl) {
+    const double inv_fs = 1.0 / ax.fs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(i & 31);
+        const int64_t rest = i >> 5;
+        const int rho = (int)(rest % rows);
+        const int64_t rest2 = rest / rows;
+        const int a = (int)(rest2 % Sa);
+        const int64_t tb = rest2 / Sa;
+        const int64_t t = tb * 32 + lane;
+        float v = 0.0f;
+        if (t < T) {
+            double p[4];
+            decode_params(ax, t, p);  // flat index t has i_tc = 0: p[1..3] are the template's axes
+            const int64_t k = (int64_t)rho - (NtcP - 1);
+            const int64_t m = (int64_t)a - tc0 + (int64_t)S * k;
+            v = template_sample((double)m, inv_fs, p[1], exp(-p[2]), p[3]);
+        }
+        tpl[i] = v;
+    }
+}
+
+// One thread per (template block, lag, lane): |u|^2 over the window in FP64.
+__global__ void __launch_bounds__(256) k_shift_scales(int S, int Sa, int L, int NtcP, int Ntc, int rows, int T,
+                                                      int64_t total, const float *__restrict__ tpl,
+                                                      float *__restrict__ scale,
+                                                      unsigned long long *__restrict__ degenerate) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(i & 31);
+        const int64_t rest = i >> 5;
+        const int j = (int)(rest % NtcP);
+        const int64_t tb = rest / NtcP;
+        const int64_t t = tb * 32 + lane;
+        float sc = 0.0f;
+        if (t < T && j < Ntc) {
+            double e = 0.0;
+            const float *base = tpl + (size_t)tb * Sa * rows * 32 + lane;
+            for (int n = 0; n < L; ++n) {
+                const int a = n % S, p = n / S;
+                const float u = base[((size_t)a * rows + (p - j + NtcP - 1)) * 32];
+                e = fma((double)u, (double)u, e);
+            }
+            if (e > 0.0 && isfinite(e)) {
+                sc = (float)(1.0 / sqrt(e));
+            } else if (degenerate) {
+                atomicAdd(degenerate, 1ull);
+            }
+        }
+        scale[i] = sc;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+template <int J>
+__global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) {
+    extern __shared__ __align__(128) float sm[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ unsigned long long red[kShiftMaxThreads / 32];
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int W = A.W;
+    const int stage_floats = (A.Kc + 1) * 32;  // one slack row: the window's last look-ahead load
+    float *rpoly = sm + 2 * stage_floats;  // [Sa][P], after the two stages
+    const int units_per_b = A.G * A.TB;
+    const int n_units = A.B * units_per_b;
+    if ((int)blockIdx.x >= n_units) return;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const uint32_t chunk_bytes = (uint32_t)A.Kc * 32u * 4u;
+    auto issue = [&](int u, int a, int s) {
+        const int rem = u % units_per_b;
+        const int g = rem / A.TB, tb = rem % A.TB;
+        const int rho0 = A.NtcP - (g + 1) * W * J;
+        const float *src = A.tpl + (((size_t)tb * A.Sa + a) * A.rows + rho0) * 32;
+        mbar_expect_tx(&bar[s], chunk_bytes);
+        bulk_g2s(sm + s * stage_floats, src, chunk_bytes, &bar[s]);
+    };
+
+    if (threadIdx.x == 0) issue(blockIdx.x, 0, 0);
+    int c = 0;  // chunks consumed by this CTA
+    int cur_b = -1;
+    unsigned long long best = 0ull;
+
+    auto flush = [&](int b) {
+        const unsigned long long v = warp_max_u64(best);
+        if (lane == 0) red[w] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = 0ull;
+            for (int i = 0; i < W; ++i) m = red[i] > m ? red[i] : m;
+            if (m) atomicMax(A.keys + b, m);
+        }
+        best = 0ull;
+    };
+
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int b = u / units_per_b;
+        const int rem = u % units_per_b;
+        const int g = rem / A.TB, tb = rem % A.TB;
+        if (b != cur_b) {
+            if (cur_b >= 0 && !A.scores) flush(cur_b);
+            const float *r = A.R + (size_t)b * A.Lp;
+            for (int i = threadIdx.x; i < A.Sa * A.P; i += blockDim.x) {
+                const int a = i / A.P, p = i % A.P;
+                const int n = a + A.S * p;
+                rpoly[i] = n < A.L ? r[n] : 0.0f;
+            }
+            __syncthreads();
+            cur_b = b;
+        }
+        float acc[J];
+#pragma unroll
+        for (int q = 0; q < J; ++q) acc[q] = 0.0f;
+
+        for (int a = 0; a < A.Sa; ++a) {
+            if (threadIdx.x == 0) {
+                // the next chunk goes to the other stage, freed by the barrier
+                // that ended the previous chunk
+                if (a + 1 < A.Sa) issue(u, a + 1, (c + 1) & 1);
+                else if (u + (int)gridDim.x < n_units) issue(u + gridDim.x, 0, (c + 1) & 1);
+            }
+            const int ok = mbar_wait(&bar[c & 1], (uint32_t)((c >> 1) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(A.status, kFlagTimeout);
+                    // bounded: let the copies in flight land before exiting
+                    mbar_wait(&bar[c & 1], (uint32_t)((c >> 1) & 1));
+                    const bool next = a + 1 < A.Sa || u + (int)gridDim.x < n_units;
+                    if (next) mbar_wait(&bar[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1));
+                }
+                return;
+            }
+            const float *ts = sm + (c & 1) * stage_floats + lane;
+            const float *rp = rpoly + a * A.P;
+            const int base = (W - w) * J - 1;  // chunk row of (p = 0, q = 0)
+            float win[J];                        // slot (p - q) mod J holds row base + p - q
+#pragma unroll
+            for (int q = 0; q < J; ++q) win[(J - q) % J] = ts[(base - q) * 32];
+            for (int pb = 0; pb < A.P; pb += J) {
+#pragma unroll
+                for (int i = 0; i < J; i += 4) {
+                    const float4 r4 = *reinterpret_cast<const float4 *>(rp + pb + i);
+                    const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                        for (int q = 0; q < J; ++q) acc[q] = fmaf(rv[e], win[(i + e - q + J) % J], acc[q]);
+                        win[(i + e + 1) % J] = ts[(base + pb + i + e + 1) * 32];
+                    }
+                }
+            }
+            __syncthreads();
+            ++c;
+        }
+
+        // scores of this unit's atoms; the lowest lag wins ties (q ascending)
+        const int t = tb * 32 + lane;
+        if (t < A.T) {
+            const float *scl = A.scale + ((size_t)tb * A.NtcP + g * W * J + w * J) * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < J; ++q) {
+                const int j = g * W * J + w * J + q;
+                if (j < A.Ntc) {
+                    const float s = acc[q] * scl[q * 32];
+                    const uint32_t flat = (uint32_t)j * (uint32_t)A.T + (uint32_t)t;
+                    if (A.scores) {
+                        A.scores[(size_t)b * A.K + flat] = s;
+                    } else {
+                        const float x = fabsf(s);
+                        if (x == x) {
+                            const unsigned long long key = pack_key(x, flat);
+                            best = key > best ? key : best;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (cur_b >= 0 && !A.scores) flush(cur_b);
+}
+
+template <int J>
+cudaError_t set_smem(size_t smem) {
+    static size_t set = 0;
+    if (smem <= 48 * 1024 || smem <= set) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_shift_search<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set = smem;
+    return e;
+}
+
+size_t shift_smem(const ShiftPlan &sp, int J, int W) {
+    const int Kc = W * J + sp.P - 1;
+    return sizeof(float) * ((size_t)2 * (Kc + 1) * 32 + (size_t)sp.Sa * sp.P);
+}
+
+int shift_occupancy(const ShiftPlan &sp, int J, int W, size_t smem) {
+    int per_sm = 0;
+    cudaError_t e;
+    switch (J) {
+        case 8: e = set_smem<8>(smem); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shift_search<8>, 32 * W, smem); break;
+        case 16: e = set_smem<16>(smem); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shift_search<16>, 32 * W, smem); break;
+        case 32: e = set_smem<32>(smem); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shift_search<32>, 32 * W, smem); break;
+        default: return 0;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
+}  // namespace
+
+bool shift_config_valid(const ShiftPlan &sp, int J, int W) {
+    if (J != 8 && J != 16 && J != 32) return false;
+    if (W < 1 || W > kShiftMaxThreads / 32) return false;
+    if (sp.NtcP % (W * J) != 0 || sp.P % J != 0) return false;
+    return shift_smem(sp, J, W) <= 227 * 1024;
+}
+
+cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax) {
+    const double lo = ax.lo[0], step = ax.step[0];
+    // whole-sample time centres only: tc0 and S integers, S >= 1
+    if (!(step >= 1.0) || step != floor(step) || lo != floor(lo) || fabs(lo) > 1e9 || step > 1e6)
+        return cudaErrorNotSupported;
+    sp.S = (int)step;
+    sp.Sa = sp.S < ax.L ? sp.S : ax.L;
+    sp.tc0 = (int)lo;
+    sp.Ntc = ax.count[0];
+    sp.NtcP = (sp.Ntc + 31) / 32 * 32;
+    sp.P = ((ax.L + sp.S - 1) / sp.S + 7) / 8 * 8;
+    const int64_t T = (int64_t)ax.count[1] * ax.count[2] * ax.count[3];
+    const int64_t K = T * ax.count[0];
+    if (K >= 0xFFFFFFFFll || T > (1ll << 30)) return cudaErrorNotSupported;
+    sp.T = (int)T;
+    sp.TB = (int)((T + 31) / 32);
+    sp.rows = sp.NtcP + sp.P - 1;
+    sp.K = K;
+    return cudaSuccess;
+}
+
+cudaError_t shift_configure(ShiftPlan &sp, int J, int W, int sm_count) {
+    if (!shift_config_valid(sp, J, W)) return cudaErrorInvalidValue;
+    const size_t smem = shift_smem(sp, J, W);
+    const int per_sm = shift_occupancy(sp, J, W, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    sp.J = J;
+    sp.W = W;
+    sp.G = sp.NtcP / (W * J);
+    sp.Kc = W * J + sp.P - 1;
+    sp.smem = smem;
+    sp.ctas_per_sm = per_sm;
+    sp.ctas = per_sm * sm_count;
+    return cudaSuccess;
+}
+
+cudaError_t shift_default_config(ShiftPlan &sp, int sm_count) {
+    // widest register window first, then the most warps that divide the lags
+    static const int Js[] = {32, 16, 8};
+    static const int Ws[] = {4, 8, 2, 1};
+    for (int J : Js)
+        for (int W : Ws)
+            if (shift_config_valid(sp, J, W) && shift_configure(sp, J, W, sm_count) == cudaSuccess)
+                return cudaSuccess;
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned long long *degenerate,
+                               int sm_count, cudaStream_t st) {
+    const int64_t nt = (int64_t)sp.TB * sp.Sa * sp.rows * 32;
+    int64_t blocks = (nt + 255) / 256;
+    if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
+    k_shift_templates<<<(int)blocks, 256, 0, st>>>(ax, sp.S, sp.Sa, sp.tc0, sp.NtcP, sp.rows, sp.T, nt, sp.tpl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t ns = (int64_t)sp.TB * sp.NtcP * 32;
+    blocks = (ns + 255) / 256;
+    if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
+    k_shift_scales<<<(int)blocks, 256, 0, st>>>(sp.S, sp.Sa, ax.L, sp.NtcP, sp.Ntc, sp.rows, sp.T, ns, sp.tpl,
+                                                 sp.scale, degenerate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
+                                float *scores, int *status, cudaStream_t st) {
+    if (sp.J == 0 || !sp.tpl) return cudaErrorInvalidValue;
+    ShiftArgs A;
+    A.tpl = sp.tpl;
+    A.scale = sp.scale;
+    A.R = R;
+    A.Lp = Lp;
+    A.L = L;
+    A.B = B;
+    A.S = sp.S;
+    A.Sa = sp.Sa;
+    A.P = sp.P;
+    A.T = sp.T;
+    A.TB = sp.TB;
+    A.NtcP = sp.NtcP;
+    A.Ntc = sp.Ntc;
+    A.rows = sp.rows;
+    A.W = sp.W;
+    A.G = sp.G;
+    A.Kc = sp.Kc;
+    A.K = sp.K;
+    A.keys = keys;
+    A.scores = scores;
+    A.status = status;
+    const int64_t units = (int64_t)B * sp.G * sp.TB;
+    if (units > INT32_MAX) return cudaErrorInvalidValue;
+    const int grid = (int)(units < sp.ctas ? units : sp.ctas);
+    const int threads = 32 * sp.W;
+    switch (sp.J) {
+        case 8: k_shift_search<8><<<grid, threads, sp.smem, st>>>(A); break;
+        case 16: k_shift_search<16><<<grid, threads, sp.smem, st>>>(A); break;
+        case 32: k_shift_search<32><<<grid, threads, sp.smem, st>>>(A); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace act
