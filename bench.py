@@ -310,7 +310,11 @@ def run_ours(args):
            "h2d_bytes_per_step": hs.numel() * 4,
            "d2h_bytes_per_step": ha.numel() + hc.numel() * 4 + hr.numel() * 4 + he.numel() * 8}
     act.act_destroy(h)
+    fp32_picks = atoms.clone()
 
+    shift = None
+    if not args.no_shift:
+        shift = bench_shift(args, dev, stream, ms / args.steps, fp32_picks, clk.summary())
     bf16 = None
     if not args.no_bf16:
         bf16 = bench_bf16(args, dev, stream, peaks, peak_kind)
@@ -337,6 +341,8 @@ def run_ours(args):
                 "dictionary_build_ms": build_ms,
                 "roofline": roofline, "e2e": e2e, "gpu_launches": kernels * args.steps,
                 "clocks": clk.summary()}
+        if shift is not None:
+            line["template_shift"] = shift
         if bf16 is not None:
             line["bf16_batched"] = bf16
         if ragged is not None:
@@ -350,6 +356,100 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks):
+    """Template dictionary + shift-correlation search on the headline
+    workload (one EEG-like channel, 2,097,152 atoms, 20 orders): no atom rows
+    stored, every atom formed in-kernel from its (fc, logDt, c) template.
+    Reported beside the FP32 GEMV on the same signal, and on 64 channels."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    grid = synth.grid_eeg()
+    P, K, L = 20, grid.n_atoms, grid.n_samples
+    sig1 = torch.tensor(synth.eeg_like_signal(2, 0)[0][None, :], dtype=torch.float32, device=dev)
+    h = act.act_grid_create(grid, dev.index)
+    try:
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE, stream)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        build_ms = b0.elapsed_time(b1)
+        act.act_autotune(h, sig1, 1, stream)
+        lags, warps, ctas = act.act_get_shift_tuning(h)
+        out = [torch.empty((1, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+               torch.empty((1, P), dtype=torch.float32, device=dev),
+               torch.empty((1, L), dtype=torch.float32, device=dev),
+               torch.empty((1, P + 1), dtype=torch.float64, device=dev)]
+        for _ in range(3):
+            act.act_decompose(h, sig1, 1, P, *out, stream)
+        steps = args.steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            act.act_decompose(h, sig1, 1, P, *out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        same = bool(torch.equal(act.atom_indices(out[0]), act.atom_indices(fp32_atoms)))
+        act.act_set_profiling(h, True)
+        act.act_decompose(h, sig1, 1, P, *out, stream)
+        core_ms, core_n = 0.0, 0
+        for _ in range(steps):
+            act.act_decompose(h, sig1, 1, P, *out, stream)
+            _, c_i, n_i, kernels = act.act_profile_read(h)
+            core_ms += c_i
+            core_n += n_i
+        act.act_set_profiling(h, False)
+        # 64 channels on the same templates
+        w3 = synth.workload_c3()
+        B = w3.signals.shape[0]
+        sig64 = torch.tensor(w3.signals, dtype=torch.float32, device=dev)
+        out64 = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+                 torch.empty((B, P), dtype=torch.float32, device=dev),
+                 torch.empty((B, L), dtype=torch.float32, device=dev),
+                 torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
+        act.act_decompose(h, sig64, B, P, *out64, stream)
+        n64 = 3
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n64):
+            act.act_decompose(h, sig64, B, P, *out64, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / n64
+        st = act.act_grid_status(h, stream)
+        if st != act.ACT_OK:
+            raise RuntimeError(act.status_name(st))
+    finally:
+        act.act_destroy(h)
+    T = grid.fc.count * grid.logdt.count * grid.c.count
+    S, Ntc = int(grid.tc.step), grid.tc.count
+    rows = (Ntc + 31) // 32 * 32 + (L + S - 1) // S - 1
+    tpl_bytes = T * S * rows * 4 + T * ((Ntc + 31) // 32 * 32) * 4
+    flops = 2.0 * K * L
+    avg = core_ms / max(1, core_n)
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (avg / 1e3) / 1e12
+    return {"workload": "eeg_like_1ch_n512_k2097152_p20 (the headline signal)",
+            "value": K * P / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "speedup_vs_fp32_gemv": fp32_ms_per_step / ms,
+            "same_selections_as_fp32_gemv": same,
+            "template_build_ms": build_ms, "template_bytes": tpl_bytes,
+            "fp32_dictionary_bytes": K * L * 4,
+            "tuning": {"lags_per_thread": lags, "warps": warps, "ctas": ctas},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_shift_search (FP32 FMA, templates in shared memory)",
+                         "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg, "launches_timed": core_n,
+                         "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 FMA/clk x 2 flop x "
+                                        f"{sm_mhz:.0f} MHz (maximum SM clock)"},
+            "channels_64": {"ms_per_step": ms64, "value": B * K * P / (ms64 / 1e3), "unit": UNIT}}
 
 
 def bench_bf16(args, dev, stream, peaks, peak_kind):
@@ -614,6 +714,8 @@ def run_profile_case(args):
     import torch
 
     from paper_2607_16629_gb300 import act, synth
+    if args.case == "shift_eeg":
+        return run_shift_case(args)
     full = synth.grid_eeg()
     grid = synth.Grid(full.n_samples, full.fs, synth.Axis(full.tc.lo, full.tc.step, 64), full.fc, full.logdt,
                       full.c)
@@ -635,6 +737,34 @@ def run_profile_case(args):
     print(json.dumps({"case": args.case, "atoms": grid.n_atoms, "channels": B, "ok": True}))
 
 
+def run_shift_case(args):
+    """Template search on the full 2,097,152-atom EEG-like grid, one channel,
+    3 orders per step (templates 67 MB: the whole case holds under 100 MB)."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    grid = synth.grid_eeg()
+    sig = torch.tensor(synth.eeg_like_signal(2, 0)[0][None, :], dtype=torch.float32, device="cuda")
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        if args.shift_tuning:
+            J, W = (int(v) for v in args.shift_tuning.split("x"))
+            act.act_set_shift_tuning(h, J, W)
+        for _ in range(args.steps):
+            _, _, _, energy = act.decompose(h, sig, 3)
+        torch.cuda.synchronize()
+        st = act.act_grid_status(h)
+        if st != act.ACT_OK:
+            raise RuntimeError(act.status_name(st))
+        e = energy.cpu().numpy()[0]
+        assert np.all(np.diff(e) <= 0.0)
+        tuning = act.act_get_shift_tuning(h)
+    finally:
+        act.act_destroy(h)
+    print(json.dumps({"case": args.case, "atoms": grid.n_atoms, "channels": 1, "tuning": tuning, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -646,7 +776,9 @@ def main():
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-lem", action="store_true")
-    ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small"],
+    ap.add_argument("--no-shift", action="store_true")
+    ap.add_argument("--shift-tuning", default="", help="JxW for --case shift_eeg (default: the build's)")
+    ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small", "shift_eeg"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()
     if args.case != "default":
