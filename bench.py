@@ -378,7 +378,7 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks):
         torch.cuda.synchronize(dev)
         build_ms = b0.elapsed_time(b1)
         act.act_autotune(h, sig1, 1, stream)
-        lags, warps, ctas = act.act_get_shift_tuning(h)
+        lags, warps, stages, ctas_per_sm = act.act_get_shift_tuning(h)
         out = [torch.empty((1, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
                torch.empty((1, P), dtype=torch.float32, device=dev),
                torch.empty((1, L), dtype=torch.float32, device=dev),
@@ -442,7 +442,7 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks):
             "same_selections_as_fp32_gemv": same,
             "template_build_ms": build_ms, "template_bytes": tpl_bytes,
             "fp32_dictionary_bytes": K * L * 4,
-            "tuning": {"lags_per_thread": lags, "warps": warps, "ctas": ctas},
+            "tuning": {"lags_per_thread": lags, "warps": warps, "stages": stages, "ctas_per_sm": ctas_per_sm},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "k_shift_search (FP32 FMA, templates in shared memory)",
@@ -749,8 +749,7 @@ def run_shift_case(args):
     try:
         act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
         if args.shift_tuning:
-            J, W = (int(v) for v in args.shift_tuning.split("x"))
-            act.act_set_shift_tuning(h, J, W)
+            act.act_set_shift_tuning(h, *(int(v) for v in args.shift_tuning.split("x")))
         for _ in range(args.steps):
             _, _, _, energy = act.decompose(h, sig, 3)
         torch.cuda.synchronize()
@@ -777,7 +776,7 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-lem", action="store_true")
     ap.add_argument("--no-shift", action="store_true")
-    ap.add_argument("--shift-tuning", default="", help="JxW for --case shift_eeg (default: the build's)")
+    ap.add_argument("--shift-tuning", default="", help="JxW, JxWxS or JxWxSxC for --case shift_eeg (default: the build's)")
     ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small", "shift_eeg"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()

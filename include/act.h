@@ -265,7 +265,8 @@ ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double
  * tile width (128 or 256 atoms) x pipeline depth (2 .. what fits in shared
  * memory) of the tensor-core GEMM, each timed with its tile selection and
  * rescan; with an ACT_DICT_RECOMPUTE build, every valid (lags per thread,
- * warps) pair of the template search instead (act_set_shift_tuning).
+ * warps, stages, CTAs per SM) combination of the template search instead
+ * (act_set_shift_tuning).
  * Results never depend on the configuration, only the speed does.
  * Waits for the device.  Later act_decompose calls use the chosen
  * configuration. */
@@ -286,14 +287,17 @@ ACT_API act_status act_set_tuning(act_grid *grid, int32_t gemv_ctas, int32_t bf1
 
 /* Launch configuration of the template search (ACT_DICT_RECOMPUTE builds):
  * lags_per_thread (8, 16 or 32) time centres per thread, `warps` (1..8)
- * warps per CTA, whose product must divide the tc count rounded up to 32;
- * the grid is one persistent wave (*ctas CTAs).  act_autotune on such a
- * build times every valid pair and keeps the fastest.  Errors:
- * ACT_ERR_NOT_BUILT without a template dictionary, ACT_ERR_INVALID_ARG for
- * an invalid pair.  Setting makes ragged plans built on this grid stale. */
-ACT_API act_status act_set_shift_tuning(act_grid *grid, int32_t lags_per_thread, int32_t warps);
+ * warps per CTA, whose product must divide the tc count rounded up to 32,
+ * `stages` (1..3) shared-memory buffers of template chunks, and
+ * ctas_per_sm persistent CTAs per SM (0: as many as fit).  act_autotune on
+ * such a build times every valid combination and keeps the fastest.
+ * Errors: ACT_ERR_NOT_BUILT without a template dictionary,
+ * ACT_ERR_INVALID_ARG for an invalid combination.  Setting makes ragged
+ * plans built on this grid stale. */
+ACT_API act_status act_set_shift_tuning(act_grid *grid, int32_t lags_per_thread, int32_t warps, int32_t stages,
+                                        int32_t ctas_per_sm);
 ACT_API act_status act_get_shift_tuning(const act_grid *grid, int32_t *lags_per_thread, int32_t *warps,
-                                        int32_t *ctas);
+                                        int32_t *stages, int32_t *ctas_per_sm);
 
 /* Kernel-level measurement hooks used by the benchmark.
  * act_set_profiling(grid, 1) makes later act_decompose graphs record CUDA

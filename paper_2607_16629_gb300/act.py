@@ -119,9 +119,8 @@ def load_library(path: str = LIB_PATH):
         lib.act_set_refinement.argtypes = [_P, ctypes.c_int32]
         lib.act_chirplet_score.argtypes = [ctypes.c_int32, ctypes.c_double, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
         lib.act_set_lem.argtypes = [_P, ctypes.POINTER(act_lem_params)]
-        lib.act_set_shift_tuning.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
-        lib.act_get_shift_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                             ctypes.POINTER(ctypes.c_int32)]
+        lib.act_set_shift_tuning.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        lib.act_get_shift_tuning.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int32)] * 4
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -296,18 +295,16 @@ def act_set_tuning(grid: int, gemv_ctas: int = 0, bf16_tile_atoms: int = 0, bf16
            "act_set_tuning")
 
 
-def act_set_shift_tuning(grid: int, lags_per_thread: int, warps: int) -> None:
-    _check(load_library().act_set_shift_tuning(grid, int(lags_per_thread), int(warps)), "act_set_shift_tuning")
+def act_set_shift_tuning(grid: int, lags_per_thread: int, warps: int, stages: int = 2, ctas_per_sm: int = 0) -> None:
+    _check(load_library().act_set_shift_tuning(grid, int(lags_per_thread), int(warps), int(stages), int(ctas_per_sm)),
+           "act_set_shift_tuning")
 
 
 def act_get_shift_tuning(grid: int):
-    """(lags_per_thread, warps, ctas) of the template search."""
-    a = ctypes.c_int32()
-    b = ctypes.c_int32()
-    c = ctypes.c_int32()
-    _check(load_library().act_get_shift_tuning(grid, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
-           "act_get_shift_tuning")
-    return a.value, b.value, c.value
+    """(lags_per_thread, warps, stages, ctas_per_sm) of the template search."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(load_library().act_get_shift_tuning(grid, *(ctypes.byref(x) for x in v)), "act_get_shift_tuning")
+    return tuple(x.value for x in v)
 
 
 def act_ragged_plan_create(grids, offsets, n_atoms: int) -> int:

@@ -310,7 +310,8 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += lem_kernels(g->lem);
         } else if (mode == ACT_SEARCH_SHIFT) {
-            ACT_CK(launch_shift_search(g->shift, w.R, g->Lp, g->L, B, w.keys, nullptr, g->status, st));
+            // early launch only between kernel nodes (not after profiling events)
+            ACT_CK(launch_shift_search(g->shift, w.R, g->Lp, g->L, B, w.keys, nullptr, g->status, !profiling, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         } else if (bf16) {
@@ -339,9 +340,8 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
                                          w.energy, bf16 ? w.fb_count : nullptr, st));
             kernels += 2;
         } else if (mode == ACT_SEARCH_SHIFT) {
-            // no stored rows: the selected grid atom is generated for the update
-            ACT_CK(launch_update_refined(g->Lp, w.R, nullptr, g->Lb, B, w.keys, g->ax, nullptr, k, P, w.atoms,
-                                         w.coefs, w.energy, nullptr, st));
+            // no stored rows: the selected atom is read back from its template
+            ACT_CK(launch_shift_update(g->shift, g->ax, g->Lp, w.R, B, w.keys, k, P, w.atoms, w.coefs, w.energy, st));
             ++kernels;
         } else {
             ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
@@ -651,7 +651,7 @@ act_status act_project(act_grid *g, const float *signals, int32_t channels, floa
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, nullptr, g->Lb, nullptr, nullptr, 1, g->status, st));
     if (g->built == ACT_DICT_RECOMPUTE) {
-        ACT_CK(launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, nullptr, scores, g->status, st));
+        ACT_CK(launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, nullptr, scores, g->status, false, st));
     } else {
         ACT_CK(launch_project(g->d32, g->K, g->Lp, g->w.R, channels, scores, g->status, g->gemv_grid, st));
     }
@@ -691,13 +691,15 @@ static act_status autotune_shift(act_grid *g, int channels, cudaStream_t st, dou
     const int reps = 3;
     const ShiftPlan keep = g->shift;
     double best = 1e30;
-    int bJ = keep.J, bW = keep.W;
+    int bJ = keep.J, bW = keep.W, bS = keep.NS, bC = keep.ctas_per_sm;
     cudaError_t err = cudaSuccess;
     static const int Js[] = {8, 16, 32};
     for (int J : Js) {
-        for (int W = 1; W <= 8 && err == cudaSuccess; ++W) {
-            if (!shift_config_valid(g->shift, J, W)) continue;
-            if (shift_configure(g->shift, J, W, g->sm_count) != cudaSuccess) {
+      for (int W = 1; W <= 8 && err == cudaSuccess; ++W) {
+        for (int NS = 1; NS <= 3 && err == cudaSuccess; ++NS) {
+          const int maxc = shift_max_ctas_per_sm(g->shift, J, W, NS);
+          for (int C = 1; C <= maxc && err == cudaSuccess; ++C) {
+            if (shift_configure(g->shift, J, W, NS, g->sm_count, C) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
@@ -705,7 +707,7 @@ static act_status autotune_shift(act_grid *g, int channels, cudaStream_t st, dou
                 err = cudaEventRecord(e0, st);
                 for (int r = 0; r < reps && err == cudaSuccess; ++r)
                     err = launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, g->w.keys, nullptr, g->status,
-                                              st);
+                                              false, st);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, st);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
             }
@@ -715,17 +717,20 @@ static act_status autotune_shift(act_grid *g, int channels, cudaStream_t st, dou
                 best = t / reps;
                 bJ = J;
                 bW = W;
+                bS = NS;
+                bC = C;
             }
+          }
         }
+      }
     }
-    if (err == cudaSuccess) err = shift_configure(g->shift, bJ, bW, g->sm_count);
+    if (err == cudaSuccess) err = shift_configure(g->shift, bJ, bW, bS, g->sm_count, bC);
     if (err == cudaSuccess) err = cudaMemsetAsync(g->w.keys, 0, sizeof(unsigned long long) * (size_t)channels, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) {
-        g->shift.J = keep.J;
-        shift_configure(g->shift, keep.J, keep.W, g->sm_count);
+        shift_configure(g->shift, keep.J, keep.W, keep.NS, g->sm_count, keep.ctas_per_sm);
         note_error("act_autotune", err);
         return ACT_ERR_CUDA;
     }
@@ -864,21 +869,24 @@ act_status act_set_tuning(act_grid *g, int32_t gemv_ctas_in, int32_t bf16_tile_a
     return ACT_OK;
 }
 
-act_status act_get_shift_tuning(const act_grid *g, int32_t *lags_per_thread, int32_t *warps, int32_t *ctas) {
+act_status act_get_shift_tuning(const act_grid *g, int32_t *lags_per_thread, int32_t *warps, int32_t *stages,
+                                int32_t *ctas_per_sm) {
     if (!g) return ACT_ERR_INVALID_ARG;
     if (!g->shift.tpl) return ACT_ERR_NOT_BUILT;
     if (lags_per_thread) *lags_per_thread = g->shift.J;
     if (warps) *warps = g->shift.W;
-    if (ctas) *ctas = g->shift.ctas;
+    if (stages) *stages = g->shift.NS;
+    if (ctas_per_sm) *ctas_per_sm = g->shift.ctas_per_sm;
     return ACT_OK;
 }
 
-act_status act_set_shift_tuning(act_grid *g, int32_t lags_per_thread, int32_t warps) {
+act_status act_set_shift_tuning(act_grid *g, int32_t lags_per_thread, int32_t warps, int32_t stages,
+                                int32_t ctas_per_sm) {
     if (!g) return ACT_ERR_INVALID_ARG;
     if (!g->shift.tpl) return ACT_ERR_NOT_BUILT;
     DeviceGuard dg(g->device);
-    if (!shift_config_valid(g->shift, lags_per_thread, warps)) return ACT_ERR_INVALID_ARG;
-    if (shift_configure(g->shift, lags_per_thread, warps, g->sm_count) != cudaSuccess) {
+    if (!shift_config_valid(g->shift, lags_per_thread, warps, stages) || ctas_per_sm < 0) return ACT_ERR_INVALID_ARG;
+    if (shift_configure(g->shift, lags_per_thread, warps, stages, g->sm_count, ctas_per_sm) != cudaSuccess) {
         cudaGetLastError();
         return ACT_ERR_INVALID_ARG;
     }

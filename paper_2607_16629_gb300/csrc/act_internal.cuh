@@ -126,7 +126,6 @@ cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const f
 // grid winner decoded from keys[b].
 cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R, const unsigned long long *keys,
                           const double *theta_in, int theta_in_stride, int B, double *theta_out, cudaStream_t st);
-// theta == null: the atom is the grid atom of keys[b] (generated on the fly).
 cudaError_t launch_update_refined(int Lp, float *R, __nv_bfloat16 *R16, int Lb, int B, unsigned long long *keys,
                                   const GridAxes &ax, const double *theta, int k, int P, act_atom *atoms, float *coefs,
                                   double *energy, int *fb_count, cudaStream_t st);
@@ -136,11 +135,12 @@ struct ShiftPlan {
     int S = 0, tc0 = 0;         // tc_j = tc0 + S j, whole samples
     int Sa = 0;                 // phases holding samples: min(S, L)
     int Ntc = 0, NtcP = 0;      // lags, and lags rounded up to 32
-    int P = 0;                  // polyphase length ceil(L / S) rounded up to 8
+    int P = 0;                  // polyphase length ceil(L / S) rounded up to 16
     int T = 0, TB = 0;          // templates (fc, logDt, c triples) and 32-template blocks
     int rows = 0;               // template rows per phase: NtcP + P - 1
     int64_t K = 0;
     int J = 0, W = 0, G = 0;    // lags per thread, warps per CTA, lag groups (NtcP / (W J))
+    int NS = 0;                 // shared-memory stages of template chunks (1..3)
     int Kc = 0;                 // template rows per staged chunk: W J + P - 1
     size_t smem = 0;
     int ctas_per_sm = 0, ctas = 0;
@@ -150,15 +150,25 @@ struct ShiftPlan {
 // Layout of the template dictionary; cudaErrorNotSupported unless the tc
 // axis is whole samples (lo and step integers, step >= 1).
 cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax);
-bool shift_config_valid(const ShiftPlan &sp, int J, int W);
-cudaError_t shift_configure(ShiftPlan &sp, int J, int W, int sm_count);
+bool shift_config_valid(const ShiftPlan &sp, int J, int W, int NS);
+int shift_max_ctas_per_sm(const ShiftPlan &sp, int J, int W, int NS);
+// ctas_per_sm <= 0: as many as fit.
+cudaError_t shift_configure(ShiftPlan &sp, int J, int W, int NS, int sm_count, int ctas_per_sm);
 cudaError_t shift_default_config(ShiftPlan &sp, int sm_count);
 cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned long long *degenerate, int sm_count,
                                cudaStream_t st);
 // Selection into keys[] (packed, atomicMax; keys must be clear), or with
-// scores != null every score written to scores[b * K + flat].
+// scores != null every score written to scores[b * K + flat].  With
+// early_launch the kernel is a programmatic dependent of the previous kernel
+// in the stream (its prologue overlaps that kernel).
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, cudaStream_t st);
+                                float *scores, int *status, bool early_launch, cudaStream_t st);
+// Coefficient and residual update (Eq. (4)) with the selected atom read back
+// from its template; lets the next search launch early (programmatic
+// dependent launch).
+cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
+                                unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
+                                cudaStream_t st);
 
 // ---- tensor-core search (act_gemm.cu) -------------------------------------
 struct Bf16Search;

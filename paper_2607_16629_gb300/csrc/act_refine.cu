@@ -345,8 +345,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
 
 // Coefficient and residual update with the refined atom g(theta*) generated
 // on the fly (Eq. (4)); the record keeps the grid winner's flat index (-1
-// when the selection did not come from the grid).  Without theta the atom is
-// the grid winner of keys[b] itself (searches that store no atom rows).
+// when the selection did not come from the grid).
 __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float *__restrict__ R,
                                                                   __nv_bfloat16 *__restrict__ R16, int Lb,
                                                                   unsigned long long *__restrict__ keys, GridAxes ax,
@@ -359,13 +358,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float
     const int b = blockIdx.x;
     const int L = ax.L;
     const double inv_fs = 1.0 / ax.fs;
-    double th[4];
-    if (theta) {
-        for (int i = 0; i < 4; ++i) th[i] = theta[4 * b + i];
-    } else {
-        decode_params(ax, (int64_t)key_index(keys[b]), th);  // the grid atom itself
-    }
-    const double tc = th[0], fc = th[1], ld = th[2], cc = th[3];
+    const double tc = theta[4 * b], fc = theta[4 * b + 1], ld = theta[4 * b + 2], cc = theta[4 * b + 3];
     const double inv_dt = exp(-ld);
     float *r = R + (size_t)b * Lp;
     // |u|^2 in FP64, then g = u / |u| recomputed per sample

@@ -21,7 +21,7 @@
 //   templates [TB][Sa][rows][32]: block tb holds templates 32 tb .. 32 tb + 31
 //     (lane = template), row rho holds k = rho - (NtcP - 1); rows =
 //     NtcP + P - 1, NtcP = Ntc rounded up to 32, P = ceil(L / S) rounded up
-//     to 8.  Zero for padding templates.
+//     to 16.  Zero for padding templates.
 //   scales [TB][NtcP][32]: 1/|u| in FP32 from an FP64 sum over the window,
 //     0 for a degenerate atom, a padding template or a padding lag.
 // The flat index of (lag j, template t) is j T + t, the order of the grid.
@@ -31,9 +31,10 @@
 // the Kc = W J + P - 1 template rows the group needs into shared memory
 // (two stages: the next copy is in flight while the current one is used).
 // Warp w computes lags g W J + w J + q, q < J, for the block's 32 templates:
-// each thread keeps J accumulators and a J-entry register window of its
+// each thread keeps J accumulators and a 2J-entry register ring of its
 // template that slides by one row per p, so every p costs one shared load of
-// the template, one broadcast load of r_a[p] and J FMAs.
+// the template (issued J steps ahead of its first use), a quarter of a
+// broadcast 128-bit load of r_a and J FMAs.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -46,6 +47,7 @@ namespace act {
 namespace {
 
 constexpr int kShiftMaxThreads = 256;
+constexpr int kShiftMaxStages = 3;
 
 struct ShiftArgs {
     const float *tpl;
@@ -53,7 +55,7 @@ struct ShiftArgs {
     const float *R;
     int Lp, L, B;
     int S, Sa, P, T, TB, NtcP, Ntc, rows;
-    int W, G, Kc;
+    int W, G, Kc, NS;
     int64_t K;
     unsigned long long *keys;
     float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
@@ -138,36 +140,48 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 template <int J>
 __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) {
     extern __shared__ __align__(128) float sm[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[kShiftMaxStages];
     __shared__ unsigned long long red[kShiftMaxThreads / 32];
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int W = A.W;
-    const int stage_floats = (A.Kc + 1) * 32;  // one slack row: the window's last look-ahead load
-    float *rpoly = sm + 2 * stage_floats;  // [Sa][P], after the two stages
+    const int W = A.W, NS = A.NS, Sa = A.Sa;
+    // J slack rows: the look-ahead loads of the ring's last J steps
+    const int stage_floats = (A.Kc + J + 1) * 32;
+    float *rpoly = sm + NS * stage_floats;     // [Sa][P] + 4 slack floats, after the stages
     const int units_per_b = A.G * A.TB;
     const int n_units = A.B * units_per_b;
     if ((int)blockIdx.x >= n_units) return;
+    // chunk c of this CTA: phase c % Sa of its unit c / Sa
+    const int my_units = (n_units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int n_chunks = my_units * Sa;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
 
     const uint32_t chunk_bytes = (uint32_t)A.Kc * 32u * 4u;
-    auto issue = [&](int u, int a, int s) {
+    auto issue = [&](int cc) {  // thread 0 only
+        if (cc >= n_chunks) return;
+        const int u = (int)blockIdx.x + (cc / Sa) * (int)gridDim.x, a = cc % Sa;
         const int rem = u % units_per_b;
         const int g = rem / A.TB, tb = rem % A.TB;
         const int rho0 = A.NtcP - (g + 1) * W * J;
-        const float *src = A.tpl + (((size_t)tb * A.Sa + a) * A.rows + rho0) * 32;
+        const float *src = A.tpl + (((size_t)tb * Sa + a) * A.rows + rho0) * 32;
+        const int s = cc % NS;
         mbar_expect_tx(&bar[s], chunk_bytes);
         bulk_g2s(sm + s * stage_floats, src, chunk_bytes, &bar[s]);
     };
 
-    if (threadIdx.x == 0) issue(blockIdx.x, 0, 0);
-    int c = 0;  // chunks consumed by this CTA
+    // prologue: chunks 0 .. NS-2 in flight; iteration c issues chunk c + NS - 1
+    // into the stage that chunk c - 1 used (freed by the barrier ending it)
+    if (threadIdx.x == 0)
+        for (int i = 0; i + 1 < NS; ++i) issue(i);
+    // Launched as a programmatic dependent of the previous update: everything
+    // above (the templates are constant) overlaps it; the residuals and keys
+    // it writes are read only after this wait.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int cur_b = -1;
     unsigned long long best = 0ull;
 
@@ -183,6 +197,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
         best = 0ull;
     };
 
+    int c = 0;  // chunks consumed by this CTA
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int b = u / units_per_b;
         const int rem = u % units_per_b;
@@ -190,7 +205,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
         if (b != cur_b) {
             if (cur_b >= 0 && !A.scores) flush(cur_b);
             const float *r = A.R + (size_t)b * A.Lp;
-            for (int i = threadIdx.x; i < A.Sa * A.P; i += blockDim.x) {
+            for (int i = threadIdx.x; i < Sa * A.P; i += blockDim.x) {
                 const int a = i / A.P, p = i % A.P;
                 const int n = a + A.S * p;
                 rpoly[i] = n < A.L ? r[n] : 0.0f;
@@ -198,65 +213,73 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
             __syncthreads();
             cur_b = b;
         }
-        float acc[J];
+        const int t = tb * 32 + lane;
+        const int j0 = g * W * J + w * J;
+        const float *scl = A.scale + ((size_t)tb * A.NtcP + j0) * 32 + lane;
+        float acc[J], sc[J];
 #pragma unroll
         for (int q = 0; q < J; ++q) acc[q] = 0.0f;
 
-        for (int a = 0; a < A.Sa; ++a) {
-            if (threadIdx.x == 0) {
-                // the next chunk goes to the other stage, freed by the barrier
-                // that ended the previous chunk
-                if (a + 1 < A.Sa) issue(u, a + 1, (c + 1) & 1);
-                else if (u + (int)gridDim.x < n_units) issue(u + gridDim.x, 0, (c + 1) & 1);
+        for (int a = 0; a < Sa; ++a, ++c) {
+            if (threadIdx.x == 0) issue(c + NS - 1);
+            if (a + 1 == Sa) {
+                // the scales are needed after this phase: load them now
+#pragma unroll
+                for (int q = 0; q < J; ++q) sc[q] = scl[q * 32];
             }
-            const int ok = mbar_wait(&bar[c & 1], (uint32_t)((c >> 1) & 1));
+            const int s = c % NS;
+            const uint32_t parity = (uint32_t)((c / NS) & 1);
+            const int ok = mbar_wait(&bar[s], parity);
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) {
                     atomicOr(A.status, kFlagTimeout);
                     // bounded: let the copies in flight land before exiting
-                    mbar_wait(&bar[c & 1], (uint32_t)((c >> 1) & 1));
-                    const bool next = a + 1 < A.Sa || u + (int)gridDim.x < n_units;
-                    if (next) mbar_wait(&bar[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1));
+                    for (int cc = c; cc < c + NS && cc < n_chunks; ++cc)
+                        mbar_wait(&bar[cc % NS], (uint32_t)((cc / NS) & 1));
                 }
                 return;
             }
-            const float *ts = sm + (c & 1) * stage_floats + lane;
-            const float *rp = rpoly + a * A.P;
+            const float *ts = sm + s * stage_floats + lane;
+            const float4 *rp4 = reinterpret_cast<const float4 *>(rpoly + a * A.P);
             const int base = (W - w) * J - 1;  // chunk row of (p = 0, q = 0)
-            float win[J];                        // slot (p - q) mod J holds row base + p - q
+            // Register ring of M = 2J template rows: slot (rho - base) mod M
+            // holds chunk row rho.  Step p uses rows base + p - q (q < J); the
+            // oldest, base + p - J + 1, then dies and its slot takes row
+            // base + p + J + 1, first used J steps later (load latency hidden).
+            constexpr int M = 2 * J;
+            float win[M];
 #pragma unroll
-            for (int q = 0; q < J; ++q) win[(J - q) % J] = ts[(base - q) * 32];
-            for (int pb = 0; pb < A.P; pb += J) {
+            for (int d = 1 - J; d <= J; ++d) win[(d + M) % M] = ts[(base + d) * 32];
+            float4 r_next = rp4[0];
+            for (int pb = 0; pb < A.P; pb += M) {
 #pragma unroll
-                for (int i = 0; i < J; i += 4) {
-                    const float4 r4 = *reinterpret_cast<const float4 *>(rp + pb + i);
+                for (int i = 0; i < M; i += 4) {
+                    const float4 r4 = r_next;
+                    r_next = rp4[(pb + i + 4) >> 2];  // the next group of 4 steps (slack after the last)
                     const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
 #pragma unroll
-                        for (int q = 0; q < J; ++q) acc[q] = fmaf(rv[e], win[(i + e - q + J) % J], acc[q]);
-                        win[(i + e + 1) % J] = ts[(base + pb + i + e + 1) * 32];
+                        for (int q = 0; q < J; ++q) acc[q] = fmaf(rv[e], win[(i + e - q + M) % M], acc[q]);
+                        win[(i + e + J + 1) % M] = ts[(base + pb + i + e + J + 1) * 32];
                     }
                 }
             }
             __syncthreads();
-            ++c;
         }
 
         // scores of this unit's atoms; the lowest lag wins ties (q ascending)
-        const int t = tb * 32 + lane;
         if (t < A.T) {
-            const float *scl = A.scale + ((size_t)tb * A.NtcP + g * W * J + w * J) * 32 + lane;
 #pragma unroll
             for (int q = 0; q < J; ++q) {
-                const int j = g * W * J + w * J + q;
+                const int j = j0 + q;
                 if (j < A.Ntc) {
-                    const float s = acc[q] * scl[q * 32];
+                    const float sv = acc[q] * sc[q];
                     const uint32_t flat = (uint32_t)j * (uint32_t)A.T + (uint32_t)t;
                     if (A.scores) {
-                        A.scores[(size_t)b * A.K + flat] = s;
+                        A.scores[(size_t)b * A.K + flat] = sv;
                     } else {
-                        const float x = fabsf(s);
+                        const float x = fabsf(sv);
                         if (x == x) {
                             const unsigned long long key = pack_key(x, flat);
                             best = key > best ? key : best;
@@ -269,6 +292,55 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
     if (cur_b >= 0 && !A.scores) flush(cur_b);
 }
 
+// One block per channel: the winner (j, t) of keys[b], g = scale * u_t
+// read back from the template rows the search used, c = <g, r> (FP32),
+// r -= c g, |r|^2 in FP64, the atom record, the key cleared.
+__global__ void __launch_bounds__(256) k_shift_update(const float *__restrict__ tpl, const float *__restrict__ scale,
+                                                     int S, int Sa, int rows, int NtcP, int T, GridAxes ax, int Lp,
+                                                     float *__restrict__ R, unsigned long long *__restrict__ keys,
+                                                     int k, int P, act_atom *__restrict__ atoms,
+                                                     float *__restrict__ coefs, double *__restrict__ energy) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    __shared__ float shf[32];
+    __shared__ double shd[32];
+    const int b = blockIdx.x;
+    const int L = ax.L;
+    const uint32_t flat = key_index(keys[b]);
+    const int j = (int)(flat / (uint32_t)T), t = (int)(flat % (uint32_t)T);
+    const int tb = t >> 5, lane = t & 31;
+    const float sc = scale[((size_t)tb * NtcP + j) * 32 + lane];
+    const float *base = tpl + (size_t)tb * Sa * rows * 32 + lane;
+    float *r = R + (size_t)b * Lp;
+    float part = 0.0f;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const float g = base[((size_t)(n % S) * rows + (n / S - j + NtcP - 1)) * 32] * sc;
+        part = fmaf(g, r[n], part);
+    }
+    const float c = block_sum(part, shf);
+    double e2 = 0.0;
+    for (int n = threadIdx.x; n < L; n += blockDim.x) {
+        const float g = base[((size_t)(n % S) * rows + (n / S - j + NtcP - 1)) * 32] * sc;
+        const float v = fmaf(-c, g, r[n]);
+        r[n] = v;
+        e2 = fma((double)v, (double)v, e2);
+    }
+    const double tot = block_sum(e2, shd);
+    if (threadIdx.x == 0) {
+        double p[4];
+        decode_params(ax, (int64_t)flat, p);
+        act_atom a;
+        a.tc = p[0];
+        a.fc = p[1];
+        a.logdt = p[2];
+        a.c = p[3];
+        a.flat_index = (int64_t)flat;
+        atoms[(size_t)b * P + k] = a;
+        coefs[(size_t)b * P + k] = c;
+        energy[(size_t)b * (P + 1) + k + 1] = tot;
+        keys[b] = 0ull;
+    }
+}
+
 template <int J>
 cudaError_t set_smem(size_t smem) {
     static size_t set = 0;
@@ -278,12 +350,12 @@ cudaError_t set_smem(size_t smem) {
     return e;
 }
 
-size_t shift_smem(const ShiftPlan &sp, int J, int W) {
+size_t shift_smem(const ShiftPlan &sp, int J, int W, int NS) {
     const int Kc = W * J + sp.P - 1;
-    return sizeof(float) * ((size_t)2 * (Kc + 1) * 32 + (size_t)sp.Sa * sp.P);
+    return sizeof(float) * ((size_t)NS * (Kc + J + 1) * 32 + (size_t)sp.Sa * sp.P + 4);
 }
 
-int shift_occupancy(const ShiftPlan &sp, int J, int W, size_t smem) {
+int shift_occupancy(int J, int W, size_t smem) {
     int per_sm = 0;
     cudaError_t e;
     switch (J) {
@@ -301,11 +373,17 @@ int shift_occupancy(const ShiftPlan &sp, int J, int W, size_t smem) {
 
 }  // namespace
 
-bool shift_config_valid(const ShiftPlan &sp, int J, int W) {
+int shift_max_ctas_per_sm(const ShiftPlan &sp, int J, int W, int NS) {
+    if (!shift_config_valid(sp, J, W, NS)) return 0;
+    return shift_occupancy(J, W, shift_smem(sp, J, W, NS));
+}
+
+bool shift_config_valid(const ShiftPlan &sp, int J, int W, int NS) {
     if (J != 8 && J != 16 && J != 32) return false;
     if (W < 1 || W > kShiftMaxThreads / 32) return false;
-    if (sp.NtcP % (W * J) != 0 || sp.P % J != 0) return false;
-    return shift_smem(sp, J, W) <= 227 * 1024;
+    if (NS < 1 || NS > kShiftMaxStages) return false;
+    if (sp.NtcP % (W * J) != 0 || sp.P % (2 * J) != 0) return false;
+    return shift_smem(sp, J, W, NS) <= 227 * 1024;
 }
 
 cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax) {
@@ -318,7 +396,7 @@ cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax) {
     sp.tc0 = (int)lo;
     sp.Ntc = ax.count[0];
     sp.NtcP = (sp.Ntc + 31) / 32 * 32;
-    sp.P = ((ax.L + sp.S - 1) / sp.S + 7) / 8 * 8;
+    sp.P = ((ax.L + sp.S - 1) / sp.S + 15) / 16 * 16;
     const int64_t T = (int64_t)ax.count[1] * ax.count[2] * ax.count[3];
     const int64_t K = T * ax.count[0];
     if (K >= 0xFFFFFFFFll || T > (1ll << 30)) return cudaErrorNotSupported;
@@ -329,13 +407,16 @@ cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax) {
     return cudaSuccess;
 }
 
-cudaError_t shift_configure(ShiftPlan &sp, int J, int W, int sm_count) {
-    if (!shift_config_valid(sp, J, W)) return cudaErrorInvalidValue;
-    const size_t smem = shift_smem(sp, J, W);
-    const int per_sm = shift_occupancy(sp, J, W, smem);
+cudaError_t shift_configure(ShiftPlan &sp, int J, int W, int NS, int sm_count, int ctas_per_sm) {
+    if (!shift_config_valid(sp, J, W, NS)) return cudaErrorInvalidValue;
+    const size_t smem = shift_smem(sp, J, W, NS);
+    int per_sm = shift_occupancy(J, W, smem);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (ctas_per_sm > per_sm) return cudaErrorInvalidValue;
+    if (ctas_per_sm > 0) per_sm = ctas_per_sm;
     sp.J = J;
     sp.W = W;
+    sp.NS = NS;
     sp.G = sp.NtcP / (W * J);
     sp.Kc = W * J + sp.P - 1;
     sp.smem = smem;
@@ -346,11 +427,11 @@ cudaError_t shift_configure(ShiftPlan &sp, int J, int W, int sm_count) {
 
 cudaError_t shift_default_config(ShiftPlan &sp, int sm_count) {
     // widest register window first, then the most warps that divide the lags
-    static const int Js[] = {32, 16, 8};
-    static const int Ws[] = {4, 8, 2, 1};
+    static const int Js[] = {16, 32, 8};
+    static const int Ws[] = {8, 4, 2, 1};
     for (int J : Js)
         for (int W : Ws)
-            if (shift_config_valid(sp, J, W) && shift_configure(sp, J, W, sm_count) == cudaSuccess)
+            if (shift_config_valid(sp, J, W, 2) && shift_configure(sp, J, W, 2, sm_count, 0) == cudaSuccess)
                 return cudaSuccess;
     return cudaErrorNotSupported;
 }
@@ -372,7 +453,7 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 }
 
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, cudaStream_t st) {
+                                float *scores, int *status, bool early_launch, cudaStream_t st) {
     if (sp.J == 0 || !sp.tpl) return cudaErrorInvalidValue;
     ShiftArgs A;
     A.tpl = sp.tpl;
@@ -392,20 +473,36 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
     A.W = sp.W;
     A.G = sp.G;
     A.Kc = sp.Kc;
+    A.NS = sp.NS;
     A.K = sp.K;
     A.keys = keys;
     A.scores = scores;
     A.status = status;
     const int64_t units = (int64_t)B * sp.G * sp.TB;
     if (units > INT32_MAX) return cudaErrorInvalidValue;
-    const int grid = (int)(units < sp.ctas ? units : sp.ctas);
-    const int threads = 32 * sp.W;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(units < sp.ctas ? units : sp.ctas));
+    cfg.blockDim = dim3(32u * sp.W);
+    cfg.dynamicSmemBytes = sp.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = early_launch ? 1 : 0;
     switch (sp.J) {
-        case 8: k_shift_search<8><<<grid, threads, sp.smem, st>>>(A); break;
-        case 16: k_shift_search<16><<<grid, threads, sp.smem, st>>>(A); break;
-        case 32: k_shift_search<32><<<grid, threads, sp.smem, st>>>(A); break;
+        case 8: return cudaLaunchKernelEx(&cfg, k_shift_search<8>, A);
+        case 16: return cudaLaunchKernelEx(&cfg, k_shift_search<16>, A);
+        case 32: return cudaLaunchKernelEx(&cfg, k_shift_search<32>, A);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
+                                unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
+                                cudaStream_t st) {
+    k_shift_update<<<B, 256, 0, st>>>(sp.tpl, sp.scale, sp.S, sp.Sa, sp.rows, sp.NtcP, sp.T, ax, Lp, R, keys, k, P,
+                                      atoms, coefs, energy);
     return cudaGetLastError();
 }
 

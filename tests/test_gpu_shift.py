@@ -101,18 +101,20 @@ def test_every_launch_configuration_gives_the_same_bits(name, grid):
         tried = 0
         for J in (8, 16, 32):
             for W in range(1, 9):
-                try:
-                    act.act_set_shift_tuning(h, J, W)
-                except act.ActError:
-                    continue
-                assert act.act_get_shift_tuning(h)[:2] == (J, W)
-                assert np.array_equal(project(h, sig), ref), (J, W)
-                tried += 1
-        assert tried >= 3
-        with pytest.raises(act.ActError):
-            act.act_set_shift_tuning(h, 12, 2)
-        with pytest.raises(act.ActError):
-            act.act_set_shift_tuning(h, 32, 9)
+                for S in (1, 2, 3):
+                    for C in (0, 1):
+                        try:
+                            act.act_set_shift_tuning(h, J, W, S, C)
+                        except act.ActError:
+                            continue
+                        got = act.act_get_shift_tuning(h)
+                        assert got[:3] == (J, W, S) and (C == 0 or got[3] == C)
+                        assert np.array_equal(project(h, sig), ref), (J, W, S, C)
+                        tried += 1
+        assert tried >= 12
+        for bad in ((12, 2, 2, 0), (32, 9, 2, 0), (16, 2, 4, 0), (16, 2, 0, 0), (16, 2, 2, -1), (16, 2, 2, 99)):
+            with pytest.raises(act.ActError):
+                act.act_set_shift_tuning(h, *bad)
 
 
 @pytest.mark.parametrize("name,grid,P", [(GRIDS[0][0], GRIDS[0][1], 5), (GRIDS[1][0], GRIDS[1][1], 12),
@@ -164,8 +166,8 @@ def test_host_buffers_and_autotune_keep_the_bits():
         ref = gpu_decompose(h, sig, 6)
         ms = act.act_autotune(h, torch.tensor(sig, dtype=torch.float32, device="cuda"), 2)
         assert ms > 0.0
-        J, W, ctas = act.act_get_shift_tuning(h)
-        assert J in (8, 16, 32) and 1 <= W <= 8 and ctas > 0
+        J, W, S, per_sm = act.act_get_shift_tuning(h)
+        assert J in (8, 16, 32) and 1 <= W <= 8 and 1 <= S <= 3 and per_sm > 0
         for host in (False, True):
             got = gpu_decompose(h, sig, 6, host=host)
             for a, b in zip(ref, got):
@@ -270,7 +272,7 @@ def test_unsupported_and_invalid_uses():
         with pytest.raises(act.ActError):
             gpu_decompose(h, synth.random_signals(1, 1, grid.n_samples), 1)
         with pytest.raises(act.ActError):
-            act.act_set_shift_tuning(h, 32, 4)
+            act.act_set_shift_tuning(h, 32, 4, 2, 0)
     finally:
         act.act_destroy(h)
 
