@@ -444,7 +444,11 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks):
             "fp32_dictionary_bytes": K * L * 4,
             "tuning": {"lags_per_thread": lags, "warps": warps, "stages": stages, "ctas_per_sm": ctas_per_sm},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": _profile_traffic("shift_search_eeg_k2097152_n512.md",
+                                                     ["paper_2607_16629_gb300/csrc/act_shift.cu",
+                                                      "paper_2607_16629_gb300/csrc/act_device.cuh"]),
+                         "traffic_note": "DRAM bytes of one cold-cache launch (templates + scales read once)",
                          "kernel": "k_shift_search (FP32 FMA, templates in shared memory)",
                          "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg, "launches_timed": core_n,
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 FMA/clk x 2 flop x "
