@@ -127,6 +127,25 @@ def test_atom_with_zero_chirp_is_gausspulse():
     assert np.max(np.abs(g - ref)) < 1e-12
 
 
+@pytest.mark.parametrize("fc,logdt,c", [(7.0, -1.2, 15.0), (30.0, -2.9, -20.0), (0.5, -0.5, 0.0)])
+def test_eq1_depends_on_n_and_tc_only_through_their_difference(fc, logdt, c):
+    """Eq. (1) sees t and tc only as t - tc: an atom centred S samples later
+    is the same samples S places later (the template dictionary rests on
+    this), and a normalised atom differs from its template window only by
+    the window's own norm."""
+    fs, L, S = 256.0, 512, 4
+    a0 = oracle.atom_complex(100.0, fc, logdt, c, fs, L)
+    a1 = oracle.atom_complex(100.0 + S, fc, logdt, c, fs, L)
+    assert np.array_equal(a1[S:], a0[:-S])
+    # template over lags -L+1 .. L-1 (tc = L - 1 puts m = n - tc in that range)
+    tpl = oracle.atom_complex(float(L - 1), fc, logdt, c, fs, 2 * L - 1).real
+    for tc in (0, 37, 300, 511):
+        u = tpl[L - 1 - tc: 2 * L - 1 - tc]
+        g, deg = oracle.atom(float(tc), fc, logdt, c, fs, L)
+        assert not deg
+        np.testing.assert_allclose(g, u / np.linalg.norm(u), rtol=0, atol=1e-14)
+
+
 def test_every_dictionary_atom_has_unit_norm():
     grid = synth.scaled_grid(synth.grid_c1(), tc_count=8, fc_count=5)
     D, deg = oracle.dictionary(grid)
