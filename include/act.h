@@ -109,7 +109,15 @@ typedef enum {
  *                    dictionary needed; act_atom.flat_index is -1).
  *   ACT_SEARCH_SHIFT: the template search over an ACT_DICT_RECOMPUTE build
  *                    (FP32 CUDA cores, every atom scored, the selected atom
- *                    regenerated for the update).
+ *                    read back from its template for the update).
+ *   ACT_SEARCH_SHIFT_BF16: the same selection on tensor cores: BF16
+ *                    templates x shifted BF16 residual rows (tcgen05, FP32
+ *                    accumulation, every score scaled by its atom's 1/|u|)
+ *                    reduced to the largest |score| per (time centre,
+ *                    256-template tile); the tiles an error bound cannot
+ *                    exclude are rescored with ACT_SEARCH_SHIFT's own
+ *                    arithmetic, so the selection equals ACT_SEARCH_SHIFT's
+ *                    bit for bit.
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
  *                    SHIFT with ACT_DICT_RECOMPUTE, FP32 otherwise. */
 typedef enum {
@@ -117,7 +125,8 @@ typedef enum {
     ACT_SEARCH_FP32 = 1,
     ACT_SEARCH_BF16 = 2,
     ACT_SEARCH_LEM = 3,
-    ACT_SEARCH_SHIFT = 4
+    ACT_SEARCH_SHIFT = 4,
+    ACT_SEARCH_SHIFT_BF16 = 5
 } act_search_mode;
 
 /* Settings of the LEM-inspired hierarchical search (Sec. VII-A, Fig. 7),

@@ -26,7 +26,7 @@ ACT_ERR_NOT_BUILT = 6
 ACT_ERR_UNSUPPORTED = 7
 
 ACT_DICT_AUTO, ACT_DICT_FP32, ACT_DICT_BF16, ACT_DICT_RECOMPUTE = 0, 1, 2, 3
-ACT_SEARCH_AUTO, ACT_SEARCH_FP32, ACT_SEARCH_BF16, ACT_SEARCH_LEM, ACT_SEARCH_SHIFT = 0, 1, 2, 3, 4
+ACT_SEARCH_AUTO, ACT_SEARCH_FP32, ACT_SEARCH_BF16, ACT_SEARCH_LEM, ACT_SEARCH_SHIFT, ACT_SEARCH_SHIFT_BF16 = range(6)
 
 # Every symbol include/act.h declares (checked by the CPU tests).
 EXPORTS = (

@@ -117,6 +117,7 @@ struct act_grid {
     long long *stats = nullptr;
     Bf16Search *bf16 = nullptr;
     ShiftPlan shift;       // template dictionary (ACT_DICT_RECOMPUTE)
+    ShiftTc *shift_tc = nullptr;  // its tensor-core search (ACT_SEARCH_SHIFT_BF16)
     int gemv_grid = 0;
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
     LemConfig lem;         // hierarchical search settings
@@ -166,8 +167,13 @@ void free_dictionary(act_grid *g) {
     g->bf16 = nullptr;
     free_dev(g->d32);
     free_dev(g->d16);
+    if (g->shift_tc) shift_tc_free(g->shift_tc);
+    g->shift_tc = nullptr;
     free_dev(g->shift.tpl);
     free_dev(g->shift.scale);
+    free_dev(g->shift.tpl16);
+    free_dev(g->shift.scaleT);
+    free_dev(g->shift.eps_bits);
     g->shift = ShiftPlan();
     g->built = -1;
 }
@@ -282,6 +288,7 @@ bool search_available(const act_grid *g, act_search_mode mode) {
         case ACT_SEARCH_FP32: return g->d32 != nullptr;
         case ACT_SEARCH_BF16: return g->bf16 != nullptr && g->d16 != nullptr;
         case ACT_SEARCH_SHIFT: return g->shift.tpl != nullptr;
+        case ACT_SEARCH_SHIFT_BF16: return g->shift_tc != nullptr;
         default: return false;
     }
 }
@@ -314,6 +321,12 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             ACT_CK(launch_shift_search(g->shift, w.R, g->Lp, g->L, B, w.keys, nullptr, g->status, !profiling, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
+        } else if (mode == ACT_SEARCH_SHIFT_BF16) {
+            ACT_CK(launch_shift_tc_gemm(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, g->status, st));
+            if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+            ACT_CK(launch_shift_tc_resolve(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, w.keys, w.fb_list, w.fb_count,
+                                           g->stats, g->status, st));
+            kernels += 5;
         } else if (bf16) {
             ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
@@ -337,11 +350,12 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
         } else if (g->refine_steps > 0) {
             ACT_CK(launch_refine(g->ax, g->refine_steps, g->Lp, w.R, w.keys, nullptr, 0, B, w.theta, st));
             ACT_CK(launch_update_refined(g->Lp, w.R, R16, g->Lb, B, w.keys, g->ax, w.theta, k, P, w.atoms, w.coefs,
-                                         w.energy, bf16 ? w.fb_count : nullptr, st));
+                                         w.energy, bf16 || mode == ACT_SEARCH_SHIFT_BF16 ? w.fb_count : nullptr, st));
             kernels += 2;
-        } else if (mode == ACT_SEARCH_SHIFT) {
+        } else if (mode == ACT_SEARCH_SHIFT || mode == ACT_SEARCH_SHIFT_BF16) {
             // no stored rows: the selected atom is read back from its template
-            ACT_CK(launch_shift_update(g->shift, g->ax, g->Lp, w.R, B, w.keys, k, P, w.atoms, w.coefs, w.energy, st));
+            ACT_CK(launch_shift_update(g->shift, g->ax, g->Lp, w.R, B, w.keys, k, P, w.atoms, w.coefs, w.energy,
+                                       mode == ACT_SEARCH_SHIFT_BF16 ? w.fb_count : nullptr, st));
             ++kernels;
         } else {
             ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
@@ -528,9 +542,23 @@ static act_status build_templates(act_grid *g, cudaStream_t st) {
     const size_t bs = sizeof(float) * (size_t)sp.TB * sp.NtcP * 32;
     cudaError_t e = cudaMalloc(&sp.tpl, bt);
     if (e == cudaSuccess) e = cudaMalloc(&sp.scale, bs);
+    if (e == cudaSuccess && sp.Kt > 0) {
+        // the tensor-core view: BF16 templates, transposed scales, BF16 error bound
+        const size_t b16 = sizeof(__nv_bfloat16) * (size_t)sp.T_pad * sp.Kt;
+        const size_t bst = sizeof(float) * (size_t)sp.NtcP * sp.T_pad;
+        e = cudaMalloc(&sp.tpl16, b16);
+        if (e == cudaSuccess) e = cudaMalloc(&sp.scaleT, bst);
+        if (e == cudaSuccess) e = cudaMalloc(&sp.eps_bits, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(sp.scaleT, 0, bst, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sp.eps_bits, 0, sizeof(unsigned int), st);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_dev(sp.tpl);
+        free_dev(sp.scale);
+        free_dev(sp.tpl16);
+        free_dev(sp.scaleT);
+        free_dev(sp.eps_bits);
         note_error("template dictionary", e);
         return ACT_ERR_OOM;
     }
@@ -538,6 +566,10 @@ static act_status build_templates(act_grid *g, cudaStream_t st) {
     ACT_CK(cudaMemsetAsync(g->degenerate, 0, sizeof(unsigned long long), st));
     ACT_CK(launch_shift_build(g->shift, g->ax, g->degenerate, g->sm_count, st));
     g->built = ACT_DICT_RECOMPUTE;
+    if (sp.tpl16 && shift_tc_prepare(&g->shift_tc, g->shift, g->sm_count) != cudaSuccess) {
+        cudaGetLastError();
+        g->shift_tc = nullptr;  // the FP32 template search stays available
+    }
     return ACT_OK;
 }
 
@@ -601,7 +633,7 @@ act_status act_set_lem(act_grid *g, const act_lem_params *params) {
 }
 
 act_status act_set_search(act_grid *g, act_search_mode mode) {
-    if (!g || (int)mode < 0 || (int)mode > 4) return ACT_ERR_INVALID_ARG;
+    if (!g || (int)mode < 0 || (int)mode > 5) return ACT_ERR_INVALID_ARG;
     g->search = mode;
     return ACT_OK;
 }
@@ -619,6 +651,13 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
     act_status s = ensure_work(g, channels, n_atoms);
     if (s != ACT_OK) return s;
     if (mode == ACT_SEARCH_LEM && (s = ensure_lem(g, g->w, channels)) != ACT_OK) return s;
+    if (mode == ACT_SEARCH_SHIFT_BF16) {
+        cudaError_t re = shift_tc_reserve(g->shift_tc, g->shift, channels);
+        if (re != cudaSuccess) {
+            note_error("shift_tc_reserve", re);
+            return ACT_ERR_OOM;
+        }
+    }
     bool host_seen = !is_device_ptr(signals);
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     GraphEntry *ge = nullptr;
@@ -1045,6 +1084,8 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
         act_status s = alloc_work(g, gr.w, B, p->P);
         if (s != ACT_OK) return s;
         if (gr.mode == ACT_SEARCH_LEM && (s = ensure_lem(g, gr.w, B)) != ACT_OK) return s;
+        if (gr.mode == ACT_SEARCH_SHIFT_BF16 && shift_tc_reserve(g->shift_tc, g->shift, B) != cudaSuccess)
+            return ACT_ERR_OOM;
         std::vector<int64_t> off(B);
         for (int i = 0; i < B; ++i) off[i] = offsets[gr.chan[i]];
         ACT_CK(cudaMalloc(&gr.src_off, sizeof(int64_t) * B));

@@ -31,13 +31,15 @@
 
 #include "act_device.cuh"
 #include "act_internal.cuh"
+#include "act_tc.cuh"
 
 namespace act {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kBM = 128;           // channels per tile (MMA M)
-constexpr int kBK = 64;            // samples per stage (one 128-byte swizzle row)
 constexpr int kBlockRows = 256;    // atoms per block of the tile-major BF16 layout
 constexpr int kUmmaK = 16;         // K per tcgen05.mma (16-bit inputs)
 constexpr int kMaxRescan = 64;     // flagged tiles per channel before the FP32 full search
@@ -58,71 +60,6 @@ struct TileCfg {
                                        | ((uint32_t)(BN >> 3) << 17)  // N / 8
                                        | ((uint32_t)(kBM >> 4) << 24);  // M / 16
 };
-
-// Shared-memory matrix descriptor for a K-major operand written by TMA with
-// 128-byte swizzling: rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
-    d |= (uint64_t)1u << 16;                   // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset
-    d |= (uint64_t)1u << 46;                   // descriptor version
-    d |= (uint64_t)2u << 61;                   // 128-byte swizzle
-    return d;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t smem_dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void sleep_ns(unsigned long long ns) {
-    const unsigned long long t0 = globaltimer_ns();
-    while (globaltimer_ns() - t0 < ns) {
-    }
-}
 
 struct GemmSmem {
     uint64_t bar_a;
@@ -423,36 +360,6 @@ __global__ void __launch_bounds__(256) k_rescan(const float *__restrict__ D32, i
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
-    return fn;
-}
-
-// 2-D BF16 tensor map over a row-major [rows][cols] matrix, box [box_rows][64].
-bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t gdim[2] = {cols, rows};
-    cuuint64_t gstride[1] = {cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
-    cuuint32_t estride[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), gdim, gstride, box, estride,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // Dynamic shared memory the GEMM may use: the opt-in limit minus its static
 // shared memory (barriers), less 1 KB of slack for 1024-byte alignment.
 constexpr int kStaticSmemReserve = 512;
@@ -463,21 +370,6 @@ int max_stages(int bn, int nkc, bool a_stream) {
     const int chunk = bn * kBK * 2;
     int st = a_stream ? kSmemBudget / (chunk + kAChunkBytes) : (kSmemBudget - nkc * kAChunkBytes) / chunk;
     return st > kMaxStages ? kMaxStages : st;
-}
-
-// Raises the kernel's dynamic shared-memory limit to everything the device
-// allows next to its static shared memory (the limit is per kernel function
-// and shared by every grid in the process).
-cudaError_t allow_max_smem(const void *func, size_t needed) {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
-    if (e != cudaSuccess) return e;
-    const int limit = optin - (int)fa.sharedSizeBytes;
-    if ((size_t)limit < needed) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
 }
 
 }  // namespace

@@ -146,6 +146,12 @@ struct ShiftPlan {
     int ctas_per_sm = 0, ctas = 0;
     float *tpl = nullptr;       // [TB][Sa][rows][32]
     float *scale = nullptr;     // [TB][NtcP][32]
+    // tensor-core view (act_shift_tc.cu): templates over m = n - tc in
+    // [m_lo, m_lo + Kt) as BF16 rows, tile-major [T_pad / 256][Kt / 64][256][64]
+    int m_lo = 0, Kt = 0, T_pad = 0;
+    __nv_bfloat16 *tpl16 = nullptr;
+    float *scaleT = nullptr;         // [NtcP][T_pad]
+    unsigned int *eps_bits = nullptr;  // largest |bf16(u) - u| / |u| over the atoms (float bits)
 };
 // Layout of the template dictionary; cudaErrorNotSupported unless the tc
 // axis is whole samples (lo and step integers, step >= 1).
@@ -160,15 +166,36 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 // Selection into keys[] (packed, atomicMax; keys must be clear), or with
 // scores != null every score written to scores[b * K + flat].  With
 // early_launch the kernel is a programmatic dependent of the previous kernel
-// in the stream (its prologue overlaps that kernel).
+// in the stream (its prologue overlaps that kernel).  With chlist, only the
+// channels chlist[0 .. *count_dev - 1] (B is then their upper bound).
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, bool early_launch, cudaStream_t st);
+                                float *scores, int *status, bool early_launch, cudaStream_t st,
+                                const int *chlist = nullptr, const int *count_dev = nullptr);
 // Coefficient and residual update (Eq. (4)) with the selected atom read back
 // from its template; lets the next search launch early (programmatic
 // dependent launch).
+// counters (may be null): the tensor-core search's per-order queue lengths, reset.
 cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
                                 unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
-                                cudaStream_t st);
+                                int *counters, cudaStream_t st);
+
+// ---- tensor-core template search (act_shift_tc.cu) -------------------------
+struct ShiftTc;
+// Tensor maps and pipeline depth for the BF16 templates of sp (which must
+// hold tpl16, scaleT and eps_bits); cudaErrorNotSupported without them.
+cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count);
+void shift_tc_free(ShiftTc *s);
+// Shifted-residual, tile-maximum and item buffers for up to B channels.
+cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B);
+// One search order: shifted residual rows + tcgen05 GEMM (tile maxima of the
+// scaled scores), then item selection, FP32 rescore of the flagged items and
+// the FP32 template search for channels with too many of them.  Leaves the
+// packed key of every channel in keys[]; counters[0..1] must be zero on entry.
+cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B, int *status,
+                                 cudaStream_t st);
+cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
+                                    unsigned long long *keys, int *fb_list, int *counters, long long *stats,
+                                    int *status, cudaStream_t st);
 
 // ---- tensor-core search (act_gemm.cu) -------------------------------------
 struct Bf16Search;

@@ -35,6 +35,7 @@
 // template that slides by one row per p, so every p costs one shared load of
 // the template (issued J steps ahead of its first use), a quarter of a
 // broadcast 128-bit load of r_a and J FMAs.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +58,8 @@ struct ShiftArgs {
     int S, Sa, P, T, TB, NtcP, Ntc, rows;
     int W, G, Kc, NS;
     int64_t K;
+    const int *chlist;    // non-null: search channels chlist[0 .. *count_dev - 1] only
+    const int *count_dev;
     unsigned long long *keys;
     float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
     int *status;
@@ -97,10 +100,36 @@ __global__ void __launch_bounds__(256) k_shift_templates(GridAxes ax, int S, int
     }
 }
 
-// One thread per (template block, lag, lane): |u|^2 over the window in FP64.
+// BF16 templates for the tensor-core search, tile-major like the BF16
+// dictionary: element (t, kk) = bf16(u_t(m_lo + kk)) at
+// [t / 256][kk / 64][t % 256][kk % 64]; zero for padding templates.
+__global__ void __launch_bounds__(256) k_shift_tpl16(GridAxes ax, int m_lo, int Kt, int T, int64_t total,
+                                                     __nv_bfloat16 *__restrict__ tpl16) {
+    const double inv_fs = 1.0 / ax.fs;
+    const int nkc = Kt >> 6;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / Kt;
+        const int kk = (int)(i % Kt);
+        float v = 0.0f;
+        if (t < T) {
+            double p[4];
+            decode_params(ax, t, p);
+            v = template_sample((double)(m_lo + kk), inv_fs, p[1], exp(-p[2]), p[3]);
+        }
+        const int64_t off = (((t >> 8) * nkc + (kk >> 6)) * 256 + (t & 255)) * 64 + (kk & 63);
+        tpl16[off] = __float2bfloat16_rn(v);
+    }
+}
+
+// One thread per (template block, lag, lane): |u|^2 over the window in FP64,
+// the scale 1/|u| in both layouts ([TB][NtcP][32] for the FP32 search,
+// [NtcP][T_pad] for the tensor-core epilogue) and the largest relative BF16
+// rounding error |bf16(u) - u| / |u| over all atoms (float bits, rounded up).
 __global__ void __launch_bounds__(256) k_shift_scales(int S, int Sa, int L, int NtcP, int Ntc, int rows, int T,
-                                                      int64_t total, const float *__restrict__ tpl,
-                                                      float *__restrict__ scale,
+                                                      int T_pad, int64_t total, const float *__restrict__ tpl,
+                                                      float *__restrict__ scale, float *__restrict__ scaleT,
+                                                      unsigned int *__restrict__ eps_bits,
                                                       unsigned long long *__restrict__ degenerate) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -111,20 +140,25 @@ __global__ void __launch_bounds__(256) k_shift_scales(int S, int Sa, int L, int 
         const int64_t t = tb * 32 + lane;
         float sc = 0.0f;
         if (t < T && j < Ntc) {
-            double e = 0.0;
+            double e = 0.0, de = 0.0;
             const float *base = tpl + (size_t)tb * Sa * rows * 32 + lane;
             for (int n = 0; n < L; ++n) {
                 const int a = n % S, p = n / S;
                 const float u = base[((size_t)a * rows + (p - j + NtcP - 1)) * 32];
+                const float d = __bfloat162float(__float2bfloat16_rn(u)) - u;
                 e = fma((double)u, (double)u, e);
+                de = fma((double)d, (double)d, de);
             }
             if (e > 0.0 && isfinite(e)) {
                 sc = (float)(1.0 / sqrt(e));
+                if (eps_bits)
+                    atomicMax(eps_bits, __float_as_uint(__double2float_ru(sqrt(de / e) * (1.0 + 1e-6))));
             } else if (degenerate) {
                 atomicAdd(degenerate, 1ull);
             }
         }
         scale[i] = sc;
+        if (scaleT && t < T_pad) scaleT[(size_t)j * T_pad + t] = sc;
     }
 }
 
@@ -149,7 +183,9 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
     const int stage_floats = (A.Kc + J + 1) * 32;
     float *rpoly = sm + NS * stage_floats;     // [Sa][P] + 4 slack floats, after the stages
     const int units_per_b = A.G * A.TB;
-    const int n_units = A.B * units_per_b;
+    if (A.count_dev) asm volatile("griddepcontrol.wait;" ::: "memory");  // the count is written by the select kernel
+    const int n_ch = A.count_dev ? *A.count_dev : A.B;
+    const int n_units = n_ch * units_per_b;
     if ((int)blockIdx.x >= n_units) return;
     // chunk c of this CTA: phase c % Sa of its unit c / Sa
     const int my_units = (n_units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -199,7 +235,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
 
     int c = 0;  // chunks consumed by this CTA
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int b = u / units_per_b;
+        const int b = A.chlist ? A.chlist[u / units_per_b] : u / units_per_b;
         const int rem = u % units_per_b;
         const int g = rem / A.TB, tb = rem % A.TB;
         if (b != cur_b) {
@@ -299,7 +335,8 @@ __global__ void __launch_bounds__(256) k_shift_update(const float *__restrict__ 
                                                      int S, int Sa, int rows, int NtcP, int T, GridAxes ax, int Lp,
                                                      float *__restrict__ R, unsigned long long *__restrict__ keys,
                                                      int k, int P, act_atom *__restrict__ atoms,
-                                                     float *__restrict__ coefs, double *__restrict__ energy) {
+                                                     float *__restrict__ coefs, double *__restrict__ energy,
+                                                     int *__restrict__ counters) {
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ float shf[32];
     __shared__ double shd[32];
@@ -338,6 +375,10 @@ __global__ void __launch_bounds__(256) k_shift_update(const float *__restrict__ 
         coefs[(size_t)b * P + k] = c;
         energy[(size_t)b * (P + 1) + k + 1] = tot;
         keys[b] = 0ull;
+        if (counters && b == 0) {
+            counters[0] = 0;
+            counters[1] = 0;
+        }
     }
 }
 
@@ -404,6 +445,13 @@ cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax) {
     sp.TB = (int)((T + 31) / 32);
     sp.rows = sp.NtcP + sp.P - 1;
     sp.K = K;
+    // tensor-core view: m = n - tc over [m_lo, m_hi], Kt = its length rounded up to 64
+    const int64_t tc_last = (int64_t)sp.tc0 + (int64_t)sp.S * (sp.Ntc - 1);
+    const int64_t m_lo = -tc_last, m_hi = (int64_t)ax.L - 1 - sp.tc0;
+    const int64_t kt = (m_hi - m_lo + 1 + 63) / 64 * 64;
+    sp.m_lo = (m_lo > -(1ll << 30)) ? (int)m_lo : 0;
+    sp.Kt = kt <= (1 << 16) && m_lo > -(1ll << 30) ? (int)kt : 0;  // 0: no tensor-core view
+    sp.T_pad = (int)((T + 255) / 256 * 256);
     return cudaSuccess;
 }
 
@@ -447,13 +495,20 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
     const int64_t ns = (int64_t)sp.TB * sp.NtcP * 32;
     blocks = (ns + 255) / 256;
     if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
-    k_shift_scales<<<(int)blocks, 256, 0, st>>>(sp.S, sp.Sa, ax.L, sp.NtcP, sp.Ntc, sp.rows, sp.T, ns, sp.tpl,
-                                                 sp.scale, degenerate);
+    k_shift_scales<<<(int)blocks, 256, 0, st>>>(sp.S, sp.Sa, ax.L, sp.NtcP, sp.Ntc, sp.rows, sp.T, sp.T_pad, ns,
+                                                 sp.tpl, sp.scale, sp.scaleT, sp.eps_bits, degenerate);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !sp.tpl16) return e;
+    const int64_t n16 = (int64_t)sp.T_pad * sp.Kt;
+    blocks = (n16 + 255) / 256;
+    if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
+    k_shift_tpl16<<<(int)blocks, 256, 0, st>>>(ax, sp.m_lo, sp.Kt, sp.T, n16, sp.tpl16);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, bool early_launch, cudaStream_t st) {
+                                float *scores, int *status, bool early_launch, cudaStream_t st, const int *chlist,
+                                const int *count_dev) {
     if (sp.J == 0 || !sp.tpl) return cudaErrorInvalidValue;
     ShiftArgs A;
     A.tpl = sp.tpl;
@@ -475,6 +530,8 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
     A.Kc = sp.Kc;
     A.NS = sp.NS;
     A.K = sp.K;
+    A.chlist = chlist;
+    A.count_dev = count_dev;
     A.keys = keys;
     A.scores = scores;
     A.status = status;
@@ -500,9 +557,9 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
 
 cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
                                 unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
-                                cudaStream_t st) {
+                                int *counters, cudaStream_t st) {
     k_shift_update<<<B, 256, 0, st>>>(sp.tpl, sp.scale, sp.S, sp.Sa, sp.rows, sp.NtcP, sp.T, ax, Lp, R, keys, k, P,
-                                      atoms, coefs, energy);
+                                      atoms, coefs, energy, counters);
     return cudaGetLastError();
 }
 
