@@ -718,7 +718,7 @@ def run_profile_case(args):
     import torch
 
     from paper_2607_16629_gb300 import act, synth
-    if args.case == "shift_eeg":
+    if args.case in ("shift_eeg", "shift_tc_eeg"):
         return run_shift_case(args)
     full = synth.grid_eeg()
     grid = synth.Grid(full.n_samples, full.fs, synth.Axis(full.tc.lo, full.tc.step, 64), full.fc, full.logdt,
@@ -742,16 +742,21 @@ def run_profile_case(args):
 
 
 def run_shift_case(args):
-    """Template search on the full 2,097,152-atom EEG-like grid, one channel,
-    3 orders per step (templates 67 MB: the whole case holds under 100 MB)."""
+    """Template search on the full 2,097,152-atom EEG-like grid, 3 orders per
+    step: --channels EEG-like channels (1 or 64), the FP32 search (shift_eeg)
+    or the tensor-core one (shift_tc_eeg).  Templates take 100 MB; with 64
+    channels the shifted residual rows add 17 MB."""
     import torch
 
     from paper_2607_16629_gb300 import act, synth
     grid = synth.grid_eeg()
-    sig = torch.tensor(synth.eeg_like_signal(2, 0)[0][None, :], dtype=torch.float32, device="cuda")
+    B = args.channels
+    sig_np = synth.workload_c3().signals[:B] if B > 1 else synth.eeg_like_signal(2, 0)[0][None, :]
+    sig = torch.tensor(sig_np, dtype=torch.float32, device="cuda")
     h = act.act_grid_create(grid, 0)
     try:
         act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        act.act_set_search(h, act.ACT_SEARCH_SHIFT_BF16 if args.case == "shift_tc_eeg" else act.ACT_SEARCH_SHIFT)
         if args.shift_tuning:
             act.act_set_shift_tuning(h, *(int(v) for v in args.shift_tuning.split("x")))
         for _ in range(args.steps):
@@ -760,12 +765,12 @@ def run_shift_case(args):
         st = act.act_grid_status(h)
         if st != act.ACT_OK:
             raise RuntimeError(act.status_name(st))
-        e = energy.cpu().numpy()[0]
-        assert np.all(np.diff(e) <= 0.0)
+        e = energy.cpu().numpy()
+        assert np.all(np.diff(e, axis=1) <= 0.0)
         tuning = act.act_get_shift_tuning(h)
     finally:
         act.act_destroy(h)
-    print(json.dumps({"case": args.case, "atoms": grid.n_atoms, "channels": 1, "tuning": tuning, "ok": True}))
+    print(json.dumps({"case": args.case, "atoms": grid.n_atoms, "channels": B, "tuning": tuning, "ok": True}))
 
 
 def main():
@@ -780,8 +785,10 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-lem", action="store_true")
     ap.add_argument("--no-shift", action="store_true")
+    ap.add_argument("--channels", type=int, default=1, help="channels for the shift_* cases (1 or up to 64)")
     ap.add_argument("--shift-tuning", default="", help="JxW, JxWxS or JxWxSxC for --case shift_eeg (default: the build's)")
-    ap.add_argument("--case", default="default", choices=["default", "gemv_small", "bf16_small", "shift_eeg"],
+    ap.add_argument("--case", default="default",
+                    choices=["default", "gemv_small", "bf16_small", "shift_eeg", "shift_tc_eeg"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()
     if args.case != "default":

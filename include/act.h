@@ -115,7 +115,8 @@ typedef enum {
  *                    accumulation, every score scaled by its atom's 1/|u|)
  *                    reduced to the largest |score| per (time centre,
  *                    256-template tile); the tiles an error bound cannot
- *                    exclude are rescored with ACT_SEARCH_SHIFT's own
+ *                    exclude (all tiles of a channel with more than 64 of
+ *                    them) are rescored with ACT_SEARCH_SHIFT's own
  *                    arithmetic, so the selection equals ACT_SEARCH_SHIFT's
  *                    bit for bit.
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,

@@ -166,11 +166,9 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 // Selection into keys[] (packed, atomicMax; keys must be clear), or with
 // scores != null every score written to scores[b * K + flat].  With
 // early_launch the kernel is a programmatic dependent of the previous kernel
-// in the stream (its prologue overlaps that kernel).  With chlist, only the
-// channels chlist[0 .. *count_dev - 1] (B is then their upper bound).
+// in the stream (its prologue overlaps that kernel).
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, bool early_launch, cudaStream_t st,
-                                const int *chlist = nullptr, const int *count_dev = nullptr);
+                                float *scores, int *status, bool early_launch, cudaStream_t st);
 // Coefficient and residual update (Eq. (4)) with the selected atom read back
 // from its template; lets the next search launch early (programmatic
 // dependent launch).
@@ -188,11 +186,11 @@ void shift_tc_free(ShiftTc *s);
 // Shifted-residual, tile-maximum and item buffers for up to B channels.
 cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B);
 // One search order: shifted residual rows + tcgen05 GEMM (tile maxima of the
-// scaled scores), then item selection, FP32 rescore of the flagged items and
-// the FP32 template search for channels with too many of them.  Leaves the
+// scaled scores), then item selection and FP32 rescore of the flagged items
+// (of every item, for a channel with too many flagged ones).  Leaves the
 // packed key of every channel in keys[]; counters[0..1] must be zero on entry.
-cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B, int *status,
-                                 cudaStream_t st);
+cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
+                                 long long *stats, int *status, cudaStream_t st);
 cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
                                     unsigned long long *keys, int *fb_list, int *counters, long long *stats,
                                     int *status, cudaStream_t st);

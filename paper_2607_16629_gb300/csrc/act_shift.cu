@@ -58,8 +58,6 @@ struct ShiftArgs {
     int S, Sa, P, T, TB, NtcP, Ntc, rows;
     int W, G, Kc, NS;
     int64_t K;
-    const int *chlist;    // non-null: search channels chlist[0 .. *count_dev - 1] only
-    const int *count_dev;
     unsigned long long *keys;
     float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
     int *status;
@@ -183,9 +181,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
     const int stage_floats = (A.Kc + J + 1) * 32;
     float *rpoly = sm + NS * stage_floats;     // [Sa][P] + 4 slack floats, after the stages
     const int units_per_b = A.G * A.TB;
-    if (A.count_dev) asm volatile("griddepcontrol.wait;" ::: "memory");  // the count is written by the select kernel
-    const int n_ch = A.count_dev ? *A.count_dev : A.B;
-    const int n_units = n_ch * units_per_b;
+    const int n_units = A.B * units_per_b;
     if ((int)blockIdx.x >= n_units) return;
     // chunk c of this CTA: phase c % Sa of its unit c / Sa
     const int my_units = (n_units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -235,7 +231,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
 
     int c = 0;  // chunks consumed by this CTA
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int b = A.chlist ? A.chlist[u / units_per_b] : u / units_per_b;
+        const int b = u / units_per_b;
         const int rem = u % units_per_b;
         const int g = rem / A.TB, tb = rem % A.TB;
         if (b != cur_b) {
@@ -507,8 +503,7 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 }
 
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, bool early_launch, cudaStream_t st, const int *chlist,
-                                const int *count_dev) {
+                                float *scores, int *status, bool early_launch, cudaStream_t st) {
     if (sp.J == 0 || !sp.tpl) return cudaErrorInvalidValue;
     ShiftArgs A;
     A.tpl = sp.tpl;
@@ -530,8 +525,6 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
     A.Kc = sp.Kc;
     A.NS = sp.NS;
     A.K = sp.K;
-    A.chlist = chlist;
-    A.count_dev = count_dev;
     A.keys = keys;
     A.scores = scores;
     A.status = status;

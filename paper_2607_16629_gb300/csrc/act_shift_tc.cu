@@ -11,7 +11,7 @@
 //     (lag, tile) items that can hold the FP32 template search's argmax;
 //  4. the flagged items are rescored with the FP32 template search's own
 //     arithmetic (same FMA chain, same scale) and folded into the packed key;
-//     a channel with too many items takes the FP32 template search instead.
+//     a channel with too many items has all of its items rescored that way.
 // Steps 3 and 4 make the selection bit-identical to the FP32 template search.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -32,17 +32,23 @@ namespace {
 using namespace tc;
 
 constexpr int kBM = 128;          // shifted residual rows per tile (MMA M)
-constexpr int kBN = 256;          // templates per tile (MMA N)
+constexpr int kBlockRows = 256;   // templates per block of the tile-major BF16 layout
 constexpr int kUmmaK = 16;
 constexpr int kThreads = 256;
 constexpr int kAChunkBytes = kBM * kBK * 2;  // 16 KB
-constexpr int kBChunkBytes = kBN * kBK * 2;  // 32 KB
-constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;
-constexpr int kMaxStages = 4;
-constexpr int kMaxItems = 64;      // flagged (lag, tile) items per channel before the FP32 template search
-constexpr uint32_t kTmemCols = 2 * kBN;
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
+constexpr int kMaxStages = 6;
+
+// Tile of BN templates (128 or 256, MMA N).
+template <int BN>
+struct ShiftTile {
+    static constexpr int kBChunkBytes = BN * kBK * 2;
+    static constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;
+    static constexpr uint32_t kTmemCols = 2 * BN;
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                       ((uint32_t)(kBM >> 4) << 24);
+};
+constexpr int kMaxItems = 64;      // flagged (lag, tile) items per channel before the exhaustive rescore
+constexpr int kRescanWarps = 4;     // independent warps per rescore block
 
 struct Smem {
     uint64_t bar_full[kMaxStages];
@@ -53,20 +59,52 @@ struct Smem {
     int abort;
 };
 
-// Shifted residual rows: one thread per element of X[rows][Kt]; rows past
-// B * Ntc stay zero (set once at allocation).
-__global__ void __launch_bounds__(256) k_shift_rows(const float *__restrict__ R, int Lp, int L, int B, int Ntc,
-                                                    int S, int tc0, int m_lo, int Kt,
-                                                    __nv_bfloat16 *__restrict__ X) {
-    const int64_t total = (int64_t)B * Ntc * Kt;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = i / Kt;
-        const int kk = (int)(i % Kt);
-        const int b = (int)(row / Ntc), j = (int)(row % Ntc);
-        const int64_t n = (int64_t)m_lo + kk + tc0 + (int64_t)S * j;
-        const float v = (n >= 0 && n < L) ? R[(size_t)b * Lp + n] : 0.0f;
-        X[i] = __float2bfloat16_rn(v);
+// Shifted residual rows X[(b, j)][kk] = bf16(r_b[m_lo + kk + tc0 + S j]):
+// blockIdx.x = row (b, j), each thread 8 consecutive kk as one 16-byte
+// store.  Rows past B * Ntc stay zero (set once at allocation).  The block
+// of row (b, 0) also prepares channel b's selection for this order: |r| and
+// |bf16(r) - r| in FP64 (for the error bound), the channel maximum and item
+// count cleared.
+__global__ void __launch_bounds__(128) k_shift_rows(const float *__restrict__ R, int Lp, int L, int Ntc, int S,
+                                                    int tc0, int m_lo, int Kt, __nv_bfloat16 *__restrict__ X,
+                                                    double2 *__restrict__ chan_norm, unsigned int *__restrict__ chmax,
+                                                    int *__restrict__ chcount, long long *__restrict__ stats) {
+    __shared__ float sh[32];
+    const int row = blockIdx.x;
+    const int b = row / Ntc, j = row - b * Ntc;
+    const float *r = R + (size_t)b * Lp;
+    if (j == 0) {
+        // FP32 sums of at most 2048 squares are within 2048 * 2^-24 < 1.3e-4
+        // (relative) of the exact ones: inflated by 1e-3 they bound them
+        float e = 0.0f, de = 0.0f;
+        for (int n = threadIdx.x; n < L; n += blockDim.x) {
+            const float x = r[n];
+            const float d = __bfloat162float(__float2bfloat16_rn(x)) - x;  // exact
+            e = fmaf(x, x, e);
+            de = fmaf(d, d, de);
+        }
+        const float te = block_sum(e, sh);
+        const float tde = block_sum(de, sh);
+        if (threadIdx.x == 0) {
+            chan_norm[b] = make_double2(sqrt((double)te * (1.0 + 1e-3)), sqrt((double)tde * (1.0 + 1e-3)));
+            chmax[b] = 0u;
+            chcount[b] = 0;
+            atomicAdd((unsigned long long *)&stats[0], 1ull);
+        }
+    }
+    const int n0 = m_lo + tc0 + S * j;  // sample under kk = 0
+    uint4 *out = reinterpret_cast<uint4 *>(X + (size_t)row * Kt);
+    for (int c = threadIdx.x; c < (Kt >> 3); c += blockDim.x) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int n = n0 + 8 * c + 2 * h;
+            const float x0 = (n >= 0 && n < L) ? r[n] : 0.0f;
+            const float x1 = (n + 1 >= 0 && n + 1 < L) ? r[n + 1] : 0.0f;
+            __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
+            w[h] = *reinterpret_cast<uint32_t *>(&v);
+        }
+        out[c] = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -74,10 +112,15 @@ __global__ void __launch_bounds__(256) k_shift_rows(const float *__restrict__ R,
 // stage holds one template chunk (256 x 64) and the matching residual chunk
 // (128 x 64).  Warp 0: TMA producer; warp 1: MMA issuer; warp 2: tensor
 // memory owner; warps 4-7: epilogue (thread = residual row).
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_shift_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m_tiles,
                  int n_tiles, int nkc, int stages, int rows_valid, int Ntc, int T_pad,
-                 const float *__restrict__ scaleT, float *__restrict__ tile_max, int *status) {
+                 const float *__restrict__ scaleT, float *__restrict__ tile_max, unsigned int *__restrict__ chmax,
+                 int *status) {
+    using Cfg = ShiftTile<BN>;
+    constexpr int kBChunkBytes = Cfg::kBChunkBytes, kStageBytes = Cfg::kStageBytes;
+    constexpr uint32_t kTmemCols = Cfg::kTmemCols;
     extern __shared__ uint8_t dyn_raw[];
     __shared__ Smem sm;
     const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
@@ -124,8 +167,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const uint32_t b0 = base + (uint32_t)s * kStageBytes;
                 mbar_expect_tx(&sm.bar_full[s], (uint32_t)kStageBytes);
-                // templates: the tile-major layout seen as [tiles * nkc * 256][64]
-                tma_load_2d(b0, &tmB, 0, (int)(((int64_t)nt * nkc + kc) * kBN), &sm.bar_full[s]);
+                // templates: the tile-major layout seen as [blocks * nkc * 256][64]
+                const int64_t t0 = (int64_t)nt * BN, blk = t0 / kBlockRows, sub = t0 % kBlockRows;
+                tma_load_2d(b0, &tmB, 0, (int)((blk * nkc + kc) * kBlockRows + sub), &sm.bar_full[s]);
                 tma_load_2d(b0 + kBChunkBytes, &tmA, kc * kBK, mt * kBM, &sm.bar_full[s]);
             }
         }
@@ -140,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t d_tmem = tmem + acc * kBN;
+            const uint32_t d_tmem = tmem + acc * BN;
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
@@ -153,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t a0 = b0 + kBChunkBytes;
 #pragma unroll
                 for (int k = 0; k < kBK / kUmmaK; ++k)
-                    tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2), kIdesc,
+                    tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2), Cfg::kIdesc,
                            (kc | k) != 0 ? 1u : 0u);
                 tc_commit(&sm.bar_empty[s]);
             }
@@ -174,12 +218,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int row = mt * kBM + q * 32 + lane;
             const bool valid = row < rows_valid;
             const float4 *sc4 =
-                reinterpret_cast<const float4 *>(scaleT + (size_t)(valid ? row % Ntc : 0) * T_pad + (size_t)nt * kBN);
+                reinterpret_cast<const float4 *>(scaleT + (size_t)(valid ? row % Ntc : 0) * T_pad + (size_t)nt * BN);
             float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll 1
-            for (int c = 0; c < kBN / 32; ++c) {
+            for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * kBN + c * 32, v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c * 32, v);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const float4 s = valid ? __ldg(sc4 + c * 8 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -191,7 +235,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_before();
             mbar_arrive(&sm.bar_acc_empty[acc]);
-            if (valid) tile_max[(size_t)row * n_tiles + nt] = fmaxf(m0, m1);
+            const float mx = fmaxf(m0, m1);
+            if (valid) tile_max[(size_t)row * n_tiles + nt] = mx;
+            // channel maximum: non-negative floats order like their bits; one
+            // atomic per warp when its 32 rows belong to one channel
+            const int ch = valid ? row / Ntc : -1;
+            const unsigned bits = __float_as_uint(mx);
+            if (__all_sync(0xffffffffu, ch == __shfl_sync(0xffffffffu, ch, 0))) {
+                const unsigned wm = __reduce_max_sync(0xffffffffu, bits);
+                if (lane == 0 && ch >= 0) atomicMax(chmax + ch, wm);
+            } else if (ch >= 0) {
+                atomicMax(chmax + ch, bits);
+            }
         }
     }
 
@@ -207,7 +262,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Item selection for channel b (one block).  With s the exact score, f the
+// Item selection for channel b (blockIdx.y; blockIdx.x slices its entries).
+// With s the exact score, f the
 // FP32 template search's score and h the tensor-core score of an atom,
 //   |f - s| <= eps_r = (L + 4) 2^-23 |r|
 // (one FP32 chain of L products, the FP32 scale and the final product), and
@@ -217,128 +273,166 @@ __global__ void __launch_bounds__(kThreads, 1)
 // bf16(r) - r, the Kt term bounds FP32 accumulation in the tensor core, the
 // factor the scale product).  As for the dense BF16 search, the FP32 argmax
 // lies in an item whose largest |h| is >= hmax - 2 delta - 2 eps_r.
-__global__ void __launch_bounds__(256) k_shift_select(int Ntc, int n_tiles, int Kt, const float *__restrict__ tile_max,
-                                                      int Lp, int L, const float *__restrict__ R,
-                                                      const unsigned int *__restrict__ eps_bits,
-                                                      unsigned long long *__restrict__ keys, int *__restrict__ fb_list,
-                                                      int *__restrict__ counters, int *__restrict__ items,
-                                                      long long *__restrict__ stats) {
-    __shared__ double sh_d[32];
-    __shared__ float sh_f[32];
-    __shared__ int n_sh, base_sh;
-    __shared__ int list[kMaxItems];
-    const int b = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (int)(blockDim.x >> 5);
-    const float *r = R + (size_t)b * Lp;
-    const float *tm = tile_max + (size_t)b * Ntc * n_tiles;
-    const int n_entries = Ntc * n_tiles;
-
-    double e = 0.0, de = 0.0;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const float x = r[n];
-        const float d = __bfloat162float(__float2bfloat16_rn(x)) - x;
-        e = fma((double)x, (double)x, e);
-        de = fma((double)d, (double)d, de);
-    }
-    const double rn = sqrt(block_sum(e, sh_d));
-    const double drn = sqrt(block_sum(de, sh_d));
+__global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int Kt, int L,
+                                                    const float *__restrict__ tile_max,
+                                                    const double2 *__restrict__ chan_norm,
+                                                    const unsigned int *__restrict__ chmax,
+                                                    const unsigned int *__restrict__ eps_bits,
+                                                    int *__restrict__ chcount, int *__restrict__ fb_list,
+                                                    int *__restrict__ counters, int *__restrict__ items,
+                                                    long long *__restrict__ stats) {
+    const int b = blockIdx.y;
+    const double2 nr = chan_norm[b];
+    const double rn = nr.x, drn = nr.y;
     const double eps_u = (double)__uint_as_float(*eps_bits);
     const double rr = rn + drn;
     const double ulp = 1.1920928955078125e-07;  // 2^-23
     const double delta = (1.0 + 1e-5) * (eps_u * rr + drn + (double)Kt * ulp * (1.0 + eps_u) * rr);
     const double eps_r = (double)(L + 4) * ulp * rn;
-
-    float m = 0.0f;
-    for (int i = threadIdx.x; i < n_entries; i += blockDim.x) m = fmaxf(m, tm[i]);
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (lane == 0) sh_f[warp] = m;
-    if (threadIdx.x == 0) n_sh = 0;
-    __syncthreads();
-    float hmax = sh_f[0];
-    for (int w = 1; w < nwarps; ++w) hmax = fmaxf(hmax, sh_f[w]);
-    const double thr = (double)hmax - 2.0 * delta - 2.0 * eps_r;
-
-    for (int i = threadIdx.x; i < n_entries; i += blockDim.x) {
-        if ((double)tm[i] >= thr) {
-            const int pos = atomicAdd(&n_sh, 1);
-            if (pos < kMaxItems) list[pos] = i;  // i = j * n_tiles + tile
+    const double thr = (double)__uint_as_float(chmax[b]) - 2.0 * delta - 2.0 * eps_r;
+    // FP32 compare against the threshold rounded down: a superset of the items
+    const float thr_f = __double2float_rd(thr);
+    const float *tm = tile_max + (size_t)b * Ntc * n_tiles;
+    const int n_entries = Ntc * n_tiles;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_entries; i += gridDim.x * blockDim.x) {
+        if (tm[i] >= thr_f) {
+            const int pos = atomicAdd(chcount + b, 1);
+            if (pos < kMaxItems) {
+                const int at = atomicAdd(&counters[1], 1);
+                items[2 * at] = b;
+                items[2 * at + 1] = i;  // i = j * n_tiles + tile
+                atomicAdd((unsigned long long *)&stats[2], 1ull);
+            } else if (pos == kMaxItems) {
+                // too many: every item of this channel is rescored instead
+                fb_list[atomicAdd(&counters[0], 1)] = b;
+                atomicAdd((unsigned long long *)&stats[1], 1ull);
+                atomicAdd((unsigned long long *)&stats[0], ~0ull);  // -1: not resolved by the items
+            }
         }
-    }
-    __syncthreads();
-    const int n = n_sh;
-    if (n > kMaxItems) {
-        if (threadIdx.x == 0) {
-            keys[b] = 0ull;
-            fb_list[atomicAdd(&counters[0], 1)] = b;
-            atomicAdd((unsigned long long *)&stats[1], 1ull);
-        }
-        return;
-    }
-    if (threadIdx.x == 0) {
-        keys[b] = 0ull;
-        base_sh = atomicAdd(&counters[1], n);
-        atomicAdd((unsigned long long *)&stats[0], 1ull);
-        atomicAdd((unsigned long long *)&stats[2], (unsigned long long)n);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        items[2 * (base_sh + i)] = b;
-        items[2 * (base_sh + i) + 1] = list[i];
     }
 }
 
-// FP32 rescore of the flagged items, one block of 256 threads (one per
-// template of the tile) per item: the FMA chain over phases a and polyphase
-// steps p of the FP32 template search, in its order, then its scale.
-__global__ void __launch_bounds__(256) k_shift_rescan(const float *__restrict__ tpl, const float *__restrict__ scale,
-                                                      int S, int Sa, int P, int rows, int NtcP, int T, int n_tiles,
-                                                      int Lp, int L, const float *__restrict__ R,
-                                                      const int *__restrict__ items, const int *__restrict__ counters,
-                                                      unsigned long long *__restrict__ keys) {
-    extern __shared__ __align__(16) float rpoly[];  // [Sa][P]
-    __shared__ unsigned long long red[8];
-    const int n_items = counters[1];
+// FP32 rescore, one warp per (item, 32-template block): the flagged items
+// of every channel, and every item of the channels whose selection overflowed
+// (those are searched exhaustively this way).  Lane = template.  Per phase
+// a, the P template rows the FP32 template search reads for this lag
+// (contiguous, P x 128 bytes) arrive by a bulk copy into one of the warp's
+// two buffers (the next phase's copy is in flight while this one is used);
+// each lane runs the FP32 search's FMA chain over them in its order and
+// scales the sum the same way.  Each warp owns its barriers, buffers and
+// residual phases; warps never wait on one another.
+__global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
+    const float *__restrict__ tpl, const float *__restrict__ scale, int S, int Sa, int P, int rows, int NtcP,
+    int Ntc, int T, int n_tiles, int bpt, int Lp, int L, const float *__restrict__ R, const int *__restrict__ items,
+    const int *__restrict__ fb_list, const int *__restrict__ counters, unsigned long long *__restrict__ keys,
+    int *status) {
+    extern __shared__ __align__(128) float sm[];  // per warp: [Sa][P] residual phases, then 2 x [P][32] rows
+    __shared__ __align__(8) uint64_t bar[kRescanWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const int b = items[2 * w];
-        const int e = items[2 * w + 1];
-        const int j = e / n_tiles, tile = e % n_tiles;
-        const float *r = R + (size_t)b * Lp;
-        for (int i = threadIdx.x; i < Sa * P; i += blockDim.x) {
-            const int a = i / P, p = i % P;
-            const int n = a + S * p;
-            rpoly[i] = n < L ? r[n] : 0.0f;
+    const size_t warp_floats = (size_t)Sa * P + 2 * (size_t)P * 32;
+    float *rpoly = sm + warp * warp_floats;
+    float *buf0 = rpoly + (size_t)Sa * P;
+    const uint32_t bytes = (uint32_t)P * 128u;
+    const int n_flag = counters[1], n_fb = counters[0];
+    const int64_t per_fb = (int64_t)Ntc * n_tiles * bpt;  // warp tasks of one overflowed channel
+    const int64_t n_tasks = (int64_t)n_flag * bpt + (int64_t)n_fb * per_fb;
+    const int nw = (int)(blockDim.x >> 5);
+    if (lane == 0) {
+        mbar_init(&bar[warp][0], 1);
+        mbar_init(&bar[warp][1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t uses[2] = {0u, 0u};
+    int cur_b = -1;
+    // tasks go to the first warp of every block before the second (one task
+    // per SM while there are fewer tasks than SMs)
+    const int64_t stride = (int64_t)gridDim.x * nw;
+    for (int64_t task = (int64_t)warp * gridDim.x + blockIdx.x; task < n_tasks; task += stride) {
+        int b, j, tile, q;
+        if (task < (int64_t)n_flag * bpt) {
+            const int it = (int)(task / bpt);
+            q = (int)(task % bpt);
+            b = items[2 * it];
+            const int e = items[2 * it + 1];
+            j = e / n_tiles;
+            tile = e % n_tiles;
+        } else {
+            const int64_t f = task - (int64_t)n_flag * bpt;
+            b = fb_list[f / per_fb];
+            const int64_t rem = f % per_fb;  // (j, tile, q)
+            q = (int)(rem % bpt);
+            const int64_t e = rem / bpt;
+            j = (int)(e / n_tiles);
+            tile = (int)(e % n_tiles);
         }
-        __syncthreads();
-        const int t = tile * 256 + (int)threadIdx.x;
+        const int tb = tile * bpt + q;
+        if (tb * 32 >= T) continue;  // past the last template
+        const float *src = tpl + ((size_t)tb * Sa * rows + (size_t)(NtcP - 1 - j)) * 32;
+        __syncwarp();
+        if (lane == 0) {  // phase 0's rows, in flight while the residual is staged
+            mbar_expect_tx(&bar[warp][0], bytes);
+            bulk_g2s(buf0, src, bytes, &bar[warp][0]);
+        }
+        if (b != cur_b) {
+            __syncwarp();
+            const float *r = R + (size_t)b * Lp;
+            // zero the phases, then scatter the window (coalesced loads)
+            for (int i = lane; i < Sa * P; i += 32) rpoly[i] = 0.0f;
+            __syncwarp();
+#pragma unroll 4
+            for (int n = lane; n < L; n += 32) {
+                const int a = n % S, p = n / S;
+                rpoly[a * P + p] = r[n];
+            }
+            __syncwarp();
+            cur_b = b;
+        }
+        float acc = 0.0f;
+        int ok = 1, fail_a = 0;
+        for (int a = 0; a < Sa; ++a) {
+            const int cb = a & 1;
+            if (a + 1 < Sa && lane == 0) {
+                // the other buffer was released by the __syncwarp ending phase a - 1
+                mbar_expect_tx(&bar[warp][cb ^ 1], bytes);
+                bulk_g2s(buf0 + (size_t)(cb ^ 1) * P * 32, src + (size_t)(a + 1) * rows * 32, bytes,
+                         &bar[warp][cb ^ 1]);
+            }
+            ok = mbar_wait(&bar[warp][cb], uses[cb] & 1u) ? 1 : 0;
+            ++uses[cb];
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = 0;
+                fail_a = a;
+                break;
+            }
+            const float *rp = rpoly + a * P;
+            const float *bp = buf0 + (size_t)cb * P * 32 + lane;
+#pragma unroll 8
+            for (int p = 0; p < P; ++p) acc = fmaf(rp[p], bp[p * 32], acc);
+            __syncwarp();
+        }
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(status, kFlagTimeout);
+                // bounded: let the copies in flight land before the warp leaves
+                const int cb = fail_a & 1;
+                mbar_wait(&bar[warp][cb], (uses[cb] - 1) & 1u);
+                if (fail_a + 1 < Sa) mbar_wait(&bar[warp][cb ^ 1], uses[cb ^ 1] & 1u);
+            }
+            return;
+        }
+        const int t = tb * 32 + lane;
         unsigned long long key = 0ull;
         if (t < T) {
-            const int tb = t >> 5, tl = t & 31;
-            const float *base = tpl + (size_t)tb * Sa * rows * 32 + tl;
-            float acc = 0.0f;
-            for (int a = 0; a < Sa; ++a) {
-                const float *col = base + ((size_t)a * rows + (NtcP - 1 - j)) * 32;
-                const float *rp = rpoly + a * P;
-#pragma unroll 8
-                for (int p = 0; p < P; ++p) acc = fmaf(rp[p], col[(size_t)p * 32], acc);
-            }
-            const float s = acc * scale[((size_t)tb * NtcP + j) * 32 + tl];
-            const float x = fabsf(s);
+            const float sv = acc * scale[((size_t)tb * NtcP + j) * 32 + lane];
+            const float x = fabsf(sv);
             if (x == x) key = pack_key(x, (uint32_t)j * (uint32_t)T + (uint32_t)t);
         }
         for (int off = 16; off > 0; off >>= 1) {
             const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
             key = o > key ? o : key;
         }
-        if (lane == 0) red[warp] = key;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long m = 0ull;
-            for (int i = 0; i < 8; ++i) m = red[i] > m ? red[i] : m;
-            if (m) atomicMax(keys + b, m);
-        }
-        __syncthreads();
+        if (lane == 0 && key) atomicMax(keys + b, key);
     }
 }
 
@@ -348,14 +442,21 @@ constexpr int kSmemBudget = 232448 - kStaticReserve - 1024;
 }  // namespace
 
 struct ShiftTc {
-    CUtensorMap mapB;
-    int nkc = 0, n_tiles = 0, stages = 0, sm_count = 0;
-    size_t smem = 0;
+    CUtensorMap mapB[2];    // box heights 128 and 256
+    int nkc = 0, sm_count = 0, T_pad = 0;
+    int stages[2] = {0, 0};
+    size_t smem[2] = {0, 0};
+    int n_tiles = 0, bn = 0;  // of the current launch: n_tiles = T_pad / bn
     float *tile_max = nullptr;      // [rows_cap][n_tiles]
     int *items = nullptr;           // [B_cap * kMaxItems][2]
     __nv_bfloat16 *X = nullptr;     // [rows_cap rounded up to 128][Kt]
     int B_cap = 0;
     int rows_alloc = 0;
+    int rescan_warps = 0, rescan_blocks_per_sm = 0;
+    size_t rescan_smem = 0;
+    double2 *chan_norm = nullptr;   // [B_cap] |r|, |bf16(r) - r|
+    unsigned int *chmax = nullptr;  // [B_cap] largest tile maximum (float bits)
+    int *chcount = nullptr;         // [B_cap] items flagged this order
 };
 
 cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
@@ -364,17 +465,36 @@ cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
     ShiftTc *s = new (std::nothrow) ShiftTc();
     if (!s) return cudaErrorMemoryAllocation;
     s->nkc = sp.Kt / kBK;
-    s->n_tiles = sp.T_pad / kBN;
+    s->T_pad = sp.T_pad;
     s->sm_count = sm_count;
-    const uint64_t rows = (uint64_t)s->n_tiles * s->nkc * kBN;
-    if (rows >= ((uint64_t)1 << 31) || !make_map(&s->mapB, sp.tpl16, (uint64_t)kBK, rows, kBN)) {
+    const uint64_t rows = (uint64_t)(sp.T_pad / kBlockRows) * s->nkc * kBlockRows;
+    if (rows >= ((uint64_t)1 << 31) || !make_map(&s->mapB[0], sp.tpl16, (uint64_t)kBK, rows, 128) ||
+        !make_map(&s->mapB[1], sp.tpl16, (uint64_t)kBK, rows, 256)) {
         delete s;
         return cudaErrorNotSupported;
     }
-    int st = kSmemBudget / kStageBytes;
-    s->stages = st > kMaxStages ? kMaxStages : st;
-    s->smem = 1024 + (size_t)s->stages * kStageBytes;
-    cudaError_t e = allow_max_smem((const void *)k_shift_gemm, s->smem);
+    const int stage_bytes[2] = {ShiftTile<128>::kStageBytes, ShiftTile<256>::kStageBytes};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        int st = kSmemBudget / stage_bytes[i];
+        s->stages[i] = st > kMaxStages ? kMaxStages : st;
+        s->smem[i] = 1024 + (size_t)s->stages[i] * stage_bytes[i];
+        e = allow_max_smem(i == 0 ? (const void *)k_shift_gemm<128> : (const void *)k_shift_gemm<256>, s->smem[i]);
+    }
+    // rescore: per warp the residual phases and two P-row buffers; as many
+    // warps per block (up to kRescanWarps) as fit
+    const size_t per_warp = sizeof(float) * ((size_t)sp.Sa * sp.P + 2 * (size_t)sp.P * 32);
+    int rw = kRescanWarps;
+    while (rw > 1 && rw * per_warp > (size_t)kSmemBudget) --rw;
+    s->rescan_warps = rw;
+    s->rescan_smem = rw * per_warp;
+    if (e == cudaSuccess && s->rescan_smem > (size_t)kSmemBudget) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_shift_rescan, s->rescan_smem);
+    if (e == cudaSuccess) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shift_rescan, rw * 32, s->rescan_smem);
+        s->rescan_blocks_per_sm = per_sm < 1 ? 1 : per_sm;
+    }
     if (e != cudaSuccess) {
         delete s;
         return e;
@@ -388,6 +508,9 @@ void shift_tc_free(ShiftTc *s) {
     if (s->tile_max) cudaFree(s->tile_max);
     if (s->items) cudaFree(s->items);
     if (s->X) cudaFree(s->X);
+    if (s->chan_norm) cudaFree(s->chan_norm);
+    if (s->chmax) cudaFree(s->chmax);
+    if (s->chcount) cudaFree(s->chcount);
     delete s;
 }
 
@@ -397,17 +520,26 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
     if (s->tile_max) cudaFree(s->tile_max);
     if (s->items) cudaFree(s->items);
     if (s->X) cudaFree(s->X);
+    if (s->chan_norm) cudaFree(s->chan_norm);
+    if (s->chmax) cudaFree(s->chmax);
+    if (s->chcount) cudaFree(s->chcount);
     s->tile_max = nullptr;
     s->items = nullptr;
     s->X = nullptr;
+    s->chan_norm = nullptr;
+    s->chmax = nullptr;
+    s->chcount = nullptr;
     s->B_cap = 0;
     const int64_t rows = (int64_t)B * sp.Ntc;
     const int64_t rows_alloc = (rows + kBM - 1) / kBM * kBM;
     if (rows_alloc > (1ll << 30)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)rows * s->n_tiles);
+    cudaError_t e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)rows * (sp.T_pad / 128));
     if (e == cudaSuccess) e = cudaMalloc(&s->items, sizeof(int) * 2 * (size_t)B * kMaxItems);
     if (e == cudaSuccess) e = cudaMalloc(&s->X, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
     if (e == cudaSuccess) e = cudaMemset(s->X, 0, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
+    if (e == cudaSuccess) e = cudaMalloc(&s->chan_norm, sizeof(double2) * (size_t)B);
+    if (e == cudaSuccess) e = cudaMalloc(&s->chmax, sizeof(unsigned int) * (size_t)B);
+    if (e == cudaSuccess) e = cudaMalloc(&s->chcount, sizeof(int) * (size_t)B);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cudaErrorMemoryAllocation;
@@ -417,23 +549,32 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
     return cudaSuccess;
 }
 
-cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B, int *status,
-                                 cudaStream_t st) {
+cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
+                                 long long *stats, int *status, cudaStream_t st) {
     if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
-    const int64_t nx = (int64_t)B * sp.Ntc * sp.Kt;
-    int64_t blocks = (nx + 255) / 256;
-    if (blocks > (int64_t)s->sm_count * 8) blocks = (int64_t)s->sm_count * 8;
-    k_shift_rows<<<(int)blocks, 256, 0, st>>>(R, Lp, L, B, sp.Ntc, sp.S, sp.tc0, sp.m_lo, sp.Kt, s->X);
+    k_shift_rows<<<B * sp.Ntc, 128, 0, st>>>(R, Lp, L, sp.Ntc, sp.S, sp.tc0, sp.m_lo, sp.Kt, s->X, s->chan_norm,
+                                             s->chmax, s->chcount, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int rows_valid = B * sp.Ntc;
     const int m_tiles = (rows_valid + kBM - 1) / kBM;
     CUtensorMap mapA;
     if (!make_map(&mapA, s->X, (uint64_t)sp.Kt, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
+    // 256-template tiles unless they leave SMs idle
+    const int bn = (int64_t)m_tiles * (sp.T_pad / 256) >= s->sm_count ? 256 : 128;
+    const int i = bn == 256 ? 1 : 0;
+    s->bn = bn;
+    s->n_tiles = sp.T_pad / bn;
     const int64_t items = (int64_t)m_tiles * s->n_tiles;
     const int grid = (int)(items < s->sm_count ? items : s->sm_count);
-    k_shift_gemm<<<grid, kThreads, s->smem, st>>>(mapA, s->mapB, m_tiles, s->n_tiles, s->nkc, s->stages, rows_valid,
-                                                  sp.Ntc, sp.T_pad, sp.scaleT, s->tile_max, status);
+    if (bn == 256)
+        k_shift_gemm<256><<<grid, kThreads, s->smem[i], st>>>(mapA, s->mapB[i], m_tiles, s->n_tiles, s->nkc,
+                                                              s->stages[i], rows_valid, sp.Ntc, sp.T_pad, sp.scaleT,
+                                                              s->tile_max, s->chmax, status);
+    else
+        k_shift_gemm<128><<<grid, kThreads, s->smem[i], st>>>(mapA, s->mapB[i], m_tiles, s->n_tiles, s->nkc,
+                                                              s->stages[i], rows_valid, sp.Ntc, sp.T_pad, sp.scaleT,
+                                                              s->tile_max, s->chmax, status);
     return cudaGetLastError();
 }
 
@@ -441,21 +582,18 @@ cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float
                                     unsigned long long *keys, int *fb_list, int *counters, long long *stats,
                                     int *status, cudaStream_t st) {
     if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
-    k_shift_select<<<B, 256, 0, st>>>(sp.Ntc, s->n_tiles, sp.Kt, s->tile_max, Lp, L, R, sp.eps_bits, keys, fb_list,
-                                      counters, s->items, stats);
+    const int entries = sp.Ntc * s->n_tiles;
+    int slices = (entries + 255) / 256;
+    const int max_slices = (4 * s->sm_count + B - 1) / B;
+    if (slices > max_slices) slices = max_slices;
+    k_shift_flag<<<dim3(slices, B), 256, 0, st>>>(sp.Ntc, s->n_tiles, sp.Kt, L, s->tile_max, s->chan_norm, s->chmax,
+                                                  sp.eps_bits, s->chcount, fb_list, counters, s->items, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t rsmem = sizeof(float) * (size_t)sp.Sa * sp.P;
-    if (rsmem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_shift_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
-        if (e != cudaSuccess) return e;
-    }
-    k_shift_rescan<<<2 * s->sm_count, 256, rsmem, st>>>(sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.T,
-                                                       s->n_tiles, Lp, L, R, s->items, counters, keys);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // the FP32 template search for the channels with too many flagged items
-    return launch_shift_search(sp, R, Lp, L, B, keys, nullptr, status, false, st, fb_list, counters);
+    k_shift_rescan<<<s->sm_count * s->rescan_blocks_per_sm, s->rescan_warps * 32, s->rescan_smem, st>>>(
+        sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.Ntc, sp.T, s->n_tiles, s->bn / 32, Lp, L, R, s->items,
+        fb_list, counters, keys, status);
+    return cudaGetLastError();
 }
 
 

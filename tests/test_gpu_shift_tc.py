@@ -1,9 +1,9 @@
 """GPU checks of the tensor-core template search (ACT_SEARCH_SHIFT_BF16).
 
 The BF16 tcgen05 GEMM only narrows the search: every (time centre,
-256-template) tile that the BF16 error bound cannot exclude is rescored with
-the FP32 template search's own arithmetic, and channels with too many such
-tiles take the FP32 template search itself.  So the whole decomposition must
+template tile) that the BF16 error bound cannot exclude is rescored with the
+FP32 template search's own arithmetic, and a channel with too many such
+tiles has every tile rescored that way.  So the whole decomposition must
 equal ACT_SEARCH_SHIFT's bit for bit, and through it the oracle parity of
 tests/test_gpu_shift.py carries over; one lock-step check against the
 oracle is repeated here directly."""
@@ -103,8 +103,8 @@ def test_lockstep_against_oracle():
 
 
 def test_zero_signal_takes_the_fallback():
-    """All scores 0: every item ties, the channel has too many items and the
-    FP32 template search decides (index 0)."""
+    """All scores 0: every item ties, the channel has too many items and all
+    of its items are rescored (index 0 wins)."""
     grid = eeg_small()
     a, b, (resolved, items, fallbacks) = both(grid, np.zeros((2, grid.n_samples), np.float32), 2)
     assert_same(a, b)
