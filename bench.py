@@ -314,7 +314,7 @@ def run_ours(args):
 
     shift = None
     if not args.no_shift:
-        shift = bench_shift(args, dev, stream, ms / args.steps, fp32_picks, clk.summary())
+        shift = bench_shift(args, dev, stream, ms / args.steps, fp32_picks, clk.summary(), peaks, peak_kind)
     bf16 = None
     if not args.no_bf16:
         bf16 = bench_bf16(args, dev, stream, peaks, peak_kind)
@@ -358,17 +358,57 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks):
-    """Template dictionary + shift-correlation search on the headline
-    workload (one EEG-like channel, 2,097,152 atoms, 20 orders): no atom rows
-    stored, every atom formed in-kernel from its (fc, logDt, c) template.
-    Reported beside the FP32 GEMV on the same signal, and on 64 channels."""
+def _time_decompose(act, torch, h, sig, P, steps, stream, dev):
+    """ms per decomposition (clean pass), then a profiled pass: average search
+    and dominant-kernel ms per order, kernels per call; and the outputs."""
+    B, L = sig.shape
+    out = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+           torch.empty((B, P), dtype=torch.float32, device=dev),
+           torch.empty((B, L), dtype=torch.float32, device=dev),
+           torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
+    for _ in range(3):
+        act.act_decompose(h, sig, B, P, *out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        act.act_decompose(h, sig, B, P, *out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    act.act_set_profiling(h, True)
+    act.act_decompose(h, sig, B, P, *out, stream)
+    search, core, n = 0.0, 0.0, 0
+    for _ in range(max(2, steps // 4)):
+        act.act_decompose(h, sig, B, P, *out, stream)
+        s_i, c_i, n_i, kernels = act.act_profile_read(h)
+        search += s_i
+        core += c_i
+        n += n_i
+    act.act_set_profiling(h, False)
+    st = act.act_grid_status(h, stream)
+    if st != act.ACT_OK:
+        raise RuntimeError(act.status_name(st))
+    return ms, search / max(1, n), core / max(1, n), kernels, n, [o.clone() for o in out]
+
+
+def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks, peaks, peak_kind):
+    """Template dictionary (no atom rows stored; every atom formed in-kernel
+    from its (fc, logDt, c) template) on the headline workload (one EEG-like
+    channel, 2,097,152 atoms, 20 orders) and on 64 EEG-like channels: the
+    FP32 template search (CUDA cores) and the tensor-core template search
+    (BF16 tcgen05 GEMM + exact FP32 rescore), whose selections are checked
+    equal bit for bit."""
     import torch
 
     from paper_2607_16629_gb300 import act, synth
     grid = synth.grid_eeg()
     P, K, L = 20, grid.n_atoms, grid.n_samples
     sig1 = torch.tensor(synth.eeg_like_signal(2, 0)[0][None, :], dtype=torch.float32, device=dev)
+    w3 = synth.workload_c3()
+    B = w3.signals.shape[0]
+    sig64 = torch.tensor(w3.signals, dtype=torch.float32, device=dev)
+    steps = args.steps
     h = act.act_grid_create(grid, dev.index)
     try:
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -379,81 +419,76 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks):
         build_ms = b0.elapsed_time(b1)
         act.act_autotune(h, sig1, 1, stream)
         lags, warps, stages, ctas_per_sm = act.act_get_shift_tuning(h)
-        out = [torch.empty((1, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
-               torch.empty((1, P), dtype=torch.float32, device=dev),
-               torch.empty((1, L), dtype=torch.float32, device=dev),
-               torch.empty((1, P + 1), dtype=torch.float64, device=dev)]
-        for _ in range(3):
-            act.act_decompose(h, sig1, 1, P, *out, stream)
-        steps = args.steps
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(steps):
-            act.act_decompose(h, sig1, 1, P, *out, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / steps
-        same = bool(torch.equal(act.atom_indices(out[0]), act.atom_indices(fp32_atoms)))
-        act.act_set_profiling(h, True)
-        act.act_decompose(h, sig1, 1, P, *out, stream)
-        core_ms, core_n = 0.0, 0
-        for _ in range(steps):
-            act.act_decompose(h, sig1, 1, P, *out, stream)
-            _, c_i, n_i, kernels = act.act_profile_read(h)
-            core_ms += c_i
-            core_n += n_i
-        act.act_set_profiling(h, False)
-        # 64 channels on the same templates
-        w3 = synth.workload_c3()
-        B = w3.signals.shape[0]
-        sig64 = torch.tensor(w3.signals, dtype=torch.float32, device=dev)
-        out64 = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
-                 torch.empty((B, P), dtype=torch.float32, device=dev),
-                 torch.empty((B, L), dtype=torch.float32, device=dev),
-                 torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
-        act.act_decompose(h, sig64, B, P, *out64, stream)
-        n64 = 3
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(n64):
-            act.act_decompose(h, sig64, B, P, *out64, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = e0.elapsed_time(e1) / n64
-        st = act.act_grid_status(h, stream)
-        if st != act.ACT_OK:
-            raise RuntimeError(act.status_name(st))
+        act.act_set_search(h, act.ACT_SEARCH_SHIFT)
+        f1 = _time_decompose(act, torch, h, sig1, P, steps, stream, dev)
+        act.act_set_search(h, act.ACT_SEARCH_SHIFT_BF16)
+        t1 = _time_decompose(act, torch, h, sig1, P, steps, stream, dev)
+        st0 = act.act_bf16_stats(h)
+        t64 = _time_decompose(act, torch, h, sig64, P, max(3, steps // 4), stream, dev)
+        st1 = act.act_bf16_stats(h)
+        act.act_set_search(h, act.ACT_SEARCH_SHIFT)
+        f64 = _time_decompose(act, torch, h, sig64, P, 2, stream, dev)
     finally:
         act.act_destroy(h)
+    same_fp32 = all(torch.equal(a, b) for a, b in zip(f1[5], t1[5])) and \
+        all(torch.equal(a, b) for a, b in zip(f64[5], t64[5]))
+    same_gemv = bool(torch.equal(act.atom_indices(f1[5][0]), act.atom_indices(fp32_atoms)))
     T = grid.fc.count * grid.logdt.count * grid.c.count
     S, Ntc = int(grid.tc.step), grid.tc.count
     rows = (Ntc + 31) // 32 * 32 + (L + S - 1) // S - 1
-    tpl_bytes = T * S * rows * 4 + T * ((Ntc + 31) // 32 * 32) * 4
-    flops = 2.0 * K * L
-    avg = core_ms / max(1, core_n)
+    kt = (L - 1 + S * (Ntc - 1) + 1 + 63) // 64 * 64
+    tpl_bytes = T * S * rows * 4 + 2 * T * ((Ntc + 31) // 32 * 32) * 4 + T * kt * 2
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (avg / 1e3) / 1e12
-    return {"workload": "eeg_like_1ch_n512_k2097152_p20 (the headline signal)",
-            "value": K * P / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "speedup_vs_fp32_gemv": fp32_ms_per_step / ms,
-            "same_selections_as_fp32_gemv": same,
-            "template_build_ms": build_ms, "template_bytes": tpl_bytes,
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu = 2.0 * K * L / (f1[2] / 1e3) / 1e12
+    tc_peak = peaks["bf16_tflops_sustained"]
+    alg64 = 2.0 * B * K * L / (t64[2] / 1e3) / 1e12
+    mma64 = 2.0 * B * Ntc * T * kt / (t64[2] / 1e3) / 1e12
+    fb = [y - x for x, y in zip(st0, st1)]
+    return {"workload": "eeg_like_n512_k2097152_p20: 1 channel (the headline signal) and 64 channels",
+            "value": K * P / (t1[0] / 1e3), "unit": UNIT, "ms_per_step": t1[0],
+            "search": "tensor-core template search (default for a template build)",
+            "speedup_vs_fp32_gemv": fp32_ms_per_step / t1[0],
+            "same_selections_as_fp32_gemv": same_gemv,
+            "tensor_equals_fp32_template_search_bit_for_bit": bool(same_fp32),
+            "template_build_ms": build_ms, "template_bytes": int(tpl_bytes),
             "fp32_dictionary_bytes": K * L * 4,
-            "tuning": {"lags_per_thread": lags, "warps": warps, "stages": stages, "ctas_per_sm": ctas_per_sm},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": _profile_traffic("shift_search_eeg_k2097152_n512.md",
-                                                     ["paper_2607_16629_gb300/csrc/act_shift.cu",
-                                                      "paper_2607_16629_gb300/csrc/act_device.cuh"]),
-                         "traffic_note": "DRAM bytes of one cold-cache launch (templates + scales read once)",
-                         "kernel": "k_shift_search (FP32 FMA, templates in shared memory)",
-                         "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg, "launches_timed": core_n,
-                         "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 FMA/clk x 2 flop x "
-                                        f"{sm_mhz:.0f} MHz (maximum SM clock)"},
-            "channels_64": {"ms_per_step": ms64, "value": B * K * P / (ms64 / 1e3), "unit": UNIT}}
+            "fp32_template_search": {
+                "ms_per_step": f1[0], "value": K * P / (f1[0] / 1e3), "unit": UNIT,
+                "tuning": {"lags_per_thread": lags, "warps": warps, "stages": stages, "ctas_per_sm": ctas_per_sm},
+                "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+                             "frac": alu / alu_peak,
+                             "traffic": _profile_traffic("shift_search_eeg_k2097152_n512.md",
+                                                         ["paper_2607_16629_gb300/csrc/act_shift.cu",
+                                                          "paper_2607_16629_gb300/csrc/act_device.cuh"]),
+                             "kernel": "k_shift_search (FP32 FMA, templates in shared memory)",
+                             "algorithmic_flops_per_launch": 2.0 * K * L, "avg_launch_ms": f1[2],
+                             "launches_timed": f1[4],
+                             "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 FMA/clk x 2 flop x "
+                                            f"{sm_mhz:.0f} MHz (maximum SM clock)"}},
+            "tensor_template_search_1ch": {"ms_per_step": t1[0], "search_ms_per_order": t1[1],
+                                           "rows_gemm_ms_per_order": t1[2], "kernels_per_call": t1[3]},
+            "channels_64": {
+                "tensor_ms_per_step": t64[0], "tensor_value": B * K * P / (t64[0] / 1e3),
+                "fp32_template_ms_per_step": f64[0], "fp32_template_value": B * K * P / (f64[0] / 1e3),
+                "unit": UNIT, "search_ms_per_order": t64[1], "rows_gemm_ms_per_order": t64[2],
+                "resolved_items_fallbacks": fb,
+                "roofline": {"bound": "tensor", "achieved": alg64, "peak": tc_peak, "unit": "TFLOP/s",
+                             "frac": alg64 / tc_peak,
+                             "traffic": _profile_traffic("shift_gemm_tc_eeg_b64.md",
+                                                         ["paper_2607_16629_gb300/csrc/act_shift_tc.cu",
+                                                          "paper_2607_16629_gb300/csrc/act_tc.cuh",
+                                                          "paper_2607_16629_gb300/csrc/act_device.cuh"]),
+                             "kernel": "k_shift_rows + k_shift_gemm<256> (BF16 tcgen05, scaled tile maxima)",
+                             "algorithmic_flops_per_launch": 2.0 * B * K * L,
+                             "mma_flops_per_launch": 2.0 * B * Ntc * T * kt, "mma_tflops": mma64,
+                             "mma_frac": mma64 / tc_peak, "avg_launch_ms": t64[2],
+                             "peak_source": f"{peak_kind} bf16_tflops_sustained",
+                             "note": "the shifted-residual GEMM multiplies Kt = 1024 lags per atom, L = 512 of "
+                                     "them nonzero: achieved counts 2 K L flops per channel, mma_tflops "
+                                     "everything the tensor cores execute; timed by an event pair around the "
+                                     "shifted-row build and the GEMM"}}}
 
 
 def bench_bf16(args, dev, stream, peaks, peak_kind):

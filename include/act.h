@@ -120,7 +120,8 @@ typedef enum {
  *                    arithmetic, so the selection equals ACT_SEARCH_SHIFT's
  *                    bit for bit.
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
- *                    SHIFT with ACT_DICT_RECOMPUTE, FP32 otherwise. */
+ *                    SHIFT_BF16 with ACT_DICT_RECOMPUTE (SHIFT where the
+ *                    tensor-core view could not be set up), FP32 otherwise. */
 typedef enum {
     ACT_SEARCH_AUTO = 0,
     ACT_SEARCH_FP32 = 1,

@@ -277,7 +277,7 @@ act_status lem_configure(act_grid *g, const act_lem_params *p) {
 act_search_mode effective_search(const act_grid *g) {
     if (g->search != ACT_SEARCH_AUTO) return g->search;
     if (g->built == ACT_DICT_BF16) return ACT_SEARCH_BF16;
-    if (g->built == ACT_DICT_RECOMPUTE) return ACT_SEARCH_SHIFT;
+    if (g->built == ACT_DICT_RECOMPUTE) return g->shift_tc ? ACT_SEARCH_SHIFT_BF16 : ACT_SEARCH_SHIFT;
     return ACT_SEARCH_FP32;
 }
 

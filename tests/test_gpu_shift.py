@@ -38,6 +38,7 @@ class Templates:
     def __enter__(self):
         self.h = act.act_grid_create(self.grid, 0)
         act.act_dictionary_build(self.h, act.ACT_DICT_RECOMPUTE)
+        act.act_set_search(self.h, act.ACT_SEARCH_SHIFT)  # the FP32 template search (AUTO picks tensor cores)
         if self.refine:
             act.act_set_refinement(self.h, self.refine)
         return self.h
@@ -225,6 +226,7 @@ def test_ragged_plan_with_template_grids():
     try:
         for h in hs:
             act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+            act.act_set_search(h, act.ACT_SEARCH_SHIFT)
         plan = act.act_ragged_plan_create(hs, offsets, 5)
         try:
             flat = torch.tensor(np.concatenate(sigs), dtype=torch.float32, device="cuda")
