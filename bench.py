@@ -580,24 +580,19 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
             "gpu_launches": kernels * steps}
 
 
-def bench_ragged(args, dev, stream, peaks, peak_kind):
-    """Uneven batch: 256 EMG-like signals, N uniform in {256, 512, 1024, 2048}
-    at fs = 500 Hz, each over the 256 x 96 x 8 x 24 = 4,718,592-atom grid of
-    its length (four stored BF16 + FP32 dictionaries, 108 GB), 30 orders, BF16
-    search, all length groups in one CUDA graph."""
-    import torch
-
-    from paper_2607_16629_gb300 import act, synth
-    sigs, grids_py, P = synth.workload_c4()
-    lengths = sorted({int(len(x)) for x in sigs})
-    offsets = np.concatenate([[0], np.cumsum([len(x) for x in sigs])]).astype(np.int64)
+def _ragged_run(act, torch, synth, sigs, lengths, offsets, P, dict_mode, steps, dev, stream):
+    """One ragged plan over per-length grids built with dict_mode: ms per
+    decomposition of all channels, build seconds, device bytes held by the
+    grids and the plan, plan info, and the selected flat indices."""
     handles = {}
+    torch.cuda.synchronize(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
     t0 = time.perf_counter()
     try:
         for L in lengths:
             h = act.act_grid_create(synth.grid_emg(L), dev.index)
             handles[L] = h
-            act.act_dictionary_build(h, act.ACT_DICT_BF16, stream)
+            act.act_dictionary_build(h, dict_mode, stream)
         torch.cuda.synchronize(dev)
         build_s = time.perf_counter() - t0
         flat = torch.tensor(np.concatenate(sigs).astype(np.float32), device=dev)
@@ -614,49 +609,73 @@ def bench_ragged(args, dev, stream, peaks, peak_kind):
                    torch.empty((C, P + 1), dtype=torch.float64, device=dev)]
             act.act_ragged_decompose(plan, flat, *out, stream)
             torch.cuda.synchronize(dev)
-            steps = max(2, args.steps // 10)
+            used = free0 - torch.cuda.mem_get_info(dev)[0]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(steps):
                 act.act_ragged_decompose(plan, flat, *out, stream)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1)
+            ms = e0.elapsed_time(e1) / steps
             for L in lengths:
                 st = act.act_grid_status(handles[L], stream)
                 if st != act.ACT_OK:
                     raise RuntimeError(act.status_name(st))
             groups, kernels = act.act_ragged_plan_info(plan)
+            idx_out = act.atom_indices(out[0]).cpu().numpy()
         finally:
             act.act_ragged_plan_destroy(plan)
-        K = synth.grid_emg(256).n_atoms
-        bf16_bytes = sum(K * L * 2 for L in lengths)
-        counts = {L: sum(1 for x in sigs if len(x) == L) for L in lengths}
-        return {"workload": "emg_like_ragged_256ch_n256-2048_fs500_grid256x96x8x24_k4718592_p30",
-                "value": C * K * P * steps / (ms / 1e3), "unit": UNIT, "atoms_per_s": C * P * steps / (ms / 1e3),
-                "ms_per_step": ms / steps, "steps": steps, "channels_per_length": counts,
-                "dictionary_build_s": build_s, "length_groups": groups, "gpu_launches": kernels * steps,
-                "hbm_frac_of_bf16_dictionary_stream": bf16_bytes * P / (ms / steps / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 tile rescan"}
     finally:
         for h in handles.values():
             act.act_destroy(h)
+    return ms, build_s, int(used), groups, kernels, idx_out
 
 
-def bench_refine(args, dev, stream, peaks, peak_kind):
-    """Radar-like workload: 32 channels, N = 1024, fs = 1 kHz, 4 off-grid
-    chirplets each, 256 x 128 x 8 x 32 = 8,388,608-atom grid (stored FP32 +
-    BF16, 51 GB), 10 orders, each grid selection followed by 20 BFGS
-    iterations of off-grid refinement on the GPU; compared with the grid-only
-    search on the same signals."""
+def bench_ragged(args, dev, stream, peaks, peak_kind):
+    """Uneven batch: 256 EMG-like signals, N uniform in {256, 512, 1024, 2048}
+    at fs = 500 Hz, each over the 256 x 96 x 8 x 24 = 4,718,592-atom grid of
+    its length, 30 orders, all length groups in one CUDA graph.  Two builds:
+    template dictionaries (atoms generated in-kernel from per-(fc, logDt, c)
+    templates, tensor-core template search), the configuration's own
+    "generated in-kernel" reading; and stored BF16 + FP32 dictionaries (108 GB)
+    with the dense BF16 tensor-core search."""
     import torch
 
     from paper_2607_16629_gb300 import act, synth
-    w = synth.workload_c5()
+    sigs, grids_py, P = synth.workload_c4()
+    lengths = sorted({int(len(x)) for x in sigs})
+    offsets = np.concatenate([[0], np.cumsum([len(x) for x in sigs])]).astype(np.int64)
+    steps = max(2, args.steps // 10)
+    C = len(sigs)
+    K = synth.grid_emg(256).n_atoms
+    t_ms, t_build, t_bytes, groups, kernels, t_idx = _ragged_run(act, torch, synth, sigs, lengths, offsets, P,
+                                                                  act.ACT_DICT_RECOMPUTE, steps, dev, stream)
+    d_ms, d_build, d_bytes, _, d_kernels, d_idx = _ragged_run(act, torch, synth, sigs, lengths, offsets, P,
+                                                               act.ACT_DICT_BF16, steps, dev, stream)
+    bf16_bytes = sum(K * L * 2 for L in lengths)
+    counts = {L: sum(1 for x in sigs if len(x) == L) for L in lengths}
+    return {"workload": "emg_like_ragged_256ch_n256-2048_fs500_grid256x96x8x24_k4718592_p30",
+            "value": C * K * P / (t_ms / 1e3), "unit": UNIT, "atoms_per_s": C * P / (t_ms / 1e3),
+            "ms_per_step": t_ms, "steps": steps, "channels_per_length": counts,
+            "search": "template dictionaries, tensor-core template search (atoms generated in-kernel)",
+            "dictionary_build_s": t_build, "device_bytes": t_bytes, "length_groups": groups,
+            "gpu_launches": kernels * steps,
+            "stored_bf16_dictionaries": {
+                "value": C * K * P / (d_ms / 1e3), "unit": UNIT, "ms_per_step": d_ms,
+                "dictionary_build_s": d_build, "device_bytes": d_bytes, "gpu_launches": d_kernels * steps,
+                "hbm_frac_of_bf16_dictionary_stream": bf16_bytes * P / (d_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "same_selections_as_template_search": float(np.mean(d_idx == t_idx)),
+                "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 tile rescan"},
+            "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 rescore"}
+
+
+def _refine_runs(act, torch, w, dict_mode, steps_list, n, dev, stream):
     B, P, K, L = w.signals.shape[0], w.n_atoms, w.grid.n_atoms, w.grid.n_samples
+    torch.cuda.synchronize(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
     h = act.act_grid_create(w.grid, dev.index)
     try:
-        act.act_dictionary_build(h, act.ACT_DICT_BF16, stream)
+        act.act_dictionary_build(h, dict_mode, stream)
         sig = torch.tensor(w.signals, dtype=torch.float32, device=dev)
         act.act_autotune(h, sig, B, stream)
         out = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
@@ -664,11 +683,11 @@ def bench_refine(args, dev, stream, peaks, peak_kind):
                torch.empty((B, L), dtype=torch.float32, device=dev),
                torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
         res = {}
-        for steps in (0, 20):
+        for steps in steps_list:
             act.act_set_refinement(h, steps)
             act.act_decompose(h, sig, B, P, *out, stream)
             torch.cuda.synchronize(dev)
-            n = max(2, args.steps // 10)
+            used = free0 - torch.cuda.mem_get_info(dev)[0]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(n):
@@ -681,16 +700,43 @@ def bench_refine(args, dev, stream, peaks, peak_kind):
                 raise RuntimeError(act.status_name(st))
             en = out[3].cpu().numpy()
             res[steps] = {"ms_per_step": ms, "projections_per_s": B * K * P / (ms / 1e3),
-                          "mean_normalised_residue": float(np.mean(en[:, -1] / en[:, 0]))}
-        extra_ms = res[20]["ms_per_step"] - res[0]["ms_per_step"]
-        return {"workload": "radar_like_32ch_n1024_fs1000_grid256x128x8x32_k8388608_p10_bfgs20",
-                "value": res[20]["projections_per_s"], "unit": UNIT, "ms_per_step": res[20]["ms_per_step"],
-                "grid_only": res[0], "refined": res[20],
-                "bfgs_iterations_per_s": B * P * 20 / (max(extra_ms, 1e-6) / 1e3),
-                "refinement_ms_per_order": extra_ms / P,
-                "dtype": "bf16 search + f32 tile rescan; refinement f32 samples, f64 sums"}
+                          "mean_normalised_residue": float(np.mean(en[:, -1] / en[:, 0])), "device_bytes": int(used),
+                          "coefs": out[1].clone()}
     finally:
         act.act_destroy(h)
+    return res
+
+
+def bench_refine(args, dev, stream, peaks, peak_kind):
+    """Radar-like workload: 32 channels, N = 1024, fs = 1 kHz, 4 off-grid
+    chirplets each, 256 x 128 x 8 x 32 = 8,388,608-atom grid, 10 orders, each
+    grid selection followed by 20 BFGS iterations of off-grid refinement on
+    the GPU; compared with the grid-only search on the same signals.  Atoms
+    generated in-kernel from a template dictionary (tensor-core template
+    search), the configuration's "recomputed in-kernel" reading; and, for
+    comparison, the stored FP32 + BF16 dictionary (51 GB) with the dense BF16
+    search."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    w = synth.workload_c5()
+    B, P = w.signals.shape[0], w.n_atoms
+    n = max(2, args.steps // 10)
+    t = _refine_runs(act, torch, w, act.ACT_DICT_RECOMPUTE, (0, 20), n, dev, stream)
+    d = _refine_runs(act, torch, w, act.ACT_DICT_BF16, (20,), n, dev, stream)
+    extra_ms = t[20]["ms_per_step"] - t[0]["ms_per_step"]
+    same = bool(torch.equal(t[20]["coefs"], d[20]["coefs"]))
+    for r in (t[0], t[20], d[20]):
+        r.pop("coefs")
+    return {"workload": "radar_like_32ch_n1024_fs1000_grid256x128x8x32_k8388608_p10_bfgs20",
+            "value": t[20]["projections_per_s"], "unit": UNIT, "ms_per_step": t[20]["ms_per_step"],
+            "search": "template dictionary, tensor-core template search (atoms generated in-kernel)",
+            "grid_only": t[0], "refined": t[20],
+            "bfgs_iterations_per_s": B * P * 20 / (max(extra_ms, 1e-6) / 1e3),
+            "refinement_ms_per_order": extra_ms / P,
+            "stored_dictionary_refined": d[20],
+            "same_coefficients_as_stored_dictionary": same,
+            "dtype": "bf16 search + f32 rescore; refinement f32 samples, f64 sums"}
 
 
 def bench_lem(args, dev, stream, peaks, peak_kind):
