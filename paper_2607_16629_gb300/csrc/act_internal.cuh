@@ -134,6 +134,7 @@ cudaError_t launch_update_refined(int Lp, float *R, __nv_bfloat16 *R16, int Lb, 
 struct ShiftPlan {
     int S = 0, tc0 = 0;         // tc_j = tc0 + S j, whole samples
     int Sa = 0;                 // phases holding samples: min(S, L)
+    int L = 0;                  // window length
     int Ntc = 0, NtcP = 0;      // lags, and lags rounded up to 32
     int P = 0;                  // polyphase length ceil(L / S) rounded up to 16
     int T = 0, TB = 0;          // templates (fc, logDt, c triples) and 32-template blocks

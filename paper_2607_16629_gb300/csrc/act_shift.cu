@@ -430,6 +430,7 @@ cudaError_t shift_plan(ShiftPlan &sp, const GridAxes &ax) {
         return cudaErrorNotSupported;
     sp.S = (int)step;
     sp.Sa = sp.S < ax.L ? sp.S : ax.L;
+    sp.L = ax.L;
     sp.tc0 = (int)lo;
     sp.Ntc = ax.count[0];
     sp.NtcP = (sp.Ntc + 31) / 32 * 32;

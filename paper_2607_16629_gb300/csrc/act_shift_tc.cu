@@ -59,19 +59,63 @@ struct Smem {
     int abort;
 };
 
+// Named barrier 1 over the 128 epilogue threads, returning whether any of
+// them passed a nonzero predicate (all of them get the same answer).
+__device__ __forceinline__ int epilogue_bar_or(int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, 128, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred)
+        : "memory");
+    return r;
+}
+
+// Row tiles of the GEMM: tile mt = g * n_cb + cb holds Bg = 128 / Jt
+// channels (cb * Bg ..) times Jt neighbouring time centres (g * Jt ..); local
+// row lr = (b - cb Bg) Jt + (j - g Jt).  Rows of one tile see the window
+// only over lags [kc_lo, kc_hi] (in 64-lag chunks): L + (Jt - 1) S lags
+// instead of Kt, the chunks outside hold only zero products and are skipped.
+struct RowTiling {
+    int B, Ntc, Jt, Bg, n_cb, m_tiles;
+    int S, L, span0;  // span0 = -m_lo - tc0 = S (Ntc - 1); sample n at time centre j sits at lag n + span0 - S j
+};
+
+__host__ __device__ inline void tile_row(const RowTiling &t, int mt, int lr, int &b, int &j) {
+    const int g = mt / t.n_cb, cb = mt - g * t.n_cb;
+    b = cb * t.Bg + lr / t.Jt;
+    j = g * t.Jt + lr % t.Jt;
+}
+
+__host__ __device__ inline void tile_chunks(const RowTiling &t, int mt, int &kc_lo, int &kc_hi) {
+    const int g = mt / t.n_cb;
+    const int j_first = g * t.Jt;
+    const int j_last = min(j_first + t.Jt, t.Ntc) - 1;
+    const int kk_min = t.span0 - t.S * j_last;           // sample 0 at the last time centre
+    const int kk_max = t.L - 1 + t.span0 - t.S * j_first;  // sample L - 1 at the first
+    kc_lo = kk_min / kBK;
+    kc_hi = kk_max / kBK;
+}
+
 // Shifted residual rows X[(b, j)][kk] = bf16(r_b[m_lo + kk + tc0 + S j]):
-// blockIdx.x = row (b, j), each thread 8 consecutive kk as one 16-byte
-// store.  Rows past B * Ntc stay zero (set once at allocation).  The block
-// of row (b, 0) also prepares channel b's selection for this order: |r| and
-// |bf16(r) - r| in FP64 (for the error bound), the channel maximum and item
-// count cleared.
-__global__ void __launch_bounds__(128) k_shift_rows(const float *__restrict__ R, int Lp, int L, int Ntc, int S,
-                                                    int tc0, int m_lo, int Kt, __nv_bfloat16 *__restrict__ X,
+// blockIdx.x = X row (tile mt, local row lr), each thread 8 consecutive kk as
+// one 16-byte store; padding rows (b >= B or j >= Ntc) are not written (the
+// GEMM's epilogue ignores them).  The block of (b, 0) also prepares channel
+// b's selection for this order: |r| and |bf16(r) - r| (for the error bound),
+// the channel maximum and item count cleared.
+__global__ void __launch_bounds__(128) k_shift_rows(RowTiling t, const float *__restrict__ R, int Lp, int tc0,
+                                                    int m_lo, int Kt, __nv_bfloat16 *__restrict__ X,
                                                     double2 *__restrict__ chan_norm, unsigned int *__restrict__ chmax,
                                                     int *__restrict__ chcount, long long *__restrict__ stats) {
     __shared__ float sh[32];
     const int row = blockIdx.x;
-    const int b = row / Ntc, j = row - b * Ntc;
+    int b, j;
+    tile_row(t, row / kBM, row % kBM, b, j);
+    if (b >= t.B || j >= t.Ntc) return;
+    const int L = t.L, S = t.S;
     const float *r = R + (size_t)b * Lp;
     if (j == 0) {
         // FP32 sums of at most 2048 squares are within 2048 * 2^-24 < 1.3e-4
@@ -114,10 +158,11 @@ __global__ void __launch_bounds__(128) k_shift_rows(const float *__restrict__ R,
 // memory owner; warps 4-7: epilogue (thread = residual row).
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_shift_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m_tiles,
-                 int n_tiles, int nkc, int stages, int rows_valid, int Ntc, int T_pad,
-                 const float *__restrict__ scaleT, float *__restrict__ tile_max, unsigned int *__restrict__ chmax,
-                 int *status) {
+    k_shift_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowTiling tl,
+                 int n_tiles, int nkc, int stages, int T_pad, const float *__restrict__ scaleT,
+                 float *__restrict__ tile_max, unsigned int *__restrict__ chmax, int *status) {
+    // shared memory: stages, then the item's scales [Jt][BN + 4] (the +4
+    // floats of padding spread the Jt rows a warp reads over the banks)
     using Cfg = ShiftTile<BN>;
     constexpr int kBChunkBytes = Cfg::kBChunkBytes, kStageBytes = Cfg::kStageBytes;
     constexpr uint32_t kTmemCols = Cfg::kTmemCols;
@@ -125,7 +170,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ Smem sm;
     const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t items = (int64_t)m_tiles * n_tiles;
+    const int64_t items = (int64_t)tl.m_tiles * n_tiles;
+    const int Ntc = tl.Ntc;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -158,7 +204,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t it = 0;
         for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
             const int mt = (int)(w / n_tiles), nt = (int)(w % n_tiles);
-            for (int kc = 0; kc < nkc; ++kc, ++it) {
+            int kc_lo, kc_hi;
+            tile_chunks(tl, mt, kc_lo, kc_hi);
+            for (int kc = kc_lo; kc <= kc_hi; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
                 if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u)) {
@@ -185,7 +233,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const uint32_t d_tmem = tmem + acc * BN;
-            for (int kc = 0; kc < nkc; ++kc, ++it) {
+            int kc_lo, kc_hi;
+            tile_chunks(tl, (int)(w / n_tiles), kc_lo, kc_hi);
+            for (int kc = kc_lo; kc <= kc_hi; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
                 if (!mbar_wait(&sm.bar_full[s], ph)) {
@@ -198,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int k = 0; k < kBK / kUmmaK; ++k)
                     tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2), Cfg::kIdesc,
-                           (kc | k) != 0 ? 1u : 0u);
+                           (kc != kc_lo || k != 0) ? 1u : 0u);
                 tc_commit(&sm.bar_empty[s]);
             }
             tc_commit(&sm.bar_acc_full[acc]);
@@ -206,19 +256,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 4) {
         // ---------------- epilogue: thread = shifted residual row ----------------
         const int q = warp - 4;
+        const int et = threadIdx.x - 128;  // 0..127 over the epilogue warps
+        constexpr int kScaleLd = BN + 4;
+        float *sc_sm = reinterpret_cast<float *>(dyn_raw + (base - smem_u32(dyn_raw)) + (size_t)stages * kStageBytes);
         uint32_t local = 0;
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++local) {
             const int mt = (int)(w / n_tiles), nt = (int)(w % n_tiles);
+            // the tile's Jt scale rows (j0 .. j0 + Jt - 1, those below Ntc), BN each
+            {
+                const int j0 = (mt / tl.n_cb) * tl.Jt;
+                const int rows = min(tl.Jt, Ntc - j0);
+                const int per_row = BN / 4;  // 16-byte pieces
+                for (int i = et; i < rows * per_row; i += 128) {
+                    const int rr = i / per_row, cc = i % per_row;
+                    const float *src = scaleT + (size_t)(j0 + rr) * T_pad + (size_t)nt * BN + 4 * cc;
+                    const uint32_t dst = smem_u32(sc_sm + rr * kScaleLd + 4 * cc);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                }
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            if (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph)) {
+            const int failed = (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph)) ? 1 : 0;
+            if (epilogue_bar_or(failed)) {  // the epilogue warps leave together
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const int row = mt * kBM + q * 32 + lane;
-            const bool valid = row < rows_valid;
-            const float4 *sc4 =
-                reinterpret_cast<const float4 *>(scaleT + (size_t)(valid ? row % Ntc : 0) * T_pad + (size_t)nt * BN);
+            const int lr = q * 32 + lane;
+            int b, j;
+            tile_row(tl, mt, lr, b, j);
+            const bool valid = b < tl.B && j < Ntc;
+            const float4 *sc4 = reinterpret_cast<const float4 *>(sc_sm + (valid ? lr % tl.Jt : 0) * kScaleLd);
             float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
@@ -226,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c * 32, v);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const float4 s = valid ? __ldg(sc4 + c * 8 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 s = valid ? sc4[c * 8 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
                     m0 = fmaxf(m0, fabsf(v[4 * e] * s.x));
                     m1 = fmaxf(m1, fabsf(v[4 * e + 1] * s.y));
                     m0 = fmaxf(m0, fabsf(v[4 * e + 2] * s.z));
@@ -236,17 +305,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             mbar_arrive(&sm.bar_acc_empty[acc]);
             const float mx = fmaxf(m0, m1);
-            if (valid) tile_max[(size_t)row * n_tiles + nt] = mx;
-            // channel maximum: non-negative floats order like their bits; one
-            // atomic per warp when its 32 rows belong to one channel
-            const int ch = valid ? row / Ntc : -1;
-            const unsigned bits = __float_as_uint(mx);
-            if (__all_sync(0xffffffffu, ch == __shfl_sync(0xffffffffu, ch, 0))) {
-                const unsigned wm = __reduce_max_sync(0xffffffffu, bits);
-                if (lane == 0 && ch >= 0) atomicMax(chmax + ch, wm);
-            } else if (ch >= 0) {
-                atomicMax(chmax + ch, bits);
+            if (valid) tile_max[((size_t)b * Ntc + j) * n_tiles + nt] = mx;
+            // channel maximum: non-negative floats order like their bits; the
+            // rows of one channel are Jt consecutive lanes (or the whole warp)
+            unsigned bits = valid ? __float_as_uint(mx) : 0u;
+            if (tl.Jt >= 32) {
+                bits = __reduce_max_sync(0xffffffffu, bits);
+                if (lane == 0 && b < tl.B) atomicMax(chmax + b, bits);
+            } else {
+                for (int off = tl.Jt >> 1; off > 0; off >>= 1) {
+                    const unsigned o = __shfl_xor_sync(0xffffffffu, bits, off);
+                    bits = o > bits ? o : bits;
+                }
+                if (lr % tl.Jt == 0 && b < tl.B) atomicMax(chmax + b, bits);
             }
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // the scale rows are reloaded for the next item
         }
     }
 
@@ -514,6 +587,27 @@ void shift_tc_free(ShiftTc *s) {
     delete s;
 }
 
+// Row tiling for B channels: Bg channels x Jt time centres per 128-row tile,
+// Jt as small as B allows (fewer lag chunks per tile), at most the time
+// centres (rounded up to a power of two).
+static RowTiling make_tiling(const ShiftPlan &sp, int B) {
+    RowTiling t;
+    int bg = 1;
+    while (bg < B && bg < 16) bg <<= 1;
+    int ntc2 = 1;
+    while (ntc2 < sp.Ntc) ntc2 <<= 1;
+    t.Jt = kBM / bg < ntc2 ? kBM / bg : ntc2;
+    t.Bg = kBM / t.Jt;
+    t.B = B;
+    t.Ntc = sp.Ntc;
+    t.n_cb = (B + t.Bg - 1) / t.Bg;
+    t.m_tiles = ((sp.Ntc + t.Jt - 1) / t.Jt) * t.n_cb;
+    t.S = sp.S;
+    t.L = sp.L;
+    t.span0 = -sp.m_lo - sp.tc0;
+    return t;
+}
+
 // Buffers for B channels (kept when large enough).
 cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
     if (B <= s->B_cap) return cudaSuccess;
@@ -531,7 +625,11 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
     s->chcount = nullptr;
     s->B_cap = 0;
     const int64_t rows = (int64_t)B * sp.Ntc;
-    const int64_t rows_alloc = (rows + kBM - 1) / kBM * kBM;
+    int64_t rows_alloc = 0;  // the largest row-tile count of any B' <= B
+    for (int b2 = 1; b2 <= B; ++b2) {
+        const int64_t r2 = (int64_t)make_tiling(sp, b2).m_tiles * kBM;
+        rows_alloc = r2 > rows_alloc ? r2 : rows_alloc;
+    }
     if (rows_alloc > (1ll << 30)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)rows * (sp.T_pad / 128));
     if (e == cudaSuccess) e = cudaMalloc(&s->items, sizeof(int) * 2 * (size_t)B * kMaxItems);
@@ -552,13 +650,20 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
 cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
                                  long long *stats, int *status, cudaStream_t st) {
     if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
-    k_shift_rows<<<B * sp.Ntc, 128, 0, st>>>(R, Lp, L, sp.Ntc, sp.S, sp.tc0, sp.m_lo, sp.Kt, s->X, s->chan_norm,
-                                             s->chmax, s->chcount, stats);
+    const RowTiling tl = make_tiling(sp, B);
+    k_shift_rows<<<tl.m_tiles * kBM, 128, 0, st>>>(tl, R, Lp, sp.tc0, sp.m_lo, sp.Kt, s->X, s->chan_norm, s->chmax,
+                                                   s->chcount, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int rows_valid = B * sp.Ntc;
-    const int m_tiles = (rows_valid + kBM - 1) / kBM;
+    const int m_tiles = tl.m_tiles;
     CUtensorMap mapA;
+    auto smem_for = [&](int bn, int stage_bytes, int *stages) {
+        const size_t sc = (size_t)tl.Jt * (bn + 4) * sizeof(float);
+        int stg = (int)((kSmemBudget - (int64_t)sc) / stage_bytes);
+        stg = stg > kMaxStages ? kMaxStages : stg;
+        *stages = stg;
+        return 1024 + (size_t)stg * stage_bytes + sc;
+    };
     if (!make_map(&mapA, s->X, (uint64_t)sp.Kt, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
     // 256-template tiles unless they leave SMs idle
     const int bn = (int64_t)m_tiles * (sp.T_pad / 256) >= s->sm_count ? 256 : 128;
@@ -567,14 +672,16 @@ cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R
     s->n_tiles = sp.T_pad / bn;
     const int64_t items = (int64_t)m_tiles * s->n_tiles;
     const int grid = (int)(items < s->sm_count ? items : s->sm_count);
+    int stages = 0;
+    const size_t smem = bn == 256 ? smem_for(256, ShiftTile<256>::kStageBytes, &stages)
+                                  : smem_for(128, ShiftTile<128>::kStageBytes, &stages);
+    if (stages < 2) return cudaErrorInvalidValue;
     if (bn == 256)
-        k_shift_gemm<256><<<grid, kThreads, s->smem[i], st>>>(mapA, s->mapB[i], m_tiles, s->n_tiles, s->nkc,
-                                                              s->stages[i], rows_valid, sp.Ntc, sp.T_pad, sp.scaleT,
-                                                              s->tile_max, s->chmax, status);
+        k_shift_gemm<256><<<grid, kThreads, smem, st>>>(mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad,
+                                                        sp.scaleT, s->tile_max, s->chmax, status);
     else
-        k_shift_gemm<128><<<grid, kThreads, s->smem[i], st>>>(mapA, s->mapB[i], m_tiles, s->n_tiles, s->nkc,
-                                                              s->stages[i], rows_valid, sp.Ntc, sp.T_pad, sp.scaleT,
-                                                              s->tile_max, s->chmax, status);
+        k_shift_gemm<128><<<grid, kThreads, smem, st>>>(mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad,
+                                                        sp.scaleT, s->tile_max, s->chmax, status);
     return cudaGetLastError();
 }
 
