@@ -114,8 +114,8 @@ typedef enum {
  *                    templates x shifted BF16 residual rows (tcgen05, FP32
  *                    accumulation, every score scaled by its atom's 1/|u|)
  *                    reduced to the largest |score| per (time centre,
- *                    256-template tile); the tiles an error bound cannot
- *                    exclude (all tiles of a channel with more than 64 of
+ *                    32-template block); the blocks an error bound cannot
+ *                    exclude (all blocks of a channel with more than 64 of
  *                    them) are rescored with ACT_SEARCH_SHIFT's own
  *                    arithmetic, so the selection equals ACT_SEARCH_SHIFT's
  *                    bit for bit.

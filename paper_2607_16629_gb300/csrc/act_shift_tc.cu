@@ -6,9 +6,11 @@
 //     the BF16 templates (N = 256 templates per tile) against the shifted
 //     residual rows (M = 128 rows per tile), K = Kt lags;
 //  2. the tcgen05 GEMM scales every accumulator by its atom's 1/|u| and keeps,
-//     per row and template tile, the largest |score|;
-//  3. a select kernel bounds the BF16 error per channel and flags the
-//     (lag, tile) items that can hold the FP32 template search's argmax;
+//     per row, the largest |score| of every template tile and of every
+//     32-template block;
+//  3. a flag kernel bounds the BF16 error per channel and flags the
+//     (time centre, 32-template block) items that can hold the FP32 template
+//     search's argmax (scanning the tile maxima, then the flagged tiles' blocks);
 //  4. the flagged items are rescored with the FP32 template search's own
 //     arithmetic (same FMA chain, same scale) and folded into the packed key;
 //     a channel with too many items has all of its items rescored that way.
@@ -160,7 +162,8 @@ template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_shift_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowTiling tl,
                  int n_tiles, int nkc, int stages, int T_pad, const float *__restrict__ scaleT,
-                 float *__restrict__ tile_max, unsigned int *__restrict__ chmax, int *status) {
+                 float *__restrict__ tile_max, float *__restrict__ blk_max, unsigned int *__restrict__ chmax,
+                 int *status) {
     // shared memory: stages, then the item's scales [Jt][BN + 4] (the +4
     // floats of padding spread the Jt rows a warp reads over the banks)
     using Cfg = ShiftTile<BN>;
@@ -288,11 +291,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             tile_row(tl, mt, lr, b, j);
             const bool valid = b < tl.B && j < Ntc;
             const float4 *sc4 = reinterpret_cast<const float4 *>(sc_sm + (valid ? lr % tl.Jt : 0) * kScaleLd);
-            float m0 = 0.0f, m1 = 0.0f;
+            // per 32-template block and per tile: the largest scaled |score|
+            float *bm = blk_max + ((size_t)(valid ? b : 0) * Ntc + (valid ? j : 0)) * (T_pad / 32) +
+                        (size_t)nt * (BN / 32);
+            float mx = 0.0f;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c * 32, v);
+                float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const float4 s = valid ? sc4[c * 8 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -301,10 +308,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     m0 = fmaxf(m0, fabsf(v[4 * e + 2] * s.z));
                     m1 = fmaxf(m1, fabsf(v[4 * e + 3] * s.w));
                 }
+                const float mc = fmaxf(m0, m1);
+                if (valid) bm[c] = mc;
+                mx = fmaxf(mx, mc);
             }
             tc_fence_before();
             mbar_arrive(&sm.bar_acc_empty[acc]);
-            const float mx = fmaxf(m0, m1);
             if (valid) tile_max[((size_t)b * Ntc + j) * n_tiles + nt] = mx;
             // channel maximum: non-negative floats order like their bits; the
             // rows of one channel are Jt consecutive lanes (or the whole warp)
@@ -346,8 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // bf16(r) - r, the Kt term bounds FP32 accumulation in the tensor core, the
 // factor the scale product).  As for the dense BF16 search, the FP32 argmax
 // lies in an item whose largest |h| is >= hmax - 2 delta - 2 eps_r.
-__global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int Kt, int L,
+__global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bpt, int Kt, int L,
                                                     const float *__restrict__ tile_max,
+                                                    const float *__restrict__ blk_max,
                                                     const double2 *__restrict__ chan_norm,
                                                     const unsigned int *__restrict__ chmax,
                                                     const unsigned int *__restrict__ eps_bits,
@@ -365,21 +375,29 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int Kt
     const double thr = (double)__uint_as_float(chmax[b]) - 2.0 * delta - 2.0 * eps_r;
     // FP32 compare against the threshold rounded down: a superset of the items
     const float thr_f = __double2float_rd(thr);
+    // scan the tile maxima; a tile at or above the threshold is narrowed to
+    // its 32-template blocks at or above it (the items: i = j * n_blocks + block)
     const float *tm = tile_max + (size_t)b * Ntc * n_tiles;
     const int n_entries = Ntc * n_tiles;
+    const int n_blocks = n_tiles * bpt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_entries; i += gridDim.x * blockDim.x) {
         if (tm[i] >= thr_f) {
-            const int pos = atomicAdd(chcount + b, 1);
-            if (pos < kMaxItems) {
-                const int at = atomicAdd(&counters[1], 1);
-                items[2 * at] = b;
-                items[2 * at + 1] = i;  // i = j * n_tiles + tile
-                atomicAdd((unsigned long long *)&stats[2], 1ull);
-            } else if (pos == kMaxItems) {
-                // too many: every item of this channel is rescored instead
-                fb_list[atomicAdd(&counters[0], 1)] = b;
-                atomicAdd((unsigned long long *)&stats[1], 1ull);
-                atomicAdd((unsigned long long *)&stats[0], ~0ull);  // -1: not resolved by the items
+            const int j = i / n_tiles, tile = i - j * n_tiles;
+            const float *bm = blk_max + ((size_t)b * Ntc + j) * n_blocks + (size_t)tile * bpt;
+            for (int k = 0; k < bpt; ++k) {
+                if (bm[k] < thr_f) continue;
+                const int pos = atomicAdd(chcount + b, 1);
+                if (pos < kMaxItems) {
+                    const int at = atomicAdd(&counters[1], 1);
+                    items[2 * at] = b;
+                    items[2 * at + 1] = j * n_blocks + tile * bpt + k;
+                    atomicAdd((unsigned long long *)&stats[2], 1ull);
+                } else if (pos == kMaxItems) {
+                    // too many: every block of this channel is rescored instead
+                    fb_list[atomicAdd(&counters[0], 1)] = b;
+                    atomicAdd((unsigned long long *)&stats[1], 1ull);
+                    atomicAdd((unsigned long long *)&stats[0], ~0ull);  // -1: not resolved by the items
+                }
             }
         }
     }
@@ -521,6 +539,7 @@ struct ShiftTc {
     size_t smem[2] = {0, 0};
     int n_tiles = 0, bn = 0;  // of the current launch: n_tiles = T_pad / bn
     float *tile_max = nullptr;      // [rows_cap][n_tiles]
+    float *blk_max = nullptr;       // [rows_cap][T_pad / 32] maxima per 32-template block
     int *items = nullptr;           // [B_cap * kMaxItems][2]
     __nv_bfloat16 *X = nullptr;     // [rows_cap rounded up to 128][Kt]
     int B_cap = 0;
@@ -579,6 +598,7 @@ cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
 void shift_tc_free(ShiftTc *s) {
     if (!s) return;
     if (s->tile_max) cudaFree(s->tile_max);
+    if (s->blk_max) cudaFree(s->blk_max);
     if (s->items) cudaFree(s->items);
     if (s->X) cudaFree(s->X);
     if (s->chan_norm) cudaFree(s->chan_norm);
@@ -612,12 +632,14 @@ static RowTiling make_tiling(const ShiftPlan &sp, int B) {
 cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
     if (B <= s->B_cap) return cudaSuccess;
     if (s->tile_max) cudaFree(s->tile_max);
+    if (s->blk_max) cudaFree(s->blk_max);
     if (s->items) cudaFree(s->items);
     if (s->X) cudaFree(s->X);
     if (s->chan_norm) cudaFree(s->chan_norm);
     if (s->chmax) cudaFree(s->chmax);
     if (s->chcount) cudaFree(s->chcount);
     s->tile_max = nullptr;
+    s->blk_max = nullptr;
     s->items = nullptr;
     s->X = nullptr;
     s->chan_norm = nullptr;
@@ -632,6 +654,7 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
     }
     if (rows_alloc > (1ll << 30)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)rows * (sp.T_pad / 128));
+    if (e == cudaSuccess) e = cudaMalloc(&s->blk_max, sizeof(float) * (size_t)rows * (sp.T_pad / 32));
     if (e == cudaSuccess) e = cudaMalloc(&s->items, sizeof(int) * 2 * (size_t)B * kMaxItems);
     if (e == cudaSuccess) e = cudaMalloc(&s->X, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
     if (e == cudaSuccess) e = cudaMemset(s->X, 0, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
@@ -678,10 +701,10 @@ cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R
     if (stages < 2) return cudaErrorInvalidValue;
     if (bn == 256)
         k_shift_gemm<256><<<grid, kThreads, smem, st>>>(mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad,
-                                                        sp.scaleT, s->tile_max, s->chmax, status);
+                                                        sp.scaleT, s->tile_max, s->blk_max, s->chmax, status);
     else
         k_shift_gemm<128><<<grid, kThreads, smem, st>>>(mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad,
-                                                        sp.scaleT, s->tile_max, s->chmax, status);
+                                                        sp.scaleT, s->tile_max, s->blk_max, s->chmax, status);
     return cudaGetLastError();
 }
 
@@ -693,12 +716,13 @@ cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float
     int slices = (entries + 255) / 256;
     const int max_slices = (4 * s->sm_count + B - 1) / B;
     if (slices > max_slices) slices = max_slices;
-    k_shift_flag<<<dim3(slices, B), 256, 0, st>>>(sp.Ntc, s->n_tiles, sp.Kt, L, s->tile_max, s->chan_norm, s->chmax,
+    k_shift_flag<<<dim3(slices, B), 256, 0, st>>>(sp.Ntc, s->n_tiles, s->bn / 32, sp.Kt, L, s->tile_max, s->blk_max,
+                                                  s->chan_norm, s->chmax,
                                                   sp.eps_bits, s->chcount, fb_list, counters, s->items, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_shift_rescan<<<s->sm_count * s->rescan_blocks_per_sm, s->rescan_warps * 32, s->rescan_smem, st>>>(
-        sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.Ntc, sp.T, s->n_tiles, s->bn / 32, Lp, L, R, s->items,
+        sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, 1, Lp, L, R, s->items,
         fb_list, counters, keys, status);
     return cudaGetLastError();
 }
