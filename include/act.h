@@ -272,7 +272,7 @@ ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double
  * [channels][n_samples] (device or host memory) as residuals, keeps the
  * fastest, and returns its time per order in *best_ms (may be NULL).
  * Candidates: resident CTAs per SM of the FP32 GEMV (1..4, as occupancy
- * allows) and, when the grid holds a BF16 dictionary and channels <= 128,
+ * allows), the bulk-copy streaming GEMV and, when the grid holds a BF16 dictionary and channels <= 128,
  * tile width (128 or 256 atoms) x pipeline depth (2 .. what fits in shared
  * memory) of the tensor-core GEMM, each timed with its tile selection and
  * rescan; with an ACT_DICT_RECOMPUTE build, every valid (lags per thread,
@@ -284,13 +284,17 @@ ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double
 ACT_API act_status act_autotune(act_grid *grid, const float *signals, int32_t channels, void *cuda_stream,
                                 double *best_ms);
 
-/* The configuration in use: FP32 GEMV grid size in CTAs, tensor-core tile
- * width in atoms and pipeline stages (0 and 0 without a BF16 dictionary). */
+/* The configuration in use: FP32 GEMV grid size in CTAs (-1: the
+ * bulk-copy streaming GEMV, one CTA per SM), tensor-core tile width in atoms
+ * and pipeline stages (0 and 0 without a BF16 dictionary). */
 ACT_API act_status act_get_tuning(const act_grid *grid, int32_t *gemv_ctas, int32_t *bf16_tile_atoms,
                                   int32_t *bf16_stages);
 
 /* Sets the configuration by hand: gemv_ctas > 0 sets the FP32 GEMV grid
- * (at most the resident limit); bf16_tile_atoms (128 or 256) > 0 sets the
+ * (at most the resident limit), -1 selects the bulk-copy streaming GEMV (the
+ * dictionary brought into shared memory by TMA bulk copies, one CTA per SM;
+ * same scores and selections), 0 keeps the current choice;
+ * bf16_tile_atoms (128 or 256) > 0 sets the
  * tensor-core tile width with bf16_stages pipeline stages (<= 0: the most
  * that fit).  Out-of-range values return ACT_ERR_INVALID_ARG. */
 ACT_API act_status act_set_tuning(act_grid *grid, int32_t gemv_ctas, int32_t bf16_tile_atoms,

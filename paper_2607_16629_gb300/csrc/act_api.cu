@@ -119,6 +119,7 @@ struct act_grid {
     ShiftPlan shift;       // template dictionary (ACT_DICT_RECOMPUTE)
     ShiftTc *shift_tc = nullptr;  // its tensor-core search (ACT_SEARCH_SHIFT_BF16)
     int gemv_grid = 0;
+    bool gemv_stream = false;  // FP32 search by the bulk-copy streaming GEMV (one CTA per SM)
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
     LemConfig lem;         // hierarchical search settings
     cudaStream_t cap = nullptr;
@@ -334,8 +335,12 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
                                        g->stats, g->status, g->gemv_grid, st));
             kernels += 4;
         } else {
-            ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
-                                      g->gemv_grid, st));
+            if (g->gemv_stream)
+                ACT_CK(launch_gemv_stream_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
+                                                 g->sm_count, st));
+            else
+                ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
+                                          g->gemv_grid, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         }
@@ -814,8 +819,11 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
                         e = launch_bf16_resolve(g->bf16, channels, g->d32, g->Lp, g->L, g->w.R, g->w.keys, g->w.fb_list,
                                                 g->w.fb_count, g->stats, g->status, g->gemv_grid, st);
                 } else {
-                    e = launch_gemv_argmax(g->d32, g->K, g->Lp, g->w.R, channels, nullptr, nullptr, g->w.keys,
-                                           g->status, g->gemv_grid, st);
+                    e = g->gemv_stream
+                            ? launch_gemv_stream_argmax(g->d32, g->K, g->Lp, g->w.R, channels, nullptr, nullptr,
+                                                        g->w.keys, g->status, g->sm_count, st)
+                            : launch_gemv_argmax(g->d32, g->K, g->Lp, g->w.R, channels, nullptr, nullptr, g->w.keys,
+                                                 g->status, g->gemv_grid, st);
                 }
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -827,9 +835,12 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
         return e;
     };
     cudaError_t err = cudaSuccess;
-    // FP32 GEMV: resident CTAs per SM
+    // FP32 GEMV: resident CTAs per SM of the load-streaming GEMV, and the
+    // bulk-copy streaming GEMV
     double best32 = 1e30;
     int best_grid = g->gemv_grid;
+    bool best_stream = false;
+    g->gemv_stream = false;
     const int max_per_sm = gemv_max_ctas_per_sm(g->Lp);
     for (int per_sm = 1; per_sm <= max_per_sm && err == cudaSuccess; ++per_sm) {
         g->gemv_grid = g->sm_count * per_sm;
@@ -841,6 +852,16 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
         }
     }
     g->gemv_grid = best_grid;
+    if (err == cudaSuccess) {
+        g->gemv_stream = true;
+        double ms = 0.0;
+        err = time_search(false, &ms);
+        if (err == cudaSuccess && ms < best32) {
+            best32 = ms;
+            best_stream = true;
+        }
+    }
+    g->gemv_stream = best_stream;
     // tensor-core search: tile width x pipeline depth
     double best16 = 1e30;
     if (bf16 && err == cudaSuccess) {
@@ -882,7 +903,7 @@ act_status act_get_tuning(const act_grid *g, int32_t *gemv_ctas_out, int32_t *bf
     if (!g) return ACT_ERR_INVALID_ARG;
     int bn = 0, stg = 0;
     if (g->bf16) bf16_search_get_config(g->bf16, &bn, &stg, nullptr);
-    if (gemv_ctas_out) *gemv_ctas_out = g->gemv_grid;
+    if (gemv_ctas_out) *gemv_ctas_out = g->gemv_stream ? -1 : g->gemv_grid;
     if (bf16_tile_atoms) *bf16_tile_atoms = bn;
     if (bf16_stages) *bf16_stages = stg;
     return ACT_OK;
@@ -894,6 +915,11 @@ act_status act_set_tuning(act_grid *g, int32_t gemv_ctas_in, int32_t bf16_tile_a
     if (gemv_ctas_in > 0) {
         if (gemv_ctas_in > g->sm_count * gemv_max_ctas_per_sm(g->Lp)) return ACT_ERR_INVALID_ARG;
         g->gemv_grid = gemv_ctas_in;
+        g->gemv_stream = false;
+    } else if (gemv_ctas_in == -1) {
+        g->gemv_stream = true;
+    } else if (gemv_ctas_in < -1) {
+        return ACT_ERR_INVALID_ARG;
     }
     if (bf16_tile_atoms > 0) {
         if (!g->bf16) return ACT_ERR_NOT_BUILT;

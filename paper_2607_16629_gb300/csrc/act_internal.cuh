@@ -87,6 +87,11 @@ cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, 
                                   const act_atom *atoms, const float *coefs, const double *energy, const float *R,
                                   act_atom *out_atoms, float *out_coefs, double *out_energy, float *out_resid,
                                   cudaStream_t st);
+// The same search with the dictionary streamed by TMA bulk copies through
+// shared memory, one CTA per SM (act_gemv_stream.cu); same scores, same keys.
+cudaError_t launch_gemv_stream_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
+                                      const int *count_dev, unsigned long long *keys, int *status, int sm_count,
+                                      cudaStream_t st);
 int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
 int gemv_max_ctas_per_sm(int Lp);
 

@@ -289,3 +289,31 @@ def test_degenerate_atoms_match_oracle():
     assert not deg[idx[0]].any()
     o_idx, o_coef, _, _ = oracle.mp(D, s.astype(np.float32).astype(np.float64), 3)
     assert np.array_equal(idx[0], o_idx)
+
+
+@pytest.mark.parametrize("name,grid", [
+    ("c1", synth.grid_c1()),
+    ("eeg_small", None),
+    ("l2048", synth.Grid(2048, 500.0, synth.Axis(0.0, 300.0, 7), synth.Axis(20, 35, 6),
+                         synth.Axis(-4.0, 0.5, 3), synth.Axis(-50, 50, 3))),
+    ("l37", synth.Grid(37, 500.0, synth.Axis(0.0, 6.0, 6), synth.Axis(20, 35, 6), synth.Axis(-4.0, 0.5, 3),
+                       synth.Axis(-50, 50, 3))),
+])
+def test_streaming_gemv_gives_the_same_bits(name, grid):
+    """The bulk-copy streaming GEMV scores rows in the load-streaming GEMV's
+    order: every output of a decomposition is identical, for one and several
+    channels."""
+    if grid is None:
+        grid = eeg_small()
+    sig = synth.random_signals(61, 3, grid.n_samples)
+    with Grid(grid) as h:
+        ref1 = gpu_decompose(h, sig[:1], 6)
+        ref3 = gpu_decompose(h, sig, 6)
+        act.act_set_tuning(h, -1)
+        assert act.act_get_tuning(h)[0] == -1
+        for ref, s in ((ref1, sig[:1]), (ref3, sig)):
+            got = gpu_decompose(h, s, 6)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b)
+        with pytest.raises(act.ActError):
+            act.act_set_tuning(h, -2)
