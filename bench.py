@@ -278,12 +278,19 @@ def run_ours(args):
     gemv_bytes = K * grid.n_samples * 4 + grid.n_samples * 4
     avg_ms = search_ms / max(1, search_n)
     achieved = gemv_bytes / (avg_ms / 1e3) / 1e9
-    traffic = _profile_traffic("gemv_argmax_eeg_k2097152_n512.md",
-                               ["paper_2607_16629_gb300/csrc/act_gemv.cu",
-                                "paper_2607_16629_gb300/csrc/act_device.cuh"])
+    if gemv_ctas == -1:  # the bulk-copy streaming GEMV won the autotune
+        gemv_kernel = "k_gemv_stream<4> (FP32 GEMV, TMA bulk-copy stream, fused argmax)"
+        traffic = _profile_traffic("gemv_stream_eeg_k2097152_n512.md",
+                                   ["paper_2607_16629_gb300/csrc/act_gemv_stream.cu",
+                                    "paper_2607_16629_gb300/csrc/act_device.cuh"])
+    else:
+        gemv_kernel = "k_gemv<4,1> (FP32 GEMV + fused argmax)"
+        traffic = _profile_traffic("gemv_argmax_eeg_k2097152_n512.md",
+                                   ["paper_2607_16629_gb300/csrc/act_gemv.cu",
+                                    "paper_2607_16629_gb300/csrc/act_device.cuh"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_gemv<4,1> (FP32 GEMV + fused argmax)", "autotuned_gemv_ctas": gemv_ctas,
+                "kernel": gemv_kernel, "autotuned_gemv_ctas": gemv_ctas,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": gemv_bytes, "avg_launch_ms": avg_ms,
                 "launches_timed": search_n,
@@ -836,6 +843,8 @@ def run_profile_case(args):
     try:
         act.act_dictionary_build(h, act.ACT_DICT_FP32 if B == 1 else act.ACT_DICT_BF16)
         act.act_set_search(h, act.ACT_SEARCH_FP32 if B == 1 else act.ACT_SEARCH_BF16)
+        if B == 1 and args.gemv == "stream":
+            act.act_set_tuning(h, -1)
         for _ in range(args.steps):
             act.decompose(h, sig, 3)
         torch.cuda.synchronize()
@@ -892,6 +901,8 @@ def main():
     ap.add_argument("--no-lem", action="store_true")
     ap.add_argument("--no-shift", action="store_true")
     ap.add_argument("--channels", type=int, default=1, help="channels for the shift_* cases (1 or up to 64)")
+    ap.add_argument("--gemv", default="stream", choices=["stream", "load"],
+                    help="FP32 GEMV of the gemv_small case: bulk-copy streaming or load-streaming")
     ap.add_argument("--shift-tuning", default="", help="JxW, JxWxS or JxWxSxC for --case shift_eeg (default: the build's)")
     ap.add_argument("--case", default="default",
                     choices=["default", "gemv_small", "bf16_small", "shift_eeg", "shift_tc_eeg"],
