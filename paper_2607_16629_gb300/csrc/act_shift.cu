@@ -48,6 +48,8 @@ namespace act {
 namespace {
 
 constexpr int kShiftMaxThreads = 256;
+constexpr int kShiftUpdateThreads = 512;
+constexpr int kUpdatePerThread = kMaxSamples / kShiftUpdateThreads;
 constexpr int kShiftMaxStages = 3;
 
 struct ShiftArgs {
@@ -327,7 +329,8 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
 // One block per channel: the winner (j, t) of keys[b], g = scale * u_t
 // read back from the template rows the search used, c = <g, r> (FP32),
 // r -= c g, |r|^2 in FP64, the atom record, the key cleared.
-__global__ void __launch_bounds__(256) k_shift_update(const float *__restrict__ tpl, const float *__restrict__ scale,
+__global__ void __launch_bounds__(kShiftUpdateThreads) k_shift_update(const float *__restrict__ tpl,
+                                                                     const float *__restrict__ scale,
                                                      int S, int Sa, int rows, int NtcP, int T, GridAxes ax, int Lp,
                                                      float *__restrict__ R, unsigned long long *__restrict__ keys,
                                                      int k, int P, act_atom *__restrict__ atoms,
@@ -344,18 +347,29 @@ __global__ void __launch_bounds__(256) k_shift_update(const float *__restrict__ 
     const float sc = scale[((size_t)tb * NtcP + j) * 32 + lane];
     const float *base = tpl + (size_t)tb * Sa * rows * 32 + lane;
     float *r = R + (size_t)b * Lp;
+    // the atom's samples stay in registers between the two passes
+    // (L <= kMaxSamples = kShiftUpdateThreads * kUpdatePerThread)
+    float gv[kUpdatePerThread];
     float part = 0.0f;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const float g = base[((size_t)(n % S) * rows + (n / S - j + NtcP - 1)) * 32] * sc;
-        part = fmaf(g, r[n], part);
+#pragma unroll
+    for (int i = 0; i < kUpdatePerThread; ++i) {
+        const int n = threadIdx.x + i * kShiftUpdateThreads;
+        gv[i] = 0.0f;
+        if (n < L) {
+            gv[i] = base[((size_t)(n % S) * rows + (n / S - j + NtcP - 1)) * 32] * sc;
+            part = fmaf(gv[i], r[n], part);
+        }
     }
     const float c = block_sum(part, shf);
     double e2 = 0.0;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const float g = base[((size_t)(n % S) * rows + (n / S - j + NtcP - 1)) * 32] * sc;
-        const float v = fmaf(-c, g, r[n]);
-        r[n] = v;
-        e2 = fma((double)v, (double)v, e2);
+#pragma unroll
+    for (int i = 0; i < kUpdatePerThread; ++i) {
+        const int n = threadIdx.x + i * kShiftUpdateThreads;
+        if (n < L) {
+            const float v = fmaf(-c, gv[i], r[n]);
+            r[n] = v;
+            e2 = fma((double)v, (double)v, e2);
+        }
     }
     const double tot = block_sum(e2, shd);
     if (threadIdx.x == 0) {
@@ -552,8 +566,8 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
 cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
                                 unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
                                 int *counters, cudaStream_t st) {
-    k_shift_update<<<B, 256, 0, st>>>(sp.tpl, sp.scale, sp.S, sp.Sa, sp.rows, sp.NtcP, sp.T, ax, Lp, R, keys, k, P,
-                                      atoms, coefs, energy, counters);
+    k_shift_update<<<B, kShiftUpdateThreads, 0, st>>>(sp.tpl, sp.scale, sp.S, sp.Sa, sp.rows, sp.NtcP, sp.T, ax,
+                                                      Lp, R, keys, k, P, atoms, coefs, energy, counters);
     return cudaGetLastError();
 }
 

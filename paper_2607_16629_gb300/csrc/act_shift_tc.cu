@@ -365,16 +365,21 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bp
                                                     int *__restrict__ counters, int *__restrict__ items,
                                                     long long *__restrict__ stats) {
     const int b = blockIdx.y;
-    const double2 nr = chan_norm[b];
-    const double rn = nr.x, drn = nr.y;
-    const double eps_u = (double)__uint_as_float(*eps_bits);
-    const double rr = rn + drn;
-    const double ulp = 1.1920928955078125e-07;  // 2^-23
-    const double delta = (1.0 + 1e-5) * (eps_u * rr + drn + (double)Kt * ulp * (1.0 + eps_u) * rr);
-    const double eps_r = (double)(L + 4) * ulp * rn;
-    const double thr = (double)__uint_as_float(chmax[b]) - 2.0 * delta - 2.0 * eps_r;
-    // FP32 compare against the threshold rounded down: a superset of the items
-    const float thr_f = __double2float_rd(thr);
+    __shared__ float thr_sh;
+    if (threadIdx.x == 0) {  // the bound in FP64, once per block
+        const double2 nr = chan_norm[b];
+        const double rn = nr.x, drn = nr.y;
+        const double eps_u = (double)__uint_as_float(*eps_bits);
+        const double rr = rn + drn;
+        const double ulp = 1.1920928955078125e-07;  // 2^-23
+        const double delta = (1.0 + 1e-5) * (eps_u * rr + drn + (double)Kt * ulp * (1.0 + eps_u) * rr);
+        const double eps_r = (double)(L + 4) * ulp * rn;
+        const double thr = (double)__uint_as_float(chmax[b]) - 2.0 * delta - 2.0 * eps_r;
+        // FP32 compare against the threshold rounded down: a superset of the items
+        thr_sh = __double2float_rd(thr);
+    }
+    __syncthreads();
+    const float thr_f = thr_sh;
     // scan the tile maxima; a tile at or above the threshold is narrowed to
     // its 32-template blocks at or above it (the items: i = j * n_blocks + block)
     const float *tm = tile_max + (size_t)b * Ntc * n_tiles;
