@@ -542,6 +542,7 @@ act_status act_grid_size(const act_grid *g, int64_t *n_atoms, int32_t *row_strid
 static act_status build_templates(act_grid *g, cudaStream_t st) {
     ShiftPlan sp;
     if (shift_plan(sp, g->ax) != cudaSuccess) return ACT_ERR_UNSUPPORTED;
+    sp.Lp = g->Lp;
     if (shift_default_config(sp, g->sm_count) != cudaSuccess) return ACT_ERR_UNSUPPORTED;
     const size_t bt = sizeof(float) * (size_t)sp.TB * sp.Sa * sp.rows * 32;
     const size_t bs = sizeof(float) * (size_t)sp.TB * sp.NtcP * 32;

@@ -140,6 +140,7 @@ struct ShiftPlan {
     int S = 0, tc0 = 0;         // tc_j = tc0 + S j, whole samples
     int Sa = 0;                 // phases holding samples: min(S, L)
     int L = 0;                  // window length
+    int Lp = 0;                 // residual row stride of the grid (floats)
     int Ntc = 0, NtcP = 0;      // lags, and lags rounded up to 32
     int P = 0;                  // polyphase length ceil(L / S) rounded up to 16
     int T = 0, TB = 0;          // templates (fc, logDt, c triples) and 32-template blocks

@@ -422,12 +422,12 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     int Ntc, int T, int n_tiles, int bpt, int Lp, int L, const float *__restrict__ R, const int *__restrict__ items,
     const int *__restrict__ fb_list, const int *__restrict__ counters, unsigned long long *__restrict__ keys,
     int *status) {
-    extern __shared__ __align__(128) float sm[];  // per warp: [Sa][P] residual phases, then 2 x [P][32] rows
+    extern __shared__ __align__(128) float sm[];  // per warp: the residual [Lp], then 2 x [P][32] rows
     __shared__ __align__(8) uint64_t bar[kRescanWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t warp_floats = (size_t)Sa * P + 2 * (size_t)P * 32;
-    float *rpoly = sm + warp * warp_floats;
-    float *buf0 = rpoly + (size_t)Sa * P;
+    const size_t warp_floats = (size_t)Lp + 2 * (size_t)P * 32;
+    float *rres = sm + warp * warp_floats;
+    float *buf0 = rres + Lp;
     const uint32_t bytes = (uint32_t)P * 128u;
     const int n_flag = counters[1], n_fb = counters[0];
     const int64_t per_fb = (int64_t)Ntc * n_tiles * bpt;  // warp tasks of one overflowed channel
@@ -466,24 +466,13 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
         if (tb * 32 >= T) continue;  // past the last template
         const float *src = tpl + ((size_t)tb * Sa * rows + (size_t)(NtcP - 1 - j)) * 32;
         __syncwarp();
-        if (lane == 0) {  // phase 0's rows, in flight while the residual is staged
-            mbar_expect_tx(&bar[warp][0], bytes);
+        if (lane == 0) {  // phase 0's rows and, for a new channel, its residual on the same barrier
+            const bool new_b = b != cur_b;
+            mbar_expect_tx(&bar[warp][0], bytes + (new_b ? (uint32_t)Lp * 4u : 0u));
             bulk_g2s(buf0, src, bytes, &bar[warp][0]);
+            if (new_b) bulk_g2s(rres, R + (size_t)b * Lp, (uint32_t)Lp * 4u, &bar[warp][0]);
         }
-        if (b != cur_b) {
-            __syncwarp();
-            const float *r = R + (size_t)b * Lp;
-            // zero the phases, then scatter the window (coalesced loads)
-            for (int i = lane; i < Sa * P; i += 32) rpoly[i] = 0.0f;
-            __syncwarp();
-#pragma unroll 4
-            for (int n = lane; n < L; n += 32) {
-                const int a = n % S, p = n / S;
-                rpoly[a * P + p] = r[n];
-            }
-            __syncwarp();
-            cur_b = b;
-        }
+        cur_b = b;
         float acc = 0.0f;
         int ok = 1, fail_a = 0;
         for (int a = 0; a < Sa; ++a) {
@@ -501,10 +490,13 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
                 fail_a = a;
                 break;
             }
-            const float *rp = rpoly + a * P;
+            // sample n = a + S p of the window (0 past it, as in the FP32 search's phases)
             const float *bp = buf0 + (size_t)cb * P * 32 + lane;
 #pragma unroll 8
-            for (int p = 0; p < P; ++p) acc = fmaf(rp[p], bp[p * 32], acc);
+            for (int p = 0; p < P; ++p) {
+                const int n = a + S * p;
+                acc = fmaf(n < L ? rres[n] : 0.0f, bp[p * 32], acc);
+            }
             __syncwarp();
         }
         if (!ok) {
@@ -578,9 +570,9 @@ cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
         s->smem[i] = 1024 + (size_t)s->stages[i] * stage_bytes[i];
         e = allow_max_smem(i == 0 ? (const void *)k_shift_gemm<128> : (const void *)k_shift_gemm<256>, s->smem[i]);
     }
-    // rescore: per warp the residual phases and two P-row buffers; as many
-    // warps per block (up to kRescanWarps) as fit
-    const size_t per_warp = sizeof(float) * ((size_t)sp.Sa * sp.P + 2 * (size_t)sp.P * 32);
+    // rescore: per warp the residual and two P-row buffers; as many warps per
+    // block (up to kRescanWarps) as fit
+    const size_t per_warp = sizeof(float) * ((size_t)sp.Lp + 2 * (size_t)sp.P * 32);
     int rw = kRescanWarps;
     while (rw > 1 && rw * per_warp > (size_t)kSmemBudget) --rw;
     s->rescan_warps = rw;
