@@ -327,7 +327,7 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             ACT_CK(launch_shift_tc_resolve(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, w.keys, w.fb_list, w.fb_count,
                                            g->stats, g->status, st));
-            kernels += 4;
+            kernels += 5;
         } else if (bf16) {
             ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));

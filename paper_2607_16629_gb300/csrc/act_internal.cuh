@@ -173,9 +173,12 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 // Selection into keys[] (packed, atomicMax; keys must be clear), or with
 // scores != null every score written to scores[b * K + flat].  With
 // early_launch the kernel is a programmatic dependent of the previous kernel
-// in the stream (its prologue overlaps that kernel).
+// in the stream (its prologue overlaps that kernel).  With count_dev, only
+// the channels chlist[0 .. min(*count_dev, B)) are searched (the grid is
+// sized for B; never an early launch).
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, bool early_launch, cudaStream_t st);
+                                float *scores, int *status, bool early_launch, cudaStream_t st,
+                                const int *chlist = nullptr, const int *count_dev = nullptr);
 // Coefficient and residual update (Eq. (4)) with the selected atom read back
 // from its template; lets the next search launch early (programmatic
 // dependent launch).
@@ -193,9 +196,11 @@ void shift_tc_free(ShiftTc *s);
 // Shifted-residual, tile-maximum and item buffers for up to B channels.
 cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B);
 // One search order: shifted residual rows + tcgen05 GEMM (tile maxima of the
-// scaled scores), then item selection and FP32 rescore of the flagged items
-// (of every item, for a channel with too many flagged ones).  Leaves the
-// packed key of every channel in keys[]; counters[0..1] must be zero on entry.
+// scaled scores), then item selection and FP32 rescore of the flagged items;
+// a channel with too many flagged items is queued in fb_list and searched in
+// full by the FP32 template search (launch_shift_search over the queue).
+// Leaves the packed key of every channel in keys[]; counters[0..1] must be
+// zero on entry.
 cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
                                  long long *stats, int *status, cudaStream_t st);
 cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,

@@ -63,6 +63,10 @@ struct ShiftArgs {
     unsigned long long *keys;
     float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
     int *status;
+    // non-null: search only the channels chlist[0 .. *count_dev) (the count
+    // is read when the kernel starts; such a launch is never an early one)
+    const int *chlist;
+    const int *count_dev;
 };
 
 // Template value u_t(m), computed exactly as the dictionary generator
@@ -183,7 +187,8 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
     const int stage_floats = (A.Kc + J + 1) * 32;
     float *rpoly = sm + NS * stage_floats;     // [Sa][P] + 4 slack floats, after the stages
     const int units_per_b = A.G * A.TB;
-    const int n_units = A.B * units_per_b;
+    const int n_b = A.count_dev ? min(*A.count_dev, A.B) : A.B;
+    const int n_units = n_b * units_per_b;
     if ((int)blockIdx.x >= n_units) return;
     // chunk c of this CTA: phase c % Sa of its unit c / Sa
     const int my_units = (n_units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
 
     int c = 0;  // chunks consumed by this CTA
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int b = u / units_per_b;
+        const int b = A.chlist ? A.chlist[u / units_per_b] : u / units_per_b;
         const int rem = u % units_per_b;
         const int g = rem / A.TB, tb = rem % A.TB;
         if (b != cur_b) {
@@ -518,8 +523,10 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 }
 
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
-                                float *scores, int *status, bool early_launch, cudaStream_t st) {
-    if (sp.J == 0 || !sp.tpl) return cudaErrorInvalidValue;
+                                float *scores, int *status, bool early_launch, cudaStream_t st, const int *chlist,
+                                const int *count_dev) {
+    if (sp.J == 0 || !sp.tpl || (count_dev && !chlist)) return cudaErrorInvalidValue;
+    if (count_dev) early_launch = false;  // the count must be written before the kernel reads it
     ShiftArgs A;
     A.tpl = sp.tpl;
     A.scale = sp.scale;
@@ -543,6 +550,8 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
     A.keys = keys;
     A.scores = scores;
     A.status = status;
+    A.chlist = chlist;
+    A.count_dev = count_dev;
     const int64_t units = (int64_t)B * sp.G * sp.TB;
     if (units > INT32_MAX) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};

@@ -49,7 +49,7 @@ struct ShiftTile {
     static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                        ((uint32_t)(kBM >> 4) << 24);
 };
-constexpr int kMaxItems = 64;      // flagged (lag, tile) items per channel before the exhaustive rescore
+constexpr int kMaxItems = 1024;    // flagged (lag, block) items per channel before the full FP32 search
 constexpr int kRescanWarps = 4;     // independent warps per rescore block
 
 struct Smem {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bp
                     items[2 * at + 1] = j * n_blocks + tile * bpt + k;
                     atomicAdd((unsigned long long *)&stats[2], 1ull);
                 } else if (pos == kMaxItems) {
-                    // too many: every block of this channel is rescored instead
+                    // too many: the FP32 template search scores this channel in full
                     fb_list[atomicAdd(&counters[0], 1)] = b;
                     atomicAdd((unsigned long long *)&stats[1], 1ull);
                     atomicAdd((unsigned long long *)&stats[0], ~0ull);  // -1: not resolved by the items
@@ -408,9 +408,8 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bp
     }
 }
 
-// FP32 rescore, one warp per (item, 32-template block): the flagged items
-// of every channel, and every item of the channels whose selection overflowed
-// (those are searched exhaustively this way).  Lane = template.  Per phase
+// FP32 rescore, one warp per flagged (lag, 32-template block) item.  Lane =
+// template.  Per phase
 // a, the P template rows the FP32 template search reads for this lag
 // (contiguous, P x 128 bytes) arrive by a bulk copy into one of the warp's
 // two buffers (the next phase's copy is in flight while this one is used);
@@ -419,9 +418,8 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bp
 // residual phases; warps never wait on one another.
 __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     const float *__restrict__ tpl, const float *__restrict__ scale, int S, int Sa, int P, int rows, int NtcP,
-    int Ntc, int T, int n_tiles, int bpt, int Lp, int L, const float *__restrict__ R, const int *__restrict__ items,
-    const int *__restrict__ fb_list, const int *__restrict__ counters, unsigned long long *__restrict__ keys,
-    int *status) {
+    int Ntc, int T, int n_blocks, int Lp, int L, const float *__restrict__ R, const int *__restrict__ items,
+    const int *__restrict__ counters, unsigned long long *__restrict__ keys, int *status) {
     extern __shared__ __align__(128) float sm[];  // per warp: the residual [Lp], then 2 x [P][32] rows
     __shared__ __align__(8) uint64_t bar[kRescanWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -429,9 +427,7 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     float *rres = sm + warp * warp_floats;
     float *buf0 = rres + Lp;
     const uint32_t bytes = (uint32_t)P * 128u;
-    const int n_flag = counters[1], n_fb = counters[0];
-    const int64_t per_fb = (int64_t)Ntc * n_tiles * bpt;  // warp tasks of one overflowed channel
-    const int64_t n_tasks = (int64_t)n_flag * bpt + (int64_t)n_fb * per_fb;
+    const int n_tasks = counters[1];  // at most kMaxItems per channel
     const int nw = (int)(blockDim.x >> 5);
     if (lane == 0) {
         mbar_init(&bar[warp][0], 1);
@@ -445,24 +441,9 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     // per SM while there are fewer tasks than SMs)
     const int64_t stride = (int64_t)gridDim.x * nw;
     for (int64_t task = (int64_t)warp * gridDim.x + blockIdx.x; task < n_tasks; task += stride) {
-        int b, j, tile, q;
-        if (task < (int64_t)n_flag * bpt) {
-            const int it = (int)(task / bpt);
-            q = (int)(task % bpt);
-            b = items[2 * it];
-            const int e = items[2 * it + 1];
-            j = e / n_tiles;
-            tile = e % n_tiles;
-        } else {
-            const int64_t f = task - (int64_t)n_flag * bpt;
-            b = fb_list[f / per_fb];
-            const int64_t rem = f % per_fb;  // (j, tile, q)
-            q = (int)(rem % bpt);
-            const int64_t e = rem / bpt;
-            j = (int)(e / n_tiles);
-            tile = (int)(e % n_tiles);
-        }
-        const int tb = tile * bpt + q;
+        const int b = items[2 * task];
+        const int e = items[2 * task + 1];  // j * n_blocks + block
+        const int j = e / n_blocks, tb = e % n_blocks;
         if (tb * 32 >= T) continue;  // past the last template
         const float *src = tpl + ((size_t)tb * Sa * rows + (size_t)(NtcP - 1 - j)) * 32;
         __syncwarp();
@@ -719,9 +700,13 @@ cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_shift_rescan<<<s->sm_count * s->rescan_blocks_per_sm, s->rescan_warps * 32, s->rescan_smem, st>>>(
-        sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, 1, Lp, L, R, s->items,
-        fb_list, counters, keys, status);
-    return cudaGetLastError();
+        sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, Lp, L, R, s->items,
+        counters, keys, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // channels with more than kMaxItems flagged items: the FP32 template
+    // search over the queue (an empty queue leaves every CTA idle)
+    return launch_shift_search(sp, R, Lp, L, B, keys, nullptr, status, false, st, fb_list, &counters[0]);
 }
 
 

@@ -3,7 +3,8 @@
 The BF16 tcgen05 GEMM only narrows the search: every (time centre,
 template tile) that the BF16 error bound cannot exclude is rescored with the
 FP32 template search's own arithmetic, and a channel with too many such
-tiles has every tile rescored that way.  So the whole decomposition must
+items is searched in full by the FP32 template search itself (over a device
+queue of such channels).  So the whole decomposition must
 equal ACT_SEARCH_SHIFT's bit for bit, and through it the oracle parity of
 tests/test_gpu_shift.py carries over; one lock-step check against the
 oracle is repeated here directly."""
@@ -103,12 +104,27 @@ def test_lockstep_against_oracle():
 
 
 def test_zero_signal_takes_the_fallback():
-    """All scores 0: every item ties, the channel has too many items and all
-    of its items are rescored (index 0 wins)."""
+    """All scores 0: every item ties, the channel has too many items and is
+    searched in full (index 0 wins)."""
     grid = eeg_small()
     a, b, (resolved, items, fallbacks) = both(grid, np.zeros((2, grid.n_samples), np.float32), 2)
     assert_same(a, b)
     assert fallbacks == 4 and np.all(b[0] == 0)
+
+
+def test_fallback_queue_holds_only_the_overflowed_channels():
+    """Zero channels among EEG-like ones: only the zero channels overflow, the
+    full FP32 search runs over the queue of those channels alone, and every
+    channel's decomposition still equals the FP32 template search's."""
+    grid = eeg_small()
+    sig = np.stack([synth.eeg_like_signal(2, 40 + b)[0] for b in range(6)]).astype(np.float32)
+    sig[1] = 0.0
+    sig[4] = 0.0
+    P = 3
+    a, b, (resolved, items, fallbacks) = both(grid, sig, P)
+    assert_same(a, b)
+    assert fallbacks == 2 * P and resolved == 4 * P
+    assert np.all(b[0][[1, 4]] == 0)
 
 
 def test_refinement_after_tensor_core_search():
