@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "act_device.cuh"
+#include "act_ff.cuh"
 #include "act_internal.cuh"
 
 namespace act {
@@ -37,78 +38,88 @@ __device__ __forceinline__ uint64_t lem_counter(int channel, int order, int axis
            (uint64_t)i;
 }
 
-// 1. Latin hypercube: one block per channel; keys sorted in shared memory
-// (bitonic sort over npow2 >= n entries, padding keys sort last).
+// 1. Latin hypercube: one block per (channel, axis); keys sorted in shared
+// memory (bitonic sort over npow2 >= n entries, padding keys sort last).
 __global__ void __launch_bounds__(kLemThreads) k_lem_lhs(int n, int npow2, LemBox box, uint64_t seed, int order,
                                                         int cap, double *__restrict__ cand, int *__restrict__ ncand) {
     extern __shared__ uint8_t sm_raw[];
     uint64_t *key = reinterpret_cast<uint64_t *>(sm_raw);
     uint32_t *idx = reinterpret_cast<uint32_t *>(key + npow2);
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, a = blockIdx.y;
     double *out = cand + (size_t)b * cap * 4;
-    for (int a = 0; a < 4; ++a) {
-        for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-            key[i] = i < n ? splitmix64_at(seed, lem_counter(b, order, a, 0, i)) : ~0ull;
-            idx[i] = (uint32_t)i;
-        }
-        __syncthreads();
-        for (int size = 2; size <= npow2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-                    const int j = i ^ stride;
-                    if (j > i) {
-                        const bool up = (i & size) == 0;
-                        const uint64_t ki = key[i], kj = key[j];
-                        if ((ki > kj) == up) {
-                            key[i] = kj;
-                            key[j] = ki;
-                            const uint32_t t = idx[i];
-                            idx[i] = idx[j];
-                            idx[j] = t;
-                        }
+    for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+        key[i] = i < n ? splitmix64_at(seed, lem_counter(b, order, a, 0, i)) : ~0ull;
+        idx[i] = (uint32_t)i;
+    }
+    __syncthreads();
+    for (int size = 2; size <= npow2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint64_t ki = key[i], kj = key[j];
+                    if ((ki > kj) == up) {
+                        key[i] = kj;
+                        key[j] = ki;
+                        const uint32_t t = idx[i];
+                        idx[i] = idx[j];
+                        idx[j] = t;
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
-        // sorted position p is the stratum (rank) of sample idx[p]
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int i = (int)idx[p];
-            const uint64_t h = splitmix64_at(seed, lem_counter(b, order, a, 1, i));
-            const double u = (double)(h >> 11) * 0x1.0p-53;
-            const double t = __ddiv_rn(__dadd_rn((double)p, u), (double)n);
-            out[4 * i + a] = __dadd_rn(box.lo[a], __dmul_rn(t, __dadd_rn(box.hi[a], -box.lo[a])));
-        }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) ncand[b] = n;
+    // sorted position p is the stratum (rank) of sample idx[p]
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int i = (int)idx[p];
+        const uint64_t h = splitmix64_at(seed, lem_counter(b, order, a, 1, i));
+        const double u = (double)(h >> 11) * 0x1.0p-53;
+        const double t = __ddiv_rn(__dadd_rn((double)p, u), (double)n);
+        out[4 * i + a] = __dadd_rn(box.lo[a], __dmul_rn(t, __dadd_rn(box.hi[a], -box.lo[a])));
+    }
+    if (threadIdx.x == 0 && a == 0) ncand[b] = n;
 }
 
-// 2. Scores s = <r, u>/|u| of every candidate of every channel, one warp per
-// candidate (samples as the dictionary generator evaluates them, FP64 sums).
+// 2. Scores s = <r, u>/|u| of every candidate of every channel.  A block
+// takes kScoreCands candidates of one channel: their per-atom constants are
+// formed once (FP64, one thread per candidate), then each warp runs its
+// candidates one after another, lane = sample stride 32, with the phase and
+// both sums in float-float (samples as FP32 from the same expressions as the
+// dictionary generator's).
+constexpr int kScoreCands = 64;
+
 __global__ void __launch_bounds__(kLemThreads) k_lem_score(int cap, const double *__restrict__ cand,
                                                           const int *__restrict__ ncand, const float *__restrict__ R,
                                                           int Lp, int L, double inv_fs, double *__restrict__ score) {
+    __shared__ ChirpFF ks[kScoreCands];
     const int b = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (kLemThreads / 32) + (threadIdx.x >> 5);
-    if (i >= ncand[b]) return;
-    const double *th = cand + ((size_t)b * cap + i) * 4;
-    const double tc = th[0], fc = th[1], inv_dt = exp(-th[2]), c = th[3];
-    const float *r = R + (size_t)b * Lp;
-    double ru = 0.0, uu = 0.0;
-    for (int n = lane; n < L; n += 32) {
-        const double tau = ((double)n - tc) * inv_fs;
-        double ph = fma(c, tau, fc) * tau;
-        ph -= rint(ph);
-        const float x = (float)(tau * inv_dt);
-        const float u = expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
-        ru = fma((double)r[n], (double)u, ru);
-        uu = fma((double)u, (double)u, uu);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i0 = blockIdx.x * kScoreCands;
+    const int n_here = min(kScoreCands, ncand[b] - i0);
+    if (n_here <= 0) return;
+    if (threadIdx.x < n_here) {
+        const double *th = cand + ((size_t)b * cap + i0 + threadIdx.x) * 4;
+        ks[threadIdx.x] = chirp_ff(th[0], inv_fs, th[1], th[3], exp(-th[2]));
     }
-    ru = warp_sum(ru);
-    uu = warp_sum(uu);
-    if (lane == 0) score[(size_t)b * cap + i] = (uu > 0.0 && isfinite(uu)) ? ru / sqrt(uu) : 0.0;
+    __syncthreads();
+    const float *r = R + (size_t)b * Lp;
+    for (int q = warp; q < n_here; q += kLemThreads / 32) {
+        const ChirpFF k = ks[q];
+        ff ru = {0.0f, 0.0f}, uu = {0.0f, 0.0f};
+        for (int n = lane; n < L; n += 32) {
+            const float u = chirp_sample_ff(n, k);
+            ff_fma_acc(ru, __ldg(r + n), u);
+            ff_fma_acc(uu, u, u);
+        }
+        ru = ff_warp_sum(ru);
+        uu = ff_warp_sum(uu);
+        if (lane == 0) {
+            const double e = ff_to_double(uu);
+            score[(size_t)b * cap + i0 + q] = (e > 0.0 && isfinite(e)) ? ff_to_double(ru) / sqrt(e) : 0.0;
+        }
+    }
 }
 
 // 3. Top-k by |score| with duplicates skipped: one block per channel, k
@@ -219,9 +230,8 @@ cudaError_t launch_lem_select(const LemConfig &cfg, int B, int order, const floa
         cudaError_t ea = cudaFuncSetAttribute(k_lem_lhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ea != cudaSuccess) return ea;
     }
-    k_lem_lhs<<<B, kLemThreads, smem, st>>>(cfg.n_coarse, npow2, cfg.box, cfg.seed, order, lb.cap, lb.cand, lb.ncand);
+    k_lem_lhs<<<dim3(B, 4), kLemThreads, smem, st>>>(cfg.n_coarse, npow2, cfg.box, cfg.seed, order, lb.cap, lb.cand, lb.ncand);
     cudaError_t e = cudaGetLastError();
-    const int per_block = kLemThreads / 32;
     const double inv_fs = 1.0 / fs;
     int n = cfg.n_coarse;
     for (int lev = 0; lev <= cfg.levels && e == cudaSuccess; ++lev) {
@@ -234,7 +244,7 @@ cudaError_t launch_lem_select(const LemConfig &cfg, int B, int order, const floa
             n = cfg.top_k * per;
         }
         if (e != cudaSuccess) break;
-        dim3 grid((n + per_block - 1) / per_block, B);
+        dim3 grid((n + kScoreCands - 1) / kScoreCands, B);
         k_lem_score<<<grid, kLemThreads, 0, st>>>(lb.cap, lb.cand, lb.ncand, R, Lp, L, inv_fs, lb.score);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;

@@ -13,8 +13,9 @@
 // Samples are evaluated as the dictionary generator does (phase formed in
 // FP64 and range-reduced before FP32 cospi/sinpi, Gaussian argument in
 // FP64).  The standalone score kernel accumulates all ten sums in FP64; the
-// refinement keeps FP64 for the two sums that define the objective and FP32
-// for the eight gradient sums (FP64 throughput is low on this GPU).
+// refinement carries the phase and the two sums that define the objective in
+// float-float and the eight gradient sums in FP32 (FP64 throughput is low on
+// this GPU).
 //
 // Refinement.  BFGS on f(z) = -|s(w (.) z)| in coordinates scaled by the
 // grid steps w, one block per channel: p = -H grad f (H reset to I when p
@@ -28,6 +29,7 @@
 #include <stdint.h>
 
 #include "act_device.cuh"
+#include "act_ff.cuh"
 #include "act_internal.cuh"
 
 namespace act {
@@ -142,49 +144,61 @@ struct RefineBox {
     double w[4], lo[4], hi[4];
 };
 
-// Score and gradient of one warp's candidate (lane-strided samples, warp
-// reductions only): same arithmetic per sample as eval_score.
-__device__ EvalOut eval_warp(const double *th, const float *__restrict__ r, int L, double inv_fs) {
-    const int lane = threadIdx.x & 31;
-    const double tc = th[0], fc = th[1], inv_dt = exp(-th[2]), c = th[3];
-    const float inv_dt_f = (float)inv_dt, inv_fs_f = (float)inv_fs, two_pi = (float)kTwoPi;
-    const float c_f = (float)c, fc_f = (float)fc;
-    double ru = 0.0, uu = 0.0;                    // the objective: FP64 sums
-    float rd[4] = {0, 0, 0, 0}, ud[4] = {0, 0, 0, 0};  // its gradient: FP32 sums
-    for (int n = lane; n < L; n += 32) {
-        const double tau = ((double)n - tc) * inv_fs;
-        double ph = fma(c, tau, fc) * tau;
-        ph -= rint(ph);
-        const float t = (float)tau;
-        const float C = cospif(2.0f * (float)ph);
-        const float S = sinpif(2.0f * (float)ph);
-        const float x = t * inv_dt_f;
-        const float E = expf(-0.5f * x * x);
-        const float u = E * C;
-        const float ES = E * S;
-        const float du0 = (E * x * C * inv_dt_f + ES * two_pi * fmaf(2.0f * c_f, t, fc_f)) * inv_fs_f;
-        const float du1 = -ES * two_pi * t;
-        const float du2 = E * x * x * C;
-        const float du3 = -ES * two_pi * t * t;
-        const float rv = r[n];
-        ru = fma((double)rv, (double)u, ru);
-        uu = fma((double)u, (double)u, uu);
-        rd[0] = fmaf(rv, du0, rd[0]);
-        rd[1] = fmaf(rv, du1, rd[1]);
-        rd[2] = fmaf(rv, du2, rd[2]);
-        rd[3] = fmaf(rv, du3, rd[3]);
-        ud[0] = fmaf(u, du0, ud[0]);
-        ud[1] = fmaf(u, du1, ud[1]);
-        ud[2] = fmaf(u, du2, ud[2]);
-        ud[3] = fmaf(u, du3, ud[3]);
-    }
-    ru = warp_sum(ru);
-    uu = warp_sum(uu);
+// Sums of one evaluation: the objective's two in float-float, the eight of
+// its gradient in FP32.
+struct EvalAcc {
+    ff ru, uu;
+    float rd[4], ud[4];
+};
+
+// Per-atom constants of an evaluation.
+struct EvalConst {
+    ChirpFF k;
+    float inv_dt, inv_fs, c, fc;
+};
+
+__device__ __forceinline__ EvalConst eval_const(const double *th, double inv_fs) {
+    const double inv_dt = exp(-th[2]);
+    return {chirp_ff(th[0], inv_fs, th[1], th[3], inv_dt), (float)inv_dt, (float)inv_fs, (float)th[3],
+            (float)th[1]};
+}
+
+// Adds sample n: the phase in float-float, the sample and its four
+// derivatives in FP32 (expressions of the header comment).
+__device__ __forceinline__ void eval_add(EvalAcc &a, int n, float rv, const EvalConst &e) {
+    constexpr float two_pi = (float)kTwoPi;
+    ff tau;
+    const float frac = chirp_phase_ff(n, e.k, &tau);
+    const float t = tau.hi;
+    const float C = cospif(2.0f * frac);
+    const float S = sinpif(2.0f * frac);
+    const float x = chirp_x_ff(tau, e.k);
+    const float E = expf(-0.5f * x * x);
+    const float u = E * C;
+    const float ES = E * S;
+    const float du[4] = {(E * x * C * e.inv_dt + ES * two_pi * fmaf(2.0f * e.c, t, e.fc)) * e.inv_fs,
+                         -ES * two_pi * t, E * x * x * C, -ES * two_pi * t * t};
+    ff_fma_acc(a.ru, rv, u);
+    ff_fma_acc(a.uu, u, u);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        rd[i] = warp_sum(rd[i]);
-        ud[i] = warp_sum(ud[i]);
+        a.rd[i] = fmaf(rv, du[i], a.rd[i]);
+        a.ud[i] = fmaf(u, du[i], a.ud[i]);
     }
+}
+
+__device__ __forceinline__ void eval_warp_reduce(EvalAcc &a) {
+    a.ru = ff_warp_sum(a.ru);
+    a.uu = ff_warp_sum(a.uu);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        a.rd[i] = warp_sum(a.rd[i]);
+        a.ud[i] = warp_sum(a.ud[i]);
+    }
+}
+
+__device__ __forceinline__ EvalOut eval_finish(const EvalAcc &a) {
+    const double ru = ff_to_double(a.ru), uu = ff_to_double(a.uu);
     EvalOut o;
     if (!(uu > 0.0) || !isfinite(uu)) {
         o.s = 0.0;
@@ -193,32 +207,105 @@ __device__ EvalOut eval_warp(const double *th, const float *__restrict__ r, int 
         return o;
     }
     o.nu = sqrt(uu);
-    o.s = ru / o.nu;
-    for (int i = 0; i < 4; ++i) o.g[i] = (double)rd[i] / o.nu - o.s * (double)ud[i] / uu;
+    const double inv_nu = 1.0 / o.nu;
+    o.s = ru * inv_nu;
+    const double s_uu = o.s * inv_nu * inv_nu;
+    for (int i = 0; i < 4; ++i) o.g[i] = (double)a.rd[i] * inv_nu - s_uu * (double)a.ud[i];
+    return o;
+}
+
+// Score and gradient of one warp's candidate (lane-strided samples, warp
+// reductions only); every lane receives the result.
+__device__ EvalOut eval_warp(const double *th, const float *__restrict__ r, int L, double inv_fs) {
+    const EvalConst e = eval_const(th, inv_fs);
+    EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    for (int n = threadIdx.x & 31; n < L; n += 32) eval_add(a, n, r[n], e);
+    eval_warp_reduce(a);
+    return eval_finish(a);
+}
+
+// The same evaluation by all kWarps warps of the block (samples strided by
+// the block; the warps' sums added in warp order): the result is valid in
+// thread 0 only.  red holds one EvalAcc per warp; ec is a shared slot for
+// the constants (formed once, by thread 0: FP64 is slow on this GPU).
+template <int kWarps>
+__device__ EvalOut eval_block(const double *th, const float *__restrict__ r, int L, double inv_fs, EvalAcc *red,
+                              EvalConst *ec) {
+    if (threadIdx.x == 0) *ec = eval_const(th, inv_fs);
+    __syncthreads();
+    const EvalConst e = *ec;
+    EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    for (int n = threadIdx.x; n < L; n += 32 * kWarps) eval_add(a, n, r[n], e);
+    eval_warp_reduce(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    EvalOut o = {};
+    if (threadIdx.x == 0) {
+        EvalAcc t = red[0];
+        for (int w = 1; w < kWarps; ++w) {
+            t.ru = ff_add(t.ru, red[w].ru);
+            t.uu = ff_add(t.uu, red[w].uu);
+            for (int i = 0; i < 4; ++i) {
+                t.rd[i] += red[w].rd[i];
+                t.ud[i] += red[w].ud[i];
+            }
+        }
+        o = eval_finish(t);
+    }
     return o;
 }
 
 constexpr int kLineSearch = 20;  // Armijo halvings per iteration
 
-// BFGS refinement of channel b's grid winner; theta_out[b][4].  The 8 warps
-// of the block evaluate 8 consecutive step sizes alpha0 2^-j at once; the
-// first (largest) that satisfies the Armijo condition is taken, which is
-// what sequential backtracking would take.
+// Sum over each group of 4 lanes (lane i of a group holds parameter i).
+__device__ __forceinline__ double sum4(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+
+// BFGS refinement of channel b's grid winner; theta_out[b][4].  Each
+// iteration evaluates the full step alpha0 and then, if the Armijo
+// condition fails, half of it with the whole block (the usual outcomes);
+// after that the 8 warps evaluate the next 8 step sizes alpha0 2^-j at once,
+// and so on.  The first (largest) step that satisfies the condition is
+// taken, which is what sequential backtracking would take.  The per-parameter
+// bookkeeping runs on lanes of warp 0 (lane & 3 = parameter), the 4 x 4
+// inverse update on 16 threads.
 __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBox box, int steps, int Lp,
                                                           const float *__restrict__ R,
                                                           const unsigned long long *__restrict__ keys,
                                                           const double *__restrict__ theta_in, int theta_in_stride,
                                                           double *__restrict__ theta_out) {
     constexpr int kWarps = kRefineThreads / 32;
-    __shared__ double z[4], gz[4], H[16], p[4], th_cur[4];
+    constexpr int kBlockSteps = 2;  // steps j = 0, 1 evaluated by the whole block
+    __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4];
     __shared__ double cz[kWarps][4], cth[kWarps][4], cg[kWarps][4], cf[kWarps], ca[kWarps];
-    __shared__ double f, gp, alpha0;
-    __shared__ int state;  // -1: stop; otherwise the accepted warp (or kWarps: none yet)
+    __shared__ double f, gp, alpha0, rho;
+    __shared__ EvalAcc red[kWarps];
+    __shared__ EvalConst ec;
+    __shared__ int state;  // -1: stop; otherwise the accepted slot (or kWarps: none yet)
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pi = lane & 3;  // the parameter of this lane in warp 0's bookkeeping
     const float *r = R + (size_t)b * Lp;
     const int L = ax.L;
     const double inv_fs = 1.0 / ax.fs;
+
+    // component i of the trial point of step j into slot q
+    auto trial = [&](int j, int q, int i) {
+        const double a = alpha0 * ldexp(1.0, -j);
+        double v = (z[i] + a * p[i]) * box.w[i];
+        v = v < box.lo[i] ? box.lo[i] : (v > box.hi[i] ? box.hi[i] : v);
+        cz[q][i] = v / box.w[i];
+        cth[q][i] = v;
+        if (i == 0) ca[q] = a;
+    };
+    auto record = [&](const EvalOut &o, int q) {  // f and scaled gradient of slot q (one thread)
+        const double sg = o.s < 0.0 ? -1.0 : 1.0;
+        cf[q] = -fabs(o.s);
+        for (int i = 0; i < 4; ++i) cg[q][i] = -sg * o.g[i] * box.w[i];
+    };
+    auto armijo = [&](int q) { return cf[q] <= f + 1e-4 * ca[q] * gp; };
 
     if (threadIdx.x == 0) {
         double p0[4];
@@ -231,14 +318,12 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
             z[i] = p0[i] / box.w[i];
             th_cur[i] = p0[i];  // the parameters themselves: returned unchanged if no step is taken
         }
-        for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
     }
+    if (threadIdx.x < 16) H[threadIdx.x] = (threadIdx.x % 5 == 0) ? 1.0 : 0.0;
     __syncthreads();
-    if (warp == 0) {
-        double th[4];
-        for (int i = 0; i < 4; ++i) th[i] = th_cur[i];
-        const EvalOut o = eval_warp(th, r, L, inv_fs);
-        if (lane == 0) {
+    {
+        const EvalOut o = eval_block<kWarps>(th_cur, r, L, inv_fs, red, &ec);
+        if (threadIdx.x == 0) {
             const double sg = o.s < 0.0 ? -1.0 : 1.0;
             f = -fabs(o.s);
             for (int i = 0; i < 4; ++i) gz[i] = -sg * o.g[i] * box.w[i];
@@ -246,98 +331,99 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
     }
     __syncthreads();
     for (int it = 0; it < steps; ++it) {
-        if (threadIdx.x == 0) {
-            double g_p = 0.0, pn = 0.0;
-            for (int i = 0; i < 4; ++i) {
-                double v = 0.0;
-                for (int j = 0; j < 4; ++j) v -= H[4 * i + j] * gz[j];
-                p[i] = v;
-                g_p += gz[i] * v;
+        if (warp == 0) {  // direction p = -H g (steepest descent, H reset, if not a descent direction)
+            double v = 0.0;
+            for (int j = 0; j < 4; ++j) v -= H[4 * pi + j] * gz[j];
+            double g_p = sum4(gz[pi] * v);
+            const bool reset = !(g_p < 0.0);
+            if (reset) {
+                v = -gz[pi];
+                g_p = sum4(gz[pi] * v);
             }
-            if (!(g_p < 0.0)) {
-                for (int i = 0; i < 16; ++i) H[i] = (i % 5 == 0) ? 1.0 : 0.0;
-                g_p = 0.0;
-                for (int i = 0; i < 4; ++i) {
-                    p[i] = -gz[i];
-                    g_p += gz[i] * p[i];
-                }
+            const double pn = sqrt(sum4(v * v));
+            __syncwarp();
+            if (lane < 4) {
+                p[pi] = v;
+                if (reset)
+                    for (int k = 0; k < 4; ++k) H[4 * pi + k] = pi == k ? 1.0 : 0.0;
             }
-            for (int i = 0; i < 4; ++i) pn += p[i] * p[i];
-            pn = sqrt(pn);
-            gp = g_p;
-            alpha0 = pn > 0.5 ? 0.5 / pn : 1.0;
-            state = (g_p < 0.0) ? kWarps : -1;
+            if (lane == 0) {
+                gp = g_p;
+                alpha0 = pn > 0.5 ? 0.5 / pn : 1.0;
+                state = (g_p < 0.0) ? kWarps : -1;
+            }
+            __syncwarp();
+            if (g_p < 0.0 && lane < 4) trial(0, 0, pi);
         }
         __syncthreads();
         if (state < 0) break;
-        for (int round = 0; round * kWarps < kLineSearch; ++round) {
-            const int j = round * kWarps + warp;
+        // the full and the half step, by the whole block
+        for (int j = 0; j < kBlockSteps && state == kWarps; ++j) {
+            if (j > 0) {
+                if (threadIdx.x < 4) trial(j, 0, threadIdx.x);
+                __syncthreads();
+            }
+            const EvalOut o = eval_block<kWarps>(cth[0], r, L, inv_fs, red, &ec);
+            if (threadIdx.x == 0) {
+                record(o, 0);
+                if (armijo(0)) state = 0;
+            }
+            __syncthreads();
+        }
+        // shorter steps, kWarps at a time (one warp each)
+        for (int j0 = kBlockSteps; state == kWarps && j0 < kLineSearch; j0 += kWarps) {
+            const int j = j0 + warp;
             if (j < kLineSearch) {
-                const double a = alpha0 * ldexp(1.0, -j);
-                double th[4], zz[4];
-                for (int i = 0; i < 4; ++i) {
-                    double v = (z[i] + a * p[i]) * box.w[i];
-                    v = v < box.lo[i] ? box.lo[i] : (v > box.hi[i] ? box.hi[i] : v);
-                    zz[i] = v / box.w[i];
-                    th[i] = v;
-                }
-                const EvalOut o = eval_warp(th, r, L, inv_fs);
-                if (lane == 0) {
-                    const double sg = o.s < 0.0 ? -1.0 : 1.0;
-                    cf[warp] = -fabs(o.s);
-                    ca[warp] = a;
-                    for (int i = 0; i < 4; ++i) {
-                        cz[warp][i] = zz[i];
-                        cth[warp][i] = th[i];
-                        cg[warp][i] = -sg * o.g[i] * box.w[i];
-                    }
-                }
+                if (lane < 4) trial(j, warp, lane);
+                __syncwarp();
+                const EvalOut o = eval_warp(cth[warp], r, L, inv_fs);
+                if (lane == 0) record(o, warp);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                for (int q = 0; q < kWarps && round * kWarps + q < kLineSearch; ++q)
-                    if (cf[q] <= f + 1e-4 * ca[q] * gp) {
+                for (int q = 0; q < kWarps && j0 + q < kLineSearch; ++q)
+                    if (armijo(q)) {
                         state = q;
                         break;
                     }
             }
             __syncthreads();
-            if (state < kWarps) break;
         }
         if (state >= kWarps) break;  // no acceptable step
-        if (threadIdx.x == 0) {
-            const int q = state;
-            double sv[4], yv[4], ys = 0.0;
-            for (int i = 0; i < 4; ++i) {
-                sv[i] = cz[q][i] - z[i];
-                yv[i] = cg[q][i] - gz[i];
-                ys += yv[i] * sv[i];
+        // BFGS inverse update H' = (I - rho s y^T) H (I - rho y s^T) + rho s s^T
+        // when <y, s> > 0
+        const int q = state;
+        if (warp == 0) {
+            const double si = cz[q][pi] - z[pi], yi = cg[q][pi] - gz[pi];
+            const double ys = sum4(yi * si);
+            if (lane < 4) {
+                sv[pi] = si;
+                yv[pi] = yi;
             }
-            if (ys > 1e-300) {
-                const double rho = 1.0 / ys;
-                double A[16], T[16];
-                for (int i = 0; i < 4; ++i)
-                    for (int j = 0; j < 4; ++j) A[4 * i + j] = (i == j ? 1.0 : 0.0) - rho * sv[i] * yv[j];
-                for (int i = 0; i < 4; ++i)
-                    for (int j = 0; j < 4; ++j) {
-                        double a = 0.0;
-                        for (int k = 0; k < 4; ++k) a += A[4 * i + k] * H[4 * k + j];
-                        T[4 * i + j] = a;
-                    }
-                for (int i = 0; i < 4; ++i)
-                    for (int j = 0; j < 4; ++j) {
-                        double a = 0.0;
-                        for (int k = 0; k < 4; ++k) a += T[4 * i + k] * A[4 * j + k];
-                        H[4 * i + j] = a + rho * sv[i] * sv[j];
-                    }
-            }
-            for (int i = 0; i < 4; ++i) {
-                z[i] = cz[q][i];
-                th_cur[i] = cth[q][i];
-                gz[i] = cg[q][i];
-            }
-            f = cf[q];
+            if (lane == 0) rho = ys > 1e-300 ? 1.0 / ys : 0.0;
         }
+        __syncthreads();
+        if (rho != 0.0) {
+            if (threadIdx.x < 16) {  // Hn = (I - rho s y^T) H
+                const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
+                double a = 0.0;
+                for (int k = 0; k < 4; ++k) a += ((i == k ? 1.0 : 0.0) - rho * sv[i] * yv[k]) * H[4 * k + j];
+                Hn[threadIdx.x] = a;
+            }
+            __syncthreads();
+            if (threadIdx.x < 16) {  // H = Hn (I - rho y s^T) + rho s s^T
+                const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
+                double a = 0.0;
+                for (int k = 0; k < 4; ++k) a += Hn[4 * i + k] * ((j == k ? 1.0 : 0.0) - rho * sv[j] * yv[k]);
+                H[threadIdx.x] = a + rho * sv[i] * sv[j];
+            }
+        }
+        if (threadIdx.x < 4) {
+            z[threadIdx.x] = cz[q][threadIdx.x];
+            th_cur[threadIdx.x] = cth[q][threadIdx.x];
+            gz[threadIdx.x] = cg[q][threadIdx.x];
+        }
+        if (threadIdx.x == 0) f = cf[q];
         __syncthreads();
     }
     if (threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = th_cur[threadIdx.x];
