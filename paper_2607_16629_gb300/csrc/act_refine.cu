@@ -36,7 +36,8 @@ namespace act {
 
 namespace {
 
-constexpr int kRefineThreads = 256;
+constexpr int kRefineThreads = 256;  // standalone score and update kernels
+constexpr int kBfgsThreads = 512;    // the refinement: one block per channel
 constexpr double kTwoPi = 6.283185307179586;
 
 struct EvalOut {
@@ -170,8 +171,8 @@ __device__ __forceinline__ void eval_add(EvalAcc &a, int n, float rv, const Eval
     ff tau;
     const float frac = chirp_phase_ff(n, e.k, &tau);
     const float t = tau.hi;
-    const float C = cospif(2.0f * frac);
-    const float S = sinpif(2.0f * frac);
+    float S, C;
+    sincospif(2.0f * frac, &S, &C);
     const float x = chirp_x_ff(tau, e.k);
     const float E = expf(-0.5f * x * x);
     const float u = E * C;
@@ -214,43 +215,40 @@ __device__ __forceinline__ EvalOut eval_finish(const EvalAcc &a) {
     return o;
 }
 
-// Score and gradient of one warp's candidate (lane-strided samples, warp
-// reductions only); every lane receives the result.
-__device__ EvalOut eval_warp(const double *th, const float *__restrict__ r, int L, double inv_fs) {
-    const EvalConst e = eval_const(th, inv_fs);
-    EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    for (int n = threadIdx.x & 31; n < L; n += 32) eval_add(a, n, r[n], e);
-    eval_warp_reduce(a);
-    return eval_finish(a);
-}
-
-// The same evaluation by all kWarps warps of the block (samples strided by
-// the block; the warps' sums added in warp order): the result is valid in
-// thread 0 only.  red holds one EvalAcc per warp; ec is a shared slot for
-// the constants (formed once, by thread 0: FP64 is slow on this GPU).
-template <int kWarps>
-__device__ EvalOut eval_block(const double *th, const float *__restrict__ r, int L, double inv_fs, EvalAcc *red,
-                              EvalConst *ec) {
-    if (threadIdx.x == 0) *ec = eval_const(th, inv_fs);
+// Score and gradient by a group of G consecutive warps (samples strided by
+// the group, the warps' sums added in warp order); every group of the block
+// calls it at once (it holds block barriers), each on its own candidate th
+// (inactive groups take part without evaluating).  The result is valid in
+// the group's first thread.  red holds one EvalAcc per warp; ec one slot of
+// constants per group (formed once, by that thread: FP64 is slow on this
+// GPU).
+template <int G>
+__device__ EvalOut eval_group(const double *th, bool active, const float *__restrict__ r, int L, double inv_fs,
+                              EvalAcc *red, EvalConst *ec) {
+    const int warp = threadIdx.x >> 5, g = warp / G, t = (int)threadIdx.x - g * G * 32;
+    if (t == 0 && active) ec[g] = eval_const(th, inv_fs);
     __syncthreads();
-    const EvalConst e = *ec;
     EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    for (int n = threadIdx.x; n < L; n += 32 * kWarps) eval_add(a, n, r[n], e);
+    if (active) {
+        const EvalConst e = ec[g];
+        for (int n = t; n < L; n += 32 * G) eval_add(a, n, r[n], e);
+    }
     eval_warp_reduce(a);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    if ((threadIdx.x & 31) == 0) red[warp] = a;
     __syncthreads();
     EvalOut o = {};
-    if (threadIdx.x == 0) {
-        EvalAcc t = red[0];
-        for (int w = 1; w < kWarps; ++w) {
-            t.ru = ff_add(t.ru, red[w].ru);
-            t.uu = ff_add(t.uu, red[w].uu);
+    if (t == 0 && active) {
+        EvalAcc u = red[g * G];
+        for (int w = 1; w < G; ++w) {
+            const EvalAcc &v = red[g * G + w];
+            u.ru = ff_add(u.ru, v.ru);
+            u.uu = ff_add(u.uu, v.uu);
             for (int i = 0; i < 4; ++i) {
-                t.rd[i] += red[w].rd[i];
-                t.ud[i] += red[w].ud[i];
+                u.rd[i] += v.rd[i];
+                u.ud[i] += v.ud[i];
             }
         }
-        o = eval_finish(t);
+        o = eval_finish(u);
     }
     return o;
 }
@@ -266,24 +264,27 @@ __device__ __forceinline__ double sum4(double v) {
 // BFGS refinement of channel b's grid winner; theta_out[b][4].  Each
 // iteration evaluates the full step alpha0 and then, if the Armijo
 // condition fails, half of it with the whole block (the usual outcomes);
-// after that the 8 warps evaluate the next 8 step sizes alpha0 2^-j at once,
-// and so on.  The first (largest) step that satisfies the condition is
-// taken, which is what sequential backtracking would take.  The per-parameter
-// bookkeeping runs on lanes of warp 0 (lane & 3 = parameter), the 4 x 4
-// inverse update on 16 threads.
-__global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBox box, int steps, int Lp,
+// after that groups of 4 warps evaluate the next 4 step sizes alpha0 2^-j at
+// once, and so on.  The first (largest) step that satisfies the condition
+// is taken, which is what sequential backtracking would take.  The
+// per-parameter bookkeeping runs on lanes of warp 0 (lane & 3 = parameter),
+// the 4 x 4 inverse update on 16 threads.
+__global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox box, int steps, int Lp,
                                                           const float *__restrict__ R,
                                                           const unsigned long long *__restrict__ keys,
                                                           const double *__restrict__ theta_in, int theta_in_stride,
                                                           double *__restrict__ theta_out) {
-    constexpr int kWarps = kRefineThreads / 32;
+    constexpr int kWarps = kBfgsThreads / 32;
     constexpr int kBlockSteps = 2;  // steps j = 0, 1 evaluated by the whole block
+    constexpr int kGroupWarps = 4;  // then kSlots steps at a time, one per group of warps
+    constexpr int kSlots = kWarps / kGroupWarps;
+    constexpr int kNone = kSlots;   // state: no step accepted yet
     __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4];
-    __shared__ double cz[kWarps][4], cth[kWarps][4], cg[kWarps][4], cf[kWarps], ca[kWarps];
+    __shared__ double cz[kSlots][4], cth[kSlots][4], cg[kSlots][4], cf[kSlots], ca[kSlots];
     __shared__ double f, gp, alpha0, rho;
     __shared__ EvalAcc red[kWarps];
-    __shared__ EvalConst ec;
-    __shared__ int state;  // -1: stop; otherwise the accepted slot (or kWarps: none yet)
+    __shared__ EvalConst ec[kSlots];
+    __shared__ int state;  // -1: stop; otherwise the accepted slot (or kNone)
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pi = lane & 3;  // the parameter of this lane in warp 0's bookkeeping
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
     if (threadIdx.x < 16) H[threadIdx.x] = (threadIdx.x % 5 == 0) ? 1.0 : 0.0;
     __syncthreads();
     {
-        const EvalOut o = eval_block<kWarps>(th_cur, r, L, inv_fs, red, &ec);
+        const EvalOut o = eval_group<kWarps>(th_cur, true, r, L, inv_fs, red, ec);
         if (threadIdx.x == 0) {
             const double sg = o.s < 0.0 ? -1.0 : 1.0;
             f = -fabs(o.s);
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
             if (lane == 0) {
                 gp = g_p;
                 alpha0 = pn > 0.5 ? 0.5 / pn : 1.0;
-                state = (g_p < 0.0) ? kWarps : -1;
+                state = (g_p < 0.0) ? kNone : -1;
             }
             __syncwarp();
             if (g_p < 0.0 && lane < 4) trial(0, 0, pi);
@@ -358,30 +359,29 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
         __syncthreads();
         if (state < 0) break;
         // the full and the half step, by the whole block
-        for (int j = 0; j < kBlockSteps && state == kWarps; ++j) {
+        for (int j = 0; j < kBlockSteps && state == kNone; ++j) {
             if (j > 0) {
                 if (threadIdx.x < 4) trial(j, 0, threadIdx.x);
                 __syncthreads();
             }
-            const EvalOut o = eval_block<kWarps>(cth[0], r, L, inv_fs, red, &ec);
+            const EvalOut o = eval_group<kWarps>(cth[0], true, r, L, inv_fs, red, ec);
             if (threadIdx.x == 0) {
                 record(o, 0);
                 if (armijo(0)) state = 0;
             }
             __syncthreads();
         }
-        // shorter steps, kWarps at a time (one warp each)
-        for (int j0 = kBlockSteps; state == kWarps && j0 < kLineSearch; j0 += kWarps) {
-            const int j = j0 + warp;
-            if (j < kLineSearch) {
-                if (lane < 4) trial(j, warp, lane);
-                __syncwarp();
-                const EvalOut o = eval_warp(cth[warp], r, L, inv_fs);
-                if (lane == 0) record(o, warp);
-            }
+        // shorter steps, kSlots at a time (one group of warps each)
+        for (int j0 = kBlockSteps; state == kNone && j0 < kLineSearch; j0 += kSlots) {
+            const int g = warp / kGroupWarps, t = (int)threadIdx.x - g * kGroupWarps * 32;
+            const bool active = j0 + g < kLineSearch;
+            if (active && t < 4) trial(j0 + g, g, t);
+            __syncwarp();  // the group's first thread reads the trial point
+            const EvalOut o = eval_group<kGroupWarps>(cth[g], active, r, L, inv_fs, red, ec);
+            if (active && t == 0) record(o, g);
             __syncthreads();
             if (threadIdx.x == 0) {
-                for (int q = 0; q < kWarps && j0 + q < kLineSearch; ++q)
+                for (int q = 0; q < kSlots && j0 + q < kLineSearch; ++q)
                     if (armijo(q)) {
                         state = q;
                         break;
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(GridAxes ax, RefineBo
             }
             __syncthreads();
         }
-        if (state >= kWarps) break;  // no acceptable step
+        if (state >= kNone) break;  // no acceptable step
         // BFGS inverse update H' = (I - rho s y^T) H (I - rho y s^T) + rho s s^T
         // when <y, s> > 0
         const int q = state;
@@ -520,7 +520,7 @@ cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R,
         box.lo[i] = st > 0.0 ? fmin(first, last) - st : first;
         box.hi[i] = st > 0.0 ? fmax(first, last) + st : first;
     }
-    k_refine<<<B, kRefineThreads, 0, st>>>(ax, box, steps, Lp, R, keys, theta_in, theta_in_stride, theta_out);
+    k_refine<<<B, kBfgsThreads, 0, st>>>(ax, box, steps, Lp, R, keys, theta_in, theta_in_stride, theta_out);
     return cudaGetLastError();
 }
 
