@@ -833,6 +833,8 @@ def run_profile_case(args):
     from paper_2607_16629_gb300 import act, synth
     if args.case in ("shift_eeg", "shift_tc_eeg"):
         return run_shift_case(args)
+    if args.case in ("lem_eeg", "refine_radar"):
+        return run_offgrid_case(args)
     full = synth.grid_eeg()
     grid = synth.Grid(full.n_samples, full.fs, synth.Axis(full.tc.lo, full.tc.step, 64), full.fc, full.logdt,
                       full.c)
@@ -888,6 +890,42 @@ def run_shift_case(args):
     print(json.dumps({"case": args.case, "atoms": grid.n_atoms, "channels": B, "tuning": tuning, "ok": True}))
 
 
+def run_offgrid_case(args):
+    """Off-grid cases, 2 orders per step with 20 BFGS iterations each:
+      lem_eeg: hierarchical search (no dictionary) on --channels EEG-like
+        channels (N = 512) over the 2,097,152-atom grid's box;
+      refine_radar: tensor-core template search + refinement on 32
+        radar-like channels (N = 1024, 8,388,608-atom grid)."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    if args.case == "lem_eeg":
+        w = synth.workload_c3()
+        sig_np = w.signals[:args.channels]
+    else:
+        w = synth.workload_c5()
+        sig_np = w.signals
+    sig = torch.tensor(sig_np, dtype=torch.float32, device="cuda")
+    h = act.act_grid_create(w.grid, 0)
+    try:
+        if args.case == "lem_eeg":
+            act.act_set_search(h, act.ACT_SEARCH_LEM)
+        else:
+            act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        act.act_set_refinement(h, 20)
+        for _ in range(args.steps):
+            _, _, _, energy = act.decompose(h, sig, 2)
+        torch.cuda.synchronize()
+        st = act.act_grid_status(h)
+        if st != act.ACT_OK:
+            raise RuntimeError(act.status_name(st))
+        e = energy.cpu().numpy()
+        assert np.all(np.diff(e, axis=1) <= 0.0)
+    finally:
+        act.act_destroy(h)
+    print(json.dumps({"case": args.case, "channels": int(sig.shape[0]), "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -900,12 +938,13 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-lem", action="store_true")
     ap.add_argument("--no-shift", action="store_true")
-    ap.add_argument("--channels", type=int, default=1, help="channels for the shift_* cases (1 or up to 64)")
+    ap.add_argument("--channels", type=int, default=1, help="channels for the shift_* and lem_eeg cases (1 or up to 64)")
     ap.add_argument("--gemv", default="stream", choices=["stream", "load"],
                     help="FP32 GEMV of the gemv_small case: bulk-copy streaming or load-streaming")
     ap.add_argument("--shift-tuning", default="", help="JxW, JxWxS or JxWxSxC for --case shift_eeg (default: the build's)")
     ap.add_argument("--case", default="default",
-                    choices=["default", "gemv_small", "bf16_small", "shift_eeg", "shift_tc_eeg"],
+                    choices=["default", "gemv_small", "bf16_small", "shift_eeg", "shift_tc_eeg", "lem_eeg",
+                             "refine_radar"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()
     if args.case != "default":

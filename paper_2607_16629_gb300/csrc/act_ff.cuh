@@ -46,6 +46,17 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
     return ff_fast_two_sum(r.hi, r.lo + t.lo);
 }
 
+// a + b with one error-free sum of the high parts and the low parts added
+// (error about 2^-47 (|a| + |b|); inputs need not be normalised).
+__device__ __forceinline__ ff ff_add_sloppy(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+// a mod 1 to about [-1/2, 1/2]: hi - rint(hi) is exact; the pair is left
+// unnormalised.
+__device__ __forceinline__ ff ff_frac(ff a) { return {a.hi - rintf(a.hi), a.lo}; }
+
 // a + b for a float b.
 __device__ __forceinline__ ff ff_add_f(ff a, float b) {
     const ff s = ff_two_sum(a.hi, b);
@@ -91,16 +102,20 @@ __device__ __forceinline__ ChirpFF chirp_ff(double tc, double inv_fs, double fc,
 }
 
 // tau = (n - tc) / fs of sample n and the phase (c tau + fc) tau reduced
-// mod 1 (to [-1/2, 1/2] up to one rounding).  n must be below 2^24 (exact as
-// a float).
-__device__ __forceinline__ float chirp_phase_ff(int n, const ChirpFF &k, ff *tau_out) {
+// mod 1 (to about [-1/2, 1/2]) as an unnormalised pair.  n must be below
+// 2^24 (exact as a float).
+__device__ __forceinline__ ff chirp_phase_pair(int n, const ChirpFF &k, ff *tau_out) {
     ff d = ff_two_sum((float)n, -k.tc.hi);
     d = ff_fast_two_sum(d.hi, d.lo - k.tc.lo);
     const ff tau = ff_mul(d, k.inv_fs);
-    const ff ph = ff_mul(ff_add(ff_mul(k.c, tau), k.fc), tau);
     *tau_out = tau;
-    // hi - rint(hi) is exact; adding lo rounds the reduced phase once
-    return (ph.hi - rintf(ph.hi)) + ph.lo;
+    return ff_frac(ff_mul(ff_add(ff_mul(k.c, tau), k.fc), tau));
+}
+
+// The same phase rounded once to FP32.
+__device__ __forceinline__ float chirp_phase_ff(int n, const ChirpFF &k, ff *tau_out) {
+    const ff p = chirp_phase_pair(n, k, tau_out);
+    return p.hi + p.lo;
 }
 
 // The envelope argument x = tau / dt, rounded once to FP32.

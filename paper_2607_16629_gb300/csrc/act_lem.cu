@@ -85,15 +85,25 @@ __global__ void __launch_bounds__(kLemThreads) k_lem_lhs(int n, int npow2, LemBo
 // 2. Scores s = <r, u>/|u| of every candidate of every channel.  A block
 // takes kScoreCands candidates of one channel: their per-atom constants are
 // formed once (FP64, one thread per candidate), then each warp runs its
-// candidates one after another, lane = sample stride 32, with the phase and
-// both sums in float-float (samples as FP32 from the same expressions as the
-// dictionary generator's).
-constexpr int kScoreCands = 64;
+// candidates one after another, lane = sample stride 32.  A lane's samples
+// n_k = lane + 32 k advance tau by D = 32 / fs, so the phase
+// (c tau + fc) tau steps by d1_k = D (c (2 tau_k + D) + fc), and d1 by
+// d2 = 2 c D^2: tau, the phase and d1 are carried by these recurrences in
+// float-float (phase and d1 mod 1), from exact starting values at k = 0.
+// The samples are FP32 from the same expressions as the dictionary
+// generator's; products are summed in FP32 over 4 samples, then into
+// float-float sums.
+constexpr int kScoreCands = 64;  // at most 32 per warp (one lane each)
+
+struct LemConst {
+    ChirpFF k;
+    ff D, d2;  // the lane stride in tau and the second difference of the phase (mod 1)
+};
 
 __global__ void __launch_bounds__(kLemThreads) k_lem_score(int cap, const double *__restrict__ cand,
                                                           const int *__restrict__ ncand, const float *__restrict__ R,
                                                           int Lp, int L, double inv_fs, double *__restrict__ score) {
-    __shared__ ChirpFF ks[kScoreCands];
+    __shared__ LemConst ks[kScoreCands];
     const int b = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i0 = blockIdx.x * kScoreCands;
@@ -101,63 +111,106 @@ __global__ void __launch_bounds__(kLemThreads) k_lem_score(int cap, const double
     if (n_here <= 0) return;
     if (threadIdx.x < n_here) {
         const double *th = cand + ((size_t)b * cap + i0 + threadIdx.x) * 4;
-        ks[threadIdx.x] = chirp_ff(th[0], inv_fs, th[1], th[3], exp(-th[2]));
+        const double D = 32.0 * inv_fs;
+        double d2 = 2.0 * th[3] * D * D;
+        d2 -= rint(d2);
+        ks[threadIdx.x] = {chirp_ff(th[0], inv_fs, th[1], th[3], exp(-th[2])), ff_from_double(D),
+                           ff_from_double(d2)};
     }
     __syncthreads();
     const float *r = R + (size_t)b * Lp;
-    for (int q = warp; q < n_here; q += kLemThreads / 32) {
-        const ChirpFF k = ks[q];
+    // lane i keeps the sums of the warp's i-th candidate; the FP64 finish
+    // then runs once for all of them (an FP64 instruction costs the same
+    // pipe time however few lanes are active)
+    constexpr int kWarps = kLemThreads / 32;
+    ff my_ru = {0.0f, 0.0f}, my_uu = {0.0f, 0.0f};
+    int i = 0;
+    for (int q = warp; q < n_here; q += kWarps, ++i) {
+        const LemConst kc = ks[q];
+        const ChirpFF &k = kc.k;
+        // k = 0: tau, the phase and its first difference, formed directly
+        ff tau;
+        ff ph = chirp_phase_pair(lane, k, &tau);
+        const ff two_tau_d = ff_add({2.0f * tau.hi, 2.0f * tau.lo}, kc.D);
+        ff d1 = ff_frac(ff_mul(ff_add(ff_mul(k.c, two_tau_d), k.fc), kc.D));
         ff ru = {0.0f, 0.0f}, uu = {0.0f, 0.0f};
-        for (int n = lane; n < L; n += 32) {
-            const float u = chirp_sample_ff(n, k);
-            ff_fma_acc(ru, __ldg(r + n), u);
-            ff_fma_acc(uu, u, u);
+        for (int n0 = lane; n0 < L; n0 += 128) {
+            float pr = 0.0f, pu = 0.0f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int n = n0 + 32 * e;
+                if (n < L) {
+                    const float x = chirp_x_ff(tau, k);
+                    const float u = expf(-0.5f * x * x) * cospif(2.0f * (ph.hi + ph.lo));
+                    pr = fmaf(__ldg(r + n), u, pr);
+                    pu = fmaf(u, u, pu);
+                    tau = ff_add_sloppy(tau, kc.D);
+                    ph = ff_frac(ff_add_sloppy(ph, d1));
+                    d1 = ff_frac(ff_add_sloppy(d1, kc.d2));
+                }
+            }
+            ru = ff_add_f(ru, pr);
+            uu = ff_add_f(uu, pu);
         }
         ru = ff_warp_sum(ru);
         uu = ff_warp_sum(uu);
-        if (lane == 0) {
-            const double e = ff_to_double(uu);
-            score[(size_t)b * cap + i0 + q] = (e > 0.0 && isfinite(e)) ? ff_to_double(ru) / sqrt(e) : 0.0;
+        if (lane == i) {
+            my_ru = ru;
+            my_uu = uu;
         }
+    }
+    if (lane < i) {
+        const double e = ff_to_double(my_uu);
+        score[(size_t)b * cap + i0 + warp + lane * kWarps] = (e > 0.0 && isfinite(e)) ? ff_to_double(my_ru) / sqrt(e) : 0.0;
     }
 }
 
 // 3. Top-k by |score| with duplicates skipped: one block per channel, k
-// rounds of a block-wide arg-max (largest |score|, then lowest index).
+// rounds of a block-wide arg-max (largest |score|, then lowest index).  The
+// compares run on the bit patterns (integer pipes; FP64 compares are slow
+// on this GPU): for finite non-negative doubles the patterns order as the
+// values, NaN scores are skipped, and two parameters are equal when their
+// patterns are, or both are zeros.
+__device__ __forceinline__ bool same_value(unsigned long long a, unsigned long long b) {
+    return a == b || ((a | b) << 1) == 0ull;
+}
+
 __global__ void __launch_bounds__(kLemThreads) k_lem_topk(int cap, int k, const double *__restrict__ cand,
                                                          const int *__restrict__ ncand,
                                                          const double *__restrict__ score, double *__restrict__ kept,
                                                          double *__restrict__ kept_score, int *__restrict__ nkept) {
-    __shared__ double kt[16][4];
-    __shared__ double bv_s[kLemThreads / 32];
+    constexpr unsigned long long kAbs = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
+    __shared__ unsigned long long kt[16][4];
+    __shared__ unsigned long long bv_s[kLemThreads / 32];
     __shared__ int bi_s[kLemThreads / 32];
     __shared__ int m_sh;
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = ncand[b];
-    const double *cb = cand + (size_t)b * cap * 4;
-    const double *sb = score + (size_t)b * cap;
+    const unsigned long long *cb = reinterpret_cast<const unsigned long long *>(cand) + (size_t)b * cap * 4;
+    const unsigned long long *sb = reinterpret_cast<const unsigned long long *>(score) + (size_t)b * cap;
     if (threadIdx.x == 0) m_sh = 0;
     __syncthreads();
     for (int round = 0; round < k; ++round) {
         const int m = m_sh;
-        double bv = -1.0;
+        unsigned long long bv = 0ull;
         int bi = -1;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long v = sb[i] & kAbs;
+            if (v > kInf || (bi >= 0 && v <= bv)) continue;  // NaN, or not above the best (the first index wins ties)
             bool dup = false;
             for (int q = 0; q < m && !dup; ++q)
-                dup = cb[4 * i] == kt[q][0] && cb[4 * i + 1] == kt[q][1] && cb[4 * i + 2] == kt[q][2] &&
-                      cb[4 * i + 3] == kt[q][3];
-            const double v = fabs(sb[i]);
-            if (!dup && v == v && v > bv) {  // strided ascending: the first index wins ties
+                dup = same_value(cb[4 * i], kt[q][0]) && same_value(cb[4 * i + 1], kt[q][1]) &&
+                      same_value(cb[4 * i + 2], kt[q][2]) && same_value(cb[4 * i + 3], kt[q][3]);
+            if (!dup) {
                 bv = v;
                 bi = i;
             }
         }
         for (int off = 16; off > 0; off >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+            const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, off);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+            if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
                 bv = ov;
                 bi = oi;
             }
@@ -168,17 +221,17 @@ __global__ void __launch_bounds__(kLemThreads) k_lem_topk(int cap, int k, const 
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double v = -1.0;
+            unsigned long long v = 0ull;
             int id = -1;
             for (int w = 0; w < kLemThreads / 32; ++w)
-                if (bv_s[w] > v || (bv_s[w] == v && bi_s[w] >= 0 && (id < 0 || bi_s[w] < id))) {
+                if (bi_s[w] >= 0 && (id < 0 || bv_s[w] > v || (bv_s[w] == v && bi_s[w] < id))) {
                     v = bv_s[w];
                     id = bi_s[w];
                 }
             if (id >= 0) {
                 for (int a = 0; a < 4; ++a) kt[m][a] = cb[4 * id + a];
-                kept_score[(size_t)b * k + m] = sb[id];
-                for (int a = 0; a < 4; ++a) kept[((size_t)b * k + m) * 4 + a] = cb[4 * id + a];
+                kept_score[(size_t)b * k + m] = score[(size_t)b * cap + id];
+                for (int a = 0; a < 4; ++a) kept[((size_t)b * k + m) * 4 + a] = cand[((size_t)b * cap + id) * 4 + a];
                 m_sh = m + 1;
             }
         }
