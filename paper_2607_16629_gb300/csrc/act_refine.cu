@@ -198,33 +198,24 @@ __device__ __forceinline__ void eval_warp_reduce(EvalAcc &a) {
     }
 }
 
-__device__ __forceinline__ EvalOut eval_finish(const EvalAcc &a) {
-    const double ru = ff_to_double(a.ru), uu = ff_to_double(a.uu);
-    EvalOut o;
-    if (!(uu > 0.0) || !isfinite(uu)) {
-        o.s = 0.0;
-        o.nu = 0.0;
-        for (int i = 0; i < 4; ++i) o.g[i] = 0.0;
-        return o;
-    }
-    o.nu = sqrt(uu);
-    const double inv_nu = 1.0 / o.nu;
-    o.s = ru * inv_nu;
-    const double s_uu = o.s * inv_nu * inv_nu;
-    for (int i = 0; i < 4; ++i) o.g[i] = (double)a.rd[i] * inv_nu - s_uu * (double)a.ud[i];
-    return o;
-}
+// Score and one gradient component of an evaluation, as the lanes of the
+// evaluating group's first warp hold them: s in every lane, component
+// lane & 3 of the gradient in gi.
+struct EvalLane {
+    double s, gi;
+};
 
 // Score and gradient by a group of G consecutive warps (samples strided by
 // the group, the warps' sums added in warp order); every group of the block
 // calls it at once (it holds block barriers), each on its own candidate th
 // (inactive groups take part without evaluating).  The result is valid in
-// the group's first thread.  red holds one EvalAcc per warp; ec one slot of
-// constants per group (formed once, by that thread: FP64 is slow on this
-// GPU).
+// lanes 0..3 of the group's first warp, which all add the warps' sums and
+// finish in FP64 together (an FP64 instruction costs the same pipe time
+// however few lanes are active).  red holds one EvalAcc per warp; ec one slot
+// of constants per group (formed once, by the group's first thread).
 template <int G>
-__device__ EvalOut eval_group(const double *th, bool active, const float *__restrict__ r, int L, double inv_fs,
-                              EvalAcc *red, EvalConst *ec) {
+__device__ EvalLane eval_group(const double *th, bool active, const float *__restrict__ r, int L, double inv_fs,
+                               EvalAcc *red, EvalConst *ec) {
     const int warp = threadIdx.x >> 5, g = warp / G, t = (int)threadIdx.x - g * G * 32;
     if (t == 0 && active) ec[g] = eval_const(th, inv_fs);
     __syncthreads();
@@ -236,8 +227,8 @@ __device__ EvalOut eval_group(const double *th, bool active, const float *__rest
     eval_warp_reduce(a);
     if ((threadIdx.x & 31) == 0) red[warp] = a;
     __syncthreads();
-    EvalOut o = {};
-    if (t == 0 && active) {
+    EvalLane o = {0.0, 0.0};
+    if (warp == g * G && active) {
         EvalAcc u = red[g * G];
         for (int w = 1; w < G; ++w) {
             const EvalAcc &v = red[g * G + w];
@@ -248,7 +239,16 @@ __device__ EvalOut eval_group(const double *th, bool active, const float *__rest
                 u.ud[i] += v.ud[i];
             }
         }
-        o = eval_finish(u);
+        const double ru = ff_to_double(u.ru), uu = ff_to_double(u.uu);
+        if (uu > 0.0 && isfinite(uu)) {
+            const int i = threadIdx.x & 3;
+            const float rdi = i == 0 ? u.rd[0] : (i == 1 ? u.rd[1] : (i == 2 ? u.rd[2] : u.rd[3]));
+            const float udi = i == 0 ? u.ud[0] : (i == 1 ? u.ud[1] : (i == 2 ? u.ud[2] : u.ud[3]));
+            const double inv_nu = 1.0 / sqrt(uu);
+            o.s = ru * inv_nu;
+            const double s_uu = o.s * inv_nu * inv_nu;
+            o.gi = (double)rdi * inv_nu - s_uu * (double)udi;
+        }
     }
     return o;
 }
@@ -301,10 +301,11 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
         cth[q][i] = v;
         if (i == 0) ca[q] = a;
     };
-    auto record = [&](const EvalOut &o, int q) {  // f and scaled gradient of slot q (one thread)
+    // f and scaled gradient component i of slot q (lane i < 4 of the group's first warp)
+    auto record = [&](const EvalLane &o, int q, int i) {
         const double sg = o.s < 0.0 ? -1.0 : 1.0;
-        cf[q] = -fabs(o.s);
-        for (int i = 0; i < 4; ++i) cg[q][i] = -sg * o.g[i] * box.w[i];
+        cg[q][i] = -sg * o.gi * box.w[i];
+        if (i == 0) cf[q] = -fabs(o.s);
     };
     auto armijo = [&](int q) { return cf[q] <= f + 1e-4 * ca[q] * gp; };
 
@@ -323,11 +324,11 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
     if (threadIdx.x < 16) H[threadIdx.x] = (threadIdx.x % 5 == 0) ? 1.0 : 0.0;
     __syncthreads();
     {
-        const EvalOut o = eval_group<kWarps>(th_cur, true, r, L, inv_fs, red, ec);
-        if (threadIdx.x == 0) {
+        const EvalLane o = eval_group<kWarps>(th_cur, true, r, L, inv_fs, red, ec);
+        if (threadIdx.x < 4) {
             const double sg = o.s < 0.0 ? -1.0 : 1.0;
-            f = -fabs(o.s);
-            for (int i = 0; i < 4; ++i) gz[i] = -sg * o.g[i] * box.w[i];
+            gz[threadIdx.x] = -sg * o.gi * box.w[threadIdx.x];
+            if (threadIdx.x == 0) f = -fabs(o.s);
         }
     }
     __syncthreads();
@@ -364,11 +365,9 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
                 if (threadIdx.x < 4) trial(j, 0, threadIdx.x);
                 __syncthreads();
             }
-            const EvalOut o = eval_group<kWarps>(cth[0], true, r, L, inv_fs, red, ec);
-            if (threadIdx.x == 0) {
-                record(o, 0);
-                if (armijo(0)) state = 0;
-            }
+            const EvalLane o = eval_group<kWarps>(cth[0], true, r, L, inv_fs, red, ec);
+            if (threadIdx.x < 4) record(o, 0, threadIdx.x);
+            if (threadIdx.x == 0 && armijo(0)) state = 0;
             __syncthreads();
         }
         // shorter steps, kSlots at a time (one group of warps each)
@@ -377,8 +376,8 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             const bool active = j0 + g < kLineSearch;
             if (active && t < 4) trial(j0 + g, g, t);
             __syncwarp();  // the group's first thread reads the trial point
-            const EvalOut o = eval_group<kGroupWarps>(cth[g], active, r, L, inv_fs, red, ec);
-            if (active && t == 0) record(o, g);
+            const EvalLane o = eval_group<kGroupWarps>(cth[g], active, r, L, inv_fs, red, ec);
+            if (active && t < 4) record(o, g, t);
             __syncthreads();
             if (threadIdx.x == 0) {
                 for (int q = 0; q < kSlots && j0 + q < kLineSearch; ++q)
