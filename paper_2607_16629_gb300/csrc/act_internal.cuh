@@ -175,7 +175,7 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 // early_launch the kernel is a programmatic dependent of the previous kernel
 // in the stream (its prologue overlaps that kernel).  With count_dev, only
 // the channels chlist[0 .. min(*count_dev, B)) are searched (the grid is
-// sized for B; never an early launch).
+// sized for B; the count is read after the wait on the previous kernel).
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
                                 float *scores, int *status, bool early_launch, cudaStream_t st,
                                 const int *chlist = nullptr, const int *count_dev = nullptr);

@@ -64,7 +64,7 @@ struct ShiftArgs {
     float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
     int *status;
     // non-null: search only the channels chlist[0 .. *count_dev) (the count
-    // is read when the kernel starts; such a launch is never an early one)
+    // is read after the wait on the previous kernel)
     const int *chlist;
     const int *count_dev;
 };
@@ -187,7 +187,11 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
     const int stage_floats = (A.Kc + J + 1) * 32;
     float *rpoly = sm + NS * stage_floats;     // [Sa][P] + 4 slack floats, after the stages
     const int units_per_b = A.G * A.TB;
-    const int n_b = A.count_dev ? min(*A.count_dev, A.B) : A.B;
+    int n_b = A.B;
+    if (A.count_dev) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        n_b = min(*A.count_dev, A.B);
+    }
     const int n_units = n_b * units_per_b;
     if ((int)blockIdx.x >= n_units) return;
     // chunk c of this CTA: phase c % Sa of its unit c / Sa
@@ -526,7 +530,6 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
                                 float *scores, int *status, bool early_launch, cudaStream_t st, const int *chlist,
                                 const int *count_dev) {
     if (sp.J == 0 || !sp.tpl || (count_dev && !chlist)) return cudaErrorInvalidValue;
-    if (count_dev) early_launch = false;  // the count must be written before the kernel reads it
     ShiftArgs A;
     A.tpl = sp.tpl;
     A.scale = sp.scale;

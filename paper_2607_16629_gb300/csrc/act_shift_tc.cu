@@ -428,6 +428,9 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     float *buf0 = rres + Lp;
     const uint32_t bytes = (uint32_t)P * 128u;
     const int n_tasks = counters[1];  // at most kMaxItems per channel
+    // the fallback search behind this kernel may launch now: it reads
+    // nothing of ours before its wait for our completion
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nw = (int)(blockDim.x >> 5);
     if (lane == 0) {
         mbar_init(&bar[warp][0], 1);
@@ -705,8 +708,10 @@ cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // channels with more than kMaxItems flagged items: the FP32 template
-    // search over the queue (an empty queue leaves every CTA idle)
-    return launch_shift_search(sp, R, Lp, L, B, keys, nullptr, status, false, st, fb_list, &counters[0]);
+    // search over the queue, launched early (its CTAs become resident while
+    // the rescore runs and read the queue after it; an empty queue leaves
+    // them idle)
+    return launch_shift_search(sp, R, Lp, L, B, keys, nullptr, status, true, st, fb_list, &counters[0]);
 }
 
 
