@@ -59,6 +59,7 @@ struct Smem {
     uint64_t bar_acc_empty[2];
     uint32_t tmem_base;
     int abort;
+    unsigned int chan_max[2][kBM];  // per item parity: the tile's channel maxima (float bits)
 };
 
 // Named barrier 1 over the 128 epilogue threads, returning whether any of
@@ -78,7 +79,9 @@ __device__ __forceinline__ int epilogue_bar_or(int pred) {
 
 // Row tiles of the GEMM: tile mt = g * n_cb + cb holds Bg = 128 / Jt
 // channels (cb * Bg ..) times Jt neighbouring time centres (g * Jt ..); local
-// row lr = (b - cb Bg) Jt + (j - g Jt).  Rows of one tile see the window
+// row lr = (j - g Jt) Bg + (b - cb Bg), channels fastest, so with Bg >= 32
+// the 32 rows an epilogue warp holds share one time centre (its scale loads
+// are broadcasts).  Rows of one tile see the window
 // only over lags [kc_lo, kc_hi] (in 64-lag chunks): L + (Jt - 1) S lags
 // instead of Kt, the chunks outside hold only zero products and are skipped.
 struct RowTiling {
@@ -88,8 +91,8 @@ struct RowTiling {
 
 __host__ __device__ inline void tile_row(const RowTiling &t, int mt, int lr, int &b, int &j) {
     const int g = mt / t.n_cb, cb = mt - g * t.n_cb;
-    b = cb * t.Bg + lr / t.Jt;
-    j = g * t.Jt + lr % t.Jt;
+    b = cb * t.Bg + lr % t.Bg;
+    j = g * t.Jt + lr / t.Bg;
 }
 
 __host__ __device__ inline void tile_chunks(const RowTiling &t, int mt, int &kc_lo, int &kc_hi) {
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         sm.abort = 0;
         fence_mbar_init();
     }
+    if (threadIdx.x < 2 * kBM) sm.chan_max[threadIdx.x / kBM][threadIdx.x % kBM] = 0u;
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
                      "r"(kTmemCols)
@@ -290,12 +294,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             int b, j;
             tile_row(tl, mt, lr, b, j);
             const bool valid = b < tl.B && j < Ntc;
-            const float4 *sc4 = reinterpret_cast<const float4 *>(sc_sm + (valid ? lr % tl.Jt : 0) * kScaleLd);
+            const float4 *sc4 = reinterpret_cast<const float4 *>(sc_sm + (valid ? lr / tl.Bg : 0) * kScaleLd);
             // per 32-template block and per tile: the largest scaled |score|
             float *bm = blk_max + ((size_t)(valid ? b : 0) * Ntc + (valid ? j : 0)) * (T_pad / 32) +
                         (size_t)nt * (BN / 32);
-            float mx = 0.0f;
-#pragma unroll 1
+            float mx = 0.0f, bmv[BN / 32];
+#pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c * 32, v);
@@ -308,27 +312,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                     m0 = fmaxf(m0, fabsf(v[4 * e + 2] * s.z));
                     m1 = fmaxf(m1, fabsf(v[4 * e + 3] * s.w));
                 }
-                const float mc = fmaxf(m0, m1);
-                if (valid) bm[c] = mc;
-                mx = fmaxf(mx, mc);
+                bmv[c] = fmaxf(m0, m1);
+                mx = fmaxf(mx, bmv[c]);
             }
             tc_fence_before();
             mbar_arrive(&sm.bar_acc_empty[acc]);
-            if (valid) tile_max[((size_t)b * Ntc + j) * n_tiles + nt] = mx;
-            // channel maximum: non-negative floats order like their bits; the
-            // rows of one channel are Jt consecutive lanes (or the whole warp)
-            unsigned bits = valid ? __float_as_uint(mx) : 0u;
-            if (tl.Jt >= 32) {
-                bits = __reduce_max_sync(0xffffffffu, bits);
-                if (lane == 0 && b < tl.B) atomicMax(chmax + b, bits);
-            } else {
-                for (int off = tl.Jt >> 1; off > 0; off >>= 1) {
-                    const unsigned o = __shfl_xor_sync(0xffffffffu, bits, off);
-                    bits = o > bits ? o : bits;
-                }
-                if (lr % tl.Jt == 0 && b < tl.B) atomicMax(chmax + b, bits);
+            if (valid) {  // the row's BN / 32 block maxima are contiguous: 16-byte stores
+                float4 *bm4 = reinterpret_cast<float4 *>(bm);
+#pragma unroll
+                for (int u = 0; u < BN / 128; ++u)
+                    bm4[u] = make_float4(bmv[4 * u], bmv[4 * u + 1], bmv[4 * u + 2], bmv[4 * u + 3]);
+                tile_max[((size_t)b * Ntc + j) * n_tiles + nt] = mx;
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");  // the scale rows are reloaded for the next item
+            // channel maximum: non-negative floats order like their bits.  The
+            // rows of one channel are the lanes lr % Bg equal: fold them within
+            // the warp, then across the warps in shared memory; one global
+            // atomic per channel and tile
+            unsigned bits = valid ? __float_as_uint(mx) : 0u;
+            for (int off = 16; off >= tl.Bg; off >>= 1) {
+                const unsigned o = __shfl_xor_sync(0xffffffffu, bits, off);
+                bits = o > bits ? o : bits;
+            }
+            unsigned int *cm = sm.chan_max[local & 1u];
+            if (tl.Bg >= 32 || lane < tl.Bg) atomicMax(cm + lr % tl.Bg, bits);
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // also: the scale rows are reloaded for the next item
+            if (et < tl.Bg) {
+                const int bc = (mt % tl.n_cb) * tl.Bg + et;
+                if (bc < tl.B) atomicMax(chmax + bc, cm[et]);
+                cm[et] = 0u;  // rewritten two items later, after another barrier
+            }
         }
     }
 
@@ -508,7 +520,9 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     }
 }
 
-constexpr int kStaticReserve = 512;
+// static shared memory of the kernels here (the GEMM's Smem is the largest)
+constexpr int kStaticReserve = 2048;
+static_assert(sizeof(Smem) + 256 <= kStaticReserve, "static shared memory above its reserve");
 constexpr int kSmemBudget = 232448 - kStaticReserve - 1024;
 
 }  // namespace
@@ -594,7 +608,7 @@ void shift_tc_free(ShiftTc *s) {
 static RowTiling make_tiling(const ShiftPlan &sp, int B) {
     RowTiling t;
     int bg = 1;
-    while (bg < B && bg < 16) bg <<= 1;
+    while (bg < B && bg < 32) bg <<= 1;
     int ntc2 = 1;
     while (ntc2 < sp.Ntc) ntc2 <<= 1;
     t.Jt = kBM / bg < ntc2 ? kBM / bg : ntc2;
@@ -669,8 +683,11 @@ cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R
         return 1024 + (size_t)stg * stage_bytes + sc;
     };
     if (!make_map(&mapA, s->X, (uint64_t)sp.Kt, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
-    // 256-template tiles unless they leave SMs idle
-    const int bn = (int64_t)m_tiles * (sp.T_pad / 256) >= s->sm_count ? 256 : 128;
+    // 256-template tiles unless they leave SMs idle or leave room for fewer
+    // than two stages beside the tile's scale rows
+    int st256 = 0;
+    smem_for(256, ShiftTile<256>::kStageBytes, &st256);
+    const int bn = (int64_t)m_tiles * (sp.T_pad / 256) >= s->sm_count && st256 >= 2 ? 256 : 128;
     const int i = bn == 256 ? 1 : 0;
     s->bn = bn;
     s->n_tiles = sp.T_pad / bn;

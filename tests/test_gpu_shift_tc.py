@@ -127,6 +127,18 @@ def test_fallback_queue_holds_only_the_overflowed_channels():
     assert np.all(b[0][[1, 4]] == 0)
 
 
+def test_one_channel_many_time_centres():
+    """One channel over 512 time centres and 18,432 templates (rows tile as
+    1 channel x 128 time centres): the tile width falls back to 128 templates
+    when 256 would leave room for fewer than two stages beside the scale rows."""
+    grid = synth.Grid(2048, 500.0, synth.Axis(0.0, 4.0, 512), synth.Axis.linspace(20.0, 200.0, 96),
+                      synth.Axis.linspace(-4.0, -1.5, 8), synth.Axis.linspace(-100.0, 100.0, 24))
+    sig = synth.random_signals(97, 1, grid.n_samples)
+    a, b, (resolved, items, fallbacks) = both(grid, sig, 3)
+    assert_same(a, b)
+    assert resolved + fallbacks == 3
+
+
 def test_refinement_after_tensor_core_search():
     grid = eeg_small()
     sig = np.stack([synth.eeg_like_signal(2, 90 + b)[0] for b in range(2)]).astype(np.float32)
