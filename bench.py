@@ -631,7 +631,7 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
                          "avg_search_ms_per_order": avg,
                          "search_frac_of_hbm_roofline": bytes_per / (avg / 1e3) / 1e9 / peaks["hbm_gbs"]},
             "autotuned": {"tile_atoms": tile_atoms, "stages": stages_used, "search_ms_per_order": tune_ms},
-            "orders_resolved_by_tile_rescan": c1 - c0, "tiles_rescanned": s1 - s0,
+            "orders_resolved_by_block_rescan": c1 - c0, "blocks_rescanned": s1 - s0,
             "orders_full_fp32_fallback": f1 - f0,
             "fp32_plain_per_channel": {"value": B * K * P / (fp32_ms / 1e3), "ms": fp32_ms},
             "speedup_vs_fp32_plain": (B * K * P * steps / (ms / 1e3)) / (B * K * P / (fp32_ms / 1e3)),

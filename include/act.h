@@ -327,11 +327,14 @@ ACT_API act_status act_set_profiling(act_grid *grid, int32_t enable);
 ACT_API act_status act_profile_read(act_grid *grid, double *search_ms, double *core_ms,
                                     int32_t *search_launches, int32_t *kernels);
 
-/* BF16 search statistics since the grid was created: (channel, order)
- * selections resolved by the FP32 rescan of the flagged tiles, the total
- * number of 256-atom tiles rescanned for them, and selections that took the
- * FP32 full search instead (more than 64 flagged tiles). */
-ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *resolved, int64_t *tiles_rescanned,
+/* Tensor-core search statistics since the grid was created (the dense BF16
+ * search and the tensor-core template search): (channel, order) selections
+ * resolved by the FP32 rescore of the flagged items, the total number of
+ * items rescored for them (32-atom blocks of the dense search; (time centre,
+ * 32-template block) items of the template search), and selections that took
+ * the FP32 full search instead (more than 512 flagged blocks, or more than
+ * 1,024 flagged items). */
+ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *resolved, int64_t *items_rescanned,
                                   int64_t *fallbacks);
 
 /* Uneven batches (channels of different window lengths).

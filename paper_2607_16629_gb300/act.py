@@ -254,7 +254,7 @@ def act_profile_read(grid: int):
 
 
 def act_bf16_stats(grid: int):
-    """(resolved, tiles_rescanned, fallbacks) counts of the BF16 search."""
+    """(resolved, items_rescanned, fallbacks) counts of the tensor-core searches."""
     a = ctypes.c_int64()
     r = ctypes.c_int64()
     b = ctypes.c_int64()

@@ -1007,14 +1007,14 @@ act_status act_profile_read(act_grid *g, double *search_ms, double *core_ms, int
     return ACT_OK;
 }
 
-act_status act_bf16_stats(act_grid *g, int64_t *resolved, int64_t *tiles_rescanned, int64_t *fallbacks) {
+act_status act_bf16_stats(act_grid *g, int64_t *resolved, int64_t *items_rescanned, int64_t *fallbacks) {
     if (!g) return ACT_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     long long h[3] = {0, 0, 0};
     ACT_CK(cudaMemcpy(h, g->stats, sizeof(h), cudaMemcpyDeviceToHost));
     if (resolved) *resolved = h[0];
     if (fallbacks) *fallbacks = h[1];
-    if (tiles_rescanned) *tiles_rescanned = h[2];
+    if (items_rescanned) *items_rescanned = h[2];
     return ACT_OK;
 }
 

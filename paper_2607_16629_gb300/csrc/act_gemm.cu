@@ -30,6 +30,7 @@
 #include <new>
 
 #include "act_device.cuh"
+#include "act_ff.cuh"
 #include "act_internal.cuh"
 #include "act_tc.cuh"
 
@@ -42,7 +43,7 @@ using namespace tc;
 constexpr int kBM = 128;           // channels per tile (MMA M)
 constexpr int kBlockRows = 256;    // atoms per block of the tile-major BF16 layout
 constexpr int kUmmaK = 16;         // K per tcgen05.mma (16-bit inputs)
-constexpr int kMaxRescan = 64;     // flagged tiles per channel before the FP32 full search
+constexpr int kMaxRescan = 512;    // flagged 32-atom blocks per channel before the FP32 full search
 constexpr int kGemmThreads = 256;
 constexpr int kAChunkBytes = kBM * kBK * 2;  // 16 KB
 constexpr int kMaxDynSmem = 232448;
@@ -79,7 +80,8 @@ struct GemmSmem {
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_tilemax(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t K, int nkc,
-                   int stages, int a_stream, int B, float *__restrict__ tile_max, int *status) {
+                   int stages, int a_stream, int B, float *__restrict__ tile_max, float *__restrict__ blk_max,
+                   int *status) {
     using Cfg = TileCfg<BN>;
     extern __shared__ uint8_t dyn_raw[];
     __shared__ GemmSmem sm;
@@ -187,21 +189,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc_fence_after();
-            // atoms past K in the last tile are zero rows: they score 0
-            float m0 = 0.0f, m1 = 0.0f;
-#pragma unroll 1
+            // atoms past K in the last tile are zero rows: they score 0.
+            // Per 32-atom block and per tile: the largest |score|
+            float mx = 0.0f, bmv[BN / 32];
+#pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c * 32, v);
+                float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll
                 for (int j = 0; j < 32; j += 2) {
                     m0 = fmaxf(m0, fabsf(v[j]));
                     m1 = fmaxf(m1, fabsf(v[j + 1]));
                 }
+                bmv[c] = fmaxf(m0, m1);
+                mx = fmaxf(mx, bmv[c]);
             }
             tc_fence_before();
             mbar_arrive(&sm.bar_acc_empty[acc]);
-            if (ch < B) tile_max[(size_t)ch * ntiles + tile] = fmaxf(m0, m1);
+            if (ch < B) {
+                tile_max[(size_t)ch * ntiles + tile] = mx;
+                float4 *bm4 = reinterpret_cast<float4 *>(blk_max + ((size_t)ch * ntiles + tile) * (BN / 32));
+#pragma unroll
+                for (int u = 0; u < BN / 128; ++u)
+                    bm4[u] = make_float4(bmv[4 * u], bmv[4 * u + 1], bmv[4 * u + 2], bmv[4 * u + 3]);
+            }
         }
     }
 
@@ -229,17 +241,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // and |f_j - s_j| <= eps_r.  If j* maximises |f| and jb maximises |h|:
 //   |h_j*| >= |f_j*| - eps_r - delta >= |f_jb| - eps_r - delta
 //          >= |h_jb| - 2 delta - 2 eps_r,
-// so j* lies in a tile whose largest |h| is >= bmax - 2 delta - 2 eps_r.
-// Those tiles are queued for the FP32 rescan (keys[b] cleared); a channel
-// with more than kMaxRescan of them is queued for the FP32 full search.
-__global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__restrict__ tile_max, int Lp, int L,
+// so j* lies in a 32-atom block whose largest |h| is >= bmax - 2 delta -
+// 2 eps_r.  The GEMM keeps both the per-tile and the per-block maxima; tiles
+// at or above the threshold are narrowed to their blocks, which are queued
+// for the FP32 rescan (keys[b] cleared); a channel with more than kMaxRescan
+// of them is queued for the FP32 full search.  |r| and |dr| are float-float
+// sums (inflated by 1e-6 for their rounding), the bound is formed in FP64
+// once, and the threshold is rounded down to FP32 before the comparisons
+// (the flagged set can only grow).
+__global__ void __launch_bounds__(256) k_select(int64_t ntiles, int bpt, const float *__restrict__ tile_max,
+                                                const float *__restrict__ blk_max, int Lp, int L,
                                                 const float *__restrict__ R,
                                                 const unsigned int *__restrict__ eps_bits,
                                                 unsigned long long *__restrict__ keys, int *__restrict__ fb_list,
                                                 int *__restrict__ counters, int *__restrict__ pairs,
                                                 long long *__restrict__ stats) {
-    __shared__ double sh_d[32];
-    __shared__ float sh_f[32];
+    __shared__ ff sh_e[8], sh_de[8];
+    __shared__ float sh_f[8];
+    __shared__ float thr_sh;
     __shared__ int n_sh;
     __shared__ int base_sh;
     __shared__ int list[kMaxRescan];
@@ -248,36 +267,53 @@ __global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__r
     const int nwarps = (int)(blockDim.x >> 5);
     const float *r = R + (size_t)b * Lp;
     const float *tm = tile_max + (size_t)b * ntiles;
+    const float *bmx = blk_max + (size_t)b * ntiles * bpt;
 
-    double e = 0.0, de = 0.0;
+    ff e = {0.0f, 0.0f}, de = {0.0f, 0.0f};
     for (int n = threadIdx.x; n < L; n += blockDim.x) {
         const float x = r[n];
         const float d = __bfloat162float(__float2bfloat16_rn(x)) - x;
-        e = fma((double)x, (double)x, e);
-        de = fma((double)d, (double)d, de);
+        ff_fma_acc(e, x, x);
+        ff_fma_acc(de, d, d);
     }
-    const double rn = sqrt(block_sum(e, sh_d));
-    const double drn = sqrt(block_sum(de, sh_d));
-    const double eps_g = (double)__uint_as_float(*eps_bits);
-    const double rr = rn + drn;
-    const double ulp = 1.1920928955078125e-07;  // 2^-23
-    const double delta = eps_g * rr + (1.0 + 1e-5) * drn + (double)L * ulp * (1.0 + eps_g) * rr;
-    const double eps_r = (double)L * ulp * rn;
-
+    e = ff_warp_sum(e);
+    de = ff_warp_sum(de);
     float m = 0.0f;
     for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) m = fmaxf(m, tm[t]);
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (lane == 0) sh_f[warp] = m;
+    if (lane == 0) {
+        sh_e[warp] = e;
+        sh_de[warp] = de;
+        sh_f[warp] = m;
+    }
     if (threadIdx.x == 0) n_sh = 0;
     __syncthreads();
-    float bmax = sh_f[0];
-    for (int w = 1; w < nwarps; ++w) bmax = fmaxf(bmax, sh_f[w]);
-    const double thr = (double)bmax - 2.0 * delta - 2.0 * eps_r;
-
+    if (threadIdx.x == 0) {
+        ff te = sh_e[0], tde = sh_de[0];
+        float bmax = sh_f[0];
+        for (int w = 1; w < nwarps; ++w) {
+            te = ff_add(te, sh_e[w]);
+            tde = ff_add(tde, sh_de[w]);
+            bmax = fmaxf(bmax, sh_f[w]);
+        }
+        const double rn = sqrt(ff_to_double(te)) * (1.0 + 1e-6);
+        const double drn = sqrt(ff_to_double(tde)) * (1.0 + 1e-6);
+        const double eps_g = (double)__uint_as_float(*eps_bits);
+        const double rr = rn + drn;
+        const double ulp = 1.1920928955078125e-07;  // 2^-23
+        const double delta = eps_g * rr + (1.0 + 1e-5) * drn + (double)L * ulp * (1.0 + eps_g) * rr;
+        const double eps_r = (double)L * ulp * rn;
+        thr_sh = __double2float_rd((double)bmax - 2.0 * delta - 2.0 * eps_r);
+    }
+    __syncthreads();
+    const float thr = thr_sh;
     for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        if ((double)tm[t] >= thr) {
-            const int pos = atomicAdd(&n_sh, 1);
-            if (pos < kMaxRescan) list[pos] = (int)t;
+        if (tm[t] >= thr) {
+            for (int k = 0; k < bpt; ++k) {
+                if (bmx[t * bpt + k] < thr) continue;
+                const int pos = atomicAdd(&n_sh, 1);
+                if (pos < kMaxRescan) list[pos] = (int)(t * bpt + k);
+            }
         }
     }
     __syncthreads();
@@ -303,7 +339,7 @@ __global__ void __launch_bounds__(256) k_select(int64_t ntiles, const float *__r
     }
 }
 
-// FP32 rescan of the flagged (channel, tile) pairs: every atom of the tile
+// FP32 rescan of the flagged (channel, block) pairs: every atom of the block
 // (tile_atoms of them) is scored exactly as the GEMV scores it and folded
 // into keys[b] with the packed atomicMax (largest |score|, then lowest
 // index).  One block of 8 warps per pair.
@@ -388,6 +424,7 @@ struct Bf16Search {
     int64_t ntiles = 0;
     size_t smem = 0;
     float *tile_max = nullptr;         // [kBM][ntiles at BN = 128]
+    float *blk_max = nullptr;          // [kBM][K / 32 rounded up to whole tiles]
     int *pairs = nullptr;              // [kBM * kMaxRescan][2]
     unsigned int *eps_bits = nullptr;  // owned by the caller (dictionary build)
 };
@@ -442,6 +479,7 @@ cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int6
     }
     cudaError_t e = bf16_search_configure(s, 256, 0);
     if (e == cudaSuccess) e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)kBM * ((K + 127) / 128));
+    if (e == cudaSuccess) e = cudaMalloc(&s->blk_max, sizeof(float) * (size_t)kBM * ((K + 255) / 256) * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->pairs, sizeof(int) * 2 * kBM * kMaxRescan);
     if (e != cudaSuccess) {
         bf16_search_free(s);
@@ -454,6 +492,7 @@ cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int6
 void bf16_search_free(Bf16Search *s) {
     if (!s) return;
     if (s->tile_max) cudaFree(s->tile_max);
+    if (s->blk_max) cudaFree(s->blk_max);
     if (s->pairs) cudaFree(s->pairs);
     delete s;
 }
@@ -464,10 +503,10 @@ cudaError_t launch_bf16_gemm(Bf16Search *s, int B, const __nv_bfloat16 *R16, int
     if (!make_map(&mapA, R16, (uint64_t)s->Lb, (uint64_t)kBM, kBM)) return cudaErrorInvalidValue;
     if (s->bn == 256)
         k_gemm_tilemax<256><<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB[1], s->K, s->nkc, s->stages,
-                                                                    s->a_stream, B, s->tile_max, status);
+                                                                    s->a_stream, B, s->tile_max, s->blk_max, status);
     else
         k_gemm_tilemax<128><<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB[0], s->K, s->nkc, s->stages,
-                                                                    s->a_stream, B, s->tile_max, status);
+                                                                    s->a_stream, B, s->tile_max, s->blk_max, status);
     return cudaGetLastError();
 }
 
@@ -475,14 +514,14 @@ cudaError_t launch_bf16_resolve(Bf16Search *s, int B, const float *D32, int Lp, 
                                 unsigned long long *keys, int *fb_list, int *fb_count, long long *stats, int *status,
                                 int gemv_grid, cudaStream_t st) {
     if (!s || B < 1 || B > kBM) return cudaErrorInvalidValue;
-    k_select<<<B, 256, 0, st>>>(s->ntiles, s->tile_max, Lp, L, R, s->eps_bits, keys, fb_list, fb_count, s->pairs,
-                                stats);
+    k_select<<<B, 256, 0, st>>>(s->ntiles, s->bn / 32, s->tile_max, s->blk_max, Lp, L, R, s->eps_bits, keys, fb_list,
+                                fb_count, s->pairs, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_rescan<<<2 * s->sm_count, 256, 0, st>>>(D32, s->K, Lp, s->bn, R, s->pairs, fb_count, keys);
+    k_rescan<<<2 * s->sm_count, 256, 0, st>>>(D32, s->K, Lp, 32, R, s->pairs, fb_count, keys);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // FP32 full search for the channels with too many flagged tiles
+    // FP32 full search for the channels with too many flagged blocks
     return launch_gemv_argmax(D32, s->K, Lp, R, B, fb_list, fb_count, keys, status, gemv_grid, st);
 }
 

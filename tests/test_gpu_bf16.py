@@ -1,6 +1,6 @@
 """GPU parity of the BF16 tensor-core search (tcgen05 GEMM reduced to tile
-maxima, error-bounded tile selection, FP32 rescan of the flagged tiles, FP32
-full search as the last resort) through the C ABI.
+and 32-atom block maxima, error-bounded selection of blocks, FP32 rescan of
+the flagged blocks, FP32 full search as the last resort) through the C ABI.
 
 The error bound makes the BF16 search return exactly the FP32 search's
 selection, so its outputs must equal the FP32 path's bit for bit, and the
@@ -83,7 +83,7 @@ def test_bf16_lockstep_small(name, grid, B, P):
     assert np.array_equal(idx, i_full) and np.array_equal(coef, c_full)
     assert np.array_equal(rs[-1], r_full)
     assert (c1 - c0) + (f1 - f0) == 2 * B * P
-    assert s1 - s0 >= c1 - c0  # at least one tile per resolved selection
+    assert s1 - s0 >= c1 - c0  # at least one block per resolved selection
     lockstep_all(D, rs, idx, coef)
 
 
@@ -103,16 +103,16 @@ def test_bf16_matches_fp32_search_eeg():
     for x, y in zip((ib, cb, rb, eb), (i32, c32, r32, e32)):
         assert np.array_equal(x, y)
     lockstep_all(D, rs, idx, coef)
-    print(f"resolved {cert} tiles {rescan} fallback {fb}")
+    print(f"resolved {cert} blocks {rescan} fallback {fb}")
 
 
 @pytest.mark.parametrize("grid,full_search", [
-    (synth.grid_c1(), False),                                           # 64 tiles: all rescanned
-    (synth.scaled_grid(synth.grid_eeg(), tc_count=32, fc_count=16), True),  # 512 tiles: full search
+    (synth.grid_c1(), False),                                           # 512 blocks: all rescanned
+    (synth.scaled_grid(synth.grid_eeg(), tc_count=32, fc_count=16), True),  # 4,096 blocks: full search
 ])
 def test_bf16_zero_channel(grid, full_search):
-    """An all-zero channel flags every tile (all scores tie at 0): with at
-    most 64 tiles they are all rescanned, beyond that the channel takes the
+    """An all-zero channel flags every block (all scores tie at 0): with at
+    most 512 blocks they are all rescanned, beyond that the channel takes the
     FP32 full search.  Either way it selects index 0 with coefficient 0 and
     the other channels are unaffected."""
     sig = synth.random_signals(81, 3, grid.n_samples)
@@ -172,7 +172,7 @@ def test_bf16_full_eeg_grid_64_channels():
     e0 = eb[:, 0]
     for k in range(P + 1):
         assert np.all(np.abs(e0 - (np.sum(cb[:, :k].astype(np.float64) ** 2, axis=1) + eb[:, k])) <= 1e-5 * e0)
-    print(f"resolved {cert} tiles {rescan} fallback {fb}")
+    print(f"resolved {cert} blocks {rescan} fallback {fb}")
 
 
 @pytest.mark.parametrize("L,fs", [(600, 500.0), (1024, 1000.0), (2048, 500.0)])
