@@ -323,10 +323,12 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         } else if (mode == ACT_SEARCH_SHIFT_BF16) {
-            ACT_CK(launch_shift_tc_gemm(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, g->stats, g->status, st));
+            // programmatic dependents between kernel nodes only (not next to profiling events)
+            ACT_CK(launch_shift_tc_gemm(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, g->stats, g->status, st,
+                                        !profiling));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             ACT_CK(launch_shift_tc_resolve(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, w.keys, w.fb_list, w.fb_count,
-                                           g->stats, g->status, st));
+                                           g->stats, g->status, st, !profiling));
             kernels += 5;
         } else if (bf16) {
             ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
@@ -360,7 +362,7 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
         } else if (mode == ACT_SEARCH_SHIFT || mode == ACT_SEARCH_SHIFT_BF16) {
             // no stored rows: the selected atom is read back from its template
             ACT_CK(launch_shift_update(g->shift, g->ax, g->Lp, w.R, B, w.keys, k, P, w.atoms, w.coefs, w.energy,
-                                       mode == ACT_SEARCH_SHIFT_BF16 ? w.fb_count : nullptr, st));
+                                       mode == ACT_SEARCH_SHIFT_BF16 ? w.fb_count : nullptr, st, !profiling));
             ++kernels;
         } else {
             ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,

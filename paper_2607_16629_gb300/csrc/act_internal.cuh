@@ -11,6 +11,27 @@
 
 namespace act {
 
+// Launch on st; with pdl, as a programmatic dependent of the previous kernel
+// in the stream (it may start while that kernel runs, and must execute
+// griddepcontrol.wait in every CTA before it touches what that kernel
+// writes and before it exits).  Between a kernel and an event node (or at a
+// stream's first kernel) pdl has to be false.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Device-side status flags (one int per grid, OR-ed by kernels).
 enum : int {
     kFlagNonFinite = 1,
@@ -185,7 +206,7 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
 // counters (may be null): the tensor-core search's per-order queue lengths, reset.
 cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
                                 unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
-                                int *counters, cudaStream_t st);
+                                int *counters, cudaStream_t st, bool pdl = false);
 
 // ---- tensor-core template search (act_shift_tc.cu) -------------------------
 struct ShiftTc;
@@ -201,11 +222,14 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B);
 // full by the FP32 template search (launch_shift_search over the queue).
 // Leaves the packed key of every channel in keys[]; counters[0..1] must be
 // zero on entry.
+// pdl: the first kernel of each call follows a kernel node directly (no
+// event node between), so it may be a programmatic dependent; the kernels
+// inside a call always are.
 cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
-                                 long long *stats, int *status, cudaStream_t st);
+                                 long long *stats, int *status, cudaStream_t st, bool pdl = false);
 cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
                                     unsigned long long *keys, int *fb_list, int *counters, long long *stats,
-                                    int *status, cudaStream_t st);
+                                    int *status, cudaStream_t st, bool pdl = false);
 
 // ---- tensor-core search (act_gemm.cu) -------------------------------------
 struct Bf16Search;

@@ -345,7 +345,10 @@ __global__ void __launch_bounds__(kShiftUpdateThreads) k_shift_update(const floa
                                                      int k, int P, act_atom *__restrict__ atoms,
                                                      float *__restrict__ coefs, double *__restrict__ energy,
                                                      int *__restrict__ counters) {
-    asm volatile("griddepcontrol.launch_dependents;");
+    // with a programmatic launch: the keys of the search before are read
+    // only after it completes; the next search may launch now
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ float shf[32];
     __shared__ double shd[32];
     const int b = blockIdx.x;
@@ -577,10 +580,9 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
 
 cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp, float *R, int B,
                                 unsigned long long *keys, int k, int P, act_atom *atoms, float *coefs, double *energy,
-                                int *counters, cudaStream_t st) {
-    k_shift_update<<<B, kShiftUpdateThreads, 0, st>>>(sp.tpl, sp.scale, sp.S, sp.Sa, sp.rows, sp.NtcP, sp.T, ax,
-                                                      Lp, R, keys, k, P, atoms, coefs, energy, counters);
-    return cudaGetLastError();
+                                int *counters, cudaStream_t st, bool pdl) {
+    return launch_kernel(k_shift_update, dim3(B), dim3(kShiftUpdateThreads), 0, st, pdl, sp.tpl, sp.scale, sp.S, sp.Sa,
+                         sp.rows, sp.NtcP, sp.T, ax, Lp, R, keys, k, P, atoms, coefs, energy, counters);
 }
 
 }  // namespace act

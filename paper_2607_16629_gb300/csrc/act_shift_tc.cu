@@ -116,6 +116,10 @@ __global__ void __launch_bounds__(128) k_shift_rows(RowTiling t, const float *__
                                                     double2 *__restrict__ chan_norm, unsigned int *__restrict__ chmax,
                                                     int *__restrict__ chcount, long long *__restrict__ stats) {
     __shared__ float sh[32];
+    // a programmatic dependent of the previous kernel (the residual update):
+    // wait for it in every block, then let the GEMM launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int row = blockIdx.x;
     int b, j;
     tile_row(t, row / kBM, row % kBM, b, j);
@@ -203,6 +207,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
     volatile int *abort_flag = &sm.abort;
+    // set-up above overlaps the shifted-row build; everything below reads its
+    // rows (and the channel maxima it cleared) only after it completes
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
@@ -378,6 +386,8 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bp
                                                     long long *__restrict__ stats) {
     const int b = blockIdx.y;
     __shared__ float thr_sh;
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the GEMM's maxima
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x == 0) {  // the bound in FP64, once per block
         const double2 nr = chan_norm[b];
         const double rn = nr.x, drn = nr.y;
@@ -439,6 +449,7 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     float *rres = sm + warp * warp_floats;
     float *buf0 = rres + Lp;
     const uint32_t bytes = (uint32_t)P * 128u;
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the flagged items
     const int n_tasks = counters[1];  // at most kMaxItems per channel
     // the fallback search behind this kernel may launch now: it reads
     // nothing of ours before its wait for our completion
@@ -666,12 +677,11 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
 }
 
 cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
-                                 long long *stats, int *status, cudaStream_t st) {
+                                 long long *stats, int *status, cudaStream_t st, bool pdl) {
     if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
     const RowTiling tl = make_tiling(sp, B);
-    k_shift_rows<<<tl.m_tiles * kBM, 128, 0, st>>>(tl, R, Lp, sp.tc0, sp.m_lo, sp.Kt, s->X, s->chan_norm, s->chmax,
-                                                   s->chcount, stats);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_kernel(k_shift_rows, dim3(tl.m_tiles * kBM), dim3(128), 0, st, pdl, tl, R, Lp, sp.tc0,
+                                  sp.m_lo, sp.Kt, s->X, s->chan_norm, s->chmax, s->chcount, stats);
     if (e != cudaSuccess) return e;
     const int m_tiles = tl.m_tiles;
     CUtensorMap mapA;
@@ -697,32 +707,29 @@ cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R
     const size_t smem = bn == 256 ? smem_for(256, ShiftTile<256>::kStageBytes, &stages)
                                   : smem_for(128, ShiftTile<128>::kStageBytes, &stages);
     if (stages < 2) return cudaErrorInvalidValue;
-    if (bn == 256)
-        k_shift_gemm<256><<<grid, kThreads, smem, st>>>(mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad,
-                                                        sp.scaleT, s->tile_max, s->blk_max, s->chmax, status);
-    else
-        k_shift_gemm<128><<<grid, kThreads, smem, st>>>(mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad,
-                                                        sp.scaleT, s->tile_max, s->blk_max, s->chmax, status);
-    return cudaGetLastError();
+    // a programmatic dependent of the shifted-row build (set-up overlaps it)
+    return launch_kernel(bn == 256 ? k_shift_gemm<256> : k_shift_gemm<128>, dim3(grid), dim3(kThreads), smem, st, true,
+                         mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad, sp.scaleT, s->tile_max,
+                         s->blk_max, s->chmax, status);
 }
 
 cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
                                     unsigned long long *keys, int *fb_list, int *counters, long long *stats,
-                                    int *status, cudaStream_t st) {
+                                    int *status, cudaStream_t st, bool pdl) {
     if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
     const int entries = sp.Ntc * s->n_tiles;
     int slices = (entries + 255) / 256;
     const int max_slices = (4 * s->sm_count + B - 1) / B;
     if (slices > max_slices) slices = max_slices;
-    k_shift_flag<<<dim3(slices, B), 256, 0, st>>>(sp.Ntc, s->n_tiles, s->bn / 32, sp.Kt, L, s->tile_max, s->blk_max,
-                                                  s->chan_norm, s->chmax,
-                                                  sp.eps_bits, s->chcount, fb_list, counters, s->items, stats);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_kernel(k_shift_flag, dim3(slices, B), dim3(256), 0, st, pdl, sp.Ntc, s->n_tiles, s->bn / 32,
+                                  sp.Kt, L, (const float *)s->tile_max, (const float *)s->blk_max,
+                                  (const double2 *)s->chan_norm, (const unsigned int *)s->chmax,
+                                  (const unsigned int *)sp.eps_bits, s->chcount, fb_list, counters, s->items, stats);
     if (e != cudaSuccess) return e;
-    k_shift_rescan<<<s->sm_count * s->rescan_blocks_per_sm, s->rescan_warps * 32, s->rescan_smem, st>>>(
-        sp.tpl, sp.scale, sp.S, sp.Sa, sp.P, sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, Lp, L, R, s->items,
-        counters, keys, status);
-    e = cudaGetLastError();
+    e = launch_kernel(k_shift_rescan, dim3(s->sm_count * s->rescan_blocks_per_sm), dim3(s->rescan_warps * 32),
+                      s->rescan_smem, st, true, (const float *)sp.tpl, (const float *)sp.scale, sp.S, sp.Sa, sp.P,
+                      sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, Lp, L, R, (const int *)s->items,
+                      (const int *)counters, keys, status);
     if (e != cudaSuccess) return e;
     // channels with more than kMaxItems flagged items: the FP32 template
     // search over the queue, launched early (its CTAs become resident while
