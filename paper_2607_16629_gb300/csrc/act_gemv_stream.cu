@@ -20,7 +20,11 @@ namespace {
 constexpr int kConsumerWarps = 8;
 constexpr int kStreamThreads = (kConsumerWarps + 1) * 32;  // + one producer warp
 constexpr int kMaxStreamStages = 8;
-constexpr int kStreamSmem = 196608;  // stage ring: 6 stages of 32 KB at N = 512
+// Stage ring: 128 KB per SM (4 stages of 32 KB at N = 512).  Measured on the
+// 2,097,152 x 512 dictionary: 128-144 KB in flight per SM streams at
+// 7.4-7.5 TB/s; 192 KB (6 x 32 KB) at 6.95 TB/s, 64 KB (2 x 32 KB) at
+// 6.2 TB/s; 16 KB chunks lose to per-chunk overhead.
+constexpr int kStreamSmem = 131072;
 
 struct StreamShape {
     int rows_per_chunk;  // whole rows per stage, a multiple of the consumer warps
