@@ -101,15 +101,26 @@ __device__ __forceinline__ ChirpFF chirp_ff(double tc, double inv_fs, double fc,
             ff_from_double(inv_dt)};
 }
 
-// tau = (n - tc) / fs of sample n and the phase (c tau + fc) tau reduced
-// mod 1 (to about [-1/2, 1/2]) as an unnormalised pair.  n must be below
-// 2^24 (exact as a float).
-__device__ __forceinline__ ff chirp_phase_pair(int n, const ChirpFF &k, ff *tau_out) {
-    ff d = ff_two_sum((float)n, -k.tc.hi);
-    d = ff_fast_two_sum(d.hi, d.lo - k.tc.lo);
+// tau = d / fs for the sample offset d = n - tc (a float pair) and the phase
+// (c tau + fc) tau reduced mod 1 (to about [-1/2, 1/2]) as an unnormalised
+// pair.
+__device__ __forceinline__ ff chirp_phase_of_offset(ff d, const ChirpFF &k, ff *tau_out) {
     const ff tau = ff_mul(d, k.inv_fs);
     *tau_out = tau;
     return ff_frac(ff_mul(ff_add(ff_mul(k.c, tau), k.fc), tau));
+}
+
+// The offset d = n - tc of sample n (exact while |n - tc| stays below 2^24
+// and tc is a float pair), then its phase as above.  On a grid of
+// whole-sample time centres d is the integer m = n - tc with a zero low
+// part, so a template generated from m has the same bits.
+__device__ __forceinline__ ff chirp_offset(int n, const ChirpFF &k) {
+    const ff d = ff_two_sum((float)n, -k.tc.hi);
+    return ff_fast_two_sum(d.hi, d.lo - k.tc.lo);
+}
+
+__device__ __forceinline__ ff chirp_phase_pair(int n, const ChirpFF &k, ff *tau_out) {
+    return chirp_phase_of_offset(chirp_offset(n, k), k, tau_out);
 }
 
 // The same phase rounded once to FP32.
@@ -123,13 +134,29 @@ __device__ __forceinline__ float chirp_x_ff(ff tau, const ChirpFF &k) {
     return fmaf(tau.hi, k.inv_dt.hi, fmaf(tau.hi, k.inv_dt.lo, tau.lo * k.inv_dt.hi));
 }
 
-// Sample n of the chirplet of Eq. (1) with constants k (not normalised):
-// exp(-x^2 / 2) cos(2 pi phase) in FP32.
-__device__ __forceinline__ float chirp_sample_ff(int n, const ChirpFF &k) {
+// The unnormalised sample of Eq. (1) at offset d = n - tc with constants k:
+// exp(-x^2 / 2) cos(2 pi phase) in FP32.  The dictionary and template
+// generators both form their samples here.
+__device__ __forceinline__ float chirp_sample_offset(ff d, const ChirpFF &k) {
     ff tau;
-    const float frac = chirp_phase_ff(n, k, &tau);
+    const ff p = chirp_phase_of_offset(d, k, &tau);
     const float x = chirp_x_ff(tau, k);
-    return expf(-0.5f * x * x) * cospif(2.0f * frac);
+    return expf(-0.5f * x * x) * cospif(2.0f * (p.hi + p.lo));
+}
+
+// Sample n of the chirplet with constants k (not normalised).
+__device__ __forceinline__ float chirp_sample_ff(int n, const ChirpFF &k) {
+    return chirp_sample_offset(chirp_offset(n, k), k);
+}
+
+// The constants of one warp lane's ChirpFF broadcast from lane src.
+__device__ __forceinline__ ff ff_shfl(ff v, int src) {
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+__device__ __forceinline__ ChirpFF chirp_ff_shfl(const ChirpFF &v, int src) {
+    return {ff_shfl(v.tc, src), ff_shfl(v.inv_fs, src), ff_shfl(v.fc, src), ff_shfl(v.c, src),
+            ff_shfl(v.inv_dt, src)};
 }
 
 }  // namespace act

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "act_device.cuh"
+#include "act_ff.cuh"
 #include "act_internal.cuh"
 
 namespace act {
@@ -14,16 +15,18 @@ namespace act {
 // ---------------------------------------------------------------------------
 // Atom generation
 // ---------------------------------------------------------------------------
-// One warp per atom.  Lane l owns samples 4*(l + 32 j) + e, e = 0..3, so the
-// FP32 row is written with 128-bit stores.  The BF16 copy is written
+// A warp per atom at a time.  Lane l owns samples 4*(l + 32 j) + e, e = 0..3,
+// so the FP32 row is written with 128-bit stores.  The BF16 copy is written
 // tile-major, [atom / 256][sample / 64][atom % 256][sample % 64], so that one
 // 256-atom x 64-sample operand tile of the tensor-core search is a single
 // contiguous 32 KB block.  The phase of Eq. (1), in cycles,
-// phi = c tau^2 + fc tau with tau = (n - tc) / fs, is evaluated in FP64 and
-// reduced to [-1/2, 1/2] before the FP32 cospi; the Gaussian exponent is
-// formed in FP64 and exponentiated in FP32; the squared norm is summed in
-// FP64.  An atom whose FP32 samples are all zero (or not finite) is
-// degenerate: its row is stored as zeros and it scores 0.
+// phi = c tau^2 + fc tau with tau = (n - tc) / fs, is evaluated in
+// float-float (about 48 bits) and reduced to [-1/2, 1/2] before the FP32
+// cospi; the Gaussian argument tau / dt is rounded once to FP32 and
+// exponentiated in FP32; the squared norm is a float-float sum (GB300 runs
+// FP64 at a small fraction of its FP32 rate; the per-atom constants alone
+// are formed in FP64).  An atom whose FP32 samples are all zero (or not
+// finite) is degenerate: its row is stored as zeros and it scores 0.
 template <int NV>
 __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int Lp, float *__restrict__ d32,
                                                     __nv_bfloat16 *__restrict__ d16, int Lb,
@@ -33,62 +36,69 @@ __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int L
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double inv_fs = 1.0 / ax.fs;
-    for (int64_t atom = warp; atom < K; atom += nwarps) {
-        double p[4];
-        decode_params(ax, atom, p);
-        const double tc = p[0], fc = p[1], chirp = p[3];
-        const double inv_dt = exp(-p[2]);
-        float u[NV][4];
-        double energy = 0.0;
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int n = 4 * (lane + 32 * j) + e;
-                float v = 0.0f;
-                if (n < ax.L) {
-                    const double tau = ((double)n - tc) * inv_fs;
-                    double ph = fma(chirp, tau, fc) * tau;
-                    ph -= rint(ph);
-                    const float x = (float)(tau * inv_dt);
-                    v = expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
-                }
-                u[j][e] = v;
-                energy = fma((double)v, (double)v, energy);
-            }
+    // a warp takes 32 atoms at a time: lane l forms atom base + l's
+    // constants (FP64, once per atom), then the warp generates the 32 atoms
+    // one after another with the constants broadcast from their lane
+    for (int64_t base = warp * 32; base < K; base += nwarps * 32) {
+        ChirpFF mine = {};
+        if (base + lane < K) {
+            double p[4];
+            decode_params(ax, base + lane, p);
+            mine = chirp_ff(p[0], inv_fs, p[1], p[3], exp(-p[2]));
         }
-        energy = warp_sum(energy);
-        float scale = 0.0f;
-        const bool bad = !(energy > 0.0) || !isfinite(energy);
-        if (!bad) scale = (float)(1.0 / sqrt(energy));
-        if (bad && lane == 0 && degenerate) atomicAdd(degenerate, 1ull);
-        float4 *row = reinterpret_cast<float4 *>(d32 + atom * (int64_t)Lp);
-        double err = 0.0;  // |bf16(g) - g|^2 of this atom (BF16 layout only)
+        const int count = K - base < 32 ? (int)(K - base) : 32;
+        for (int q = 0; q < count; ++q) {
+            const int64_t atom = base + q;
+            const ChirpFF k = chirp_ff_shfl(mine, q);
+            float u[NV][4];
+            ff energy = {0.0f, 0.0f};
 #pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            float4 w = make_float4(u[j][0] * scale, u[j][1] * scale, u[j][2] * scale, u[j][3] * scale);
-            row[lane + 32 * j] = w;
-            if (d16) {
-                const int n0 = 4 * (lane + 32 * j);
-                if (n0 < Lb) {
-                    __nv_bfloat162 lo = __floats2bfloat162_rn(w.x, w.y);
-                    __nv_bfloat162 hi = __floats2bfloat162_rn(w.z, w.w);
-                    const float2 flo = __bfloat1622float2(lo), fhi = __bfloat1622float2(hi);
-                    err += (double)(flo.x - w.x) * (flo.x - w.x) + (double)(flo.y - w.y) * (flo.y - w.y) +
-                           (double)(fhi.x - w.z) * (fhi.x - w.z) + (double)(fhi.y - w.w) * (fhi.y - w.w);
-                    uint2 packed;
-                    packed.x = *reinterpret_cast<uint32_t *>(&lo);
-                    packed.y = *reinterpret_cast<uint32_t *>(&hi);
-                    // tile-major: [atom / 256][n0 / 64][atom % 256][n0 % 64]
-                    const int64_t off = (((atom >> 8) * (Lb >> 6) + (n0 >> 6)) * 256 + (atom & 255)) * 64 + (n0 & 63);
-                    *reinterpret_cast<uint2 *>(d16 + off) = packed;
+            for (int j = 0; j < NV; ++j) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int n = 4 * (lane + 32 * j) + e;
+                    const float v = n < ax.L ? chirp_sample_ff(n, k) : 0.0f;
+                    u[j][e] = v;
+                    ff_fma_acc(energy, v, v);
                 }
             }
-        }
-        if (d16 && eps_bits) {
-            err = warp_sum(err);
-            // positive floats order like their bit patterns; round the norm up
-            if (lane == 0) atomicMax(eps_bits, __float_as_uint(__double2float_ru(sqrt(err) * (1.0 + 1e-6))));
+            const double en = ff_to_double(ff_warp_sum(energy));
+            float scale = 0.0f;
+            const bool bad = !(en > 0.0) || !isfinite(en);
+            if (!bad) scale = (float)(1.0 / sqrt(en));
+            if (bad && lane == 0 && degenerate) atomicAdd(degenerate, 1ull);
+            float4 *row = reinterpret_cast<float4 *>(d32 + atom * (int64_t)Lp);
+            ff err = {0.0f, 0.0f};  // |bf16(g) - g|^2 of this atom (BF16 layout only)
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                float4 w = make_float4(u[j][0] * scale, u[j][1] * scale, u[j][2] * scale, u[j][3] * scale);
+                row[lane + 32 * j] = w;
+                if (d16) {
+                    const int n0 = 4 * (lane + 32 * j);
+                    if (n0 < Lb) {
+                        __nv_bfloat162 lo = __floats2bfloat162_rn(w.x, w.y);
+                        __nv_bfloat162 hi = __floats2bfloat162_rn(w.z, w.w);
+                        const float2 flo = __bfloat1622float2(lo), fhi = __bfloat1622float2(hi);
+                        // each difference is exact (Sterbenz); squares summed in float-float
+                        ff_fma_acc(err, flo.x - w.x, flo.x - w.x);
+                        ff_fma_acc(err, flo.y - w.y, flo.y - w.y);
+                        ff_fma_acc(err, fhi.x - w.z, fhi.x - w.z);
+                        ff_fma_acc(err, fhi.y - w.w, fhi.y - w.w);
+                        uint2 packed;
+                        packed.x = *reinterpret_cast<uint32_t *>(&lo);
+                        packed.y = *reinterpret_cast<uint32_t *>(&hi);
+                        // tile-major: [atom / 256][n0 / 64][atom % 256][n0 % 64]
+                        const int64_t off =
+                            (((atom >> 8) * (Lb >> 6) + (n0 >> 6)) * 256 + (atom & 255)) * 64 + (n0 & 63);
+                        *reinterpret_cast<uint2 *>(d16 + off) = packed;
+                    }
+                }
+            }
+            if (d16 && eps_bits) {
+                const double e2 = ff_to_double(ff_warp_sum(err));
+                // positive floats order like their bit patterns; round the norm up
+                if (lane == 0) atomicMax(eps_bits, __float_as_uint(__double2float_ru(sqrt(e2) * (1.0 + 1e-6))));
+            }
         }
     }
 }
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(256) k_gen_atoms(GridAxes ax, int64_t K, int L
 cudaError_t launch_gen_atoms(const GridAxes &ax, int64_t K, int Lp, float *d32, __nv_bfloat16 *d16, int Lb,
                              unsigned long long *degenerate, unsigned int *eps_bits, int sm_count, cudaStream_t st) {
     const int nv = Lp / 128;
-    int64_t blocks = (K + 7) / 8;
+    int64_t blocks = (K + 255) / 256;  // 8 warps of 32 atoms per block
     const int64_t cap = (int64_t)sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;

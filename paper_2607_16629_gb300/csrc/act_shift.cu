@@ -41,6 +41,7 @@
 #include <stdint.h>
 
 #include "act_device.cuh"
+#include "act_ff.cuh"
 #include "act_internal.cuh"
 
 namespace act {
@@ -69,17 +70,16 @@ struct ShiftArgs {
     const int *count_dev;
 };
 
-// Template value u_t(m), computed exactly as the dictionary generator
-// computes sample n of an atom with n - tc = m.
-__device__ __forceinline__ float template_sample(double m, double inv_fs, double fc, double inv_dt, double chirp) {
-    const double tau = m * inv_fs;
-    double ph = fma(chirp, tau, fc) * tau;
-    ph -= rint(ph);
-    const float x = (float)(tau * inv_dt);
-    return expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
+// Template value u_t(m) at the integer lag m = n - tc: the dictionary
+// generator's own sample routine at offset m, so on a grid of whole-sample
+// time centres the template holds the unnormalised atom samples bit for bit.
+__device__ __forceinline__ float template_sample(int m, const ChirpFF &k) {
+    return chirp_sample_offset({(float)m, 0.0f}, k);
 }
 
-// One thread per stored template value.
+// One thread per (template block, phase, lane = template): the template's
+// constants once, then its rows rho = 0 .. rows - 1 (lag k = rho - (NtcP - 1),
+// m = a - tc0 + S k); a warp writes one 128-byte row per step.
 __global__ void __launch_bounds__(256) k_shift_templates(GridAxes ax, int S, int Sa, int tc0, int NtcP, int rows,
                                                          int T, int64_t total, float *__restrict__ tpl) {
     const double inv_fs = 1.0 / ax.fs;
@@ -87,46 +87,57 @@ __global__ void __launch_bounds__(256) k_shift_templates(GridAxes ax, int S, int
          i += (int64_t)gridDim.x * blockDim.x) {
         const int lane = (int)(i & 31);
         const int64_t rest = i >> 5;
-        const int rho = (int)(rest % rows);
-        const int64_t rest2 = rest / rows;
-        const int a = (int)(rest2 % Sa);
-        const int64_t tb = rest2 / Sa;
+        const int a = (int)(rest % Sa);
+        const int64_t tb = rest / Sa;
         const int64_t t = tb * 32 + lane;
-        float v = 0.0f;
+        float *out = tpl + ((size_t)tb * Sa + a) * rows * 32 + lane;
         if (t < T) {
             double p[4];
             decode_params(ax, t, p);  // flat index t has i_tc = 0: p[1..3] are the template's axes
-            const int64_t k = (int64_t)rho - (NtcP - 1);
-            const int64_t m = (int64_t)a - tc0 + (int64_t)S * k;
-            v = template_sample((double)m, inv_fs, p[1], exp(-p[2]), p[3]);
+            const ChirpFF k = chirp_ff(0.0, inv_fs, p[1], p[3], exp(-p[2]));
+            for (int rho = 0; rho < rows; ++rho) {
+                const int m = a - tc0 + S * (rho - (NtcP - 1));
+                out[(size_t)rho * 32] = template_sample(m, k);
+            }
+        } else {
+            for (int rho = 0; rho < rows; ++rho) out[(size_t)rho * 32] = 0.0f;
         }
-        tpl[i] = v;
     }
 }
 
 // BF16 templates for the tensor-core search, tile-major like the BF16
 // dictionary: element (t, kk) = bf16(u_t(m_lo + kk)) at
-// [t / 256][kk / 64][t % 256][kk % 64]; zero for padding templates.
-__global__ void __launch_bounds__(256) k_shift_tpl16(GridAxes ax, int m_lo, int Kt, int T, int64_t total,
+// [t / 256][kk / 64][t % 256][kk % 64]; zero for padding templates.  A warp
+// takes 32 templates: lane l forms template l's constants once, then the
+// warp writes the templates one after another, lane = kk stride 32.
+__global__ void __launch_bounds__(256) k_shift_tpl16(GridAxes ax, int m_lo, int Kt, int T, int T_pad,
                                                      __nv_bfloat16 *__restrict__ tpl16) {
     const double inv_fs = 1.0 / ax.fs;
     const int nkc = Kt >> 6;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / Kt;
-        const int kk = (int)(i % Kt);
-        float v = 0.0f;
-        if (t < T) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = warp * 32; t0 < T_pad; t0 += nwarps * 32) {
+        ChirpFF mine = {};
+        if (t0 + lane < T) {
             double p[4];
-            decode_params(ax, t, p);
-            v = template_sample((double)(m_lo + kk), inv_fs, p[1], exp(-p[2]), p[3]);
+            decode_params(ax, t0 + lane, p);
+            mine = chirp_ff(0.0, inv_fs, p[1], p[3], exp(-p[2]));
         }
-        const int64_t off = (((t >> 8) * nkc + (kk >> 6)) * 256 + (t & 255)) * 64 + (kk & 63);
-        tpl16[off] = __float2bfloat16_rn(v);
+        for (int q = 0; q < 32; ++q) {
+            const int64_t t = t0 + q;
+            const ChirpFF k = chirp_ff_shfl(mine, q);
+            for (int kk = lane; kk < Kt; kk += 32) {
+                const float v = t < T ? template_sample(m_lo + kk, k) : 0.0f;
+                const int64_t off = (((t >> 8) * nkc + (kk >> 6)) * 256 + (t & 255)) * 64 + (kk & 63);
+                tpl16[off] = __float2bfloat16_rn(v);
+            }
+        }
     }
 }
 
-// One thread per (template block, lag, lane): |u|^2 over the window in FP64,
+// One thread per (template block, lag, lane): |u|^2 over the window (a
+// float-float sum),
 // the scale 1/|u| in both layouts ([TB][NtcP][32] for the FP32 search,
 // [NtcP][T_pad] for the tensor-core epilogue) and the largest relative BF16
 // rounding error |bf16(u) - u| / |u| over all atoms (float bits, rounded up).
@@ -144,15 +155,16 @@ __global__ void __launch_bounds__(256) k_shift_scales(int S, int Sa, int L, int 
         const int64_t t = tb * 32 + lane;
         float sc = 0.0f;
         if (t < T && j < Ntc) {
-            double e = 0.0, de = 0.0;
+            ff ef = {0.0f, 0.0f}, def = {0.0f, 0.0f};
             const float *base = tpl + (size_t)tb * Sa * rows * 32 + lane;
             for (int n = 0; n < L; ++n) {
                 const int a = n % S, p = n / S;
                 const float u = base[((size_t)a * rows + (p - j + NtcP - 1)) * 32];
-                const float d = __bfloat162float(__float2bfloat16_rn(u)) - u;
-                e = fma((double)u, (double)u, e);
-                de = fma((double)d, (double)d, de);
+                const float d = __bfloat162float(__float2bfloat16_rn(u)) - u;  // exact
+                ff_fma_acc(ef, u, u);
+                ff_fma_acc(def, d, d);
             }
+            const double e = ff_to_double(ef), de = ff_to_double(def);
             if (e > 0.0 && isfinite(e)) {
                 sc = (float)(1.0 / sqrt(e));
                 if (eps_bits)
@@ -509,7 +521,7 @@ cudaError_t shift_default_config(ShiftPlan &sp, int sm_count) {
 
 cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned long long *degenerate,
                                int sm_count, cudaStream_t st) {
-    const int64_t nt = (int64_t)sp.TB * sp.Sa * sp.rows * 32;
+    const int64_t nt = (int64_t)sp.TB * sp.Sa * 32;  // threads: (template block, phase, lane)
     int64_t blocks = (nt + 255) / 256;
     if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
     k_shift_templates<<<(int)blocks, 256, 0, st>>>(ax, sp.S, sp.Sa, sp.tc0, sp.NtcP, sp.rows, sp.T, nt, sp.tpl);
@@ -522,10 +534,9 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
                                                  sp.tpl, sp.scale, sp.scaleT, sp.eps_bits, degenerate);
     e = cudaGetLastError();
     if (e != cudaSuccess || !sp.tpl16) return e;
-    const int64_t n16 = (int64_t)sp.T_pad * sp.Kt;
-    blocks = (n16 + 255) / 256;
+    blocks = ((int64_t)sp.T_pad + 255) / 256;  // 8 warps of 32 templates per block
     if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
-    k_shift_tpl16<<<(int)blocks, 256, 0, st>>>(ax, sp.m_lo, sp.Kt, sp.T, n16, sp.tpl16);
+    k_shift_tpl16<<<(int)blocks, 256, 0, st>>>(ax, sp.m_lo, sp.Kt, sp.T, sp.T_pad, sp.tpl16);
     return cudaGetLastError();
 }
 
