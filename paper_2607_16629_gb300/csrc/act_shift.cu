@@ -157,12 +157,15 @@ __global__ void __launch_bounds__(256) k_shift_scales(int S, int Sa, int L, int 
         if (t < T && j < Ntc) {
             ff ef = {0.0f, 0.0f}, def = {0.0f, 0.0f};
             const float *base = tpl + (size_t)tb * Sa * rows * 32 + lane;
-            for (int n = 0; n < L; ++n) {
-                const int a = n % S, p = n / S;
-                const float u = base[((size_t)a * rows + (p - j + NtcP - 1)) * 32];
-                const float d = __bfloat162float(__float2bfloat16_rn(u)) - u;  // exact
-                ff_fma_acc(ef, u, u);
-                ff_fma_acc(def, d, d);
+            // sample n = a + S p sits in phase a, row p - j + NtcP - 1
+            for (int a = 0; a < Sa; ++a) {
+                const float *col = base + ((size_t)a * rows + (NtcP - 1 - j)) * 32;
+                for (int p = 0; a + S * p < L; ++p) {
+                    const float u = col[(size_t)p * 32];
+                    const float d = __bfloat162float(__float2bfloat16_rn(u)) - u;  // exact
+                    ff_fma_acc(ef, u, u);
+                    ff_fma_acc(def, d, d);
+                }
             }
             const double e = ff_to_double(ef), de = ff_to_double(def);
             if (e > 0.0 && isfinite(e)) {
