@@ -331,6 +331,9 @@ def run_ours(args):
     refine = None
     if not args.no_refine:
         refine = bench_refine(args, dev, stream, peaks, peak_kind)
+    small = None
+    if not args.no_small:
+        small = bench_small_check(args, dev, stream)
     lem = None
     if not args.no_lem:
         lem = bench_lem(args, dev, stream, peaks, peak_kind)
@@ -358,6 +361,8 @@ def run_ours(args):
             line["offgrid_refinement"] = refine
         if lem is not None:
             line["hierarchical_lem"] = lem
+        if small is not None:
+            line["small_check"] = small
         line["targets"] = _targets(roofline, shift, bf16)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
@@ -727,6 +732,49 @@ def bench_ragged(args, dev, stream, peaks, peak_kind):
             "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 rescore"}
 
 
+def bench_small_check(args, dev, stream):
+    """The 16,384-atom check workload (N = 256, fs = 128 Hz, 3 on-grid atoms
+    plus white noise, 5 orders): its 16.8 MB FP32 dictionary stays in L2,
+    so a decomposition is bound by kernel latency, not HBM; reported as us
+    per order and projections/s (FP32 GEMV search, the autotuned launch)."""
+    import torch
+
+    from paper_2607_16629_gb300 import act, synth
+    w = synth.workload_c1()
+    B, P, K, L = w.signals.shape[0], w.n_atoms, w.grid.n_atoms, w.grid.n_samples
+    h = act.act_grid_create(w.grid, dev.index)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32, stream)
+        sig = torch.tensor(w.signals, dtype=torch.float32, device=dev)
+        act.act_autotune(h, sig, B, stream)
+        out = [torch.empty((B, P, act.ATOM_BYTES), dtype=torch.uint8, device=dev),
+               torch.empty((B, P), dtype=torch.float32, device=dev),
+               torch.empty((B, L), dtype=torch.float32, device=dev),
+               torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
+        for _ in range(5):
+            act.act_decompose(h, sig, B, P, *out, stream)
+        reps = 200
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            act.act_decompose(h, sig, B, P, *out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        st = act.act_grid_status(h, stream)
+        if st != act.ACT_OK:
+            raise RuntimeError(act.status_name(st))
+        gemv = act.act_get_tuning(h)[0]
+    finally:
+        act.act_destroy(h)
+    return {"workload": "plain_fp32_1ch_n256_fs128_grid32x16x4x8_k16384_p5", "value": B * K * P / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms, "us_per_order": 1e3 * ms / P, "steps": reps,
+            "bound": "latency (the 16.8 MB dictionary is L2-resident)",
+            "gemv": "bulk-copy stream" if gemv == -1 else f"load-streaming, {gemv} CTAs",
+            "l2": "dictionary smaller than L2: every step after the first reads it from L2"}
+
+
 def _refine_runs(act, torch, w, dict_mode, steps_list, n, dev, stream):
     B, P, K, L = w.signals.shape[0], w.n_atoms, w.grid.n_atoms, w.grid.n_samples
     torch.cuda.synchronize(dev)
@@ -964,6 +1012,7 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-lem", action="store_true")
     ap.add_argument("--no-shift", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--channels", type=int, default=1, help="channels for the shift_* and lem_eeg cases (1 or up to 64)")
     ap.add_argument("--gemv", default="stream", choices=["stream", "load"],
                     help="FP32 GEMV of the gemv_small case: bulk-copy streaming or load-streaming")
