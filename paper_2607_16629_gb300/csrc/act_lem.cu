@@ -71,12 +71,17 @@ __global__ void __launch_bounds__(kLemThreads) k_lem_lhs(int n, int npow2, LemBo
             __syncthreads();
         }
     }
-    // sorted position p is the stratum (rank) of sample idx[p]
+    // sorted position p is the stratum (rank) of sample idx[p].  For n a
+    // power of two the quotient (p + u) / n is the exact product with 2^-k:
+    // the same correctly rounded value without an FP64 division
+    const bool pow2 = (n & (n - 1)) == 0;
+    const double inv_n = pow2 ? __longlong_as_double((long long)(1023 - (31 - __clz(n))) << 52) : 0.0;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const int i = (int)idx[p];
         const uint64_t h = splitmix64_at(seed, lem_counter(b, order, a, 1, i));
         const double u = (double)(h >> 11) * 0x1.0p-53;
-        const double t = __ddiv_rn(__dadd_rn((double)p, u), (double)n);
+        const double q = __dadd_rn((double)p, u);
+        const double t = pow2 ? __dmul_rn(q, inv_n) : __ddiv_rn(q, (double)n);
         out[4 * i + a] = __dadd_rn(box.lo[a], __dmul_rn(t, __dadd_rn(box.hi[a], -box.lo[a])));
     }
     if (threadIdx.x == 0 && a == 0) ncand[b] = n;
