@@ -166,13 +166,11 @@ cudaError_t stream_instance(const float *D, int64_t K, int Lp, const float *R, i
     const StreamShape sh = stream_shape(Lp);
     if (sh.stages < 2) return cudaErrorInvalidValue;
     const size_t smem = (size_t)sh.stages * sh.rows_per_chunk * Lp * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemv_stream<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kStreamSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set for the current device on every launch (a per-process flag would
+    // miss the second GPU of a process); no allocation, legal in a capture
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemv_stream<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
+    if (e != cudaSuccess) return e;
     k_gemv_stream<NV><<<sm_count, kStreamThreads, smem, st>>>(D, K, Lp, R, B, chlist, count_dev, keys,
                                                               sh.rows_per_chunk, sh.stages, status);
     return cudaGetLastError();

@@ -88,9 +88,15 @@ extern "C" act_status act_search_noalloc(const float *dictionary, int64_t n_atom
         cudaSuccess)
         return ACT_ERR_CUDA;
     int *status = reinterpret_cast<int *>(scratch + kNoAllocMaxChannels);
-    if (act::launch_gemv_argmax(dictionary, n_atoms, row_stride, residuals, channels, nullptr, nullptr, scratch,
-                                status, act::gemv_ctas(sms, row_stride), st) != cudaSuccess)
-        return ACT_ERR_CUDA;
+    // one channel: the bulk-copy streaming GEMV (the faster stream); several:
+    // the load-streaming GEMV, which scores several channels per pass
+    const cudaError_t e =
+        channels == 1
+            ? act::launch_gemv_stream_argmax(dictionary, n_atoms, row_stride, residuals, 1, nullptr, nullptr,
+                                             scratch, status, sms, st)
+            : act::launch_gemv_argmax(dictionary, n_atoms, row_stride, residuals, channels, nullptr, nullptr,
+                                      scratch, status, act::gemv_ctas(sms, row_stride), st);
+    if (e != cudaSuccess) return ACT_ERR_CUDA;
     k_noalloc_finish<<<(channels + 127) / 128, 128, 0, st>>>(channels, best_index, best_score);
     if (cudaGetLastError() != cudaSuccess) return ACT_ERR_CUDA;
     return ACT_OK;

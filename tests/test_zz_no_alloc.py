@@ -23,9 +23,12 @@ def _lib():
     act.load_library()
 
 
-def test_noalloc_search_matches_allocating_entry_points():
+@pytest.mark.parametrize("B", [6, 1])
+def test_noalloc_search_matches_allocating_entry_points(B):
+    """Several channels take the load-streaming GEMV, one channel the
+    bulk-copy streaming GEMV; both must select as the allocating paths do."""
     grid = synth.scaled_grid(synth.grid_eeg(), tc_count=16, fc_count=16)   # 65,536 atoms, N = 512
-    B, L = 6, grid.n_samples
+    L = grid.n_samples
     h = act.act_grid_create(grid, 0)
     try:
         act.act_dictionary_build(h, act.ACT_DICT_FP32)
