@@ -626,8 +626,12 @@ def bench_bf16(args, dev, stream, peaks, peak_kind):
     return {"workload": f"eeg_like_bf16_{B}ch_n512_grid128x64x8x32_k2097152_p20", "value": value, "unit": UNIT,
             "atoms_per_s": B * P * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "dtype": "bf16 x bf16 -> f32 (tensor cores), f32 tile rescan",
-            "roofline": {"bound": "hbm", "kernel": "k_gemm_tilemax (tcgen05 BF16 GEMM + per-tile maxima)",
+            "roofline": {"bound": "hbm", "kernel": "k_gemm_tilemax (tcgen05 BF16 GEMM + per-tile and per-block maxima)",
                          "achieved": bw, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": bw / peaks["hbm_gbs"],
+                         "traffic": _profile_traffic("gemm_tilemax_bf16_eeg_b64.md",
+                                                     ["paper_2607_16629_gb300/csrc/act_gemm.cu",
+                                                      "paper_2607_16629_gb300/csrc/act_tc.cuh",
+                                                      "paper_2607_16629_gb300/csrc/act_device.cuh"]),
                          "peak_source": f"{peak_kind} hbm_gbs", "avg_gemm_ms": avg_gemm,
                          "algorithmic_bytes_per_launch": bytes_per,
                          "tensor_tflops": tflops,
