@@ -101,10 +101,11 @@ typedef enum {
  *   ACT_SEARCH_FP32: FP32 GEMV with the argmax fused (CUDA cores).
  *   ACT_SEARCH_BF16: BF16 tcgen05 GEMM over all atoms (tensor cores, FP32
  *                    accumulation) reduced to the largest |score| per
- *                    256-atom tile; the tiles that an error bound cannot
- *                    exclude are rescored in FP32, so the selection equals
- *                    the FP32 search's bit for bit (channels <= 128,
- *                    n_samples <= 512).
+ *                    tile and per 32-atom block; the blocks that an error
+ *                    bound cannot exclude are rescored in FP32 (a channel
+ *                    with more than 512 of them takes the FP32 search), so
+ *                    the selection equals the FP32 search's bit for bit
+ *                    (channels <= 128).
  *   ACT_SEARCH_LEM:  the hierarchical search of act_lem_params (no
  *                    dictionary needed; act_atom.flat_index is -1).
  *   ACT_SEARCH_SHIFT: the template search over an ACT_DICT_RECOMPUTE build
@@ -115,10 +116,10 @@ typedef enum {
  *                    accumulation, every score scaled by its atom's 1/|u|)
  *                    reduced to the largest |score| per (time centre,
  *                    32-template block); the blocks an error bound cannot
- *                    exclude (all blocks of a channel with more than 64 of
- *                    them) are rescored with ACT_SEARCH_SHIFT's own
- *                    arithmetic, so the selection equals ACT_SEARCH_SHIFT's
- *                    bit for bit.
+ *                    exclude are rescored with ACT_SEARCH_SHIFT's own
+ *                    arithmetic (a channel with more than 1,024 of them is
+ *                    searched by ACT_SEARCH_SHIFT in full), so the selection
+ *                    equals ACT_SEARCH_SHIFT's bit for bit.
  *   ACT_SEARCH_AUTO: BF16 when the dictionary was built with ACT_DICT_BF16,
  *                    SHIFT_BF16 with ACT_DICT_RECOMPUTE (SHIFT where the
  *                    tensor-core view could not be set up), FP32 otherwise. */
