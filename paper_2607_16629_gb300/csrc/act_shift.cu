@@ -40,6 +40,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "act_device.cuh"
 #include "act_ff.cuh"
 #include "act_internal.cuh"
@@ -419,12 +421,23 @@ __global__ void __launch_bounds__(kShiftUpdateThreads) k_shift_update(const floa
     }
 }
 
+// The largest dynamic shared memory k_shift_search<J> was opted into, per
+// device (the attribute belongs to the current device's context); it only
+// grows, so graphs captured earlier keep a valid launch.
+constexpr int kSmemDevices = 64;
+
 template <int J>
 cudaError_t set_smem(size_t smem) {
-    static size_t set = 0;
-    if (smem <= 48 * 1024 || smem <= set) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_shift_search<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) set = smem;
+    static std::mutex mu;
+    static size_t set[kSmemDevices] = {};
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < kSmemDevices && smem <= set[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_shift_search<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && dev >= 0 && dev < kSmemDevices) set[dev] = smem;
     return e;
 }
 
