@@ -163,9 +163,18 @@ def cpu_baseline(target_s: float = 12.0):
     per_col = 16384 * 20 / rate
     cols = int(max(2, min(128, target_s / per_col)))
     rate, K, dt = _oracle_sample(cols, 20)
+    # the same oracle on one core, on a smaller sample (about 2-3 s)
+    oracle.set_threads(1)
+    try:
+        cols1 = int(max(1, min(16, 2.5 / (per_col * cores))))
+        rate1, K1, dt1 = _oracle_sample(cols1, 20)
+    finally:
+        oracle.set_threads(cores)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle MP, 20 orders over the first {cols} of 128 tc columns "
-                      f"({K} of 2,097,152 atoms), N=512; {dt:.1f} s timed; dictionary build excluded"}
+                      f"({K} of 2,097,152 atoms), N=512; {dt:.1f} s timed; dictionary build excluded",
+            "one_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                         "sample": f"the same, over {cols1} tc columns ({K1} atoms); {dt1:.1f} s timed"}}
 
 
 def run_reference(args):
