@@ -52,7 +52,7 @@ typedef enum {
     ACT_ERR_NONFINITE = 4,      /* an input signal held NaN or Inf */
     ACT_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up */
     ACT_ERR_NOT_BUILT = 6,      /* act_dictionary_build has not run */
-    ACT_ERR_UNSUPPORTED = 7     /* size or mode outside what this build handles */
+    ACT_ERR_UNSUPPORTED = 7     /* size or mode outside what the library handles */
 } act_status;
 
 /* One grid axis: value_i = lo + i * step, i = 0 .. count-1. */
