@@ -78,7 +78,15 @@ typedef struct {
  *   ACT_DICT_BF16: D as FP32 [K][Lp] plus BF16 [K][Lb] (Lb = L rounded up to
  *                  64) for the tensor-core search; FP32 rows are used to
  *                  rescore candidates and for the update.
- *   ACT_DICT_AUTO: ACT_DICT_FP32.
+ *   ACT_DICT_AUTO: ACT_DICT_FP32 when the FP32 rows fit the grid's memory
+ *                  budget (act_set_memory_budget; by default 90% of the
+ *                  device memory free when the build starts), otherwise
+ *                  ACT_DICT_RECOMPUTE when the time centres are whole
+ *                  samples and the templates fit; otherwise the build
+ *                  returns ACT_ERR_OOM and keeps nothing (a grid with
+ *                  fractional time centres has no template form: its only
+ *                  search without stored rows is ACT_SEARCH_LEM).
+ *                  act_dictionary_mode reports the choice.
  *   ACT_DICT_RECOMPUTE: no atom rows are stored.  The real atom of Eq. (1)
  *                  depends on n and tc only through n - tc, so on a grid
  *                  whose time centres are whole samples (tc.lo and tc.step
@@ -105,7 +113,7 @@ typedef enum {
  *                    bound cannot exclude are rescored in FP32 (a channel
  *                    with more than 512 of them takes the FP32 search), so
  *                    the selection equals the FP32 search's bit for bit
- *                    (channels <= 128).
+ *                    (any number of channels, in tiles of 128).
  *   ACT_SEARCH_LEM:  the hierarchical search of act_lem_params (no
  *                    dictionary needed; act_atom.flat_index is -1).
  *   ACT_SEARCH_SHIFT: the template search over an ACT_DICT_RECOMPUTE build
@@ -195,6 +203,35 @@ ACT_API act_status act_grid_size(const act_grid *grid, int64_t *n_atoms, int32_t
  * whose time centres are not whole samples. */
 ACT_API act_status act_dictionary_build(act_grid *grid, act_dict_mode mode, void *cuda_stream);
 
+/* The dictionary the last successful act_dictionary_build made
+ * (ACT_DICT_FP32, ACT_DICT_BF16 or ACT_DICT_RECOMPUTE; an ACT_DICT_AUTO build
+ * reports what it chose) into *mode.  ACT_ERR_NOT_BUILT (and *mode = -1)
+ * when there is none. */
+ACT_API act_status act_dictionary_mode(const act_grid *grid, int32_t *mode);
+
+/* Device bytes an ACT_DICT_AUTO build may give the dictionary (0, the
+ * default: 90% of the device memory free when the build starts). */
+ACT_API act_status act_set_memory_budget(act_grid *grid, uint64_t bytes);
+
+/* Limit, in nanoseconds, of every bounded device-side wait in this grid's
+ * kernels (a pipeline stage waiting for its copy or its consumer).  A wait
+ * that reaches it gives up: the kernel records ACT_ERR_DEVICE_TIMEOUT for
+ * act_grid_status, lets the copies it already issued land, releases its
+ * tensor memory and exits, leaving the context usable; that decomposition's
+ * outputs are then not valid.  Default 2,000,000,000 (2 s).  0 gives up at
+ * the first unsuccessful poll (used to test the timeout path).  Errors:
+ * ACT_ERR_INVALID_ARG for ns < 0.  Changing it re-records the grid's graphs
+ * and makes ragged plans built on the grid stale. */
+ACT_API act_status act_set_wait_limit(act_grid *grid, int64_t ns);
+
+/* Test aid for out-of-memory handling: the nth device allocation made by
+ * this library from now on (any grid, any thread; nth >= 1) fails once, as
+ * if the device were out of memory.  The call that makes it returns
+ * ACT_ERR_OOM, frees what it had made for itself and keeps the grid usable
+ * (a failed dictionary build keeps no dictionary).  0 disarms it.  Errors:
+ * ACT_ERR_INVALID_ARG for nth < 0. */
+ACT_API act_status act_inject_alloc_failure(int32_t nth);
+
 /* Sets the hierarchical search (ACT_SEARCH_LEM).  A new grid starts with the
  * settings the paper reports for EEG: top_k 4, 2 levels, steps
  * (64, 2, 2, 5), (32, 1, 1, 2.5), (16, 0.5, 0.5, 0.5), radius (2, 2, 1, 2),
@@ -273,7 +310,7 @@ ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double
  * [channels][n_samples] (device or host memory) as residuals, keeps the
  * fastest, and returns its time per order in *best_ms (may be NULL).
  * Candidates: resident CTAs per SM of the FP32 GEMV (1..4, as occupancy
- * allows), the bulk-copy streaming GEMV and, when the grid holds a BF16 dictionary and channels <= 128,
+ * allows), the bulk-copy streaming GEMV and, when the grid holds a BF16 dictionary,
  * tile width (128 or 256 atoms) x pipeline depth (2 .. what fits in shared
  * memory) of the tensor-core GEMM, each timed with its tile selection and
  * rescan; with an ACT_DICT_RECOMPUTE build, every valid (lags per thread,
@@ -345,15 +382,14 @@ ACT_API act_status act_bf16_stats(act_grid *grid, int64_t *resolved, int64_t *it
  * (offsets: host memory, [channels+1], offsets[0] = 0).  Each channel is
  * decomposed over the grid in grids[0 .. n_grids-1] whose n_samples equals
  * its length (one grid per length; every grid built on the same device).
- * Each length group uses its grid's search (ACT_SEARCH_BF16 needs at most
- * 128 channels in the group, else the group uses FP32).  The whole batch --
- * gathers, every group's n_atoms orders, scatters -- is captured once as one
- * CUDA graph whose length groups are independent branches.  The plan owns
- * its work buffers; it shares each grid's dictionary and search scratch, so
- * it must not run concurrently with other calls on those grids, and it must
- * be destroyed before they are.  Rebuilding a grid's dictionary or changing
- * its tuning makes the plan stale (act_ragged_decompose then returns
- * ACT_ERR_NOT_BUILT).  Errors: ACT_ERR_INVALID_ARG (bad offsets, a length
+ * Each length group uses its grid's search.  The whole batch -- gathers,
+ * every group's n_atoms orders, scatters -- is captured once as one CUDA
+ * graph whose length groups are independent branches.  The plan owns its
+ * work buffers and search scratch (nothing a later call on a grid
+ * reallocates); it shares each grid's dictionary and status word, so it must
+ * be destroyed before the grids are.  Rebuilding a grid's dictionary or
+ * changing its tuning, refinement, hierarchical settings or wait limit makes
+ * the plan stale (act_ragged_decompose then returns ACT_ERR_NOT_BUILT).  Errors: ACT_ERR_INVALID_ARG (bad offsets, a length
  * with no grid, two grids of one length), ACT_ERR_NOT_BUILT, ACT_ERR_OOM. */
 typedef struct act_ragged_plan act_ragged_plan;
 ACT_API act_status act_ragged_plan_create(act_grid *const *grids, int32_t n_grids, const int64_t *offsets,

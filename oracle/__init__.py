@@ -87,6 +87,10 @@ def _load():
         lib.act_oracle_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.act_oracle_splitmix64_at.restype = ctypes.c_uint64
         lib.act_oracle_lhs.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _dp]
+        lib.act_oracle_lem_topk.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        lib.act_oracle_lem_topk.restype = ctypes.c_int
+        lib.act_oracle_lem_neighbours.argtypes = [_dp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
+        lib.act_oracle_lem_neighbours.restype = ctypes.c_int
         lib.act_oracle_lem_select.argtypes = [ctypes.POINTER(LemParams), _dp, _dp, ctypes.c_double, ctypes.c_int,
                                               _dp, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _dp, _dp]
         lib.act_oracle_lem_select.restype = ctypes.c_int
@@ -291,6 +295,29 @@ def lhs(lo, hi, n, seed, channel, order) -> np.ndarray:
                            _d(np.ascontiguousarray(hi, dtype=np.float64)), int(n), int(seed), int(channel),
                            int(order), _d(out))
     return out
+
+
+def lem_topk(cand, score, k):
+    """The k best candidates by |score| (lowest index on ties), a parameter
+    vector equal to one already kept skipped -> (kept[m][4], kept_score[m])."""
+    cand = np.ascontiguousarray(cand, dtype=np.float64)
+    score = np.ascontiguousarray(score, dtype=np.float64)
+    kept = np.empty((k, 4))
+    ks = np.empty(k)
+    m = _load().act_oracle_lem_topk(_d(cand), _d(score), int(score.shape[0]), int(k), _d(kept), _d(ks))
+    return kept[:m], ks[:m]
+
+
+def lem_neighbours(kept, step, radius, lo, hi):
+    """Neighbourhood candidates of the kept parameter vectors (Sec. VII-A):
+    every offset -R..R steps per axis (c fastest), clamped to [lo, hi]."""
+    kept = np.ascontiguousarray(kept, dtype=np.float64).reshape(-1, 4)
+    per = int(np.prod([2 * r + 1 for r in radius]))
+    out = np.empty((kept.shape[0] * per, 4))
+    R = (ctypes.c_int * 4)(*[int(r) for r in radius])
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    n = _load().act_oracle_lem_neighbours(_d(kept), int(kept.shape[0]), f(step), R, f(lo), f(hi), _d(out))
+    return out[:n]
 
 
 def lem_select(params: LemParams, lo, hi, fs, r, seed, channel, order):

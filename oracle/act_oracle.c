@@ -544,7 +544,7 @@ static double lem_score(const double *th, double fs, int L, const double *r, dou
 
 /* The k best candidates by |score| (lowest candidate index on ties),
  * skipping candidates whose parameters equal an already kept one. */
-static int lem_topk(const double *cand, const double *score, int n, int k, double *kept, double *kept_score) {
+int act_oracle_lem_topk(const double *cand, const double *score, int n, int k, double *kept, double *kept_score) {
     int m = 0;
     for (int round = 0; round < k; ++round) {
         int best = -1;
@@ -569,8 +569,8 @@ static int lem_topk(const double *cand, const double *score, int n, int k, doubl
  * [-R_tc..R_tc] x [-R_fc..R_fc] x [-R_ld..R_ld] x [-R_c..R_c]
  * (c fastest), theta = clamp(parent + o * step, lo, hi).  Returns the
  * number of candidates written. */
-static int lem_neighbours(const double *kept, int m, const double *step, const int *R, const double *lo,
-                          const double *hi, double *cand) {
+int act_oracle_lem_neighbours(const double *kept, int m, const double *step, const int *R, const double *lo,
+                              const double *hi, double *cand) {
     int n = 0;
     for (int j = 0; j < m; ++j)
         for (int o0 = -R[0]; o0 <= R[0]; ++o0)
@@ -616,11 +616,11 @@ int act_oracle_lem_select(const act_oracle_lem *p, const double *lo, const doubl
     }
     act_oracle_lhs(lo, hi, p->n_coarse, seed, channel, order, cand);
     for (int i = 0; i < p->n_coarse; ++i) score[i] = lem_score(cand + 4 * i, fs, L, r, g);
-    int m = lem_topk(cand, score, p->n_coarse, p->top_k, kept, kept_score);
+    int m = act_oracle_lem_topk(cand, score, p->n_coarse, p->top_k, kept, kept_score);
     for (int lev = 1; lev <= p->levels; ++lev) {
-        const int n = lem_neighbours(kept, m, p->steps[lev], p->radius, lo, hi, cand);
+        const int n = act_oracle_lem_neighbours(kept, m, p->steps[lev], p->radius, lo, hi, cand);
         for (int i = 0; i < n; ++i) score[i] = lem_score(cand + 4 * i, fs, L, r, g);
-        m = lem_topk(cand, score, n, p->top_k, kept, kept_score);
+        m = act_oracle_lem_topk(cand, score, n, p->top_k, kept, kept_score);
     }
     for (int a = 0; a < 4; ++a) theta_out[a] = kept[a];
     *score_out = kept_score[0];

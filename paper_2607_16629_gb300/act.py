@@ -36,6 +36,7 @@ EXPORTS = (
     "act_bf16_stats", "act_destroy", "act_search_noalloc", "act_autotune", "act_get_tuning", "act_set_tuning",
     "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
     "act_set_refinement", "act_chirplet_score", "act_set_lem", "act_set_shift_tuning", "act_get_shift_tuning",
+    "act_dictionary_mode", "act_set_memory_budget", "act_set_wait_limit", "act_inject_alloc_failure",
 )
 
 
@@ -121,6 +122,10 @@ def load_library(path: str = LIB_PATH):
         lib.act_set_lem.argtypes = [_P, ctypes.POINTER(act_lem_params)]
         lib.act_set_shift_tuning.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         lib.act_get_shift_tuning.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int32)] * 4
+        lib.act_dictionary_mode.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
+        lib.act_set_memory_budget.argtypes = [_P, ctypes.c_uint64]
+        lib.act_set_wait_limit.argtypes = [_P, ctypes.c_int64]
+        lib.act_inject_alloc_failure.argtypes = [ctypes.c_int32]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -360,6 +365,26 @@ def act_set_lem(grid: int, n_coarse: int = 0, top_k: int = 4, levels: int = 2,
     for a in range(4):
         p.radius[a] = int(radius[a])
     _check(load_library().act_set_lem(grid, ctypes.byref(p)), "act_set_lem")
+
+
+def act_dictionary_mode(grid: int) -> int:
+    """The dictionary mode the last build made (ACT_DICT_FP32, _BF16 or _RECOMPUTE)."""
+    m = ctypes.c_int32()
+    _check(load_library().act_dictionary_mode(grid, ctypes.byref(m)), "act_dictionary_mode")
+    return m.value
+
+
+def act_set_memory_budget(grid: int, n_bytes: int) -> None:
+    _check(load_library().act_set_memory_budget(grid, int(n_bytes)), "act_set_memory_budget")
+
+
+def act_set_wait_limit(grid: int, ns: int) -> None:
+    _check(load_library().act_set_wait_limit(grid, int(ns)), "act_set_wait_limit")
+
+
+def act_inject_alloc_failure(nth: int) -> None:
+    """Makes the nth device allocation of the library from now on fail once (0 disarms)."""
+    _check(load_library().act_inject_alloc_failure(int(nth)), "act_inject_alloc_failure")
 
 
 def act_destroy(grid: int) -> None:

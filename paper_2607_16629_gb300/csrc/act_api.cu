@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <new>
 #include <tuple>
@@ -24,6 +25,10 @@ thread_local char g_last_error[256] = "";
 void note_error(const char *what, cudaError_t e) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
 }
+
+// Countdown to the device allocation that is to fail (act_inject_alloc_failure):
+// n > 0 means the n-th dev_alloc from now fails; 0 means none.
+std::atomic<int> g_fail_at{0};
 
 #define ACT_CK(call)                                                        \
     do {                                                                    \
@@ -81,8 +86,27 @@ void free_dev(T *&p) {
 
 }  // namespace
 
+namespace act {
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    int n = g_fail_at.load();
+    while (n > 0) {
+        if (g_fail_at.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) return cudaErrorMemoryAllocation;
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+}  // namespace act
+
 // Per-decomposition device buffers: a grid owns one set, a ragged plan one
-// per length group.
+// per length group.  Invariant: a CUDA graph captures device addresses of
+// exactly one WorkBuffers (the one it was recorded with) plus the grid's
+// dictionary, templates, status and statistics words.  Only
+// act_dictionary_build replaces the latter (it drops the grid's graphs and
+// bumps its generation, which makes ragged plans stale); whoever reallocates
+// any part of a WorkBuffers first destroys every graph recorded on it.
 struct WorkBuffers {
     int cap_B = 0, cap_P = 0;
     float *sig = nullptr;             // [B][L] staged input signals
@@ -97,6 +121,8 @@ struct WorkBuffers {
     double *theta = nullptr;          // [B][4] refined parameters of the current order
     LemBuffers lem;                   // hierarchical-search candidates (allocated on first use)
     int lem_B = 0;
+    Bf16Scratch b16;                  // dense tensor-core search maxima and rescan lists (on first use)
+    ShiftTcScratch stc;               // tensor-core template search rows, maxima, items (on first use)
 };
 
 struct act_grid {
@@ -121,6 +147,8 @@ struct act_grid {
     int gemv_grid = 0;
     bool gemv_stream = false;  // FP32 search by the bulk-copy streaming GEMV (one CTA per SM)
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
+    unsigned long long wait_ns = kWaitLimitNs;  // limit of each bounded device-side wait
+    uint64_t mem_budget = 0;  // bytes ACT_DICT_AUTO may give the dictionary (0: free device memory)
     LemConfig lem;         // hierarchical search settings
     cudaStream_t cap = nullptr;
     bool profiling = false;
@@ -141,7 +169,18 @@ void drop_graphs(act_grid *g) {
     g->last = nullptr;
 }
 
-void free_work(WorkBuffers &w) {
+void free_lem(WorkBuffers &w) {
+    free_dev(w.lem.cand);
+    free_dev(w.lem.score);
+    free_dev(w.lem.kept);
+    free_dev(w.lem.kept_score);
+    free_dev(w.lem.ncand);
+    free_dev(w.lem.nkept);
+    w.lem.cap = 0;
+    w.lem_B = 0;
+}
+
+void free_base(WorkBuffers &w) {
     free_dev(w.sig);
     free_dev(w.R);
     free_dev(w.R16);
@@ -152,15 +191,14 @@ void free_work(WorkBuffers &w) {
     free_dev(w.fb_list);
     free_dev(w.fb_count);
     free_dev(w.theta);
-    free_dev(w.lem.cand);
-    free_dev(w.lem.score);
-    free_dev(w.lem.kept);
-    free_dev(w.lem.kept_score);
-    free_dev(w.lem.ncand);
-    free_dev(w.lem.nkept);
-    w.lem.cap = 0;
-    w.lem_B = 0;
     w.cap_B = w.cap_P = 0;
+}
+
+void free_work(WorkBuffers &w) {
+    free_base(w);
+    free_lem(w);
+    bf16_scratch_free(w.b16);
+    shift_tc_scratch_free(w.stc);
 }
 
 void free_dictionary(act_grid *g) {
@@ -177,40 +215,42 @@ void free_dictionary(act_grid *g) {
     free_dev(g->shift.eps_bits);
     g->shift = ShiftPlan();
     g->built = -1;
+    // the tensor-core search scratch is sized by the dictionary's shape
+    bf16_scratch_free(g->w.b16);
+    shift_tc_scratch_free(g->w.stc);
 }
+
+#define ACT_AL(ptr, bytes)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = dev_alloc((void **)&(ptr), (bytes));                     \
+        if (e_ != cudaSuccess) {                                                   \
+            cudaGetLastError();                                                    \
+            note_error("device allocation " #ptr, e_);                             \
+            return e_ == cudaErrorMemoryAllocation ? ACT_ERR_OOM : ACT_ERR_CUDA;   \
+        }                                                                          \
+    } while (0)
 
 // Work buffers for B channels and P orders on a grid of window L.  The BF16
 // residual copy always has a multiple of 128 rows (the tensor-core tile
-// height), padded with zeros.
-act_status alloc_work(const act_grid *g, WorkBuffers &w, int B, int P) {
+// height), padded with zeros.  On failure the caller frees what was made.
+act_status alloc_base(const act_grid *g, WorkBuffers &w, int B, int P) {
     const int rows16 = round_up(B, 128);
-    ACT_CK(cudaMalloc(&w.sig, sizeof(float) * (size_t)B * g->L));
-    ACT_CK(cudaMalloc(&w.R, sizeof(float) * (size_t)B * g->Lp));
-    ACT_CK(cudaMalloc(&w.R16, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb));
+    ACT_AL(w.sig, sizeof(float) * (size_t)B * g->L);
+    ACT_AL(w.R, sizeof(float) * (size_t)B * g->Lp);
+    ACT_AL(w.R16, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb);
     ACT_CK(cudaMemset(w.R16, 0, sizeof(__nv_bfloat16) * (size_t)rows16 * g->Lb));
-    ACT_CK(cudaMalloc(&w.keys, sizeof(unsigned long long) * (size_t)B));
+    ACT_AL(w.keys, sizeof(unsigned long long) * (size_t)B);
     ACT_CK(cudaMemset(w.keys, 0, sizeof(unsigned long long) * (size_t)B));
-    ACT_CK(cudaMalloc(&w.atoms, sizeof(act_atom) * (size_t)B * P));
-    ACT_CK(cudaMalloc(&w.coefs, sizeof(float) * (size_t)B * P));
-    ACT_CK(cudaMalloc(&w.energy, sizeof(double) * (size_t)B * (P + 1)));
-    ACT_CK(cudaMalloc(&w.fb_list, sizeof(int) * (size_t)B));
-    ACT_CK(cudaMalloc(&w.fb_count, 2 * sizeof(int)));
+    ACT_AL(w.atoms, sizeof(act_atom) * (size_t)B * P);
+    ACT_AL(w.coefs, sizeof(float) * (size_t)B * P);
+    ACT_AL(w.energy, sizeof(double) * (size_t)B * (P + 1));
+    ACT_AL(w.fb_list, sizeof(int) * (size_t)B);
+    ACT_AL(w.fb_count, 2 * sizeof(int));
     ACT_CK(cudaMemset(w.fb_count, 0, 2 * sizeof(int)));
-    ACT_CK(cudaMalloc(&w.theta, sizeof(double) * 4 * (size_t)B));
+    ACT_AL(w.theta, sizeof(double) * 4 * (size_t)B);
     w.cap_B = B;
     w.cap_P = P;
     return ACT_OK;
-}
-
-act_status ensure_work(act_grid *g, int B, int P) {
-    if (B <= g->w.cap_B && P <= g->w.cap_P) return ACT_OK;
-    drop_graphs(g);
-    const int nB = B > g->w.cap_B ? B : g->w.cap_B;
-    const int nP = P > g->w.cap_P ? P : g->w.cap_P;
-    free_work(g->w);
-    act_status s = alloc_work(g, g->w, nB, nP);
-    if (s != ACT_OK) free_work(g->w);
-    return s;
 }
 
 int lem_capacity(const LemConfig &c) {
@@ -224,25 +264,75 @@ int lem_capacity(const LemConfig &c) {
     return cap;
 }
 
-act_status ensure_lem(const act_grid *g, WorkBuffers &w, int B) {
+act_status alloc_lem(const act_grid *g, WorkBuffers &w, int B) {
     const int cap = lem_capacity(g->lem);
-    if (w.lem.cap >= cap && w.lem_B >= B && w.lem.cand) return ACT_OK;
-    free_dev(w.lem.cand);
-    free_dev(w.lem.score);
-    free_dev(w.lem.kept);
-    free_dev(w.lem.kept_score);
-    free_dev(w.lem.ncand);
-    free_dev(w.lem.nkept);
     const int k = g->lem.top_k;
-    ACT_CK(cudaMalloc(&w.lem.cand, sizeof(double) * 4 * (size_t)B * cap));
-    ACT_CK(cudaMalloc(&w.lem.score, sizeof(double) * (size_t)B * cap));
-    ACT_CK(cudaMalloc(&w.lem.kept, sizeof(double) * 4 * (size_t)B * k));
-    ACT_CK(cudaMalloc(&w.lem.kept_score, sizeof(double) * (size_t)B * k));
-    ACT_CK(cudaMalloc(&w.lem.ncand, sizeof(int) * (size_t)B));
-    ACT_CK(cudaMalloc(&w.lem.nkept, sizeof(int) * (size_t)B));
+    ACT_AL(w.lem.cand, sizeof(double) * 4 * (size_t)B * cap);
+    ACT_AL(w.lem.score, sizeof(double) * (size_t)B * cap);
+    ACT_AL(w.lem.kept, sizeof(double) * 4 * (size_t)B * k);
+    ACT_AL(w.lem.kept_score, sizeof(double) * (size_t)B * k);
+    ACT_AL(w.lem.ncand, sizeof(int) * (size_t)B);
+    ACT_AL(w.lem.nkept, sizeof(int) * (size_t)B);
     w.lem.cap = cap;
     w.lem_B = B;
     return ACT_OK;
+}
+
+act_status scratch_status(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return ACT_OK;
+    cudaGetLastError();
+    note_error(what, e);
+    return e == cudaErrorMemoryAllocation ? ACT_ERR_OOM : ACT_ERR_CUDA;
+}
+
+// Whether w holds everything `mode` needs for B channels and P orders.
+bool work_fits(const act_grid *g, const WorkBuffers &w, int B, int P, act_search_mode mode) {
+    if (B > w.cap_B || P > w.cap_P) return false;
+    if (mode == ACT_SEARCH_LEM && (w.lem.cap < lem_capacity(g->lem) || w.lem_B < B || !w.lem.cand)) return false;
+    if (mode == ACT_SEARCH_BF16 && w.b16.B_cap < B) return false;
+    if (mode == ACT_SEARCH_SHIFT_BF16 && w.stc.B_cap < B) return false;
+    return true;
+}
+
+// Grows w to what `mode` needs for B channels and P orders (each part to at
+// least its current size).  The caller has destroyed every graph recorded
+// on w.  On failure the parts that could not be made are left empty.
+act_status grow_work(const act_grid *g, WorkBuffers &w, int B, int P, act_search_mode mode) {
+    act_status s = ACT_OK;
+    if (B > w.cap_B || P > w.cap_P) {
+        const int nB = B > w.cap_B ? B : w.cap_B;
+        const int nP = P > w.cap_P ? P : w.cap_P;
+        free_base(w);
+        if ((s = alloc_base(g, w, nB, nP)) != ACT_OK) {
+            free_base(w);
+            return s;
+        }
+    }
+    if (mode == ACT_SEARCH_LEM && (w.lem.cap < lem_capacity(g->lem) || w.lem_B < B || !w.lem.cand)) {
+        const int nB = B > w.lem_B ? B : w.lem_B;
+        free_lem(w);
+        if ((s = alloc_lem(g, w, nB)) != ACT_OK) {
+            free_lem(w);
+            return s;
+        }
+    }
+    if (mode == ACT_SEARCH_BF16 && w.b16.B_cap < B) {
+        if ((s = scratch_status(bf16_scratch_reserve(g->bf16, B, w.b16), "bf16_scratch_reserve")) != ACT_OK)
+            return s;
+    }
+    if (mode == ACT_SEARCH_SHIFT_BF16 && w.stc.B_cap < B) {
+        if ((s = scratch_status(shift_tc_reserve(g->shift_tc, g->shift, B, w.stc), "shift_tc_reserve")) != ACT_OK)
+            return s;
+    }
+    return ACT_OK;
+}
+
+// The grid's own work buffers: any growth first destroys the grid's graphs,
+// which captured their addresses.
+act_status ensure_work(act_grid *g, int B, int P, act_search_mode mode) {
+    if (work_fits(g, g->w, B, P, mode)) return ACT_OK;
+    drop_graphs(g);
+    return grow_work(g, g->w, B, P, mode);
 }
 
 // Hierarchical-search settings from the public struct; the box is the
@@ -319,30 +409,31 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             kernels += lem_kernels(g->lem);
         } else if (mode == ACT_SEARCH_SHIFT) {
             // early launch only between kernel nodes (not after profiling events)
-            ACT_CK(launch_shift_search(g->shift, w.R, g->Lp, g->L, B, w.keys, nullptr, g->status, !profiling, st));
+            ACT_CK(launch_shift_search(g->shift, w.R, g->Lp, g->L, B, w.keys, nullptr, g->status, !profiling, st,
+                                       nullptr, nullptr, g->wait_ns));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         } else if (mode == ACT_SEARCH_SHIFT_BF16) {
             // programmatic dependents between kernel nodes only (not next to profiling events)
-            ACT_CK(launch_shift_tc_gemm(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, g->stats, g->status, st,
-                                        !profiling));
+            ACT_CK(launch_shift_tc_gemm(g->shift_tc, w.stc, g->shift, w.R, g->Lp, g->L, B, g->stats, g->status, st,
+                                        !profiling, g->wait_ns));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
-            ACT_CK(launch_shift_tc_resolve(g->shift_tc, g->shift, w.R, g->Lp, g->L, B, w.keys, w.fb_list, w.fb_count,
-                                           g->stats, g->status, st, !profiling));
+            ACT_CK(launch_shift_tc_resolve(g->shift_tc, w.stc, g->shift, w.R, g->Lp, g->L, B, w.keys, w.fb_list,
+                                           w.fb_count, g->stats, g->status, st, !profiling, g->wait_ns));
             kernels += 5;
         } else if (bf16) {
-            ACT_CK(launch_bf16_gemm(g->bf16, B, w.R16, g->status, st));
+            ACT_CK(launch_bf16_gemm(g->bf16, w.b16, B, w.R16, g->status, st, g->wait_ns));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
-            ACT_CK(launch_bf16_resolve(g->bf16, B, g->d32, g->Lp, g->L, w.R, w.keys, w.fb_list, w.fb_count,
-                                       g->stats, g->status, g->gemv_grid, st));
+            ACT_CK(launch_bf16_resolve(g->bf16, w.b16, B, g->d32, g->Lp, g->L, w.R, w.keys, w.fb_list, w.fb_count,
+                                       g->stats, g->status, g->gemv_grid, st, g->wait_ns));
             kernels += 4;
         } else {
             if (g->gemv_stream)
                 ACT_CK(launch_gemv_stream_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
-                                                 g->sm_count, st));
+                                                 g->sm_count, st, g->wait_ns));
             else
                 ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
-                                          g->gemv_grid, st));
+                                          g->gemv_grid, st, g->wait_ns));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         }
@@ -501,12 +592,12 @@ act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid *
     g->ax.L = g->L;
     cudaError_t e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&g->stats, 3 * sizeof(long long));
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->stats, 3 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(g->stats, 0, 3 * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&g->degenerate, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&g->eps_bits, sizeof(unsigned int));
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->degenerate, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->eps_bits, sizeof(unsigned int));
     if (e != cudaSuccess) {
         note_error("act_grid_create", e);
         act_destroy(g);
@@ -548,15 +639,15 @@ static act_status build_templates(act_grid *g, cudaStream_t st) {
     if (shift_default_config(sp, g->sm_count) != cudaSuccess) return ACT_ERR_UNSUPPORTED;
     const size_t bt = sizeof(float) * (size_t)sp.TB * sp.Sa * sp.rows * 32;
     const size_t bs = sizeof(float) * (size_t)sp.TB * sp.NtcP * 32;
-    cudaError_t e = cudaMalloc(&sp.tpl, bt);
-    if (e == cudaSuccess) e = cudaMalloc(&sp.scale, bs);
+    cudaError_t e = dev_alloc((void **)&sp.tpl, bt);
+    if (e == cudaSuccess) e = dev_alloc((void **)&sp.scale, bs);
     if (e == cudaSuccess && sp.Kt > 0) {
         // the tensor-core view: BF16 templates, transposed scales, BF16 error bound
         const size_t b16 = sizeof(__nv_bfloat16) * (size_t)sp.T_pad * sp.Kt;
         const size_t bst = sizeof(float) * (size_t)sp.NtcP * sp.T_pad;
-        e = cudaMalloc(&sp.tpl16, b16);
-        if (e == cudaSuccess) e = cudaMalloc(&sp.scaleT, bst);
-        if (e == cudaSuccess) e = cudaMalloc(&sp.eps_bits, sizeof(unsigned int));
+        e = dev_alloc((void **)&sp.tpl16, b16);
+        if (e == cudaSuccess) e = dev_alloc((void **)&sp.scaleT, bst);
+        if (e == cudaSuccess) e = dev_alloc((void **)&sp.eps_bits, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemsetAsync(sp.scaleT, 0, bst, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(sp.eps_bits, 0, sizeof(unsigned int), st);
     }
@@ -581,19 +672,60 @@ static act_status build_templates(act_grid *g, cudaStream_t st) {
     return ACT_OK;
 }
 
+// Device bytes of the template dictionary of g (0 when its time centres are
+// not whole samples).
+static uint64_t template_bytes(const act_grid *g) {
+    ShiftPlan sp;
+    if (shift_plan(sp, g->ax) != cudaSuccess) return 0;
+    uint64_t b = sizeof(float) * ((uint64_t)sp.TB * sp.Sa * sp.rows * 32 + (uint64_t)sp.TB * sp.NtcP * 32);
+    if (sp.Kt > 0) b += sizeof(__nv_bfloat16) * (uint64_t)sp.T_pad * sp.Kt + sizeof(float) * (uint64_t)sp.NtcP * sp.T_pad;
+    return b;
+}
+
+// ACT_DICT_AUTO: the FP32 rows when they fit the memory budget, else the
+// template dictionary when the time centres are whole samples (Sec. IV-C
+// pages a dictionary larger than VRAM through unified memory instead).
+static act_status resolve_auto(act_grid *g, act_dict_mode *mode) {
+    uint64_t budget = g->mem_budget;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        ACT_CK(cudaMemGetInfo(&fr, &tot));
+        budget = (uint64_t)((double)fr * 0.9);
+    }
+    const uint64_t b32 = sizeof(float) * (uint64_t)g->K * (uint64_t)g->Lp;
+    if (b32 <= budget) {
+        *mode = ACT_DICT_FP32;
+        return ACT_OK;
+    }
+    const uint64_t bt = template_bytes(g);
+    if (bt > 0 && bt <= budget) {
+        *mode = ACT_DICT_RECOMPUTE;
+        return ACT_OK;
+    }
+    snprintf(g_last_error, sizeof(g_last_error),
+             "ACT_DICT_AUTO: %llu bytes of FP32 rows exceed the budget of %llu bytes and %s",
+             (unsigned long long)b32, (unsigned long long)budget,
+             bt ? "so does the template dictionary" : "the time centres are not whole samples (no template form)");
+    return ACT_ERR_OOM;
+}
+
 act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stream) {
     if (!g) return ACT_ERR_INVALID_ARG;
-    if (mode == ACT_DICT_AUTO) mode = ACT_DICT_FP32;
-    if (mode != ACT_DICT_FP32 && mode != ACT_DICT_BF16 && mode != ACT_DICT_RECOMPUTE) return ACT_ERR_INVALID_ARG;
+    if (mode != ACT_DICT_AUTO && mode != ACT_DICT_FP32 && mode != ACT_DICT_BF16 && mode != ACT_DICT_RECOMPUTE)
+        return ACT_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     ACT_CK(cudaStreamSynchronize(st));
     drop_graphs(g);
     ++g->generation;  // ragged plans built on the old dictionary are stale
     free_dictionary(g);
+    if (mode == ACT_DICT_AUTO) {
+        const act_status s = resolve_auto(g, &mode);
+        if (s != ACT_OK) return s;
+    }
     if (mode == ACT_DICT_RECOMPUTE) return build_templates(g, st);
     const size_t b32 = sizeof(float) * (size_t)g->K * g->Lp;
-    cudaError_t e = cudaMalloc(&g->d32, b32);
+    cudaError_t e = dev_alloc((void **)&g->d32, b32);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g->d32 = nullptr;
@@ -605,7 +737,7 @@ act_status act_dictionary_build(act_grid *g, act_dict_mode mode, void *cuda_stre
         // the last tile padded with zero atoms
         const int64_t ntiles = (g->K + 255) / 256;
         const size_t b16 = sizeof(__nv_bfloat16) * (size_t)ntiles * 256 * g->Lb;
-        e = cudaMalloc(&g->d16, b16);
+        e = dev_alloc((void **)&g->d16, b16);
         if (e == cudaSuccess) e = cudaMemset(g->d16, 0, b16);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -655,17 +787,8 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
     if (mode == ACT_SEARCH_LEM && n_atoms > 4096) return ACT_ERR_UNSUPPORTED;  // draw counter holds 12 bits of order
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (mode == ACT_SEARCH_BF16 && channels > 128) return ACT_ERR_UNSUPPORTED;
-    act_status s = ensure_work(g, channels, n_atoms);
+    act_status s = ensure_work(g, channels, n_atoms, mode);
     if (s != ACT_OK) return s;
-    if (mode == ACT_SEARCH_LEM && (s = ensure_lem(g, g->w, channels)) != ACT_OK) return s;
-    if (mode == ACT_SEARCH_SHIFT_BF16) {
-        cudaError_t re = shift_tc_reserve(g->shift_tc, g->shift, channels);
-        if (re != cudaSuccess) {
-            note_error("shift_tc_reserve", re);
-            return ACT_ERR_OOM;
-        }
-    }
     bool host_seen = !is_device_ptr(signals);
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     GraphEntry *ge = nullptr;
@@ -693,14 +816,16 @@ act_status act_project(act_grid *g, const float *signals, int32_t channels, floa
     if (g->built < 0) return ACT_ERR_NOT_BUILT;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    act_status s = ensure_work(g, channels, 1);
+    act_status s = ensure_work(g, channels, 1, ACT_SEARCH_FP32);
     if (s != ACT_OK) return s;
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, nullptr, g->Lb, nullptr, nullptr, 1, g->status, st));
     if (g->built == ACT_DICT_RECOMPUTE) {
-        ACT_CK(launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, nullptr, scores, g->status, false, st));
+        ACT_CK(launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, nullptr, scores, g->status, false, st,
+                                   nullptr, nullptr, g->wait_ns));
     } else {
-        ACT_CK(launch_project(g->d32, g->K, g->Lp, g->w.R, channels, scores, g->status, g->gemv_grid, st));
+        ACT_CK(launch_project(g->d32, g->K, g->Lp, g->w.R, channels, scores, g->status, g->gemv_grid, st,
+                              g->wait_ns));
     }
     return ACT_OK;
 }
@@ -754,7 +879,7 @@ static act_status autotune_shift(act_grid *g, int channels, cudaStream_t st, dou
                 err = cudaEventRecord(e0, st);
                 for (int r = 0; r < reps && err == cudaSuccess; ++r)
                     err = launch_shift_search(g->shift, g->w.R, g->Lp, g->L, channels, g->w.keys, nullptr, g->status,
-                                              false, st);
+                                              false, st, nullptr, nullptr, g->wait_ns);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, st);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
             }
@@ -793,15 +918,15 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (g->built == ACT_DICT_RECOMPUTE) {
-        act_status s = ensure_work(g, channels, 1);
+        act_status s = ensure_work(g, channels, 1, ACT_SEARCH_SHIFT);
         if (s != ACT_OK) return s;
         ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
         ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, nullptr, g->Lb, g->w.keys, nullptr, 1, g->status,
                            st));
         return autotune_shift(g, channels, st, best_ms);
     }
-    const bool bf16 = g->bf16 != nullptr && channels <= 128;
-    act_status s = ensure_work(g, channels, 1);
+    const bool bf16 = g->bf16 != nullptr;
+    act_status s = ensure_work(g, channels, 1, bf16 ? ACT_SEARCH_BF16 : ACT_SEARCH_FP32);
     if (s != ACT_OK) return s;
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     ACT_CK(launch_init(g->w.sig, channels, g->L, g->Lp, g->w.R, g->w.R16, g->Lb, g->w.keys, nullptr, 1, g->status, st));
@@ -817,16 +942,18 @@ act_status act_autotune(act_grid *g, const float *signals, int32_t channels, voi
             for (int r = 0; r < reps && e == cudaSuccess; ++r) {
                 if (use_bf16) {
                     e = cudaMemsetAsync(g->w.fb_count, 0, 2 * sizeof(int), st);
-                    if (e == cudaSuccess) e = launch_bf16_gemm(g->bf16, channels, g->w.R16, g->status, st);
                     if (e == cudaSuccess)
-                        e = launch_bf16_resolve(g->bf16, channels, g->d32, g->Lp, g->L, g->w.R, g->w.keys, g->w.fb_list,
-                                                g->w.fb_count, g->stats, g->status, g->gemv_grid, st);
+                        e = launch_bf16_gemm(g->bf16, g->w.b16, channels, g->w.R16, g->status, st, g->wait_ns);
+                    if (e == cudaSuccess)
+                        e = launch_bf16_resolve(g->bf16, g->w.b16, channels, g->d32, g->Lp, g->L, g->w.R, g->w.keys,
+                                                g->w.fb_list, g->w.fb_count, g->stats, g->status, g->gemv_grid, st,
+                                                g->wait_ns);
                 } else {
                     e = g->gemv_stream
                             ? launch_gemv_stream_argmax(g->d32, g->K, g->Lp, g->w.R, channels, nullptr, nullptr,
-                                                        g->w.keys, g->status, g->sm_count, st)
+                                                        g->w.keys, g->status, g->sm_count, st, g->wait_ns)
                             : launch_gemv_argmax(g->d32, g->K, g->Lp, g->w.R, channels, nullptr, nullptr, g->w.keys,
-                                                 g->status, g->gemv_grid, st);
+                                                 g->status, g->gemv_grid, st, g->wait_ns);
                 }
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -1096,11 +1223,11 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
         p->groups[it->second].chan.push_back(c);
     }
     p->total = offsets[p->channels];
-    ACT_CK(cudaMalloc(&p->d_sig, sizeof(float) * (size_t)p->total));
-    ACT_CK(cudaMalloc(&p->d_resid, sizeof(float) * (size_t)p->total));
-    ACT_CK(cudaMalloc(&p->d_atoms, sizeof(act_atom) * (size_t)p->channels * p->P));
-    ACT_CK(cudaMalloc(&p->d_coefs, sizeof(float) * (size_t)p->channels * p->P));
-    ACT_CK(cudaMalloc(&p->d_energy, sizeof(double) * (size_t)p->channels * (p->P + 1)));
+    ACT_AL(p->d_sig, sizeof(float) * (size_t)p->total);
+    ACT_AL(p->d_resid, sizeof(float) * (size_t)p->total);
+    ACT_AL(p->d_atoms, sizeof(act_atom) * (size_t)p->channels * p->P);
+    ACT_AL(p->d_coefs, sizeof(float) * (size_t)p->channels * p->P);
+    ACT_AL(p->d_energy, sizeof(double) * (size_t)p->channels * (p->P + 1));
     ACT_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     ACT_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
     for (auto &gr : p->groups) {
@@ -1108,18 +1235,16 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
         if (B == 0) continue;
         act_grid *g = gr.g;
         gr.mode = effective_search(g);
-        if (gr.mode == ACT_SEARCH_BF16 && (!g->bf16 || B > 128)) gr.mode = ACT_SEARCH_FP32;
         if (!search_available(g, gr.mode)) return ACT_ERR_NOT_BUILT;
-        act_status s = alloc_work(g, gr.w, B, p->P);
+        // the plan's own buffers, search scratch included: nothing the
+        // plan's graph captures belongs to the grid's work buffers
+        act_status s = grow_work(g, gr.w, B, p->P, gr.mode);
         if (s != ACT_OK) return s;
-        if (gr.mode == ACT_SEARCH_LEM && (s = ensure_lem(g, gr.w, B)) != ACT_OK) return s;
-        if (gr.mode == ACT_SEARCH_SHIFT_BF16 && shift_tc_reserve(g->shift_tc, g->shift, B) != cudaSuccess)
-            return ACT_ERR_OOM;
         std::vector<int64_t> off(B);
         for (int i = 0; i < B; ++i) off[i] = offsets[gr.chan[i]];
-        ACT_CK(cudaMalloc(&gr.src_off, sizeof(int64_t) * B));
+        ACT_AL(gr.src_off, sizeof(int64_t) * B);
         ACT_CK(cudaMemcpy(gr.src_off, off.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice));
-        ACT_CK(cudaMalloc(&gr.d_chan, sizeof(int) * B));
+        ACT_AL(gr.d_chan, sizeof(int) * B);
         ACT_CK(cudaMemcpy(gr.d_chan, gr.chan.data(), sizeof(int) * B, cudaMemcpyHostToDevice));
         ACT_CK(cudaStreamCreateWithFlags(&gr.st, cudaStreamNonBlocking));
         ACT_CK(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
@@ -1214,6 +1339,35 @@ act_status act_ragged_plan_info(const act_ragged_plan *p, int32_t *groups, int32
 }
 
 void act_ragged_plan_destroy(act_ragged_plan *p) { ragged_free(p); }
+
+act_status act_dictionary_mode(const act_grid *g, int32_t *mode) {
+    if (!g || !mode) return ACT_ERR_INVALID_ARG;
+    *mode = g->built;
+    return g->built < 0 ? ACT_ERR_NOT_BUILT : ACT_OK;
+}
+
+act_status act_set_memory_budget(act_grid *g, uint64_t bytes) {
+    if (!g) return ACT_ERR_INVALID_ARG;
+    g->mem_budget = bytes;
+    return ACT_OK;
+}
+
+act_status act_set_wait_limit(act_grid *g, int64_t ns) {
+    if (!g || ns < 0) return ACT_ERR_INVALID_ARG;
+    const unsigned long long v = (unsigned long long)ns;
+    if (v != g->wait_ns) {
+        g->wait_ns = v;  // a kernel argument: the recorded graphs carry the old value
+        drop_graphs(g);
+        ++g->generation;
+    }
+    return ACT_OK;
+}
+
+act_status act_inject_alloc_failure(int32_t nth) {
+    if (nth < 0) return ACT_ERR_INVALID_ARG;
+    g_fail_at.store(nth);
+    return ACT_OK;
+}
 
 void act_destroy(act_grid *g) {
     if (!g) return;

@@ -7,7 +7,10 @@
 
 namespace act {
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per bounded wait
+// Default limit of a bounded wait (a grid can lower it, act_set_wait_limit);
+// the drain waits that let copies already in flight land before a CTA exits
+// always take this full limit.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -48,15 +51,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Whether the phase with the given parity has completed, without waiting.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete, for at most
-// kWaitLimitNs of wall time.  Returns false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// limit_ns of wall time; limit 0 polls once without suspending (a copy or
+// a consumer that is not already done makes it give up).  Returns false when
+// it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
+    if (limit_ns == 0) return mbar_test_wait(bar, parity);
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if (globaltimer_ns() - t0 >= limit_ns) return false;
     }
     return true;
+}
+
+// The wait of an exit path: lets a copy already issued land, with the full
+// default limit whatever the grid's setting.
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity) {
+    return mbar_wait(bar, parity, kWaitLimitNs);
 }
 
 // 1-D bulk copy global -> shared (TMA engine), completing on `bar`.

@@ -1,5 +1,5 @@
-// Tensor-core search of the batched projection P = D X^T (Sec. IV-A) for up
-// to 128 channels, exact with respect to the FP32 search:
+// Tensor-core search of the batched projection P = D X^T (Sec. IV-A), exact
+// with respect to the FP32 search:
 //  1. a persistent tcgen05 GEMM over the BF16 dictionary writes, per channel
 //     and per tile of BN atoms, the largest BF16 |score| of the tile;
 //  2. a select kernel bounds the BF16 error (delta) and flags, per channel,
@@ -11,9 +11,13 @@
 //
 // GEMM shape per tile: M = 128 channels (rows of the residual matrix, padded
 // with zero rows), N = BN atoms (128 or 256, picked by the autotuner),
-// K = Lb samples.  For windows up to 512 samples the residual matrix (A,
-// <= 128 KB of BF16) is loaded once per CTA by TMA and stays in shared
-// memory; longer windows stream its 16 KB chunks with the dictionary chunks.
+// K = Lb samples.  A work item is (dictionary tile, 128-channel row tile),
+// row tiles fastest, so the CTAs working on one dictionary tile at a time
+// read it from DRAM once and from L2 after that.  With one row tile and a
+// window of up to 512 samples the residual matrix (A, <= 128 KB of BF16) is
+// loaded once per CTA by TMA and stays in shared memory; otherwise its 16 KB
+// chunks are streamed with the dictionary chunks (from L2: the whole residual
+// matrix is B x Lb x 2 bytes).
 // Dictionary chunks (B, BN atoms x 64 samples, contiguous in the tile-major
 // BF16 layout) are streamed by TMA through a ring of stages; FP32
 // accumulators live in tensor memory (two BN-column buffers, so the epilogue
@@ -72,16 +76,17 @@ struct GemmSmem {
     int abort;
 };
 
-// a_stream = 0: the whole residual matrix (nkc chunks of 16 KB) is loaded
-// once and stays resident; stages hold dictionary chunks only.
-// a_stream = 1 (windows longer than 512 samples): every stage holds a
-// dictionary chunk followed by the matching residual chunk (16 KB, re-read
-// from L2 for every tile).
+// a_stream = 0 (one row tile, windows up to 512 samples): the whole
+// residual matrix (nkc chunks of 16 KB) is loaded once and stays resident;
+// stages hold dictionary chunks only.
+// a_stream = 1: every stage holds a dictionary chunk followed by the
+// matching chunk of the item's residual row tile (16 KB, re-read from L2 for
+// every item).
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_tilemax(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t K, int nkc,
-                   int stages, int a_stream, int B, float *__restrict__ tile_max, float *__restrict__ blk_max,
-                   int *status) {
+                   int stages, int a_stream, int B, int m_tiles, float *__restrict__ tile_max,
+                   float *__restrict__ blk_max, int *status, unsigned long long wait_ns) {
     using Cfg = TileCfg<BN>;
     extern __shared__ uint8_t dyn_raw[];
     __shared__ GemmSmem sm;
@@ -93,6 +98,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = (K + BN - 1) / BN;
+    const int64_t items = ntiles * m_tiles;  // item w: dictionary tile w / m_tiles, row tile w % m_tiles
 
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar_a, 1);
@@ -128,14 +134,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int kc = 0; kc < nkc; ++kc) tma_load_2d(a_smem + kc * kAChunkBytes, &tmA, kc * kBK, 0, &sm.bar_a);
         }
         uint32_t it = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+        for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+            const int64_t tile = w / m_tiles;
+            const int mt = (int)(w - tile * m_tiles);
             // row of this tile's first chunk in the tile-major layout viewed as [rows][64]
             const int64_t atom0 = tile * BN;
             const int64_t blk = atom0 / kBlockRows, sub = atom0 % kBlockRows;
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
-                if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u)) {
+                if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u, wait_ns)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -143,17 +151,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tma_load_2d(b_smem + s * stage_bytes, &tmB, 0, (int)((blk * nkc + kc) * kBlockRows + sub),
                             &sm.bar_full[s]);
                 if (a_stream)
-                    tma_load_2d(b_smem + s * stage_bytes + Cfg::kStageBytes, &tmA, kc * kBK, 0, &sm.bar_full[s]);
+                    tma_load_2d(b_smem + s * stage_bytes + Cfg::kStageBytes, &tmA, kc * kBK, mt * kBM,
+                                &sm.bar_full[s]);
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        if (!a_stream && !mbar_wait(&sm.bar_a, 0)) *abort_flag = 1;
+        if (!a_stream && !mbar_wait(&sm.bar_a, 0, wait_ns)) *abort_flag = 1;
         tc_fence_after();
         uint32_t it = 0, local = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++local) {
+        for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++local) {
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            if (!mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u)) {
+            if (!mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u, wait_ns)) {
                 *abort_flag = 1;
                 break;
             }
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
-                if (!mbar_wait(&sm.bar_full[s], ph)) {
+                if (!mbar_wait(&sm.bar_full[s], ph, wait_ns)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -180,11 +189,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     } else if (warp >= 4) {
         // ---------------- epilogue: thread = channel ----------------
         const int q = warp - 4;
-        const int ch = q * 32 + lane;
         uint32_t local = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
+        for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++local) {
+            const int64_t tile = w / m_tiles;
+            const int ch = (int)(w - tile * m_tiles) * kBM + q * 32 + lane;
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            if (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph)) {
+            if (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph, wait_ns)) {
                 *abort_flag = 1;
                 break;
             }
@@ -415,17 +425,11 @@ struct Bf16Search {
     int64_t K = 0;
     int Lb = 0;
     int nkc = 0;
-    int a_stream = 0;
+    int a_stream = 0;     // with one row tile: 1 when the residual matrix cannot stay resident
     int sm_count = 0;
     // current configuration
     int bn = 256;
     int stages = 0;
-    int grid = 0;
-    int64_t ntiles = 0;
-    size_t smem = 0;
-    float *tile_max = nullptr;         // [kBM][ntiles at BN = 128]
-    float *blk_max = nullptr;          // [kBM][K / 32 rounded up to whole tiles]
-    int *pairs = nullptr;              // [kBM * kMaxRescan][2]
     unsigned int *eps_bits = nullptr;  // owned by the caller (dictionary build)
 };
 
@@ -434,17 +438,15 @@ cudaError_t bf16_search_configure(Bf16Search *s, int bn, int stages) {
     const int ms = max_stages(bn, s->nkc, s->a_stream != 0);
     if (stages <= 0) stages = ms;
     if (stages < 2 || stages > ms) return cudaErrorInvalidValue;
-    const size_t chunk = (size_t)bn * kBK * 2;
-    const size_t smem = s->a_stream ? 1024 + (size_t)stages * (chunk + kAChunkBytes)
-                                    : 1024 + (size_t)s->nkc * kAChunkBytes + (size_t)stages * chunk;
-    cudaError_t e = bn == 256 ? allow_max_smem((const void *)k_gemm_tilemax<256>, smem)
-                              : allow_max_smem((const void *)k_gemm_tilemax<128>, smem);
+    // several row tiles stream the residual chunks: that form must fit too
+    if (max_stages(bn, s->nkc, true) < 2) return cudaErrorInvalidValue;
+    // the limit is set to everything the device allows, so every stage count
+    // of either form can be launched
+    cudaError_t e = bn == 256 ? allow_max_smem((const void *)k_gemm_tilemax<256>, 1024)
+                              : allow_max_smem((const void *)k_gemm_tilemax<128>, 1024);
     if (e != cudaSuccess) return e;
     s->bn = bn;
     s->stages = stages;
-    s->smem = smem;
-    s->ntiles = (s->K + bn - 1) / bn;
-    s->grid = (int)(s->ntiles < s->sm_count ? s->ntiles : s->sm_count);
     return cudaSuccess;
 }
 
@@ -478,51 +480,79 @@ cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int6
         return cudaErrorInvalidValue;
     }
     cudaError_t e = bf16_search_configure(s, 256, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)kBM * ((K + 127) / 128));
-    if (e == cudaSuccess) e = cudaMalloc(&s->blk_max, sizeof(float) * (size_t)kBM * ((K + 255) / 256) * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&s->pairs, sizeof(int) * 2 * kBM * kMaxRescan);
     if (e != cudaSuccess) {
-        bf16_search_free(s);
+        delete s;
         return e;
     }
     *out = s;
     return cudaSuccess;
 }
 
-void bf16_search_free(Bf16Search *s) {
-    if (!s) return;
-    if (s->tile_max) cudaFree(s->tile_max);
-    if (s->blk_max) cudaFree(s->blk_max);
-    if (s->pairs) cudaFree(s->pairs);
-    delete s;
+void bf16_search_free(Bf16Search *s) { delete s; }
+
+void bf16_scratch_free(Bf16Scratch &x) {
+    if (x.tile_max) cudaFree(x.tile_max);
+    if (x.blk_max) cudaFree(x.blk_max);
+    if (x.pairs) cudaFree(x.pairs);
+    x = Bf16Scratch();
 }
 
-cudaError_t launch_bf16_gemm(Bf16Search *s, int B, const __nv_bfloat16 *R16, int *status, cudaStream_t st) {
-    if (!s || B < 1 || B > kBM) return cudaErrorInvalidValue;
+cudaError_t bf16_scratch_reserve(const Bf16Search *s, int B, Bf16Scratch &x) {
+    if (B <= x.B_cap) return cudaSuccess;
+    bf16_scratch_free(x);
+    // tile maxima at the narrowest tile (128 atoms), block maxima over whole 256-atom tiles
+    cudaError_t e = dev_alloc((void **)&x.tile_max, sizeof(float) * (size_t)B * ((s->K + 127) / 128));
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.blk_max, sizeof(float) * (size_t)B * ((s->K + 255) / 256) * 8);
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.pairs, sizeof(int) * 2 * (size_t)B * kMaxRescan);
+    if (e != cudaSuccess) {
+        bf16_scratch_free(x);
+        return e;
+    }
+    x.B_cap = B;
+    return cudaSuccess;
+}
+
+cudaError_t launch_bf16_gemm(const Bf16Search *s, const Bf16Scratch &x, int B, const __nv_bfloat16 *R16, int *status,
+                             cudaStream_t st, unsigned long long wait_ns) {
+    if (!s || B < 1 || B > x.B_cap) return cudaErrorInvalidValue;
+    const int m_tiles = (B + kBM - 1) / kBM;
+    const bool astr = s->a_stream || m_tiles > 1;
+    const int ms = max_stages(s->bn, s->nkc, astr);
+    const int stages = s->stages < ms ? s->stages : ms;
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t chunk = (size_t)s->bn * kBK * 2;
+    const size_t smem = astr ? 1024 + (size_t)stages * (chunk + kAChunkBytes)
+                             : 1024 + (size_t)s->nkc * kAChunkBytes + (size_t)stages * chunk;
+    const int64_t ntiles = (s->K + s->bn - 1) / s->bn;
+    const int64_t items = ntiles * m_tiles;
+    const int grid = (int)(items < s->sm_count ? items : s->sm_count);
+    // the residual rows [m_tiles * 128][Lb] (rows past B are zero)
     CUtensorMap mapA;
-    if (!make_map(&mapA, R16, (uint64_t)s->Lb, (uint64_t)kBM, kBM)) return cudaErrorInvalidValue;
+    if (!make_map(&mapA, R16, (uint64_t)s->Lb, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
     if (s->bn == 256)
-        k_gemm_tilemax<256><<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB[1], s->K, s->nkc, s->stages,
-                                                                    s->a_stream, B, s->tile_max, s->blk_max, status);
+        k_gemm_tilemax<256><<<grid, kGemmThreads, smem, st>>>(mapA, s->mapB[1], s->K, s->nkc, stages, astr ? 1 : 0,
+                                                              B, m_tiles, x.tile_max, x.blk_max, status, wait_ns);
     else
-        k_gemm_tilemax<128><<<s->grid, kGemmThreads, s->smem, st>>>(mapA, s->mapB[0], s->K, s->nkc, s->stages,
-                                                                    s->a_stream, B, s->tile_max, s->blk_max, status);
+        k_gemm_tilemax<128><<<grid, kGemmThreads, smem, st>>>(mapA, s->mapB[0], s->K, s->nkc, stages, astr ? 1 : 0,
+                                                              B, m_tiles, x.tile_max, x.blk_max, status, wait_ns);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bf16_resolve(Bf16Search *s, int B, const float *D32, int Lp, int L, const float *R,
-                                unsigned long long *keys, int *fb_list, int *fb_count, long long *stats, int *status,
-                                int gemv_grid, cudaStream_t st) {
-    if (!s || B < 1 || B > kBM) return cudaErrorInvalidValue;
-    k_select<<<B, 256, 0, st>>>(s->ntiles, s->bn / 32, s->tile_max, s->blk_max, Lp, L, R, s->eps_bits, keys, fb_list,
-                                fb_count, s->pairs, stats);
+cudaError_t launch_bf16_resolve(const Bf16Search *s, const Bf16Scratch &x, int B, const float *D32, int Lp, int L,
+                                const float *R, unsigned long long *keys, int *fb_list, int *fb_count,
+                                long long *stats, int *status, int gemv_grid, cudaStream_t st,
+                                unsigned long long wait_ns) {
+    if (!s || B < 1 || B > x.B_cap) return cudaErrorInvalidValue;
+    const int64_t ntiles = (s->K + s->bn - 1) / s->bn;
+    k_select<<<B, 256, 0, st>>>(ntiles, s->bn / 32, x.tile_max, x.blk_max, Lp, L, R, s->eps_bits, keys, fb_list,
+                                fb_count, x.pairs, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_rescan<<<2 * s->sm_count, 256, 0, st>>>(D32, s->K, Lp, 32, R, s->pairs, fb_count, keys);
+    k_rescan<<<2 * s->sm_count, 256, 0, st>>>(D32, s->K, Lp, 32, R, x.pairs, fb_count, keys);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // FP32 full search for the channels with too many flagged blocks
-    return launch_gemv_argmax(D32, s->K, Lp, R, B, fb_list, fb_count, keys, status, gemv_grid, st);
+    return launch_gemv_argmax(D32, s->K, Lp, R, B, fb_list, fb_count, keys, status, gemv_grid, st, wait_ns);
 }
 
 }  // namespace act

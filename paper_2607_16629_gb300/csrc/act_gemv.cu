@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const float *__restrict__
                                                        const int *__restrict__ chlist,
                                                        const int *__restrict__ count_dev,
                                                        unsigned long long *__restrict__ keys,
-                                                       float *__restrict__ scores, int *status) {
+                                                       float *__restrict__ scores, int *status,
+                                                       unsigned long long wait_ns) {
     extern __shared__ __align__(128) float smem_r[];  // NB * Lp floats
     __shared__ __align__(8) uint64_t bar;
     __shared__ float red_s[kGemvThreads / 32][NB];
@@ -57,10 +58,12 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const float *__restrict__
                 bulk_g2s(smem_r + c * Lp, R + (int64_t)ch * Lp, (uint32_t)(Lp * 4), &bar);
             }
         }
-        const int timed_out = mbar_wait(&bar, parity) ? 0 : 1;
+        const int timed_out = mbar_wait(&bar, parity, wait_ns) ? 0 : 1;
         if (__syncthreads_or(timed_out)) {
-            if (threadIdx.x == 0) atomicOr(status, kFlagTimeout);
-            mbar_wait(&bar, parity);  // bounded: let an in-flight copy land before exiting
+            if (threadIdx.x == 0) {
+                atomicOr(status, kFlagTimeout);
+                mbar_drain(&bar, parity);  // bounded: let the in-flight copy land before exiting
+            }
             return;
         }
         parity ^= 1u;
@@ -183,36 +186,37 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const float *__restrict__
 template <int NV, int NB, bool WS>
 static cudaError_t gemv_instance(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                  const int *count_dev, unsigned long long *keys, float *scores, int *status,
-                                 int grid_ctas, cudaStream_t st) {
+                                 int grid_ctas, unsigned long long wait_ns, cudaStream_t st) {
     const size_t smem = (size_t)NB * Lp * sizeof(float);
     k_gemv<NV, NB, WS><<<grid_ctas, kGemvThreads, smem, st>>>(D, K, Lp, R, B, chlist, count_dev, keys, scores,
-                                                              status);
+                                                              status, wait_ns);
     return cudaGetLastError();
 }
 
 template <bool WS>
 static cudaError_t gemv_dispatch(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                  const int *count_dev, unsigned long long *keys, float *scores, int *status,
-                                 int grid_ctas, cudaStream_t st) {
+                                 int grid_ctas, unsigned long long wait_ns, cudaStream_t st) {
     const int nv = Lp / 128;
     // Several channels per pass over D only when the count is known on the host.
     const bool multi = (count_dev == nullptr) && B >= 4 && nv <= 4;
 #define ACT_GEMV_CASE(NVV)                                                                                 \
     case NVV:                                                                                              \
         return multi ? gemv_instance<NVV, 4, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, \
-                                                 grid_ctas, st)                                            \
+                                                 grid_ctas, wait_ns, st)                                   \
                      : gemv_instance<NVV, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, \
-                                                 grid_ctas, st);
+                                                 grid_ctas, wait_ns, st);
     switch (nv) {
         ACT_GEMV_CASE(1)
         ACT_GEMV_CASE(2)
         ACT_GEMV_CASE(3)
         ACT_GEMV_CASE(4)
         case 8:
-            return gemv_instance<8, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, grid_ctas, st);
+            return gemv_instance<8, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, grid_ctas,
+                                           wait_ns, st);
         case 16:
             return gemv_instance<16, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, grid_ctas,
-                                            st);
+                                            wait_ns, st);
         default:
             return cudaErrorInvalidValue;
     }
@@ -242,13 +246,13 @@ int gemv_max_ctas_per_sm(int Lp) {
 
 cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                const int *count_dev, unsigned long long *keys, int *status, int grid_ctas,
-                               cudaStream_t st) {
-    return gemv_dispatch<false>(D, K, Lp, R, B, chlist, count_dev, keys, nullptr, status, grid_ctas, st);
+                               cudaStream_t st, unsigned long long wait_ns) {
+    return gemv_dispatch<false>(D, K, Lp, R, B, chlist, count_dev, keys, nullptr, status, grid_ctas, wait_ns, st);
 }
 
 cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, int B, float *scores, int *status,
-                           int grid_ctas, cudaStream_t st) {
-    return gemv_dispatch<true>(D, K, Lp, R, B, nullptr, nullptr, nullptr, scores, status, grid_ctas, st);
+                           int grid_ctas, cudaStream_t st, unsigned long long wait_ns) {
+    return gemv_dispatch<true>(D, K, Lp, R, B, nullptr, nullptr, nullptr, scores, status, grid_ctas, wait_ns, st);
 }
 
 }  // namespace act

@@ -45,12 +45,14 @@ template <int NV>
 __global__ void __launch_bounds__(kStreamThreads, 1)
     k_gemv_stream(const float *__restrict__ D, int64_t K, int Lp, const float *__restrict__ R, int B,
                   const int *__restrict__ chlist, const int *__restrict__ count_dev,
-                  unsigned long long *__restrict__ keys, int rows_per_chunk, int stages, int *status) {
+                  unsigned long long *__restrict__ keys, int rows_per_chunk, int stages, int *status,
+                  unsigned long long wait_ns) {
     extern __shared__ __align__(128) float sm[];  // stages x rows_per_chunk x Lp
     __shared__ __align__(8) uint64_t full[kMaxStreamStages], empty[kMaxStreamStages];
     __shared__ float red_s[kConsumerWarps];
     __shared__ uint32_t red_i[kConsumerWarps];
     __shared__ int abort_sh;
+    __shared__ unsigned long long issued_sh;  // bulk copies issued by the producer so far (all channels)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int count = count_dev ? *count_dev : B;
     // this CTA's chunks: k-th is chunk blockIdx.x + k gridDim.x of the dictionary
@@ -65,6 +67,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             mbar_init(&empty[s], kConsumerWarps);
         }
         abort_sh = 0;
+        issued_sh = 0ull;
         fence_mbar_init();
     }
     __syncthreads();
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     const uint64_t it = (uint64_t)c * n_chunks + k;  // chunks issued over all channels
                     const int s = (int)(it % stages);
                     const uint32_t ph = (uint32_t)((it / stages) & 1);
-                    if (!mbar_wait(&empty[s], ph ^ 1u)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, wait_ns)) {
                         abort_sh = 1;
                         break;
                     }
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     const uint32_t bytes = (uint32_t)(nrows * Lp * 4);
                     mbar_expect_tx(&full[s], bytes);
                     bulk_g2s(sm + s * stage_floats, D + row * Lp, bytes, &full[s]);
+                    *(volatile unsigned long long *)&issued_sh = it + 1;
                 }
             }
         } else {
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 const uint64_t it = (uint64_t)c * n_chunks + k;
                 const int s = (int)(it % stages);
                 const uint32_t ph = (uint32_t)((it / stages) & 1);
-                const int ok = mbar_wait(&full[s], ph) ? 1 : 0;
+                const int ok = mbar_wait(&full[s], ph, wait_ns) ? 1 : 0;
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) abort_sh = 1;
                     break;
@@ -141,7 +145,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         if (abort_sh) {
             if (threadIdx.x == 0) {
                 atomicOr(status, kFlagTimeout);
-                for (int s = 0; s < stages; ++s) mbar_wait(&full[s], 0);  // bounded: copies in flight land
+                // let every copy in flight land before the CTA exits: stage s
+                // took issue numbers s, s + stages, ...; wait for the phase of
+                // its last one (a completed phase returns at once)
+                const unsigned long long n = issued_sh;
+                for (int s = 0; s < stages; ++s)
+                    if (n > (unsigned long long)s)
+                        mbar_drain(&full[s], (uint32_t)(((n - 1 - s) / (unsigned long long)stages) & 1ull));
             }
             return;
         }
@@ -162,7 +172,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 template <int NV>
 cudaError_t stream_instance(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                             const int *count_dev, unsigned long long *keys, int *status, int sm_count,
-                            cudaStream_t st) {
+                            cudaStream_t st, unsigned long long wait_ns) {
     const StreamShape sh = stream_shape(Lp);
     if (sh.stages < 2) return cudaErrorInvalidValue;
     const size_t smem = (size_t)sh.stages * sh.rows_per_chunk * Lp * sizeof(float);
@@ -172,7 +182,7 @@ cudaError_t stream_instance(const float *D, int64_t K, int Lp, const float *R, i
         cudaFuncSetAttribute(k_gemv_stream<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
     if (e != cudaSuccess) return e;
     k_gemv_stream<NV><<<sm_count, kStreamThreads, smem, st>>>(D, K, Lp, R, B, chlist, count_dev, keys,
-                                                              sh.rows_per_chunk, sh.stages, status);
+                                                              sh.rows_per_chunk, sh.stages, status, wait_ns);
     return cudaGetLastError();
 }
 
@@ -180,14 +190,14 @@ cudaError_t stream_instance(const float *D, int64_t K, int Lp, const float *R, i
 
 cudaError_t launch_gemv_stream_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                       const int *count_dev, unsigned long long *keys, int *status, int sm_count,
-                                      cudaStream_t st) {
+                                      cudaStream_t st, unsigned long long wait_ns) {
     switch (Lp / 128) {
-        case 1: return stream_instance<1>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st);
-        case 2: return stream_instance<2>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st);
-        case 3: return stream_instance<3>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st);
-        case 4: return stream_instance<4>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st);
-        case 8: return stream_instance<8>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st);
-        case 16: return stream_instance<16>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st);
+        case 1: return stream_instance<1>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
+        case 2: return stream_instance<2>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
+        case 3: return stream_instance<3>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
+        case 4: return stream_instance<4>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
+        case 8: return stream_instance<8>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
+        case 16: return stream_instance<16>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
         default: return cudaErrorInvalidValue;
     }
 }

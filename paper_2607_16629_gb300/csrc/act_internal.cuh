@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "../../include/act.h"
+#include "act_device.cuh"
 
 namespace act {
 
@@ -84,6 +85,11 @@ __host__ __device__ inline uint32_t key_index(unsigned long long key) {
 }
 
 constexpr int kGemvThreads = 256;
+
+// Every device allocation of the library goes through dev_alloc (act_api.cu),
+// so that act_inject_alloc_failure can make one of them fail as if the
+// device were out of memory.
+cudaError_t dev_alloc(void **p, size_t bytes);
 constexpr int kUpdateThreads = 256;
 constexpr int kMaxSamples = 2048;
 constexpr int kRowAlign = 128;   // FP32 row stride granule (floats)
@@ -95,11 +101,13 @@ cudaError_t launch_gen_atoms(const GridAxes &ax, int64_t K, int Lp, float *d32, 
                              cudaStream_t st);
 cudaError_t launch_init(const float *sig, int B, int L, int Lp, float *R, __nv_bfloat16 *R16, int Lb,
                         unsigned long long *keys, double *energy, int P1, int *status, cudaStream_t st);
+// wait_ns (here and below): limit of each bounded device-side wait.
 cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B,
                                const int *chlist, const int *count_dev, unsigned long long *keys,
-                               int *status, int grid_ctas, cudaStream_t st);
+                               int *status, int grid_ctas, cudaStream_t st,
+                               unsigned long long wait_ns = kWaitLimitNs);
 cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, int B, float *scores,
-                           int *status, int grid_ctas, cudaStream_t st);
+                           int *status, int grid_ctas, cudaStream_t st, unsigned long long wait_ns = kWaitLimitNs);
 cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
                           float *coefs, double *energy, int *fb_count, cudaStream_t st);
@@ -112,7 +120,7 @@ cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, 
 // shared memory, one CTA per SM (act_gemv_stream.cu); same scores, same keys.
 cudaError_t launch_gemv_stream_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                       const int *count_dev, unsigned long long *keys, int *status, int sm_count,
-                                      cudaStream_t st);
+                                      cudaStream_t st, unsigned long long wait_ns = kWaitLimitNs);
 int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
 int gemv_max_ctas_per_sm(int Lp);
 
@@ -199,7 +207,8 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 // sized for B; the count is read after the wait on the previous kernel).
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
                                 float *scores, int *status, bool early_launch, cudaStream_t st,
-                                const int *chlist = nullptr, const int *count_dev = nullptr);
+                                const int *chlist = nullptr, const int *count_dev = nullptr,
+                                unsigned long long wait_ns = kWaitLimitNs);
 // Coefficient and residual update (Eq. (4)) with the selected atom read back
 // from its template; lets the next search launch early (programmatic
 // dependent launch).
@@ -209,13 +218,31 @@ cudaError_t launch_shift_update(const ShiftPlan &sp, const GridAxes &ax, int Lp,
                                 int *counters, cudaStream_t st, bool pdl = false);
 
 // ---- tensor-core template search (act_shift_tc.cu) -------------------------
+// ShiftTc holds what a template build fixes (tensor maps of the BF16
+// templates, pipeline depths); ShiftTcScratch the per-call buffers, owned by
+// the work buffers of whoever launches (a grid, or one group of a ragged
+// plan), so that graphs recorded on different work buffers share nothing
+// that can be reallocated.
 struct ShiftTc;
+struct ShiftTcScratch {
+    float *tile_max = nullptr;      // [rows][T_pad / 128]: per (row, template tile)
+    float *blk_max = nullptr;       // [rows][T_pad / 32] maxima per 32-template block
+    int *items = nullptr;           // [B_cap * 1024][2] flagged (channel, item) pairs
+    __nv_bfloat16 *X = nullptr;     // [rows_alloc][Kt] shifted BF16 residual rows
+    double2 *chan_norm = nullptr;   // [B_cap] |r|, |bf16(r) - r|
+    unsigned int *chmax = nullptr;  // [B_cap] largest tile maximum (float bits)
+    int *chcount = nullptr;         // [B_cap] items flagged this order
+    int B_cap = 0;
+    int rows_alloc = 0;
+};
 // Tensor maps and pipeline depth for the BF16 templates of sp (which must
 // hold tpl16, scaleT and eps_bits); cudaErrorNotSupported without them.
 cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count);
 void shift_tc_free(ShiftTc *s);
-// Shifted-residual, tile-maximum and item buffers for up to B channels.
-cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B);
+// Grows x to hold up to B channels (frees and reallocates: the caller drops
+// every graph that captured x first).
+cudaError_t shift_tc_reserve(const ShiftTc *s, const ShiftPlan &sp, int B, ShiftTcScratch &x);
+void shift_tc_scratch_free(ShiftTcScratch &x);
 // One search order: shifted residual rows + tcgen05 GEMM (tile maxima of the
 // scaled scores), then item selection and FP32 rescore of the flagged items;
 // a channel with too many flagged items is queued in fb_list and searched in
@@ -225,17 +252,28 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B);
 // pdl: the first kernel of each call follows a kernel node directly (no
 // event node between), so it may be a programmatic dependent; the kernels
 // inside a call always are.
-cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
-                                 long long *stats, int *status, cudaStream_t st, bool pdl = false);
-cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
-                                    unsigned long long *keys, int *fb_list, int *counters, long long *stats,
-                                    int *status, cudaStream_t st, bool pdl = false);
+cudaError_t launch_shift_tc_gemm(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
+                                 int Lp, int L, int B, long long *stats, int *status, cudaStream_t st, bool pdl = false,
+                                 unsigned long long wait_ns = kWaitLimitNs);
+cudaError_t launch_shift_tc_resolve(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
+                                    int Lp, int L, int B, unsigned long long *keys, int *fb_list, int *counters,
+                                    long long *stats, int *status, cudaStream_t st, bool pdl = false,
+                                    unsigned long long wait_ns = kWaitLimitNs);
 
 // ---- tensor-core search (act_gemm.cu) -------------------------------------
+// Bf16Search holds what a BF16 dictionary build fixes (tensor maps, tile
+// configuration); Bf16Scratch the per-call maxima and rescan lists, owned by
+// the caller's work buffers (as ShiftTcScratch).
 struct Bf16Search;
+struct Bf16Scratch {
+    float *tile_max = nullptr;  // [B_cap][K / 128 rounded up]
+    float *blk_max = nullptr;   // [B_cap][K / 32 rounded up to whole 256-atom tiles]
+    int *pairs = nullptr;       // [B_cap * 512][2] flagged (channel, block) pairs
+    int B_cap = 0;
+};
 // Prepares the tensor-core search over the BF16 dictionary d16 [K][Lb]
-// (tensor map, partial top-k buffers).  Returns cudaErrorNotSupported when
-// the shape is outside what the kernel handles.
+// (tensor maps, tile configuration).  Returns cudaErrorNotSupported when the
+// shape is outside what the kernel handles.
 // eps_bits: device word holding (as float bits) the largest |bf16(g) - g|_2
 // over the dictionary, written by the atom generator.
 cudaError_t bf16_search_prepare(Bf16Search **out, const __nv_bfloat16 *d16, int64_t K, int Lb, int sm_count,
@@ -246,13 +284,19 @@ void bf16_search_free(Bf16Search *s);
 cudaError_t bf16_search_configure(Bf16Search *s, int bn, int stages);
 void bf16_search_get_config(const Bf16Search *s, int *bn, int *stages, int *max_stages);
 int bf16_search_max_stages(const Bf16Search *s, int bn);
-// One search order for B <= 128 channels, in two launches sequences:
-// the tensor-core GEMM writing per-tile maxima, then tile selection, FP32
-// rescan of the flagged tiles and the FP32 full search for channels with too
-// many of them.  Leaves the packed selection key of every channel in keys[].
-cudaError_t launch_bf16_gemm(Bf16Search *s, int B, const __nv_bfloat16 *R16, int *status, cudaStream_t st);
-cudaError_t launch_bf16_resolve(Bf16Search *s, int B, const float *D32, int Lp, int L, const float *R,
-                                unsigned long long *keys, int *fb_list, int *fb_count, long long *stats, int *status,
-                                int gemv_grid, cudaStream_t st);
+// Grows x to hold up to B channels (frees and reallocates, as shift_tc_reserve).
+cudaError_t bf16_scratch_reserve(const Bf16Search *s, int B, Bf16Scratch &x);
+void bf16_scratch_free(Bf16Scratch &x);
+// One search order for B channels (any number: 128-channel row tiles), in
+// two launch sequences: the tensor-core GEMM writing per-tile and per-block
+// maxima, then tile selection, FP32 rescan of the flagged blocks and the FP32
+// full search for channels with too many of them.  Leaves the packed
+// selection key of every channel in keys[].
+cudaError_t launch_bf16_gemm(const Bf16Search *s, const Bf16Scratch &x, int B, const __nv_bfloat16 *R16, int *status,
+                             cudaStream_t st, unsigned long long wait_ns = kWaitLimitNs);
+cudaError_t launch_bf16_resolve(const Bf16Search *s, const Bf16Scratch &x, int B, const float *D32, int Lp, int L,
+                                const float *R, unsigned long long *keys, int *fb_list, int *fb_count,
+                                long long *stats, int *status, int gemv_grid, cudaStream_t st,
+                                unsigned long long wait_ns = kWaitLimitNs);
 
 }  // namespace act

@@ -66,6 +66,7 @@ struct ShiftArgs {
     unsigned long long *keys;
     float *scores;  // non-null: write every score to scores[b * K + flat] instead of selecting
     int *status;
+    unsigned long long wait_ns;  // limit of each bounded wait
     // non-null: search only the channels chlist[0 .. *count_dev) (the count
     // is read after the wait on the previous kernel)
     const int *chlist;
@@ -289,13 +290,13 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
             }
             const int s = c % NS;
             const uint32_t parity = (uint32_t)((c / NS) & 1);
-            const int ok = mbar_wait(&bar[s], parity);
+            const int ok = mbar_wait(&bar[s], parity, A.wait_ns);
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) {
                     atomicOr(A.status, kFlagTimeout);
                     // bounded: let the copies in flight land before exiting
                     for (int cc = c; cc < c + NS && cc < n_chunks; ++cc)
-                        mbar_wait(&bar[cc % NS], (uint32_t)((cc / NS) & 1));
+                        mbar_drain(&bar[cc % NS], (uint32_t)((cc / NS) & 1));
                 }
                 return;
             }
@@ -558,7 +559,7 @@ cudaError_t launch_shift_build(const ShiftPlan &sp, const GridAxes &ax, unsigned
 
 cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int L, int B, unsigned long long *keys,
                                 float *scores, int *status, bool early_launch, cudaStream_t st, const int *chlist,
-                                const int *count_dev) {
+                                const int *count_dev, unsigned long long wait_ns) {
     if (sp.J == 0 || !sp.tpl || (count_dev && !chlist)) return cudaErrorInvalidValue;
     ShiftArgs A;
     A.tpl = sp.tpl;
@@ -583,6 +584,7 @@ cudaError_t launch_shift_search(const ShiftPlan &sp, const float *R, int Lp, int
     A.keys = keys;
     A.scores = scores;
     A.status = status;
+    A.wait_ns = wait_ns;
     A.chlist = chlist;
     A.count_dev = count_dev;
     const int64_t units = (int64_t)B * sp.G * sp.TB;

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_shift_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowTiling tl,
                  int n_tiles, int nkc, int stages, int T_pad, const float *__restrict__ scaleT,
                  float *__restrict__ tile_max, float *__restrict__ blk_max, unsigned int *__restrict__ chmax,
-                 int *status) {
+                 int *status, unsigned long long wait_ns) {
     // shared memory: stages, then the item's scales [Jt][BN + 4] (the +4
     // floats of padding spread the Jt rows a warp reads over the banks)
     using Cfg = ShiftTile<BN>;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kc = kc_lo; kc <= kc_hi; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
-                if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u)) {
+                if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u, wait_ns)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t it = 0, local = 0;
         for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++local) {
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            if (!mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u)) {
+            if (!mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u, wait_ns)) {
                 *abort_flag = 1;
                 break;
             }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kc = kc_lo; kc <= kc_hi; ++kc, ++it) {
                 const int s = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
-                if (!mbar_wait(&sm.bar_full[s], ph)) {
+                if (!mbar_wait(&sm.bar_full[s], ph, wait_ns)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            const int failed = (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph)) ? 1 : 0;
+            const int failed = (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph, wait_ns)) ? 1 : 0;
             if (epilogue_bar_or(failed)) {  // the epilogue warps leave together
                 *abort_flag = 1;
                 break;
@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(256) k_shift_flag(int Ntc, int n_tiles, int bp
 __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
     const float *__restrict__ tpl, const float *__restrict__ scale, int S, int Sa, int P, int rows, int NtcP,
     int Ntc, int T, int n_blocks, int Lp, int L, const float *__restrict__ R, const int *__restrict__ items,
-    const int *__restrict__ counters, unsigned long long *__restrict__ keys, int *status) {
+    const int *__restrict__ counters, unsigned long long *__restrict__ keys, int *status,
+    unsigned long long wait_ns) {
     extern __shared__ __align__(128) float sm[];  // per warp: the residual [Lp], then 2 x [P][32] rows
     __shared__ __align__(8) uint64_t bar[kRescanWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
                 bulk_g2s(buf0 + (size_t)(cb ^ 1) * P * 32, src + (size_t)(a + 1) * rows * 32, bytes,
                          &bar[warp][cb ^ 1]);
             }
-            ok = mbar_wait(&bar[warp][cb], uses[cb] & 1u) ? 1 : 0;
+            ok = mbar_wait(&bar[warp][cb], uses[cb] & 1u, wait_ns) ? 1 : 0;
             ++uses[cb];
             if (!__all_sync(0xffffffffu, ok)) {
                 ok = 0;
@@ -511,8 +512,8 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
                 atomicOr(status, kFlagTimeout);
                 // bounded: let the copies in flight land before the warp leaves
                 const int cb = fail_a & 1;
-                mbar_wait(&bar[warp][cb], (uses[cb] - 1) & 1u);
-                if (fail_a + 1 < Sa) mbar_wait(&bar[warp][cb ^ 1], uses[cb ^ 1] & 1u);
+                mbar_drain(&bar[warp][cb], (uses[cb] - 1) & 1u);
+                if (fail_a + 1 < Sa) mbar_drain(&bar[warp][cb ^ 1], uses[cb ^ 1] & 1u);
             }
             return;
         }
@@ -543,18 +544,8 @@ struct ShiftTc {
     int nkc = 0, sm_count = 0, T_pad = 0;
     int stages[2] = {0, 0};
     size_t smem[2] = {0, 0};
-    int n_tiles = 0, bn = 0;  // of the current launch: n_tiles = T_pad / bn
-    float *tile_max = nullptr;      // [rows_cap][n_tiles]
-    float *blk_max = nullptr;       // [rows_cap][T_pad / 32] maxima per 32-template block
-    int *items = nullptr;           // [B_cap * kMaxItems][2]
-    __nv_bfloat16 *X = nullptr;     // [rows_cap rounded up to 128][Kt]
-    int B_cap = 0;
-    int rows_alloc = 0;
     int rescan_warps = 0, rescan_blocks_per_sm = 0;
     size_t rescan_smem = 0;
-    double2 *chan_norm = nullptr;   // [B_cap] |r|, |bf16(r) - r|
-    unsigned int *chmax = nullptr;  // [B_cap] largest tile maximum (float bits)
-    int *chcount = nullptr;         // [B_cap] items flagged this order
 };
 
 cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
@@ -601,16 +592,17 @@ cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
     return cudaSuccess;
 }
 
-void shift_tc_free(ShiftTc *s) {
-    if (!s) return;
-    if (s->tile_max) cudaFree(s->tile_max);
-    if (s->blk_max) cudaFree(s->blk_max);
-    if (s->items) cudaFree(s->items);
-    if (s->X) cudaFree(s->X);
-    if (s->chan_norm) cudaFree(s->chan_norm);
-    if (s->chmax) cudaFree(s->chmax);
-    if (s->chcount) cudaFree(s->chcount);
-    delete s;
+void shift_tc_free(ShiftTc *s) { delete s; }
+
+void shift_tc_scratch_free(ShiftTcScratch &x) {
+    if (x.tile_max) cudaFree(x.tile_max);
+    if (x.blk_max) cudaFree(x.blk_max);
+    if (x.items) cudaFree(x.items);
+    if (x.X) cudaFree(x.X);
+    if (x.chan_norm) cudaFree(x.chan_norm);
+    if (x.chmax) cudaFree(x.chmax);
+    if (x.chcount) cudaFree(x.chcount);
+    x = ShiftTcScratch();
 }
 
 // Row tiling for B channels: Bg channels x Jt time centres per 128-row tile,
@@ -635,23 +627,10 @@ static RowTiling make_tiling(const ShiftPlan &sp, int B) {
 }
 
 // Buffers for B channels (kept when large enough).
-cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
-    if (B <= s->B_cap) return cudaSuccess;
-    if (s->tile_max) cudaFree(s->tile_max);
-    if (s->blk_max) cudaFree(s->blk_max);
-    if (s->items) cudaFree(s->items);
-    if (s->X) cudaFree(s->X);
-    if (s->chan_norm) cudaFree(s->chan_norm);
-    if (s->chmax) cudaFree(s->chmax);
-    if (s->chcount) cudaFree(s->chcount);
-    s->tile_max = nullptr;
-    s->blk_max = nullptr;
-    s->items = nullptr;
-    s->X = nullptr;
-    s->chan_norm = nullptr;
-    s->chmax = nullptr;
-    s->chcount = nullptr;
-    s->B_cap = 0;
+cudaError_t shift_tc_reserve(const ShiftTc *s, const ShiftPlan &sp, int B, ShiftTcScratch &x) {
+    (void)s;
+    if (B <= x.B_cap) return cudaSuccess;
+    shift_tc_scratch_free(x);
     const int64_t rows = (int64_t)B * sp.Ntc;
     int64_t rows_alloc = 0;  // the largest row-tile count of any B' <= B
     for (int b2 = 1; b2 <= B; ++b2) {
@@ -659,83 +638,99 @@ cudaError_t shift_tc_reserve(ShiftTc *s, const ShiftPlan &sp, int B) {
         rows_alloc = r2 > rows_alloc ? r2 : rows_alloc;
     }
     if (rows_alloc > (1ll << 30)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMalloc(&s->tile_max, sizeof(float) * (size_t)rows * (sp.T_pad / 128));
-    if (e == cudaSuccess) e = cudaMalloc(&s->blk_max, sizeof(float) * (size_t)rows * (sp.T_pad / 32));
-    if (e == cudaSuccess) e = cudaMalloc(&s->items, sizeof(int) * 2 * (size_t)B * kMaxItems);
-    if (e == cudaSuccess) e = cudaMalloc(&s->X, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
-    if (e == cudaSuccess) e = cudaMemset(s->X, 0, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
-    if (e == cudaSuccess) e = cudaMalloc(&s->chan_norm, sizeof(double2) * (size_t)B);
-    if (e == cudaSuccess) e = cudaMalloc(&s->chmax, sizeof(unsigned int) * (size_t)B);
-    if (e == cudaSuccess) e = cudaMalloc(&s->chcount, sizeof(int) * (size_t)B);
+    cudaError_t e = dev_alloc((void **)&x.tile_max, sizeof(float) * (size_t)rows * (sp.T_pad / 128));
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.blk_max, sizeof(float) * (size_t)rows * (sp.T_pad / 32));
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.items, sizeof(int) * 2 * (size_t)B * kMaxItems);
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.X, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
+    if (e == cudaSuccess) e = cudaMemset(x.X, 0, sizeof(__nv_bfloat16) * (size_t)rows_alloc * sp.Kt);
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.chan_norm, sizeof(double2) * (size_t)B);
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.chmax, sizeof(unsigned int) * (size_t)B);
+    if (e == cudaSuccess) e = dev_alloc((void **)&x.chcount, sizeof(int) * (size_t)B);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        shift_tc_scratch_free(x);
         return cudaErrorMemoryAllocation;
     }
-    s->B_cap = B;
-    s->rows_alloc = (int)rows_alloc;
+    x.B_cap = B;
+    x.rows_alloc = (int)rows_alloc;
     return cudaSuccess;
 }
 
-cudaError_t launch_shift_tc_gemm(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
-                                 long long *stats, int *status, cudaStream_t st, bool pdl) {
-    if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
-    const RowTiling tl = make_tiling(sp, B);
-    cudaError_t e = launch_kernel(k_shift_rows, dim3(tl.m_tiles * kBM), dim3(128), 0, st, pdl, tl, R, Lp, sp.tc0,
-                                  sp.m_lo, sp.Kt, s->X, s->chan_norm, s->chmax, s->chcount, stats);
-    if (e != cudaSuccess) return e;
-    const int m_tiles = tl.m_tiles;
-    CUtensorMap mapA;
-    auto smem_for = [&](int bn, int stage_bytes, int *stages) {
+// Template tile width of a B-channel launch: 256 unless that leaves SMs
+// idle or leaves room for fewer than two stages beside the tile's scale rows.
+static int shift_tc_bn(const ShiftTc *s, const ShiftPlan &sp, const RowTiling &tl, int *stages, size_t *smem) {
+    auto smem_for = [&](int bn, int stage_bytes, int *stg_out) {
         const size_t sc = (size_t)tl.Jt * (bn + 4) * sizeof(float);
         int stg = (int)((kSmemBudget - (int64_t)sc) / stage_bytes);
         stg = stg > kMaxStages ? kMaxStages : stg;
-        *stages = stg;
+        *stg_out = stg;
         return 1024 + (size_t)stg * stage_bytes + sc;
     };
-    if (!make_map(&mapA, s->X, (uint64_t)sp.Kt, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
-    // 256-template tiles unless they leave SMs idle or leave room for fewer
-    // than two stages beside the tile's scale rows
     int st256 = 0;
-    smem_for(256, ShiftTile<256>::kStageBytes, &st256);
-    const int bn = (int64_t)m_tiles * (sp.T_pad / 256) >= s->sm_count && st256 >= 2 ? 256 : 128;
-    const int i = bn == 256 ? 1 : 0;
-    s->bn = bn;
-    s->n_tiles = sp.T_pad / bn;
-    const int64_t items = (int64_t)m_tiles * s->n_tiles;
-    const int grid = (int)(items < s->sm_count ? items : s->sm_count);
+    const size_t sm256 = smem_for(256, ShiftTile<256>::kStageBytes, &st256);
+    if ((int64_t)tl.m_tiles * (sp.T_pad / 256) >= s->sm_count && st256 >= 2) {
+        *stages = st256;
+        *smem = sm256;
+        return 256;
+    }
+    *smem = smem_for(128, ShiftTile<128>::kStageBytes, stages);
+    return 128;
+}
+
+cudaError_t launch_shift_tc_gemm(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
+                                 int Lp, int L, int B, long long *stats, int *status, cudaStream_t st, bool pdl,
+                                 unsigned long long wait_ns) {
+    if (!s || B < 1 || B > x.B_cap) return cudaErrorInvalidValue;
+    const RowTiling tl = make_tiling(sp, B);
+    cudaError_t e = launch_kernel(k_shift_rows, dim3(tl.m_tiles * kBM), dim3(128), 0, st, pdl, tl, R, Lp, sp.tc0,
+                                  sp.m_lo, sp.Kt, x.X, x.chan_norm, x.chmax, x.chcount, stats);
+    if (e != cudaSuccess) return e;
+    const int m_tiles = tl.m_tiles;
+    CUtensorMap mapA;
+    if (!make_map(&mapA, x.X, (uint64_t)sp.Kt, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
     int stages = 0;
-    const size_t smem = bn == 256 ? smem_for(256, ShiftTile<256>::kStageBytes, &stages)
-                                  : smem_for(128, ShiftTile<128>::kStageBytes, &stages);
+    size_t smem = 0;
+    const int bn = shift_tc_bn(s, sp, tl, &stages, &smem);
+    const int i = bn == 256 ? 1 : 0;
+    const int n_tiles = sp.T_pad / bn;
+    const int64_t items = (int64_t)m_tiles * n_tiles;
+    const int grid = (int)(items < s->sm_count ? items : s->sm_count);
     if (stages < 2) return cudaErrorInvalidValue;
     // a programmatic dependent of the shifted-row build (set-up overlaps it)
     return launch_kernel(bn == 256 ? k_shift_gemm<256> : k_shift_gemm<128>, dim3(grid), dim3(kThreads), smem, st, true,
-                         mapA, s->mapB[i], tl, s->n_tiles, s->nkc, stages, sp.T_pad, sp.scaleT, s->tile_max,
-                         s->blk_max, s->chmax, status);
+                         mapA, s->mapB[i], tl, n_tiles, s->nkc, stages, sp.T_pad, sp.scaleT, x.tile_max, x.blk_max,
+                         x.chmax, status, wait_ns);
 }
 
-cudaError_t launch_shift_tc_resolve(ShiftTc *s, const ShiftPlan &sp, const float *R, int Lp, int L, int B,
-                                    unsigned long long *keys, int *fb_list, int *counters, long long *stats,
-                                    int *status, cudaStream_t st, bool pdl) {
-    if (!s || B < 1 || B > s->B_cap) return cudaErrorInvalidValue;
-    const int entries = sp.Ntc * s->n_tiles;
+cudaError_t launch_shift_tc_resolve(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
+                                    int Lp, int L, int B, unsigned long long *keys, int *fb_list, int *counters,
+                                    long long *stats, int *status, cudaStream_t st, bool pdl,
+                                    unsigned long long wait_ns) {
+    if (!s || B < 1 || B > x.B_cap) return cudaErrorInvalidValue;
+    const RowTiling tl = make_tiling(sp, B);
+    int stages = 0;
+    size_t smem = 0;
+    const int bn = shift_tc_bn(s, sp, tl, &stages, &smem);  // the GEMM's tile width for B channels
+    const int n_tiles = sp.T_pad / bn;
+    const int entries = sp.Ntc * n_tiles;
     int slices = (entries + 255) / 256;
     const int max_slices = (4 * s->sm_count + B - 1) / B;
     if (slices > max_slices) slices = max_slices;
-    cudaError_t e = launch_kernel(k_shift_flag, dim3(slices, B), dim3(256), 0, st, pdl, sp.Ntc, s->n_tiles, s->bn / 32,
-                                  sp.Kt, L, (const float *)s->tile_max, (const float *)s->blk_max,
-                                  (const double2 *)s->chan_norm, (const unsigned int *)s->chmax,
-                                  (const unsigned int *)sp.eps_bits, s->chcount, fb_list, counters, s->items, stats);
+    cudaError_t e = launch_kernel(k_shift_flag, dim3(slices, B), dim3(256), 0, st, pdl, sp.Ntc, n_tiles, bn / 32,
+                                  sp.Kt, L, (const float *)x.tile_max, (const float *)x.blk_max,
+                                  (const double2 *)x.chan_norm, (const unsigned int *)x.chmax,
+                                  (const unsigned int *)sp.eps_bits, x.chcount, fb_list, counters, x.items, stats);
     if (e != cudaSuccess) return e;
     e = launch_kernel(k_shift_rescan, dim3(s->sm_count * s->rescan_blocks_per_sm), dim3(s->rescan_warps * 32),
                       s->rescan_smem, st, true, (const float *)sp.tpl, (const float *)sp.scale, sp.S, sp.Sa, sp.P,
-                      sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, Lp, L, R, (const int *)s->items,
-                      (const int *)counters, keys, status);
+                      sp.rows, sp.NtcP, sp.Ntc, sp.T, sp.T_pad / 32, Lp, L, R, (const int *)x.items,
+                      (const int *)counters, keys, status, wait_ns);
     if (e != cudaSuccess) return e;
     // channels with more than kMaxItems flagged items: the FP32 template
     // search over the queue, launched early (its CTAs become resident while
     // the rescore runs and read the queue after it; an empty queue leaves
     // them idle)
-    return launch_shift_search(sp, R, Lp, L, B, keys, nullptr, status, true, st, fb_list, &counters[0]);
+    return launch_shift_search(sp, R, Lp, L, B, keys, nullptr, status, true, st, fb_list, &counters[0], wait_ns);
 }
 
 

@@ -78,17 +78,6 @@ class Grid:
     def n_atoms(self) -> int:
         return self.tc.count * self.fc.count * self.logdt.count * self.c.count
 
-    def params_of(self, flat: int) -> Tuple[float, float, float, float]:
-        flat = int(flat)
-        ic = flat % self.c.count
-        flat //= self.c.count
-        il = flat % self.logdt.count
-        flat //= self.logdt.count
-        ifc = flat % self.fc.count
-        itc = flat // self.fc.count
-        return (self.tc.lo + itc * self.tc.step, self.fc.lo + ifc * self.fc.step,
-                self.logdt.lo + il * self.logdt.step, self.c.lo + ic * self.c.step)
-
     def flat_of(self, itc: int, ifc: int, il: int, ic: int) -> int:
         return ((itc * self.fc.count + ifc) * self.logdt.count + il) * self.c.count + ic
 
@@ -245,8 +234,11 @@ def workload_c1(channels: int = 1) -> Workload:
         rng = rng_for(1, ch)
         idx = rng.choice(g.n_atoms, size=3, replace=False)
         truth = []
+        axes = (g.tc, g.fc, g.logdt, g.c)
         for i in idx:
-            tc, fc, ld, c = g.params_of(int(i))
+            # the grid point of that position (c fastest, tc slowest)
+            pos = np.unravel_index(int(i), tuple(a.count for a in axes))
+            tc, fc, ld, c = (float(a.values()[k]) for a, k in zip(axes, pos))
             truth.append((tc, fc, ld, c, rng.uniform(0.5, 2.0)))
         s = _assemble(truth, g.n_samples, g.fs) + 0.05 * white_noise(rng, g.n_samples)
         sigs.append(s)

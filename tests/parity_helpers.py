@@ -6,6 +6,8 @@ oracle's top-two |scores| on the same residual differ by more than 1e-5
 relative; coefficients and residual energies must agree within 1e-5
 relative.  Near the noise floor the relative bound is measured against the
 residual norm instead (absolute floor ATOL_REL * |r|)."""
+import functools
+
 import numpy as np
 import torch
 
@@ -81,3 +83,12 @@ def check_lockstep(score_fn, rs, idx, coef, energy=None, dictionary_row=None):
             assert abs(energy[k + 1] - e_ref) <= RTOL * e_ref + 4 * ATOL_REL * rn * rn, \
                 f"order {k}: energy {energy[k + 1]} vs {e_ref}"
     return ties
+
+
+@functools.lru_cache(maxsize=1)
+def full_dictionary(grid):
+    """The oracle's FP64 dictionary of a grid, built once per test session
+    (the 2,097,152-atom EEG-like grid takes 8.6 GB of host memory)."""
+    D, deg = oracle.dictionary(grid)
+    assert not deg.any()
+    return D

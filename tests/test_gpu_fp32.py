@@ -6,7 +6,8 @@ import torch
 
 import oracle
 from paper_2607_16629_gb300 import act, synth
-from parity_helpers import (ATOL_REL, RTOL, check_lockstep, gpu_decompose, gpu_residual_chain)
+from parity_helpers import (ATOL_REL, RTOL, check_lockstep, full_dictionary, gpu_decompose,
+                            gpu_residual_chain)
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +79,7 @@ def test_atoms_full_eeg_grid_sampled():
     with Grid(grid) as h:
         for i in rows:
             g = _rows(h, grid, int(i), 1)[0]
-            ref, _ = oracle.atom(*grid.params_of(int(i)), grid.fs, grid.n_samples)
+            ref, _ = oracle.atom(*oracle.atom_params(grid, int(i)), grid.fs, grid.n_samples)
             assert np.max(np.abs(g - ref)) <= ATOM_ATOL, i
 
 
@@ -127,7 +128,7 @@ def test_mp_lockstep(name, grid, P):
     assert np.array_equal(rs[-1], resid[0])
     check_lockstep(lambda r: D @ r, rs, idx[0], coef[0], energy[0], lambda i: D[i])
     for k in range(P):
-        assert par[0, k] == pytest.approx(grid.params_of(idx[0, k]), abs=0)
+        assert par[0, k] == pytest.approx(oracle.atom_params(grid, idx[0, k]), abs=0)
 
 
 def test_mp_matches_oracle_trajectory_c1():
@@ -194,7 +195,7 @@ def test_energy_identity_and_monotone_on_gpu():
 def test_lone_on_grid_atom_recovered():
     grid = synth.grid_c1()
     for j, a in [(0, 1.3), (9999, -0.7), (grid.n_atoms - 1, 2.0)]:
-        g, _ = oracle.atom(*grid.params_of(j), grid.fs, grid.n_samples)
+        g, _ = oracle.atom(*oracle.atom_params(grid, j), grid.fs, grid.n_samples)
         with Grid(grid) as h:
             idx, _, coef, resid, energy = gpu_decompose(h, (a * g)[None, :], 1)
         assert idx[0, 0] == j
@@ -254,19 +255,25 @@ def test_window_lengths(L):
     check_lockstep(lambda r: D @ r, rs, idx[0], coef[0], energy[0], lambda i: D[i])
 
 
-def test_full_eeg_grid_lockstep_first_orders():
-    """The 2,097,152-atom EEG-like workload at full size, in the launch
-    configuration the benchmark times: the first orders are checked
-    against the oracle scoring every atom (regenerated on the fly)."""
+@pytest.mark.parametrize("gemv", ["load_stream", "bulk_stream"])
+def test_full_eeg_grid_lockstep_all_orders(gemv):
+    """The 2,097,152-atom EEG-like workload at full size, all 20 orders, in
+    both FP32 GEMV forms (the benchmark times the bulk-copy streaming GEMV):
+    every order is checked against the oracle scoring every atom of its FP64
+    dictionary from the GPU's own residual."""
     w = synth.workload_c2()
     P = w.n_atoms
     s = w.signals[0]
+    D = full_dictionary(w.grid)
     with Grid(w.grid) as h:
+        if gemv == "bulk_stream":
+            act.act_set_tuning(h, -1)
         idx, _, coef, resid, energy = gpu_decompose(h, s[None, :], P)
-        rs, cidx, ccoef = gpu_residual_chain(h, s, 4)
-    assert np.array_equal(cidx, idx[0, :4])
-    check_lockstep(lambda r: oracle.scores_grid(w.grid, r), rs, cidx, ccoef)
-    # every order: energy identity and monotone residual (property at any size)
+        rs, cidx, ccoef = gpu_residual_chain(h, s, P)
+    assert np.array_equal(cidx, idx[0]) and np.array_equal(ccoef, coef[0])
+    ties = check_lockstep(lambda r: D @ r, rs, cidx, ccoef, energy[0], lambda i: D[i])
+    print(f"{gemv}: {ties} near-ties in {P} orders")
+    # every order: energy identity and monotone residual
     e0 = energy[0, 0]
     for k in range(P + 1):
         assert abs(e0 - (np.sum(coef[0, :k].astype(np.float64) ** 2) + energy[0, k])) <= 1e-5 * e0

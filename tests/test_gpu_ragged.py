@@ -1,12 +1,15 @@
 """GPU checks of uneven batches (channels of different window lengths in one
 plan): the plan's outputs equal the per-length act_decompose calls bit for
 bit, in the caller's channel order, for FP32 and BF16 grids, with device or
-host buffers."""
+host buffers; and every channel is checked order by order against the FP64
+oracle of its window length."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2607_16629_gb300 import act, synth
+from parity_helpers import check_lockstep
 
 pytestmark = pytest.mark.gpu
 
@@ -102,3 +105,56 @@ def test_ragged_plan_rejects_bad_layouts_and_goes_stale():
     finally:
         act.act_destroy(h256)
         act.act_destroy(h512)
+
+
+@pytest.mark.parametrize("mode", [act.ACT_DICT_FP32, act.ACT_DICT_BF16, act.ACT_DICT_RECOMPUTE])
+def test_ragged_lockstep_against_oracle(mode):
+    """Every channel of an uneven batch, order by order, against the FP64
+    oracle of its window length (Eq. (4)): a one-order plan is chained (its
+    residuals fed back as the next signals), each order is checked from the
+    plan's own residual, and a P-order plan gives the chain's selections."""
+    lengths = [256, 1024, 512, 256, 2048, 512, 1024, 256]
+    sigs, offsets = batch(lengths, seed_base=20)
+    C, P = len(lengths), 5
+    grids = {L: small_emg_grid(L) for L in sorted(set(lengths))}
+    dicts = {L: oracle.dictionary(g)[0] for L, g in grids.items()}
+    hs = {L: act.act_grid_create(g, 0) for L, g in grids.items()}
+    try:
+        for h in hs.values():
+            act.act_dictionary_build(h, mode)
+        plan1 = act.act_ragged_plan_create(list(hs.values()), offsets, 1)
+        planP = act.act_ragged_plan_create(list(hs.values()), offsets, P)
+        try:
+            def run(plan, flat, p):
+                atoms = torch.empty((C, p, act.ATOM_BYTES), dtype=torch.uint8, device="cuda")
+                coef = torch.empty((C, p), dtype=torch.float32, device="cuda")
+                res = torch.empty_like(flat)
+                act.act_ragged_decompose(plan, flat, atoms, coef, res, None)
+                torch.cuda.synchronize()
+                for h in hs.values():
+                    assert act.act_grid_status(h) == act.ACT_OK
+                return act.atom_indices(atoms).cpu().numpy(), coef.cpu().numpy(), res
+
+            flat = torch.tensor(np.concatenate(sigs).astype(np.float32), device="cuda")
+            rs = [flat.cpu().numpy()]
+            idx, coef = [], []
+            for _ in range(P):
+                i1, c1, flat = run(plan1, flat, 1)
+                idx.append(i1[:, 0])
+                coef.append(c1[:, 0])
+                rs.append(flat.cpu().numpy())
+            idx, coef = np.stack(idx, 1), np.stack(coef, 1)
+            iP, cP, _ = run(planP, torch.tensor(np.concatenate(sigs).astype(np.float32), device="cuda"), P)
+            assert np.array_equal(iP, idx) and np.array_equal(cP, coef)
+            ties = 0
+            for c, L in enumerate(lengths):
+                seg = slice(offsets[c], offsets[c + 1])
+                D = dicts[L]
+                ties += check_lockstep(lambda r: D @ r, [r[seg] for r in rs], idx[c], coef[c])
+            print(f"{ties} near-ties in {C * P} orders")
+        finally:
+            act.act_ragged_plan_destroy(plan1)
+            act.act_ragged_plan_destroy(planP)
+    finally:
+        for h in hs.values():
+            act.act_destroy(h)

@@ -145,7 +145,7 @@ def test_refinement_lockstep_at_twenty_iterations():
             rr = r.astype(np.float64)
             sc = D @ rr
             assert j == oracle.select(sc)[0]
-            th_o, J_o = oracle.refine(grid.params_of(j), grid.fs, rr, 20, w, lo, hi)
+            th_o, J_o = oracle.refine(oracle.atom_params(grid, j), grid.fs, rr, 20, w, lo, hi)
             J_gpu = abs(oracle.score_grad(th_gpu, grid.fs, rr)[0])
             assert abs(J_gpu - J_o) <= 1e-3 * J_o
             assert J_gpu >= abs(sc[j]) * (1 - 1e-6)

@@ -135,7 +135,7 @@ def test_mp_lockstep(name, grid, P):
     assert np.array_equal(rs[-1], resid[0])
     check_lockstep(lambda r: D @ r, rs, idx[0], coef[0], energy[0], lambda i: D[i])
     for k in range(P):
-        assert par[0, k] == pytest.approx(grid.params_of(idx[0, k]), abs=0)
+        assert par[0, k] == pytest.approx(oracle.atom_params(grid, idx[0, k]), abs=0)
 
 
 def test_mp_matches_oracle_trajectory_c1():
@@ -295,7 +295,7 @@ def test_full_eeg_grid():
         rs, cidx, ccoef = gpu_residual_chain(h, s, 3)
     x = s.astype(np.float32).astype(np.float64)
     for i in rows:
-        g, _ = oracle.atom(*grid.params_of(int(i)), grid.fs, grid.n_samples)
+        g, _ = oracle.atom(*oracle.atom_params(grid, int(i)), grid.fs, grid.n_samples)
         assert abs(sc[i] - g @ x) <= SCORE_TOL * np.linalg.norm(x), i
     assert np.array_equal(cidx, idx[0, :3])
     check_lockstep(lambda r: oracle.scores_grid(grid, r), rs, cidx, ccoef)

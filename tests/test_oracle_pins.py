@@ -159,7 +159,10 @@ def test_dictionary_row_order_and_params():
     D, _ = oracle.dictionary(grid)
     for i in [0, 1, 5, 17, grid.n_atoms - 1]:
         p = oracle.atom_params(grid, i)
-        assert p == pytest.approx(grid.params_of(i), abs=0)
+        # the grid point at that position of numpy's row-major (C-order) layout
+        axes = (grid.tc, grid.fc, grid.logdt, grid.c)
+        pos = np.unravel_index(i, tuple(a.count for a in axes))
+        assert p == tuple(float(a.values()[k]) for a, k in zip(axes, pos))
         g, _ = oracle.atom(*p, grid.fs, grid.n_samples)
         assert np.array_equal(D[i], g)
     assert oracle.atom_params(grid, 1)[3] == grid.c.lo + grid.c.step
@@ -342,7 +345,7 @@ def test_refinement_reaches_the_bfgs_optimum():
     r = w0.signals[0]
     D, _ = oracle.dictionary(grid)
     j = int(np.argmax(np.abs(D @ r)))
-    start = grid.params_of(j)
+    start = oracle.atom_params(grid, j)
     w, lo, hi = oracle.refine_box(grid)
     th, J = oracle.refine(start, grid.fs, r, 60, w, lo, hi)
 
@@ -427,3 +430,50 @@ def test_lem_levels_never_lose_score_and_find_a_lone_atom():
         assert abs(sc - g @ x) <= 1e-12
     assert best[0] <= best[1] <= best[2]
     assert best[2] > 0.9
+
+
+def test_lem_neighbours_are_the_clamped_offset_lattice():
+    """The neighbourhood dictionary of Sec. VII-A: around every kept vector,
+    each offset -R..R steps per axis (radius (2, 2, 1, 2): 375 candidates per
+    parent), clamped to the box; built here independently with numpy's
+    meshgrid (index order 'ij', so c runs fastest as in the oracle)."""
+    grid = synth.grid_eeg()
+    lo, hi = _lem_box(grid)
+    step = np.array([32.0, 1.0, 1.0, 2.5])
+    radius = (2, 2, 1, 2)
+    kept = np.array([[300.0, 12.0, -1.5, 5.0],      # interior
+                     [10.0, 0.75, -3.0, 19.0],      # clamped on tc, fc, logdt and c
+                     [511.0, 31.5, -0.5, -20.0]])   # at the top corner
+    got = oracle.lem_neighbours(kept, step, radius, lo, hi)
+    assert got.shape == (3 * 375, 4)
+    offs = np.stack(np.meshgrid(*[np.arange(-r, r + 1) for r in radius], indexing="ij"), -1).reshape(-1, 4)
+    want = np.concatenate([np.clip(k + offs * step, lo, hi) for k in kept])
+    assert np.array_equal(got, want)
+    assert np.array_equal(got[:375][np.all(offs == 0, axis=1)][0], kept[0])  # the parent itself is a candidate
+
+
+def test_lem_topk_is_a_stable_sort_without_duplicates():
+    """top-k of Sec. VII-A: the k largest |score| in a stable order (lowest
+    index first among equal |score|), a parameter vector equal to one already
+    kept skipped; compared with numpy's stable argsort."""
+    rng = np.random.default_rng(17)
+    n, k = 400, 12
+    cand = rng.integers(0, 6, size=(n, 4)).astype(np.float64)     # many repeated vectors
+    score = rng.integers(-20, 21, size=n).astype(np.float64) / 4.0  # many equal |scores|
+    kept, ks = oracle.lem_topk(cand, score, k)
+    order = np.argsort(-np.abs(score), kind="stable")
+    want, seen = [], set()
+    for i in order:
+        key = tuple(cand[i])
+        if key in seen:
+            continue
+        seen.add(key)
+        want.append(i)
+        if len(want) == k:
+            break
+    assert np.array_equal(kept, cand[want]) and np.array_equal(ks, score[want])
+    # fewer distinct vectors than k: all of them, once
+    c2 = np.repeat(cand[:3], 5, axis=0)
+    s2 = np.arange(15, dtype=np.float64)
+    kept2, _ = oracle.lem_topk(c2, s2, 8)
+    assert len(kept2) == len({tuple(v) for v in c2})
