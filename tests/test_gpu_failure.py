@@ -170,7 +170,7 @@ def test_auto_dictionary_choice():
         assert act.act_dictionary_mode(h) == act.ACT_DICT_FP32
         st, fp32 = _run(h, sig, P)
         assert st == act.ACT_OK
-        act.act_set_memory_budget(h, 16 << 20)               # rows 32 MB > 16 MB: templates
+        act.act_set_memory_budget(h, 64 << 20)               # rows 268 MB > 64 MB > templates 26 MB
         act.act_dictionary_build(h, act.ACT_DICT_AUTO)
         assert act.act_dictionary_mode(h) == act.ACT_DICT_RECOMPUTE
         st, tpl = _run(h, sig, P)

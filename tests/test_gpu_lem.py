@@ -71,6 +71,7 @@ def test_lem_lockstep_against_oracle(top_k, levels):
                     assert abs(abs(s_g) - abs(s_o)) <= 1e-5 * abs(s_o), (k, b, th_gpu[b], th_o)
                     ties += 1
             r = resid.cpu().numpy().astype(np.float32)
+        print(f"top_k {top_k} levels {levels}: {ties} near-ties in {B * P} picks")
         assert ties <= B * P // 4, ties
     finally:
         act.act_destroy(h)
