@@ -18,12 +18,12 @@
 // this GPU).
 //
 // Refinement.  BFGS on f(z) = -|s(w (.) z)| in coordinates scaled by the
-// grid steps w, one block per channel: p = -H grad f (H reset to I when p
-// is not a descent direction), a first step of at most half a grid step,
-// Armijo backtracking (c1 = 1e-4, up to 20 halvings, evaluated 8 at a time
-// by the 8 warps), the standard BFGS inverse update when <y, s> > 0,
-// parameters clamped to the grid box widened by one step; it stops early
-// when no step is accepted.
+// grid steps w, one cluster of 4 CTAs per channel: p = -H grad f (H reset to
+// I when p is not a descent direction), a first step of at most half a grid
+// step, Armijo backtracking (c1 = 1e-4, up to 20 halvings, evaluated four
+// step sizes at a time, one per CTA), the standard BFGS inverse update when
+// <y, s> > 0, parameters clamped to the grid box widened by one step; it
+// stops early when no step is accepted.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -158,15 +158,9 @@ struct EvalConst {
     float inv_dt, inv_fs, c, fc;
 };
 
-__device__ __forceinline__ EvalConst eval_const(const double *th, double inv_fs) {
-    const double inv_dt = exp(-th[2]);
-    return {chirp_ff(th[0], inv_fs, th[1], th[3], inv_dt), (float)inv_dt, (float)inv_fs, (float)th[3],
-            (float)th[1]};
-}
-
-// Adds sample n: the phase in float-float, the sample and its four
-// derivatives in FP32 (expressions of the header comment).
-__device__ __forceinline__ void eval_add(EvalAcc &a, int n, float rv, const EvalConst &e) {
+// Sample n: the phase in float-float, the sample u and its four
+// derivatives du in FP32 (expressions of the header comment).
+__device__ __forceinline__ void eval_sample(int n, const EvalConst &e, float &u, float (&du)[4]) {
     constexpr float two_pi = (float)kTwoPi;
     ff tau;
     const float frac = chirp_phase_ff(n, e.k, &tau);
@@ -175,10 +169,15 @@ __device__ __forceinline__ void eval_add(EvalAcc &a, int n, float rv, const Eval
     sincospif(2.0f * frac, &S, &C);
     const float x = chirp_x_ff(tau, e.k);
     const float E = expf(-0.5f * x * x);
-    const float u = E * C;
+    u = E * C;
     const float ES = E * S;
-    const float du[4] = {(E * x * C * e.inv_dt + ES * two_pi * fmaf(2.0f * e.c, t, e.fc)) * e.inv_fs,
-                         -ES * two_pi * t, E * x * x * C, -ES * two_pi * t * t};
+    du[0] = (E * x * C * e.inv_dt + ES * two_pi * fmaf(2.0f * e.c, t, e.fc)) * e.inv_fs;
+    du[1] = -ES * two_pi * t;
+    du[2] = E * x * x * C;
+    du[3] = -ES * two_pi * t * t;
+}
+
+__device__ __forceinline__ void eval_accumulate(EvalAcc &a, float rv, float u, const float (&du)[4]) {
     ff_fma_acc(a.ru, rv, u);
     ff_fma_acc(a.uu, u, u);
 #pragma unroll
@@ -198,62 +197,11 @@ __device__ __forceinline__ void eval_warp_reduce(EvalAcc &a) {
     }
 }
 
-// Score and one gradient component of an evaluation, as the lanes of the
-// evaluating group's first warp hold them: s in every lane, component
-// lane & 3 of the gradient in gi.
-struct EvalLane {
-    double s, gi;
-};
-
-// Score and gradient by a group of G consecutive warps (samples strided by
-// the group, the warps' sums added in warp order); every group of the block
-// calls it at once (it holds block barriers), each on its own candidate th
-// (inactive groups take part without evaluating).  The result is valid in
-// lanes 0..3 of the group's first warp, which all add the warps' sums and
-// finish in FP64 together (an FP64 instruction costs the same pipe time
-// however few lanes are active).  red holds one EvalAcc per warp; ec one slot
-// of constants per group (formed once, by the group's first thread).
-template <int G>
-__device__ EvalLane eval_group(const double *th, bool active, const float *__restrict__ r, int L, double inv_fs,
-                               EvalAcc *red, EvalConst *ec) {
-    const int warp = threadIdx.x >> 5, g = warp / G, t = (int)threadIdx.x - g * G * 32;
-    if (t == 0 && active) ec[g] = eval_const(th, inv_fs);
-    __syncthreads();
-    EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    if (active) {
-        const EvalConst e = ec[g];
-        for (int n = t; n < L; n += 32 * G) eval_add(a, n, r[n], e);
-    }
-    eval_warp_reduce(a);
-    if ((threadIdx.x & 31) == 0) red[warp] = a;
-    __syncthreads();
-    EvalLane o = {0.0, 0.0};
-    if (warp == g * G && active) {
-        EvalAcc u = red[g * G];
-        for (int w = 1; w < G; ++w) {
-            const EvalAcc &v = red[g * G + w];
-            u.ru = ff_add(u.ru, v.ru);
-            u.uu = ff_add(u.uu, v.uu);
-            for (int i = 0; i < 4; ++i) {
-                u.rd[i] += v.rd[i];
-                u.ud[i] += v.ud[i];
-            }
-        }
-        const double ru = ff_to_double(u.ru), uu = ff_to_double(u.uu);
-        if (uu > 0.0 && isfinite(uu)) {
-            const int i = threadIdx.x & 3;
-            const float rdi = i == 0 ? u.rd[0] : (i == 1 ? u.rd[1] : (i == 2 ? u.rd[2] : u.rd[3]));
-            const float udi = i == 0 ? u.ud[0] : (i == 1 ? u.ud[1] : (i == 2 ? u.ud[2] : u.ud[3]));
-            const double inv_nu = 1.0 / sqrt(uu);
-            o.s = ru * inv_nu;
-            const double s_uu = o.s * inv_nu * inv_nu;
-            o.gi = (double)rdi * inv_nu - s_uu * (double)udi;
-        }
-    }
-    return o;
-}
-
 constexpr int kLineSearch = 20;  // Armijo halvings per iteration
+constexpr int kRefineCluster = 4;  // CTAs per channel
+constexpr int kRefineWarps = kBfgsThreads / 32;
+constexpr int kCandPerCta = 2;     // line-search step sizes each CTA evaluates per round
+constexpr int kCandWarps = kRefineWarps / kCandPerCta;  // warps per step size
 
 // Sum over each group of 4 lanes (lane i of a group holds parameter i).
 __device__ __forceinline__ double sum4(double v) {
@@ -261,176 +209,342 @@ __device__ __forceinline__ double sum4(double v) {
     return v + __shfl_xor_sync(0xffffffffu, v, 2);
 }
 
-// BFGS refinement of channel b's grid winner; theta_out[b][4].  Each
-// iteration evaluates the full step alpha0 and then, if the Armijo
-// condition fails, half of it with the whole block (the usual outcomes);
-// after that groups of 4 warps evaluate the next 4 step sizes alpha0 2^-j at
-// once, and so on.  The first (largest) step that satisfies the condition
-// is taken, which is what sequential backtracking would take.  The
-// per-parameter bookkeeping runs on lanes of warp 0 (lane & 3 = parameter),
-// the 4 x 4 inverse update on 16 threads.
+// 1 / sqrt(x) for a positive finite double: the FP32 reciprocal square root
+// as the seed, then two Newton-Raphson steps y <- y (3 - x y^2) / 2 in FP64
+// (each squares the relative error: 2^-22 -> 2^-43 -> below 2^-53 + rounding).
+// x below 2^-100 is scaled by 2^100 first (exact, so the seed stays a normal
+// FP32 number), without a branch.  On this GPU an FP64 square root followed
+// by a division costs about ten dependent FP64 operations more.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    const bool tiny = x < 0x1p-100;
+    const double xs = tiny ? x * 0x1p100 : x;
+    double y = (double)rsqrtf((float)xs);
+    const double h = 0.5 * xs;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return tiny ? y * 0x1p50 : y;
+}
+
+// 2^-j for 0 <= j < 1023, exact (built from the exponent bits).
+__device__ __forceinline__ double pow2_neg(int j) {
+    return __longlong_as_double((long long)(1023 - j) << 52);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier over every thread of every CTA of the cluster; shared-memory
+// writes before it are visible to the cluster's reads after it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// A double in the shared memory of CTA `rank` of this cluster, at the offset
+// of p in this CTA's (C == 1: this CTA's own).
+__device__ __forceinline__ double ld_cluster_f64(const double *p, uint32_t rank, int C) {
+    if (C == 1) return *(volatile const double *)p;
+    uint32_t addr;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(addr) : "r"(smem_u32(p)), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// One line-search candidate's evaluation, published to the cluster:
+// f = -|s|, the scaled gradient, and the candidate in scaled and natural
+// coordinates.
+struct Candidate {
+    double f;
+    double valid;  // 1: a step size of this round (j < kLineSearch)
+    double g[4], z[4], th[4];
+};
+
+// The per-candidate constants of Eq. (1) for lane i = parameter i of warp 0,
+// formed in parallel: lane 0 tc, lane 1 fc, lane 2 1/dt = exp(-logDt),
+// lane 3 c (each a float pair; 1/fs is fixed).
+__device__ __forceinline__ void put_const(EvalConst *ec, int i, double v, double inv_fs) {
+    if (i == 0) {
+        ec->k.tc = ff_from_double(v);
+        ec->k.inv_fs = ff_from_double(inv_fs);
+        ec->inv_fs = (float)inv_fs;
+    } else if (i == 1) {
+        ec->k.fc = ff_from_double(v);
+        ec->fc = (float)v;
+    } else if (i == 2) {
+        const double inv_dt = exp(-v);
+        ec->k.inv_dt = ff_from_double(inv_dt);
+        ec->inv_dt = (float)inv_dt;
+    } else {
+        ec->k.c = ff_from_double(v);
+        ec->c = (float)v;
+    }
+}
+
+// Score and gradient of kCandPerCta candidates at once: warp group h (warps
+// h kCandWarps ..) evaluates the candidate whose constants are in ec[h],
+// every thread of the group taking samples n = t, t + 32 kCandWarps, ....
+// Partial sums go to red[warp]; after the barrier the group's first warp
+// adds its warps' sums by a tree over kCandWarps lanes and finishes in FP64.
+// Returned in every lane of each group's first warp: the score s and
+// component (lane & 3) of its gradient (zeros elsewhere).
+__device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__restrict__ r, int L, EvalAcc *red,
+                                           double *s_out, double *gi_out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = warp / kCandWarps, t = (int)threadIdx.x - h * kCandWarps * 32;
+    EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    {
+        // kSpan samples of the thread at once: their evaluations are
+        // independent (the latency of one overlaps the others), then they
+        // are accumulated in sample order
+        constexpr int kStride = 32 * kCandWarps, kSpan = 4;
+        const EvalConst e = ec[h];
+        for (int n0 = t; n0 < L; n0 += kSpan * kStride) {
+            float u[kSpan], du[kSpan][4], rv[kSpan];
+#pragma unroll
+            for (int k = 0; k < kSpan; ++k) {
+                const int n = n0 + k * kStride;
+                rv[k] = n < L ? r[n] : 0.0f;
+                eval_sample(n < L ? n : 0, e, u[k], du[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < kSpan; ++k)
+                if (n0 + k * kStride < L) eval_accumulate(a, rv[k], u[k], du[k]);
+        }
+    }
+    eval_warp_reduce(a);
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    *s_out = 0.0;
+    *gi_out = 0.0;
+    if (warp != h * kCandWarps) return;
+    __syncwarp();  // the finish runs with the whole warp converged
+    EvalAcc u = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    if (lane < kCandWarps) u = red[warp + lane];
+#pragma unroll
+    for (int off = kCandWarps / 2; off > 0; off >>= 1) {
+        u.ru = ff_add(u.ru, ff_shfl_xor(u.ru, off));
+        u.uu = ff_add(u.uu, ff_shfl_xor(u.uu, off));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            u.rd[i] += __shfl_xor_sync(0xffffffffu, u.rd[i], off);
+            u.ud[i] += __shfl_xor_sync(0xffffffffu, u.ud[i], off);
+        }
+    }
+    // lanes 0 .. kCandWarps-1 hold the total (the other lanes the same tree over zeros)
+    const double ru = ff_to_double(ff_shfl(u.ru, 0)), uu = ff_to_double(ff_shfl(u.uu, 0));
+    const int i = lane & 3;
+    float rdi = i == 0 ? u.rd[0] : (i == 1 ? u.rd[1] : (i == 2 ? u.rd[2] : u.rd[3]));
+    float udi = i == 0 ? u.ud[0] : (i == 1 ? u.ud[1] : (i == 2 ? u.ud[2] : u.ud[3]));
+    rdi = __shfl_sync(0xffffffffu, rdi, i);
+    udi = __shfl_sync(0xffffffffu, udi, i);
+    // uniform in the warp (no divergent route): a degenerate atom scores 0
+    const bool ok = uu > 0.0 && isfinite(uu);
+    const double inv_nu = rsqrt_newton(ok ? uu : 1.0);
+    const double sv = ok ? ru * inv_nu : 0.0;
+    *s_out = sv;
+    *gi_out = ok ? (double)rdi * inv_nu - sv * inv_nu * inv_nu * (double)udi : 0.0;
+}
+
+// BFGS refinement of channel b's grid winner; theta_out[b][4].  A cluster of
+// C CTAs serves one channel; all of them hold the same BFGS state and make
+// the same decisions (they compute them from the same bits), so nothing but
+// the candidates is exchanged.  Each iteration: the direction p = -H g
+// (H reset to I if p is not a descent direction) and the first step alpha0
+// (at most half a grid step); then rounds of line search in which CTA q
+// evaluates the step alpha0 2^-(j0 + q); after a round every CTA reads the
+// C candidates from the cluster's shared memory and takes the first (largest)
+// step that satisfies the Armijo condition -- what sequential backtracking
+// would take -- or, if none does, the next round j0 += C, up to kLineSearch
+// halvings.  Then the BFGS inverse update (when <y, s> > 0).  It stops early
+// when no step is accepted.  Bookkeeping runs on warp 0 (lane & 3 =
+// parameter, the 4 x 4 update on 16 lanes); the other warps only evaluate.
 __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox box, int steps, int Lp,
                                                           const float *__restrict__ R,
                                                           const unsigned long long *__restrict__ keys,
                                                           const double *__restrict__ theta_in, int theta_in_stride,
-                                                          double *__restrict__ theta_out) {
-    constexpr int kWarps = kBfgsThreads / 32;
-    constexpr int kBlockSteps = 2;  // steps j = 0, 1 evaluated by the whole block
-    constexpr int kGroupWarps = 4;  // then kSlots steps at a time, one per group of warps
-    constexpr int kSlots = kWarps / kGroupWarps;
-    constexpr int kNone = kSlots;   // state: no step accepted yet
-    __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4];
-    __shared__ double cz[kSlots][4], cth[kSlots][4], cg[kSlots][4], cf[kSlots], ca[kSlots];
-    __shared__ double f, gp, alpha0, rho;
-    __shared__ EvalAcc red[kWarps];
-    __shared__ EvalConst ec[kSlots];
-    __shared__ int state;  // -1: stop; otherwise the accepted slot (or kNone)
-    const int b = blockIdx.x;
+                                                          double *__restrict__ theta_out, int C) {
+    __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4], inv_w[4];
+    __shared__ double f, gp, alpha0;
+    __shared__ Candidate res[2][kCandPerCta];  // this CTA's candidates of the round, by round parity
+    __shared__ EvalAcc red[kRefineWarps];
+    __shared__ EvalConst ec[kCandPerCta];
+    __shared__ int done;
+    const int b = blockIdx.x / C;
+    const uint32_t rank = C > 1 ? cluster_rank() : 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pi = lane & 3;  // the parameter of this lane in warp 0's bookkeeping
     const float *r = R + (size_t)b * Lp;
     const int L = ax.L;
     const double inv_fs = 1.0 / ax.fs;
 
-    // component i of the trial point of step j into slot q
-    auto trial = [&](int j, int q, int i) {
-        const double a = alpha0 * ldexp(1.0, -j);
-        double v = (z[i] + a * p[i]) * box.w[i];
-        v = v < box.lo[i] ? box.lo[i] : (v > box.hi[i] ? box.hi[i] : v);
-        cz[q][i] = v / box.w[i];
-        cth[q][i] = v;
-        if (i == 0) ca[q] = a;
-    };
-    // f and scaled gradient component i of slot q (lane i < 4 of the group's first warp)
-    auto record = [&](const EvalLane &o, int q, int i) {
-        const double sg = o.s < 0.0 ? -1.0 : 1.0;
-        cg[q][i] = -sg * o.gi * box.w[i];
-        if (i == 0) cf[q] = -fabs(o.s);
-    };
-    auto armijo = [&](int q) { return cf[q] <= f + 1e-4 * ca[q] * gp; };
-
-    if (threadIdx.x == 0) {
-        double p0[4];
+    if (warp == 0) {
+        double p0 = 0.0;
         if (theta_in) {
-            for (int i = 0; i < 4; ++i) p0[i] = theta_in[(size_t)b * theta_in_stride + i];
+            p0 = theta_in[(size_t)b * theta_in_stride + pi];
         } else {
-            decode_params(ax, (int64_t)key_index(keys[b]), p0);
+            double pp[4];
+            decode_params(ax, (int64_t)key_index(keys[b]), pp);
+            p0 = pi == 0 ? pp[0] : (pi == 1 ? pp[1] : (pi == 2 ? pp[2] : pp[3]));
         }
-        for (int i = 0; i < 4; ++i) {
-            z[i] = p0[i] / box.w[i];
-            th_cur[i] = p0[i];  // the parameters themselves: returned unchanged if no step is taken
+        if (lane < 4) {
+            inv_w[pi] = 1.0 / box.w[pi];
+            z[pi] = p0 * inv_w[pi];
+            th_cur[pi] = p0;  // the parameters themselves: returned unchanged if no step is taken
         }
-    }
-    if (threadIdx.x < 16) H[threadIdx.x] = (threadIdx.x % 5 == 0) ? 1.0 : 0.0;
-    __syncthreads();
-    {
-        const EvalLane o = eval_group<kWarps>(th_cur, true, r, L, inv_fs, red, ec);
-        if (threadIdx.x < 4) {
-            const double sg = o.s < 0.0 ? -1.0 : 1.0;
-            gz[threadIdx.x] = -sg * o.gi * box.w[threadIdx.x];
-            if (threadIdx.x == 0) f = -fabs(o.s);
-        }
+        if (lane < 4 * kCandPerCta) put_const(&ec[lane >> 2], pi, p0, inv_fs);
+        if (lane < 16) H[lane] = (lane % 5 == 0) ? 1.0 : 0.0;
+        if (lane == 0) done = steps > 0 ? 0 : 1;
     }
     __syncthreads();
-    for (int it = 0; it < steps; ++it) {
-        if (warp == 0) {  // direction p = -H g (steepest descent, H reset, if not a descent direction)
-            double v = 0.0;
-            for (int j = 0; j < 4; ++j) v -= H[4 * pi + j] * gz[j];
-            double g_p = sum4(gz[pi] * v);
-            const bool reset = !(g_p < 0.0);
-            if (reset) {
-                v = -gz[pi];
-                g_p = sum4(gz[pi] * v);
-            }
-            const double pn = sqrt(sum4(v * v));
-            __syncwarp();
-            if (lane < 4) {
-                p[pi] = v;
-                if (reset)
-                    for (int k = 0; k < 4; ++k) H[4 * pi + k] = pi == k ? 1.0 : 0.0;
-            }
-            if (lane == 0) {
-                gp = g_p;
-                alpha0 = pn > 0.5 ? 0.5 / pn : 1.0;
-                state = (g_p < 0.0) ? kNone : -1;
-            }
-            __syncwarp();
-            if (g_p < 0.0 && lane < 4) trial(0, 0, pi);
+    {  // the start point (every group of every CTA of the cluster evaluates it, with the same bits)
+        double s0, g0;
+        eval_cands(ec, r, L, red, &s0, &g0);
+        if (warp == 0 && lane < 4) {
+            const double sg = s0 < 0.0 ? -1.0 : 1.0;
+            gz[pi] = -sg * g0 * box.w[pi];
+            if (lane == 0) f = -fabs(s0);
         }
-        __syncthreads();
-        if (state < 0) break;
-        // the full and the half step, by the whole block
-        for (int j = 0; j < kBlockSteps && state == kNone; ++j) {
-            if (j > 0) {
-                if (threadIdx.x < 4) trial(j, 0, threadIdx.x);
-                __syncthreads();
-            }
-            const EvalLane o = eval_group<kWarps>(cth[0], true, r, L, inv_fs, red, ec);
-            if (threadIdx.x < 4) record(o, 0, threadIdx.x);
-            if (threadIdx.x == 0 && armijo(0)) state = 0;
-            __syncthreads();
-        }
-        // shorter steps, kSlots at a time (one group of warps each)
-        for (int j0 = kBlockSteps; state == kNone && j0 < kLineSearch; j0 += kSlots) {
-            const int g = warp / kGroupWarps, t = (int)threadIdx.x - g * kGroupWarps * 32;
-            const bool active = j0 + g < kLineSearch;
-            if (active && t < 4) trial(j0 + g, g, t);
-            __syncwarp();  // the group's first thread reads the trial point
-            const EvalLane o = eval_group<kGroupWarps>(cth[g], active, r, L, inv_fs, red, ec);
-            if (active && t < 4) record(o, g, t);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int q = 0; q < kSlots && j0 + q < kLineSearch; ++q)
-                    if (armijo(q)) {
-                        state = q;
-                        break;
-                    }
-            }
-            __syncthreads();
-        }
-        if (state >= kNone) break;  // no acceptable step
-        // BFGS inverse update H' = (I - rho s y^T) H (I - rho y s^T) + rho s s^T
-        // when <y, s> > 0
-        const int q = state;
+    }
+    int it = 0, j0 = 0, par = 0;
+    bool new_dir = true;
+    for (;;) {
         if (warp == 0) {
-            const double si = cz[q][pi] - z[pi], yi = cg[q][pi] - gz[pi];
-            const double ys = sum4(yi * si);
-            if (lane < 4) {
-                sv[pi] = si;
-                yv[pi] = yi;
+            __syncwarp();
+            if (!done && new_dir) {  // p = -H g (steepest descent, H reset, if not a descent direction)
+                double v = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v = fma(-H[4 * pi + j], gz[j], v);
+                double g_p = sum4(gz[pi] * v);
+                const bool reset = !(g_p < 0.0);
+                if (reset) {
+                    v = -gz[pi];
+                    g_p = sum4(gz[pi] * v);
+                }
+                const double pn2 = sum4(v * v);
+                __syncwarp();
+                if (lane < 4) {
+                    p[pi] = v;
+                    if (reset)
+                        for (int k = 0; k < 4; ++k) H[4 * pi + k] = pi == k ? 1.0 : 0.0;
+                }
+                if (lane == 0) {
+                    gp = g_p;
+                    alpha0 = pn2 > 0.25 ? 0.5 * rsqrt_newton(pn2) : 1.0;
+                    if (!(g_p < 0.0)) done = 1;
+                }
+                new_dir = false;
+                j0 = 0;
+                __syncwarp();
             }
-            if (lane == 0) rho = ys > 1e-300 ? 1.0 / ys : 0.0;
+            if (!done && lane < 4 * kCandPerCta) {  // this CTA's steps of the round: alpha0 2^-(j0 + q)
+                const int hh = lane >> 2;
+                const int j = j0 + (int)rank * kCandPerCta + hh;
+                const double a = alpha0 * pow2_neg(j < kLineSearch ? j : 0);
+                double v = fma(a, p[pi], z[pi]) * box.w[pi];
+                v = v < box.lo[pi] ? box.lo[pi] : (v > box.hi[pi] ? box.hi[pi] : v);
+                res[par][hh].z[pi] = v * inv_w[pi];
+                res[par][hh].th[pi] = v;
+                put_const(&ec[hh], pi, v, inv_fs);
+                if (pi == 0) res[par][hh].valid = j < kLineSearch ? 1.0 : 0.0;
+            }
+            __syncwarp();
         }
         __syncthreads();
-        if (rho != 0.0) {
-            if (threadIdx.x < 16) {  // Hn = (I - rho s y^T) H
-                const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
-                double a = 0.0;
-                for (int k = 0; k < 4; ++k) a += ((i == k ? 1.0 : 0.0) - rho * sv[i] * yv[k]) * H[4 * k + j];
-                Hn[threadIdx.x] = a;
-            }
+        if (done) break;
+        double sc, gi;
+        eval_cands(ec, r, L, red, &sc, &gi);
+        if (warp % kCandWarps == 0 && lane < 4) {
+            const int hh = warp / kCandWarps;
+            const double sg = sc < 0.0 ? -1.0 : 1.0;
+            res[par][hh].g[pi] = -sg * gi * box.w[pi];
+            if (lane == 0) res[par][hh].f = -fabs(sc);
+        }
+        // every CTA's candidate of this round is published
+        if (C > 1)
+            cluster_sync_all();
+        else
             __syncthreads();
-            if (threadIdx.x < 16) {  // H = Hn (I - rho y s^T) + rho s s^T
-                const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
-                double a = 0.0;
-                for (int k = 0; k < 4; ++k) a += Hn[4 * i + k] * ((j == k ? 1.0 : 0.0) - rho * sv[j] * yv[k]);
-                H[threadIdx.x] = a + rho * sv[i] * sv[j];
+        if (warp == 0) {
+            // lane q < C kCandPerCta: candidate q of the round (slot q % kCandPerCta
+            // of CTA q / kCandPerCta, step alpha0 2^-(j0 + q)) and its Armijo test
+            int ok = 0;
+            if (lane < C * kCandPerCta) {
+                const Candidate &cq = res[par][lane % kCandPerCta];
+                const uint32_t owner = (uint32_t)(lane / kCandPerCta);
+                const double fq = ld_cluster_f64(&cq.f, owner, C);
+                const double vq = ld_cluster_f64(&cq.valid, owner, C);
+                const double aq = alpha0 * pow2_neg(j0 + lane < kLineSearch ? j0 + lane : 0);
+                ok = vq != 0.0 && fq <= f + 1e-4 * aq * gp;
+            }
+            const unsigned acc = __ballot_sync(0xffffffffu, ok);
+            if (acc) {
+                const int q = __ffs((int)acc) - 1;  // the largest accepted step
+                const Candidate &cq = res[par][q % kCandPerCta];
+                const uint32_t owner = (uint32_t)(q / kCandPerCta);
+                const double zq = ld_cluster_f64(&cq.z[pi], owner, C);
+                const double gq = ld_cluster_f64(&cq.g[pi], owner, C);
+                const double tq = ld_cluster_f64(&cq.th[pi], owner, C);
+                const double fq = ld_cluster_f64(&cq.f, owner, C);
+                // BFGS inverse update H' = (I - rho s y^T) H (I - rho y s^T) + rho s s^T when <y, s> > 0
+                const double si = zq - z[pi], yi = gq - gz[pi];
+                const double ys = sum4(yi * si);
+                const double rho = ys > 1e-300 ? 1.0 / ys : 0.0;
+                if (lane < 4) {
+                    sv[pi] = si;
+                    yv[pi] = yi;
+                }
+                __syncwarp();
+                if (rho != 0.0) {
+                    if (lane < 16) {  // Hn = (I - rho s y^T) H
+                        const int i = lane >> 2, j = lane & 3;
+                        const double rs = rho * sv[i];
+                        double t = 0.0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) t = fma((i == k ? 1.0 : 0.0) - rs * yv[k], H[4 * k + j], t);
+                        Hn[lane] = t;
+                    }
+                    __syncwarp();
+                    if (lane < 16) {  // H = Hn (I - rho y s^T) + rho s s^T
+                        const int i = lane >> 2, j = lane & 3;
+                        const double rs = rho * sv[j];
+                        double t = 0.0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) t = fma(Hn[4 * i + k], (j == k ? 1.0 : 0.0) - rs * yv[k], t);
+                        H[lane] = fma(rho * sv[i], sv[j], t);
+                    }
+                }
+                __syncwarp();
+                if (lane < 4) {
+                    z[pi] = zq;
+                    th_cur[pi] = tq;
+                    gz[pi] = gq;
+                }
+                if (lane == 0) {
+                    f = fq;
+                    if (++it >= steps) done = 1;
+                }
+                new_dir = true;
+            } else {
+                j0 += C * kCandPerCta;
+                if (j0 >= kLineSearch && lane == 0) done = 1;  // no acceptable step: stop
             }
         }
-        if (threadIdx.x < 4) {
-            z[threadIdx.x] = cz[q][threadIdx.x];
-            th_cur[threadIdx.x] = cth[q][threadIdx.x];
-            gz[threadIdx.x] = cg[q][threadIdx.x];
-        }
-        if (threadIdx.x == 0) f = cf[q];
-        __syncthreads();
+        par ^= 1;
     }
-    if (threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = th_cur[threadIdx.x];
+    // no CTA leaves while another may still read its candidates
+    if (C > 1) cluster_sync_all();
+    if (rank == 0 && threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = th_cur[threadIdx.x];
 }
 
 // Coefficient and residual update with the refined atom g(theta*) generated
 // on the fly (Eq. (4)); the record keeps the grid winner's flat index (-1
-// when the selection did not come from the grid).
+// when the selection did not come from the grid).  The samples are those of
+// the dictionary generator (float-float phase, chirp_sample_ff), formed once
+// into registers; |u|^2 is a float-float sum, c = <g, r> an FP32 block sum,
+// |r|^2 an FP64 sum.
 __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float *__restrict__ R,
                                                                   __nv_bfloat16 *__restrict__ R16, int Lb,
                                                                   unsigned long long *__restrict__ keys, GridAxes ax,
@@ -438,47 +552,57 @@ __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float
                                                                   act_atom *__restrict__ atoms,
                                                                   float *__restrict__ coefs,
                                                                   double *__restrict__ energy, int *fb_count) {
+    constexpr int kPer = kMaxSamples / kRefineThreads;
     __shared__ float shf[32];
     __shared__ double shd[32];
+    __shared__ ff shff[32];
+    __shared__ ChirpFF kc;
     const int b = blockIdx.x;
     const int L = ax.L;
-    const double inv_fs = 1.0 / ax.fs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kRefineThreads / 32;
     const double tc = theta[4 * b], fc = theta[4 * b + 1], ld = theta[4 * b + 2], cc = theta[4 * b + 3];
-    const double inv_dt = exp(-ld);
+    if (threadIdx.x == 0) kc = chirp_ff(tc, 1.0 / ax.fs, fc, cc, exp(-ld));
+    __syncthreads();
+    const ChirpFF kk = kc;
     float *r = R + (size_t)b * Lp;
-    // |u|^2 in FP64, then g = u / |u| recomputed per sample
-    double e = 0.0;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const double tau = ((double)n - tc) * inv_fs;
-        double ph = fma(cc, tau, fc) * tau;
-        ph -= rint(ph);
-        const float x = (float)(tau * inv_dt);
-        const float u = expf(-0.5f * x * x) * cospif(2.0f * (float)ph);
-        e = fma((double)u, (double)u, e);
+    float u[kPer];
+    ff e = {0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int n = (int)threadIdx.x + i * kRefineThreads;
+        u[i] = n < L ? chirp_sample_ff(n, kk) : 0.0f;
+        ff_fma_acc(e, u[i], u[i]);
     }
-    const double uu = block_sum(e, shd);
+    e = ff_warp_sum(e);
+    if (lane == 0) shff[warp] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff t = shff[0];
+        for (int w = 1; w < nw; ++w) t = ff_add(t, shff[w]);
+        shd[0] = ff_to_double(t);
+    }
+    __syncthreads();
+    const double uu = shd[0];
+    __syncthreads();
     const float scale = (uu > 0.0 && isfinite(uu)) ? (float)(1.0 / sqrt(uu)) : 0.0f;
     float part = 0.0f;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const double tau = ((double)n - tc) * inv_fs;
-        double ph = fma(cc, tau, fc) * tau;
-        ph -= rint(ph);
-        const float x = (float)(tau * inv_dt);
-        const float g = expf(-0.5f * x * x) * cospif(2.0f * (float)ph) * scale;
-        part = fmaf(g, r[n], part);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int n = (int)threadIdx.x + i * kRefineThreads;
+        u[i] *= scale;  // g
+        if (n < L) part = fmaf(u[i], r[n], part);
     }
     const float c = block_sum(part, shf);
     double e2 = 0.0;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        const double tau = ((double)n - tc) * inv_fs;
-        double ph = fma(cc, tau, fc) * tau;
-        ph -= rint(ph);
-        const float x = (float)(tau * inv_dt);
-        const float g = expf(-0.5f * x * x) * cospif(2.0f * (float)ph) * scale;
-        const float v = fmaf(-c, g, r[n]);
-        r[n] = v;
-        e2 = fma((double)v, (double)v, e2);
-        if (R16) R16[(size_t)b * Lb + n] = __float2bfloat16_rn(v);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int n = (int)threadIdx.x + i * kRefineThreads;
+        if (n < L) {
+            const float v = fmaf(-c, u[i], r[n]);
+            r[n] = v;
+            e2 = fma((double)v, (double)v, e2);
+            if (R16) R16[(size_t)b * Lb + n] = __float2bfloat16_rn(v);
+        }
     }
     const double tot = block_sum(e2, shd);
     if (threadIdx.x == 0) {
@@ -513,14 +637,35 @@ cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R,
     for (int i = 0; i < 4; ++i) {
         // scale = grid step; box = grid range widened by one step (an axis
         // with a zero step is held fixed)
-        const double st = fabs(ax.step[i]);
+        const double st_i = fabs(ax.step[i]);
         const double first = ax.lo[i], last = ax.lo[i] + (double)(ax.count[i] - 1) * ax.step[i];
-        box.w[i] = st > 0.0 ? st : 1.0;
-        box.lo[i] = st > 0.0 ? fmin(first, last) - st : first;
-        box.hi[i] = st > 0.0 ? fmax(first, last) + st : first;
+        box.w[i] = st_i > 0.0 ? st_i : 1.0;
+        box.lo[i] = st_i > 0.0 ? fmin(first, last) - st_i : first;
+        box.hi[i] = st_i > 0.0 ? fmax(first, last) + st_i : first;
     }
-    k_refine<<<B, kBfgsThreads, 0, st>>>(ax, box, steps, Lp, R, keys, theta_in, theta_in_stride, theta_out);
-    return cudaGetLastError();
+    // a cluster of kRefineCluster CTAs per channel when the device can place
+    // one, else one CTA per channel (the same search, one step size a round)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kRefineCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kBfgsThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.gridDim = dim3((unsigned)(B * kRefineCluster));
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    int C = kRefineCluster;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_refine, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        C = 1;
+        cfg.gridDim = dim3((unsigned)B);
+        cfg.numAttrs = 0;
+    }
+    return cudaLaunchKernelEx(&cfg, k_refine, ax, box, steps, Lp, R, keys, theta_in, theta_in_stride, theta_out, C);
 }
 
 cudaError_t launch_update_refined(int Lp, float *R, __nv_bfloat16 *R16, int Lb, int B, unsigned long long *keys,
