@@ -432,7 +432,9 @@ ACT_API void act_ragged_plan_destroy(act_ragged_plan *plan);
  * channel plus a status word), held by every GPU that loads the library
  * until exit.  The first call on a device looks up that array's address with
  * cudaGetSymbolAddress while the device is current; make that first call
- * before any stream capture.  Every call clears and reuses the same array,
+ * before any stream capture.  The first call with each row stride, and with
+ * one and with several channels, also loads that kernel's code on the
+ * device; make those first calls before any stream capture as well.  Every call clears and reuses the same array,
  * so calls whose GPU work overlaps (different streams, or different host
  * threads on one device) race and must be serialised by the caller.
  * Enqueued on cuda_stream; nothing is waited for. */

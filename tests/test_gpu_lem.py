@@ -71,8 +71,10 @@ def test_lem_lockstep_against_oracle(top_k, levels):
                     assert abs(abs(s_g) - abs(s_o)) <= 1e-5 * abs(s_o), (k, b, th_gpu[b], th_o)
                     ties += 1
             r = resid.cpu().numpy().astype(np.float32)
+        # measured on GB300: no near-tie in any of these configurations; one is
+        # allowed (a near-tie of distinct candidates may resolve either way)
         print(f"top_k {top_k} levels {levels}: {ties} near-ties in {B * P} picks")
-        assert ties <= B * P // 4, ties
+        assert ties <= 1, ties
     finally:
         act.act_destroy(h)
 
