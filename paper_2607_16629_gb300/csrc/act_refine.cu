@@ -187,16 +187,6 @@ __device__ __forceinline__ void eval_accumulate(EvalAcc &a, float rv, float u, c
     }
 }
 
-__device__ __forceinline__ void eval_warp_reduce(EvalAcc &a) {
-    a.ru = ff_warp_sum(a.ru);
-    a.uu = ff_warp_sum(a.uu);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        a.rd[i] = warp_sum(a.rd[i]);
-        a.ud[i] = warp_sum(a.ud[i]);
-    }
-}
-
 constexpr int kLineSearch = 20;  // Armijo halvings per iteration
 constexpr int kRefineCluster = 4;  // CTAs per channel
 constexpr int kRefineWarps = kBfgsThreads / 32;
@@ -283,14 +273,41 @@ __device__ __forceinline__ void put_const(EvalConst *ec, int i, double v, double
     }
 }
 
+// The warp's sums of one evaluation by reduce-scatter: at every level a lane
+// sends the half of its values its partner keeps and adds the half it keeps
+// (xor 16: gradient sums 0-3 / 4-7 and ru / uu; then 8, 4 on the gradient
+// sums; then plain butterflies), 19 shuffles instead of 60.  On return lane l
+// holds the warp's total of gradient sum (l >> 2) (rd[0..3], ud[0..3]) in
+// *gsum, and of ru (lanes 0-15) or uu (lanes 16-31) in *fsum.  Fixed order.
+__device__ __forceinline__ void eval_warp_scatter(const EvalAcc &a, int lane, float *gsum, ff *fsum) {
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+    const float g[8] = {a.rd[0], a.rd[1], a.rd[2], a.rd[3], a.ud[0], a.ud[1], a.ud[2], a.ud[3]};
+    float w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        w[k] = (b4 ? g[4 + k] : g[k]) + __shfl_xor_sync(0xffffffffu, b4 ? g[k] : g[4 + k], 16);
+    float x[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        x[k] = (b3 ? w[2 + k] : w[k]) + __shfl_xor_sync(0xffffffffu, b3 ? w[k] : w[2 + k], 8);
+    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    *gsum = y;
+    ff v = ff_add(b4 ? a.uu : a.ru, ff_shfl_xor(b4 ? a.ru : a.uu, 16));
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) v = ff_add(v, ff_shfl_xor(v, off));
+    *fsum = v;
+}
+
 // Score and gradient of kCandPerCta candidates at once: warp group h (warps
 // h kCandWarps ..) evaluates the candidate whose constants are in ec[h],
 // every thread of the group taking samples n = t, t + 32 kCandWarps, ....
 // Partial sums go to red[warp]; after the barrier the group's first warp
-// adds its warps' sums by a tree over kCandWarps lanes and finishes in FP64.
+// adds its warps' sums in warp order and finishes on the FP32 pipes.
 // Returned in every lane of each group's first warp: the score s and
 // component (lane & 3) of its gradient (zeros elsewhere).
-__device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__restrict__ r, int L, EvalAcc *red,
+__device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__restrict__ r, int L, float (*red)[12],
                                            double *s_out, double *gi_out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = warp / kCandWarps, t = (int)threadIdx.x - h * kCandWarps * 32;
@@ -314,38 +331,56 @@ __device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__r
                 if (n0 + k * kStride < L) eval_accumulate(a, rv[k], u[k], du[k]);
         }
     }
-    eval_warp_reduce(a);
-    if (lane == 0) red[warp] = a;
+    {
+        // the warp's totals into red[warp]: [0..1] ru, [2..3] uu, [4 + c] gradient sum c
+        float gs;
+        ff fs;
+        eval_warp_scatter(a, lane, &gs, &fs);
+        if ((lane & 3) == 0) red[warp][4 + (lane >> 2)] = gs;
+        if (lane == 0 || lane == 16) {
+            red[warp][lane >> 3] = fs.hi;
+            red[warp][(lane >> 3) + 1] = fs.lo;
+        }
+    }
     __syncthreads();
     *s_out = 0.0;
     *gi_out = 0.0;
     if (warp != h * kCandWarps) return;
     __syncwarp();  // the finish runs with the whole warp converged
-    EvalAcc u = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    if (lane < kCandWarps) u = red[warp + lane];
-#pragma unroll
-    for (int off = kCandWarps / 2; off > 0; off >>= 1) {
-        u.ru = ff_add(u.ru, ff_shfl_xor(u.ru, off));
-        u.uu = ff_add(u.uu, ff_shfl_xor(u.uu, off));
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            u.rd[i] += __shfl_xor_sync(0xffffffffu, u.rd[i], off);
-            u.ud[i] += __shfl_xor_sync(0xffffffffu, u.ud[i], off);
-        }
+    // lane 0: ru, lane 2: uu (float-float), lanes 4..11: the gradient sums,
+    // each added over the group's warps in warp order
+    ff tot = {0.0f, 0.0f};
+    if (lane == 0 || lane == 2) {
+        for (int w = 0; w < kCandWarps; ++w) tot = ff_add(tot, ff{red[warp + w][lane], red[warp + w][lane + 1]});
+    } else if (lane >= 4 && lane < 12) {
+        float t = 0.0f;
+        for (int w = 0; w < kCandWarps; ++w) t += red[warp + w][lane];
+        tot.hi = t;
     }
-    // lanes 0 .. kCandWarps-1 hold the total (the other lanes the same tree over zeros)
-    const double ru = ff_to_double(ff_shfl(u.ru, 0)), uu = ff_to_double(ff_shfl(u.uu, 0));
+    const ff ru = ff_shfl(tot, 0), uu = ff_shfl(tot, 2);
     const int i = lane & 3;
-    float rdi = i == 0 ? u.rd[0] : (i == 1 ? u.rd[1] : (i == 2 ? u.rd[2] : u.rd[3]));
-    float udi = i == 0 ? u.ud[0] : (i == 1 ? u.ud[1] : (i == 2 ? u.ud[2] : u.ud[3]));
-    rdi = __shfl_sync(0xffffffffu, rdi, i);
-    udi = __shfl_sync(0xffffffffu, udi, i);
-    // uniform in the warp (no divergent route): a degenerate atom scores 0
-    const bool ok = uu > 0.0 && isfinite(uu);
-    const double inv_nu = rsqrt_newton(ok ? uu : 1.0);
-    const double sv = ok ? ru * inv_nu : 0.0;
-    *s_out = sv;
-    *gi_out = ok ? (double)rdi * inv_nu - sv * inv_nu * inv_nu * (double)udi : 0.0;
+    const float rdi = __shfl_sync(0xffffffffu, tot.hi, 4 + i);
+    const float udi = __shfl_sync(0xffffffffu, tot.hi, 8 + i);
+    // The finish on the FP32 pipes, uniform in the warp.  s = <r, u> / |u|
+    // in float-float: 1/|u| is the FP32 reciprocal square root y0 corrected by
+    // Newton-Raphson steps y <- y + y (1 - |u|^2 y^2) / 2 in float-float
+    // (relative error 2^-22 -> about 2^-44 -> the pair's precision).  The gradient components come from
+    // FP32 sums, so they are finished in FP32.  An atom with |u|^2 below
+    // 1e-30 (every sample underflowed) scores 0.
+    const bool ok = uu.hi > 1e-30f && uu.hi < 3.0e38f;
+    const float y0 = rsqrtf(ok ? uu.hi : 1.0f);
+    const ff y0sq = ff_fast_two_sum(y0 * y0, fmaf(y0, y0, -(y0 * y0)));
+    const ff uy = ff_mul(ok ? uu : ff{1.0f, 0.0f}, y0sq);  // 1 - uy is exact in its high part
+    const float e = (1.0f - uy.hi) - uy.lo;
+    const ff y1 = ff_add_f(ff{y0, 0.0f}, 0.5f * y0 * e);
+    // a second step in float-float brings 1/|u| to the pair's own precision
+    const ff uy1 = ff_mul(ok ? uu : ff{1.0f, 0.0f}, ff_mul(y1, y1));
+    const float e1 = (1.0f - uy1.hi) - uy1.lo;
+    const ff y2 = ff_add_f(y1, 0.5f * y1.hi * e1);
+    const ff sff = ff_mul(ru, y2);
+    const float sf = sff.hi + sff.lo;
+    *s_out = ok ? ff_to_double(sff) : 0.0;
+    *gi_out = ok ? (double)fmaf(rdi, y2.hi, -sf * y2.hi * y2.hi * udi) : 0.0;
 }
 
 // BFGS refinement of channel b's grid winner; theta_out[b][4].  A cluster of
@@ -369,9 +404,13 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
     __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4], inv_w[4];
     __shared__ double f, gp, alpha0;
     __shared__ Candidate res[2][kCandPerCta];  // this CTA's candidates of the round, by round parity
-    __shared__ EvalAcc red[kRefineWarps];
-    __shared__ EvalConst ec[kCandPerCta];
-    __shared__ int done;
+    __shared__ float red[kRefineWarps][12];
+    // every step size this CTA evaluates in one line search, formed with the
+    // direction: slot s = round * kCandPerCta + h
+    constexpr int kMaxSlots = kLineSearch * kCandPerCta;  // enough for C = 1
+    __shared__ EvalConst slot_ec[kMaxSlots];
+    __shared__ double slot_z[kMaxSlots][4], slot_th[kMaxSlots][4];
+    __shared__ int done, slot0;
     const int b = blockIdx.x / C;
     const uint32_t rank = C > 1 ? cluster_rank() : 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -394,22 +433,24 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             z[pi] = p0 * inv_w[pi];
             th_cur[pi] = p0;  // the parameters themselves: returned unchanged if no step is taken
         }
-        if (lane < 4 * kCandPerCta) put_const(&ec[lane >> 2], pi, p0, inv_fs);
+        if (lane < 4 * kCandPerCta) put_const(&slot_ec[lane >> 2], pi, p0, inv_fs);
         if (lane < 16) H[lane] = (lane % 5 == 0) ? 1.0 : 0.0;
         if (lane == 0) done = steps > 0 ? 0 : 1;
     }
     __syncthreads();
     {  // the start point (every group of every CTA of the cluster evaluates it, with the same bits)
         double s0, g0;
-        eval_cands(ec, r, L, red, &s0, &g0);
+        eval_cands(slot_ec, r, L, red, &s0, &g0);
         if (warp == 0 && lane < 4) {
             const double sg = s0 < 0.0 ? -1.0 : 1.0;
             gz[pi] = -sg * g0 * box.w[pi];
             if (lane == 0) f = -fabs(s0);
         }
     }
-    int it = 0, j0 = 0, par = 0;
+    int it = 0, j0 = 0, par = 0, rr = 0;
     bool new_dir = true;
+    const int per_round = C * kCandPerCta;
+    const int n_slots = (kLineSearch + per_round - 1) / per_round * kCandPerCta;
     for (;;) {
         if (warp == 0) {
             __syncwarp();
@@ -437,30 +478,41 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
                 }
                 new_dir = false;
                 j0 = 0;
+                rr = 0;
+                __syncwarp();
+                // the steps alpha0 2^-j of every round for this CTA, one (slot,
+                // parameter) pair per lane: their set-up (an FP64 exp each for
+                // 1/dt) runs side by side once per iteration
+                for (int t = lane; t < 4 * n_slots; t += 32) {
+                    const int sl = t >> 2, i = t & 3;
+                    const int j = (sl / kCandPerCta) * per_round + (int)rank * kCandPerCta + sl % kCandPerCta;
+                    const double a = alpha0 * pow2_neg(j < kLineSearch ? j : 0);
+                    double v = fma(a, p[i], z[i]) * box.w[i];
+                    v = v < box.lo[i] ? box.lo[i] : (v > box.hi[i] ? box.hi[i] : v);
+                    slot_z[sl][i] = v * inv_w[i];
+                    slot_th[sl][i] = v;
+                    put_const(&slot_ec[sl], i, v, inv_fs);
+                }
                 __syncwarp();
             }
-            if (!done && lane < 4 * kCandPerCta) {  // this CTA's steps of the round: alpha0 2^-(j0 + q)
-                const int hh = lane >> 2;
-                const int j = j0 + (int)rank * kCandPerCta + hh;
-                const double a = alpha0 * pow2_neg(j < kLineSearch ? j : 0);
-                double v = fma(a, p[pi], z[pi]) * box.w[pi];
-                v = v < box.lo[pi] ? box.lo[pi] : (v > box.hi[pi] ? box.hi[pi] : v);
-                res[par][hh].z[pi] = v * inv_w[pi];
-                res[par][hh].th[pi] = v;
-                put_const(&ec[hh], pi, v, inv_fs);
-                if (pi == 0) res[par][hh].valid = j < kLineSearch ? 1.0 : 0.0;
-            }
-            __syncwarp();
+            if (lane == 0) slot0 = rr * kCandPerCta;
         }
         __syncthreads();
         if (done) break;
+        const int s0 = slot0;
         double sc, gi;
-        eval_cands(ec, r, L, red, &sc, &gi);
+        eval_cands(slot_ec + s0, r, L, red, &sc, &gi);
         if (warp % kCandWarps == 0 && lane < 4) {
-            const int hh = warp / kCandWarps;
+            const int hh = warp / kCandWarps, sl = s0 + hh;
             const double sg = sc < 0.0 ? -1.0 : 1.0;
             res[par][hh].g[pi] = -sg * gi * box.w[pi];
-            if (lane == 0) res[par][hh].f = -fabs(sc);
+            res[par][hh].z[pi] = slot_z[sl][pi];
+            res[par][hh].th[pi] = slot_th[sl][pi];
+            if (lane == 0) {
+                const int j = (sl / kCandPerCta) * per_round + (int)rank * kCandPerCta + hh;
+                res[par][hh].f = -fabs(sc);
+                res[par][hh].valid = j < kLineSearch ? 1.0 : 0.0;
+            }
         }
         // every CTA's candidate of this round is published
         if (C > 1)
@@ -528,7 +580,8 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
                 }
                 new_dir = true;
             } else {
-                j0 += C * kCandPerCta;
+                j0 += per_round;
+                ++rr;
                 if (j0 >= kLineSearch && lane == 0) done = 1;  // no acceptable step: stop
             }
         }
