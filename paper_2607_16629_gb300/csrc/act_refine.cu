@@ -232,15 +232,17 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// A double in the shared memory of CTA `rank` of this cluster, at the offset
-// of p in this CTA's (C == 1: this CTA's own).
-__device__ __forceinline__ double ld_cluster_f64(const double *p, uint32_t rank, int C) {
-    if (C == 1) return *(volatile const double *)p;
+// Stores v into the shared memory of CTA `rank` of this cluster, at the
+// offset of p in this CTA's (C == 1: this CTA's own).  Made visible to that
+// CTA by the next cluster barrier (release / acquire).
+__device__ __forceinline__ void st_cluster_f64(double *p, uint32_t rank, int C, double v) {
+    if (C == 1) {
+        *p = v;
+        return;
+    }
     uint32_t addr;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(addr) : "r"(smem_u32(p)), "r"(rank));
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
-    return v;
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
 // One line-search candidate's evaluation, published to the cluster:
@@ -403,7 +405,10 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
                                                           double *__restrict__ theta_out, int C) {
     __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4], inv_w[4];
     __shared__ double f, gp, alpha0;
-    __shared__ Candidate res[2][kCandPerCta];  // this CTA's candidates of the round, by round parity
+    // the round's candidates of the whole cluster (q = rank kCandPerCta + h),
+    // pushed here by their owners before the round's cluster barrier; by
+    // round parity
+    __shared__ Candidate res[2][kRefineCluster * kCandPerCta];
     __shared__ float red[kRefineWarps][12];
     // every step size this CTA evaluates in one line search, formed with the
     // direction: slot s = round * kCandPerCta + h
@@ -502,16 +507,20 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
         const int s0 = slot0;
         double sc, gi;
         eval_cands(slot_ec + s0, r, L, red, &sc, &gi);
-        if (warp % kCandWarps == 0 && lane < 4) {
+        if (warp % kCandWarps == 0 && lane < 4 * C) {
+            // lane = (destination CTA, parameter): this candidate into every
+            // CTA's list of the round
             const int hh = warp / kCandWarps, sl = s0 + hh;
+            const uint32_t dst = (uint32_t)(lane >> 2);
+            Candidate &cd = res[par][(int)rank * kCandPerCta + hh];
             const double sg = sc < 0.0 ? -1.0 : 1.0;
-            res[par][hh].g[pi] = -sg * gi * box.w[pi];
-            res[par][hh].z[pi] = slot_z[sl][pi];
-            res[par][hh].th[pi] = slot_th[sl][pi];
-            if (lane == 0) {
+            st_cluster_f64(&cd.g[pi], dst, C, -sg * gi * box.w[pi]);
+            st_cluster_f64(&cd.z[pi], dst, C, slot_z[sl][pi]);
+            st_cluster_f64(&cd.th[pi], dst, C, slot_th[sl][pi]);
+            if (pi == 0) {
                 const int j = (sl / kCandPerCta) * per_round + (int)rank * kCandPerCta + hh;
-                res[par][hh].f = -fabs(sc);
-                res[par][hh].valid = j < kLineSearch ? 1.0 : 0.0;
+                st_cluster_f64(&cd.f, dst, C, -fabs(sc));
+                st_cluster_f64(&cd.valid, dst, C, j < kLineSearch ? 1.0 : 0.0);
             }
         }
         // every CTA's candidate of this round is published
@@ -524,22 +533,18 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             // of CTA q / kCandPerCta, step alpha0 2^-(j0 + q)) and its Armijo test
             int ok = 0;
             if (lane < C * kCandPerCta) {
-                const Candidate &cq = res[par][lane % kCandPerCta];
-                const uint32_t owner = (uint32_t)(lane / kCandPerCta);
-                const double fq = ld_cluster_f64(&cq.f, owner, C);
-                const double vq = ld_cluster_f64(&cq.valid, owner, C);
+                const Candidate &cq = res[par][lane];
                 const double aq = alpha0 * pow2_neg(j0 + lane < kLineSearch ? j0 + lane : 0);
-                ok = vq != 0.0 && fq <= f + 1e-4 * aq * gp;
+                ok = cq.valid != 0.0 && cq.f <= f + 1e-4 * aq * gp;
             }
             const unsigned acc = __ballot_sync(0xffffffffu, ok);
             if (acc) {
                 const int q = __ffs((int)acc) - 1;  // the largest accepted step
-                const Candidate &cq = res[par][q % kCandPerCta];
-                const uint32_t owner = (uint32_t)(q / kCandPerCta);
-                const double zq = ld_cluster_f64(&cq.z[pi], owner, C);
-                const double gq = ld_cluster_f64(&cq.g[pi], owner, C);
-                const double tq = ld_cluster_f64(&cq.th[pi], owner, C);
-                const double fq = ld_cluster_f64(&cq.f, owner, C);
+                const Candidate &cq = res[par][q];
+                const double zq = cq.z[pi];
+                const double gq = cq.g[pi];
+                const double tq = cq.th[pi];
+                const double fq = cq.f;
                 // BFGS inverse update H' = (I - rho s y^T) H (I - rho y s^T) + rho s s^T when <y, s> > 0
                 const double si = zq - z[pi], yi = gq - gz[pi];
                 const double ys = sum4(yi * si);
