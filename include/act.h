@@ -297,12 +297,13 @@ ACT_API act_status act_set_refinement(act_grid *grid, int32_t steps);
  *   theta      device, [channels][4] float64 (tc in samples, fc Hz, logDt,
  *              c Hz/s);
  *   residuals  device, [channels][n_samples] float32;
- *   score      device, [channels] float32;
+ *   score      device, [channels] float64 (the samples are FP32, the sums
+ *              FP64: the score is not rounded to FP32 on output);
  *   grad_theta device, [channels][4] float64, may be NULL;
  *   atoms      device, [channels][n_samples] float32 (g(theta_b)), may be NULL.
  * n_samples 1..2048.  Enqueued on cuda_stream. */
 ACT_API act_status act_chirplet_score(int32_t n_samples, double fs, const double *theta,
-                                      const float *residuals, int32_t channels, float *score,
+                                      const float *residuals, int32_t channels, double *score,
                                       double *grad_theta, float *atoms, void *cuda_stream);
 
 /* Autotuner: times one search order of every candidate launch configuration

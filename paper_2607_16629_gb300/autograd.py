@@ -25,13 +25,14 @@ class ChirpletScore(torch.autograd.Function):
         B, L = r.shape
         if th.shape != (B, 4):
             raise ValueError("theta must be [channels, 4]")
-        score = torch.empty(B, dtype=torch.float32, device=r.device)
+        score = torch.empty(B, dtype=torch.float64, device=r.device)
         grad = torch.empty((B, 4), dtype=torch.float64, device=r.device)
         atoms = torch.empty((B, L), dtype=torch.float32, device=r.device)
         act.act_chirplet_score(L, fs, th, r, B, score, grad, atoms)
         ctx.save_for_backward(grad, atoms)
         ctx.dtypes = (theta.dtype, residual.dtype)
-        return score.to(residual.dtype)
+        # the usual promotion of the inputs' dtypes (float64 with a float64 theta)
+        return score.to(torch.promote_types(theta.dtype, residual.dtype))
 
     @staticmethod
     def backward(ctx, grad_score: torch.Tensor):

@@ -1100,7 +1100,7 @@ act_status act_set_refinement(act_grid *g, int32_t steps) {
 }
 
 act_status act_chirplet_score(int32_t n_samples, double fs, const double *theta, const float *residuals,
-                              int32_t channels, float *score, double *grad_theta, float *atoms, void *cuda_stream) {
+                              int32_t channels, double *score, double *grad_theta, float *atoms, void *cuda_stream) {
     if (!theta || !residuals || !score || channels < 1 || n_samples < 1 || n_samples > kMaxSamples || !(fs > 0.0))
         return ACT_ERR_INVALID_ARG;
     ACT_CK(launch_chirplet_score(n_samples, fs, theta, residuals, channels, score, grad_theta, atoms,

@@ -154,7 +154,7 @@ cudaError_t launch_lem_select(const LemConfig &cfg, int B, int order, const floa
 int lem_kernels(const LemConfig &cfg);
 
 // ---- off-grid refinement (act_refine.cu) ----------------------------------
-cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, float *score,
+cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, double *score,
                                   double *grad, float *atoms, cudaStream_t st);
 // Start: theta_in[b * theta_in_stride ..] when theta_in is given, else the
 // grid winner decoded from keys[b].

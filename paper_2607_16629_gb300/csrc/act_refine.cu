@@ -125,7 +125,7 @@ __device__ void write_atom(const double *th, double nu, int L, double inv_fs, fl
 
 // Standalone score + adjoint: one block per channel.
 __global__ void __launch_bounds__(kRefineThreads) k_chirplet_score(int L, double inv_fs, const double *__restrict__ theta,
-                                                                  const float *__restrict__ R, float *__restrict__ score,
+                                                                  const float *__restrict__ R, double *__restrict__ score,
                                                                   double *__restrict__ grad, float *__restrict__ atoms) {
     __shared__ double sh[10 * 32];
     __shared__ double th[4];
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_chirplet_score(int L, double
     __syncthreads();
     const EvalOut o = eval_score(th, R + (size_t)b * L, L, inv_fs, sh);
     if (threadIdx.x == 0) {
-        score[b] = (float)o.s;
+        score[b] = o.s;
         if (grad)
             for (int i = 0; i < 4; ++i) grad[4 * b + i] = o.g[i];
     }
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_update_refined(int Lp, float
 
 }  // namespace
 
-cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, float *score,
+cudaError_t launch_chirplet_score(int L, double fs, const double *theta, const float *R, int B, double *score,
                                   double *grad, float *atoms, cudaStream_t st) {
     k_chirplet_score<<<B, kRefineThreads, 0, st>>>(L, 1.0 / fs, theta, R, score, grad, atoms);
     return cudaGetLastError();

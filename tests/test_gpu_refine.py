@@ -32,7 +32,7 @@ def test_adjoint_kernel_matches_oracle_gradient():
         s_ref, g_ref = oracle.score_grad(th, fs, r.astype(np.float32).astype(np.float64))
         theta = torch.tensor([th], dtype=torch.float64, device="cuda")
         res = torch.tensor(r[None, :], dtype=torch.float32, device="cuda")
-        score = torch.empty(1, device="cuda")
+        score = torch.empty(1, dtype=torch.float64, device="cuda")
         grad = torch.empty((1, 4), dtype=torch.float64, device="cuda")
         atoms = torch.empty((1, L), device="cuda")
         act.act_chirplet_score(L, fs, theta, res, 1, score, grad, atoms)
@@ -67,20 +67,25 @@ def test_autograd_function_gradients():
         assert np.linalg.norm(gt[b] - w[b].item() * g_ref) <= 1e-4 * np.linalg.norm(g_ref) * abs(w[b].item()) + 1e-7
         atom, _ = oracle.atom(*thetas[b], fs, L)
         assert np.max(np.abs(gr[b] - w[b].item() * atom)) <= 1e-6 * max(1.0, abs(w[b].item()))
-    # central differences of the GPU score (FP32 score: moderate steps, loose bound)
-    hs = [0.05, 0.005, 0.005, 0.05]
+    # fourth-order central differences of the GPU's own score (FP64 output;
+    # its samples are FP32, which sets the steps): against the adjoint kernel
+    # and the oracle
+    hs = [0.2, 0.02, 0.02, 0.2]
+    worst = 0.0
     for i, h in enumerate(hs):
-        tp = thetas.copy()
-        tm = thetas.copy()
-        tp[:, i] += h
-        tm[:, i] -= h
-        with torch.no_grad():
-            sp = chirplet_score(torch.tensor(tp, device="cuda"), res, fs).double().cpu().numpy()
-            sm = chirplet_score(torch.tensor(tm, device="cuda"), res, fs).double().cpu().numpy()
-        fd = (sp - sm) / (2 * h)
+        def s_at(d):
+            t = thetas.copy()
+            t[:, i] += d
+            with torch.no_grad():
+                return chirplet_score(torch.tensor(t, device="cuda"), res, fs).cpu().numpy()
+        fd = (8.0 * (s_at(h) - s_at(-h)) - (s_at(2 * h) - s_at(-2 * h))) / (12.0 * h)
         for b in range(B):
             _, g_ref = oracle.score_grad(thetas[b], fs, r[b].astype(np.float32).astype(np.float64))
-            assert abs(fd[b] - g_ref[i]) <= 2e-2 * np.linalg.norm(g_ref), (i, b, fd[b], g_ref[i])
+            err = abs(fd[b] - g_ref[i]) / np.linalg.norm(g_ref)
+            worst = max(worst, err)
+            assert err <= 3e-3, (i, b, fd[b], g_ref[i])  # measured worst 1.7e-3
+            assert abs(fd[b] - gt[b, i] / w[b].item()) <= 3e-3 * np.linalg.norm(g_ref)
+    print(f"finite differences vs oracle gradient: worst {worst:.2e} of |g|")
 
 
 def _refined(grid, sigs, P, steps, mode=act.ACT_DICT_FP32):
@@ -174,3 +179,50 @@ def test_refinement_after_the_tensor_core_search():
     b = _refined(grid, sigs, 3, 20, act.ACT_DICT_BF16)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_autograd_function_drives_a_refinement():
+    """The adjoint behind ChirpletScore drives an off-grid refinement on its
+    own: torch's L-BFGS maximises |s(theta)| from the grid winner through the
+    autograd Function (every score and gradient from the adjoint kernel), and
+    reaches the optimum the in-graph BFGS kernel reaches from the same start
+    (Fig. 1's refinement step)."""
+    w = synth.workload_c5(4)
+    grid = w.grid
+    sig = w.signals.astype(np.float32)
+    B, L, fs = sig.shape[0], grid.n_samples, grid.fs
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        x = torch.tensor(sig, device="cuda")
+        a0, _, _, _ = act.decompose(h, x, 1)            # grid winners
+        act.act_set_refinement(h, 20)
+        a1, c1, _, _ = act.decompose(h, x, 1)           # the kernel's refinement
+        torch.cuda.synchronize()
+    finally:
+        act.act_destroy(h)
+    start = act.atom_params(a0).cpu().numpy()[:, 0]
+    kern = act.atom_params(a1).cpu().numpy()[:, 0]
+    wgt, lo, hi = oracle.refine_box(grid)
+    wgt_t = torch.tensor(wgt, device="cuda")
+    z = torch.tensor(start / wgt, device="cuda", requires_grad=True)
+    opt = torch.optim.LBFGS([z], lr=0.5, max_iter=60, line_search_fn="strong_wolfe", tolerance_grad=1e-12,
+                            tolerance_change=1e-15)
+
+    def closure():
+        opt.zero_grad()
+        loss = -chirplet_score(z * wgt_t, x, fs).abs().sum()
+        loss.backward()
+        return loss
+    opt.step(closure)
+    th = (z.detach() * wgt_t).cpu().numpy()
+    for b in range(B):
+        r = sig[b].astype(np.float64)
+        s_auto, _ = oracle.score_grad(th[b], fs, r)
+        s_kern, _ = oracle.score_grad(kern[b], fs, r)
+        s_grid, _ = oracle.score_grad(start[b], fs, r)
+        assert abs(s_kern) >= abs(s_grid) and abs(s_auto) >= abs(s_grid)
+        assert abs(abs(s_auto) - abs(s_kern)) <= 1e-5 * abs(s_kern), (b, s_auto, s_kern)
+        # the optimum is flat along some axes (logDt): parameters within 0.05 grid steps
+        assert np.max(np.abs(th[b] - kern[b]) / wgt) <= 5e-2, (b, th[b], kern[b])
+        assert abs(abs(c1.cpu().numpy()[b, 0]) - abs(s_kern)) <= 1e-5 * abs(s_kern)
