@@ -224,6 +224,23 @@ ACT_API act_status act_set_memory_budget(act_grid *grid, uint64_t bytes);
  * and makes ragged plans built on the grid stale. */
 ACT_API act_status act_set_wait_limit(act_grid *grid, int64_t ns);
 
+/* Whether the tensor-core template search (ACT_SEARCH_SHIFT_BF16) may run
+ * its GEMM on CTA pairs: a cluster of two CTAs on two SMs shares each
+ * tcgen05 MMA (cta_group::2, M = 256: each CTA's 128 shifted residual rows
+ * against one 256-template tile), each SM staging its own rows and half of
+ * the templates.  1 (the default): pairs where they apply (256-template
+ * tiles, at least two row tiles, a work unit for every pair the device
+ * holds); 0: one SM per MMA (M = 128) always.  Selections are identical
+ * either way.  Errors: ACT_ERR_INVALID_ARG for other values.  Changing it
+ * re-records the grid's graphs. */
+ACT_API act_status act_set_cta_pairs(act_grid *grid, int32_t enable);
+
+/* *used = 1 when a `channels`-channel ACT_SEARCH_SHIFT_BF16 decomposition on
+ * this grid (as built and set now) runs its GEMM on CTA pairs, else 0
+ * (also without a template build).  Errors: ACT_ERR_INVALID_ARG for
+ * channels < 1 or a null pointer. */
+ACT_API act_status act_get_cta_pairs(const act_grid *grid, int32_t channels, int32_t *used);
+
 /* Test aid for out-of-memory handling: the nth device allocation made by
  * this library from now on (any grid, any thread; nth >= 1) fails once, as
  * if the device were out of memory.  The call that makes it returns

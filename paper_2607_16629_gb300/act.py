@@ -37,6 +37,7 @@ EXPORTS = (
     "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
     "act_set_refinement", "act_chirplet_score", "act_set_lem", "act_set_shift_tuning", "act_get_shift_tuning",
     "act_dictionary_mode", "act_set_memory_budget", "act_set_wait_limit", "act_inject_alloc_failure",
+    "act_set_cta_pairs", "act_get_cta_pairs",
 )
 
 
@@ -126,6 +127,8 @@ def load_library(path: str = LIB_PATH):
         lib.act_set_memory_budget.argtypes = [_P, ctypes.c_uint64]
         lib.act_set_wait_limit.argtypes = [_P, ctypes.c_int64]
         lib.act_inject_alloc_failure.argtypes = [ctypes.c_int32]
+        lib.act_set_cta_pairs.argtypes = [_P, ctypes.c_int32]
+        lib.act_get_cta_pairs.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -380,6 +383,18 @@ def act_set_memory_budget(grid: int, n_bytes: int) -> None:
 
 def act_set_wait_limit(grid: int, ns: int) -> None:
     _check(load_library().act_set_wait_limit(grid, int(ns)), "act_set_wait_limit")
+
+
+def act_set_cta_pairs(grid: int, enable: bool) -> None:
+    """Whether the tensor-core template GEMM may pair SMs (cta_group::2)."""
+    _check(load_library().act_set_cta_pairs(grid, 1 if enable else 0), "act_set_cta_pairs")
+
+
+def act_get_cta_pairs(grid: int, channels: int) -> bool:
+    """Whether a `channels`-channel tensor-core template search runs its GEMM on CTA pairs."""
+    used = ctypes.c_int32(0)
+    _check(load_library().act_get_cta_pairs(grid, int(channels), ctypes.byref(used)), "act_get_cta_pairs")
+    return bool(used.value)
 
 
 def act_inject_alloc_failure(nth: int) -> None:

@@ -148,6 +148,7 @@ struct act_grid {
     bool gemv_stream = false;  // FP32 search by the bulk-copy streaming GEMV (one CTA per SM)
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
     unsigned long long wait_ns = kWaitLimitNs;  // limit of each bounded device-side wait
+    bool cta_pairs = true;  // the tensor-core template GEMM may pair SMs (cta_group::2)
     uint64_t mem_budget = 0;  // bytes ACT_DICT_AUTO may give the dictionary (0: free device memory)
     LemConfig lem;         // hierarchical search settings
     cudaStream_t cap = nullptr;
@@ -416,7 +417,7 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
         } else if (mode == ACT_SEARCH_SHIFT_BF16) {
             // programmatic dependents between kernel nodes only (not next to profiling events)
             ACT_CK(launch_shift_tc_gemm(g->shift_tc, w.stc, g->shift, w.R, g->Lp, g->L, B, g->stats, g->status, st,
-                                        !profiling, g->wait_ns));
+                                        !profiling, g->wait_ns, g->cta_pairs));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             ACT_CK(launch_shift_tc_resolve(g->shift_tc, w.stc, g->shift, w.R, g->Lp, g->L, B, w.keys, w.fb_list,
                                            w.fb_count, g->stats, g->status, st, !profiling, g->wait_ns));
@@ -1360,6 +1361,21 @@ act_status act_set_wait_limit(act_grid *g, int64_t ns) {
         drop_graphs(g);
         ++g->generation;
     }
+    return ACT_OK;
+}
+
+act_status act_set_cta_pairs(act_grid *g, int32_t enable) {
+    if (!g || (enable != 0 && enable != 1)) return ACT_ERR_INVALID_ARG;
+    if ((enable != 0) != g->cta_pairs) {
+        g->cta_pairs = enable != 0;  // the recorded graphs hold the other kernel
+        drop_graphs(g);
+    }
+    return ACT_OK;
+}
+
+act_status act_get_cta_pairs(const act_grid *g, int32_t channels, int32_t *used) {
+    if (!g || !used || channels < 1) return ACT_ERR_INVALID_ARG;
+    *used = (g->shift_tc && shift_tc_uses_pairs(g->shift_tc, g->shift, channels, g->cta_pairs)) ? 1 : 0;
     return ACT_OK;
 }
 

@@ -133,16 +133,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             mbar_expect_tx(&sm.bar_a, (uint32_t)(nkc * kAChunkBytes));
             for (int kc = 0; kc < nkc; ++kc) tma_load_2d(a_smem + kc * kAChunkBytes, &tmA, kc * kBK, 0, &sm.bar_a);
         }
-        uint32_t it = 0;
+        uint32_t s = 0, ph = 0;  // the ring's stage and its phase parity
         for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
             const int64_t tile = w / m_tiles;
             const int mt = (int)(w - tile * m_tiles);
             // row of this tile's first chunk in the tile-major layout viewed as [rows][64]
             const int64_t atom0 = tile * BN;
             const int64_t blk = atom0 / kBlockRows, sub = atom0 % kBlockRows;
-            for (int kc = 0; kc < nkc; ++kc, ++it) {
-                const int s = (int)(it % (uint32_t)stages);
-                const uint32_t ph = (it / (uint32_t)stages) & 1u;
+            for (int kc = 0; kc < nkc; ++kc) {
                 if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u, wait_ns)) {
                     *abort_flag = 1;
                     break;
@@ -153,13 +151,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (a_stream)
                     tma_load_2d(b_smem + s * stage_bytes + Cfg::kStageBytes, &tmA, kc * kBK, mt * kBM,
                                 &sm.bar_full[s]);
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         if (!a_stream && !mbar_wait(&sm.bar_a, 0, wait_ns)) *abort_flag = 1;
         tc_fence_after();
-        uint32_t it = 0, local = 0;
+        // the issuing thread must keep up with the tensor core (one 128 x 256 x 16
+        // MMA per 128 cycles): no divisions, descriptors formed once per stage
+        uint32_t s = 0, ph = 0, local = 0;
         for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++local) {
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
             if (!mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u, wait_ns)) {
@@ -168,9 +172,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             }
             tc_fence_after();
             const uint32_t d_tmem = tmem + acc * BN;
-            for (int kc = 0; kc < nkc; ++kc, ++it) {
-                const int s = (int)(it % (uint32_t)stages);
-                const uint32_t ph = (it / (uint32_t)stages) & 1u;
+            for (int kc = 0; kc < nkc; ++kc) {
                 if (!mbar_wait(&sm.bar_full[s], ph, wait_ns)) {
                     *abort_flag = 1;
                     break;
@@ -178,11 +180,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tc_fence_after();
                 const uint32_t b0 = b_smem + s * stage_bytes;
                 const uint32_t a0 = a_stream ? b0 + Cfg::kStageBytes : a_smem + kc * kAChunkBytes;
+                const uint64_t adesc = smem_desc(a0), bdesc = smem_desc(b0);
 #pragma unroll
                 for (int k = 0; k < kBK / kUmmaK; ++k)
-                    tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2), Cfg::kIdesc,
+                    tc_mma(d_tmem, smem_desc_k(adesc, k), smem_desc_k(bdesc, k), Cfg::kIdesc,
                            (kc | k) != 0 ? 1u : 0u);
                 tc_commit(&sm.bar_empty[s]);
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
             }
             tc_commit(&sm.bar_acc_full[acc]);
         }

@@ -33,6 +33,27 @@ inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, 
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// launch_kernel for a 1-D cluster of cluster_x CTAs (grid a multiple of it).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel_cluster(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                         bool pdl, int cluster_x, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster_x;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Device-side status flags (one int per grid, OR-ed by kernels).
 enum : int {
     kFlagNonFinite = 1,
@@ -252,9 +273,12 @@ void shift_tc_scratch_free(ShiftTcScratch &x);
 // pdl: the first kernel of each call follows a kernel node directly (no
 // event node between), so it may be a programmatic dependent; the kernels
 // inside a call always are.
+// Whether a B-channel launch runs the paired-SM GEMM.
+bool shift_tc_uses_pairs(const ShiftTc *s, const ShiftPlan &sp, int B, bool pairs_allowed);
+// pairs_allowed: the paired-SM GEMM (cta_group::2) may be chosen where it applies.
 cudaError_t launch_shift_tc_gemm(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
                                  int Lp, int L, int B, long long *stats, int *status, cudaStream_t st, bool pdl = false,
-                                 unsigned long long wait_ns = kWaitLimitNs);
+                                 unsigned long long wait_ns = kWaitLimitNs, bool pairs_allowed = true);
 cudaError_t launch_shift_tc_resolve(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
                                     int Lp, int L, int B, unsigned long long *keys, int *fb_list, int *counters,
                                     long long *stats, int *status, cudaStream_t st, bool pdl = false,

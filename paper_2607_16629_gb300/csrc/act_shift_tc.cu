@@ -40,14 +40,17 @@ constexpr int kThreads = 256;
 constexpr int kAChunkBytes = kBM * kBK * 2;  // 16 KB
 constexpr int kMaxStages = 6;
 
-// Tile of BN templates (128 or 256, MMA N).
-template <int BN>
+// Tile of BN templates (128 or 256, MMA N).  PAIR: a CTA pair shares each
+// MMA (M = 256: the two CTAs' row tiles), each CTA loading BN / 2 of the
+// templates; every CTA still holds a 128 x BN accumulator of its own rows.
+template <int BN, bool PAIR = false>
 struct ShiftTile {
-    static constexpr int kBChunkBytes = BN * kBK * 2;
+    static constexpr int kBRows = PAIR ? BN / 2 : BN;  // template rows this CTA loads
+    static constexpr int kBChunkBytes = kBRows * kBK * 2;
     static constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;
     static constexpr uint32_t kTmemCols = 2 * BN;
     static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                       ((uint32_t)(kBM >> 4) << 24);
+                                       ((uint32_t)((PAIR ? 2 * kBM : kBM) >> 4) << 24);
 };
 constexpr int kMaxItems = 1024;    // flagged (lag, block) items per channel before the full FP32 search
 constexpr int kRescanWarps = 4;     // independent warps per rescore block
@@ -103,6 +106,21 @@ __host__ __device__ inline void tile_chunks(const RowTiling &t, int mt, int &kc_
     const int kk_max = t.L - 1 + t.span0 - t.S * j_first;  // sample L - 1 at the first
     kc_lo = kk_min / kBK;
     kc_hi = kk_max / kBK;
+}
+
+// Lag chunks of GEMM row unit u: one row tile, or (pair) the union of row
+// tiles 2u and 2u + 1 (the second clamped to the last tile).  Chunks outside
+// a tile's windows multiply zeros.
+__host__ __device__ inline void unit_chunks(const RowTiling &t, bool pair, int u, int &kc_lo, int &kc_hi) {
+    if (!pair) {
+        tile_chunks(t, u, kc_lo, kc_hi);
+        return;
+    }
+    int lo1, hi1;
+    tile_chunks(t, 2 * u, kc_lo, kc_hi);
+    tile_chunks(t, min(2 * u + 1, t.m_tiles - 1), lo1, hi1);
+    kc_lo = min(kc_lo, lo1);
+    kc_hi = max(kc_hi, hi1);
 }
 
 // Shifted residual rows X[(b, j)][kk] = bf16(r_b[m_lo + kk + tc0 + S j]):
@@ -161,11 +179,18 @@ __global__ void __launch_bounds__(128) k_shift_rows(RowTiling t, const float *__
     }
 }
 
-// GEMM work item w: row tile w / n_tiles, template tile w % n_tiles.  Every
-// stage holds one template chunk (256 x 64) and the matching residual chunk
+// GEMM work item w: row unit w / n_tiles, template tile w % n_tiles.  Every
+// stage holds one template chunk (BN x 64) and the matching residual chunk
 // (128 x 64).  Warp 0: TMA producer; warp 1: MMA issuer; warp 2: tensor
 // memory owner; warps 4-7: epilogue (thread = residual row).
-template <int BN>
+//
+// PAIR (launched as clusters of 2): a unit is the row tiles 2u and 2u + 1,
+// one per CTA of the pair, over the union of their lag chunks.  Each CTA
+// loads its rows and its half of the template chunk, both copies counted on
+// the leader's (rank 0) full barrier; the leader issues the M = 256 MMAs and
+// its commits arrive on both CTAs' barriers; each CTA's epilogue reads its
+// own accumulator and releases it on the leader's barrier.
+template <int BN, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_shift_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowTiling tl,
                  int n_tiles, int nkc, int stages, int T_pad, const float *__restrict__ scaleT,
@@ -173,14 +198,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                  int *status, unsigned long long wait_ns) {
     // shared memory: stages, then the item's scales [Jt][BN + 4] (the +4
     // floats of padding spread the Jt rows a warp reads over the banks)
-    using Cfg = ShiftTile<BN>;
+    using Cfg = ShiftTile<BN, PAIR>;
     constexpr int kBChunkBytes = Cfg::kBChunkBytes, kStageBytes = Cfg::kStageBytes;
     constexpr uint32_t kTmemCols = Cfg::kTmemCols;
     extern __shared__ uint8_t dyn_raw[];
     __shared__ Smem sm;
     const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t items = (int64_t)tl.m_tiles * n_tiles;
+    // PAIR: rank in the pair, the pair's index and count (1-D clusters of 2)
+    const uint32_t rank = PAIR ? cta_rank_in_cluster() : 0u;
+    const int64_t unit0 = PAIR ? blockIdx.x / 2 : blockIdx.x;
+    const int64_t n_units = PAIR ? gridDim.x / 2 : gridDim.x;
+    const int m_units = PAIR ? (tl.m_tiles + 1) / 2 : tl.m_tiles;
+    const int64_t items = (int64_t)m_units * n_tiles;
     const int Ntc = tl.Ntc;
 
     if (threadIdx.x == 0) {
@@ -190,20 +220,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&sm.bar_acc_full[a], 1);
-            mbar_init(&sm.bar_acc_empty[a], 128);
+            // PAIR: one arrival per epilogue warp of either CTA
+            mbar_init(&sm.bar_acc_empty[a], PAIR ? 8 : 128);
         }
         sm.abort = 0;
         fence_mbar_init();
     }
     if (threadIdx.x < 2 * kBM) sm.chan_max[threadIdx.x / kBM][threadIdx.x % kBM] = 0u;
     if (warp == 2) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {  // the same columns in both CTAs, allocated by one warp of each
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&sm.tmem_base)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&sm.tmem_base)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    // PAIR: both CTAs' barriers initialised and tensor memory allocated
+    // before either copies, commits or arrives across the pair
+    if constexpr (PAIR) cluster_barrier();
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
     volatile int *abort_flag = &sm.abort;
@@ -216,57 +259,91 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- TMA producer ----------------
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-        uint32_t it = 0;
-        for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-            const int mt = (int)(w / n_tiles), nt = (int)(w % n_tiles);
+        uint32_t s = 0, ph = 0;  // the ring's stage and its phase parity
+        for (int64_t w = unit0; w < items && !*abort_flag; w += n_units) {
+            const int u = (int)(w / n_tiles), nt = (int)(w % n_tiles);
+            // this CTA's row tile (PAIR: past the last tile, load the last one again)
+            const int mt = PAIR ? min(2 * u + (int)rank, tl.m_tiles - 1) : u;
             int kc_lo, kc_hi;
-            tile_chunks(tl, mt, kc_lo, kc_hi);
-            for (int kc = kc_lo; kc <= kc_hi; ++kc, ++it) {
-                const int s = (int)(it % (uint32_t)stages);
-                const uint32_t ph = (it / (uint32_t)stages) & 1u;
-                if (!mbar_wait(&sm.bar_empty[s], ph ^ 1u, wait_ns)) {
+            unit_chunks(tl, PAIR, u, kc_lo, kc_hi);
+            for (int kc = kc_lo; kc <= kc_hi; ++kc) {
+                const bool ok = PAIR ? mbar_wait_cluster(&sm.bar_empty[s], ph ^ 1u, wait_ns)
+                                     : mbar_wait(&sm.bar_empty[s], ph ^ 1u, wait_ns);
+                if (!ok) {
                     *abort_flag = 1;
                     break;
                 }
                 const uint32_t b0 = base + (uint32_t)s * kStageBytes;
-                mbar_expect_tx(&sm.bar_full[s], (uint32_t)kStageBytes);
                 // templates: the tile-major layout seen as [blocks * nkc * 256][64]
-                const int64_t t0 = (int64_t)nt * BN, blk = t0 / kBlockRows, sub = t0 % kBlockRows;
-                tma_load_2d(b0, &tmB, 0, (int)((blk * nkc + kc) * kBlockRows + sub), &sm.bar_full[s]);
-                tma_load_2d(b0 + kBChunkBytes, &tmA, kc * kBK, mt * kBM, &sm.bar_full[s]);
+                const int64_t t0 = (int64_t)nt * BN + (int64_t)rank * Cfg::kBRows;
+                const int64_t blk = t0 / kBlockRows, sub = t0 % kBlockRows;
+                const int yB = (int)((blk * nkc + kc) * kBlockRows + sub);
+                if constexpr (PAIR) {
+                    // both CTAs' copies complete on the leader's barrier
+                    if (rank == 0) mbar_expect_tx(&sm.bar_full[s], (uint32_t)(2 * kStageBytes));
+                    const uint32_t fb = cluster_addr(&sm.bar_full[s], 0);
+                    tma_load_2d_pair(b0, &tmB, 0, yB, fb);
+                    tma_load_2d_pair(b0 + kBChunkBytes, &tmA, kc * kBK, mt * kBM, fb);
+                } else {
+                    mbar_expect_tx(&sm.bar_full[s], (uint32_t)kStageBytes);
+                    tma_load_2d(b0, &tmB, 0, yB, &sm.bar_full[s]);
+                    tma_load_2d(b0 + kBChunkBytes, &tmA, kc * kBK, mt * kBM, &sm.bar_full[s]);
+                }
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---------------- MMA issuer (PAIR: the leader only) ----------------
         tc_fence_after();
-        uint32_t it = 0, local = 0;
-        for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++local) {
+        // the issuing thread must keep up with the tensor core (one M x 256 x 16
+        // MMA per 128 cycles): no divisions, descriptors formed once per stage
+        uint32_t s = 0, ph = 0, local = 0;
+        for (int64_t w = unit0; w < items && !*abort_flag; w += n_units, ++local) {
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            if (!mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u, wait_ns)) {
+            const bool ok = PAIR ? mbar_wait_cluster(&sm.bar_acc_empty[acc], aph ^ 1u, wait_ns)
+                                 : mbar_wait(&sm.bar_acc_empty[acc], aph ^ 1u, wait_ns);
+            if (!ok) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
             const uint32_t d_tmem = tmem + acc * BN;
             int kc_lo, kc_hi;
-            tile_chunks(tl, (int)(w / n_tiles), kc_lo, kc_hi);
-            for (int kc = kc_lo; kc <= kc_hi; ++kc, ++it) {
-                const int s = (int)(it % (uint32_t)stages);
-                const uint32_t ph = (it / (uint32_t)stages) & 1u;
-                if (!mbar_wait(&sm.bar_full[s], ph, wait_ns)) {
+            unit_chunks(tl, PAIR, (int)(w / n_tiles), kc_lo, kc_hi);
+            for (int kc = kc_lo; kc <= kc_hi; ++kc) {
+                const bool full = PAIR ? mbar_wait_cluster(&sm.bar_full[s], ph, wait_ns)
+                                       : mbar_wait(&sm.bar_full[s], ph, wait_ns);
+                if (!full) {
                     *abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t b0 = base + (uint32_t)s * kStageBytes;
-                const uint32_t a0 = b0 + kBChunkBytes;
+                const uint32_t b0 = base + s * (uint32_t)kStageBytes;
+                const uint64_t bdesc = smem_desc(b0), adesc = smem_desc(b0 + kBChunkBytes);
 #pragma unroll
-                for (int k = 0; k < kBK / kUmmaK; ++k)
-                    tc_mma(d_tmem, smem_desc(a0 + k * kUmmaK * 2), smem_desc(b0 + k * kUmmaK * 2), Cfg::kIdesc,
-                           (kc != kc_lo || k != 0) ? 1u : 0u);
-                tc_commit(&sm.bar_empty[s]);
+                for (int k = 0; k < kBK / kUmmaK; ++k) {
+                    const uint32_t accum = (kc != kc_lo || k != 0) ? 1u : 0u;
+                    if constexpr (PAIR)
+                        tc_mma_pair(d_tmem, smem_desc_k(adesc, k), smem_desc_k(bdesc, k), Cfg::kIdesc, accum);
+                    else
+                        tc_mma(d_tmem, smem_desc_k(adesc, k), smem_desc_k(bdesc, k), Cfg::kIdesc, accum);
+                }
+                if constexpr (PAIR)
+                    tc_commit_pair(&sm.bar_empty[s], 0x3);
+                else
+                    tc_commit(&sm.bar_empty[s]);
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
             }
-            tc_commit(&sm.bar_acc_full[acc]);
+            if constexpr (PAIR)
+                tc_commit_pair(&sm.bar_acc_full[acc], 0x3);
+            else
+                tc_commit(&sm.bar_acc_full[acc]);
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: thread = shifted residual row ----------------
@@ -275,8 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         constexpr int kScaleLd = BN + 4;
         float *sc_sm = reinterpret_cast<float *>(dyn_raw + (base - smem_u32(dyn_raw)) + (size_t)stages * kStageBytes);
         uint32_t local = 0;
-        for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++local) {
-            const int mt = (int)(w / n_tiles), nt = (int)(w % n_tiles);
+        for (int64_t w = unit0; w < items; w += n_units, ++local) {
+            const int unit = (int)(w / n_tiles), nt = (int)(w % n_tiles);
+            const int mt = PAIR ? 2 * unit + (int)rank : unit;  // PAIR: may be one past the last tile (no rows)
             // the tile's Jt scale rows (j0 .. j0 + Jt - 1, those below Ntc), BN each
             {
                 const int j0 = (mt / tl.n_cb) * tl.Jt;
@@ -292,7 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            const int failed = (*abort_flag || !mbar_wait(&sm.bar_acc_full[acc], aph, wait_ns)) ? 1 : 0;
+            const bool landed = PAIR ? mbar_wait_cluster(&sm.bar_acc_full[acc], aph, wait_ns)
+                                     : mbar_wait(&sm.bar_acc_full[acc], aph, wait_ns);
+            const int failed = (*abort_flag || !landed) ? 1 : 0;
             if (epilogue_bar_or(failed)) {  // the epilogue warps leave together
                 *abort_flag = 1;
                 break;
@@ -301,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int lr = q * 32 + lane;
             int b, j;
             tile_row(tl, mt, lr, b, j);
-            const bool valid = b < tl.B && j < Ntc;
+            const bool valid = mt < tl.m_tiles && b < tl.B && j < Ntc;
             const float4 *sc4 = reinterpret_cast<const float4 *>(sc_sm + (valid ? lr / tl.Bg : 0) * kScaleLd);
             // per 32-template block and per tile: the largest scaled |score|
             float *bm = blk_max + ((size_t)(valid ? b : 0) * Ntc + (valid ? j : 0)) * (T_pad / 32) +
@@ -324,7 +404,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mx = fmaxf(mx, bmv[c]);
             }
             tc_fence_before();
-            mbar_arrive(&sm.bar_acc_empty[acc]);
+            if constexpr (PAIR) {  // one arrival per warp, on the leader's barrier
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(cluster_addr(&sm.bar_acc_empty[acc], 0));
+            } else {
+                mbar_arrive(&sm.bar_acc_empty[acc]);
+            }
             if (valid) {  // the row's BN / 32 block maxima are contiguous: 16-byte stores
                 float4 *bm4 = reinterpret_cast<float4 *>(bm);
 #pragma unroll
@@ -357,10 +442,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (threadIdx.x == 0) atomicOr(status, kFlagTimeout);
         sleep_ns(200000);  // let in-flight copies and MMAs land before releasing memory
     }
+    // PAIR: neither CTA leaves (or frees tensor memory) while the other may
+    // still copy into, commit to or arrive on its shared memory
+    if constexpr (PAIR) cluster_barrier();
     tc_fence_after();
     if (warp == 2) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
-                     : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                         : "memory");
     }
 }
 
@@ -542,8 +634,7 @@ constexpr int kSmemBudget = 232448 - kStaticReserve - 1024;
 struct ShiftTc {
     CUtensorMap mapB[2];    // box heights 128 and 256
     int nkc = 0, sm_count = 0, T_pad = 0;
-    int stages[2] = {0, 0};
-    size_t smem[2] = {0, 0};
+    int pair_clusters = 0;  // co-resident CTA pairs of the paired GEMM (0: not available)
     int rescan_warps = 0, rescan_blocks_per_sm = 0;
     size_t rescan_smem = 0;
 };
@@ -562,13 +653,31 @@ cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
         delete s;
         return cudaErrorNotSupported;
     }
-    const int stage_bytes[2] = {ShiftTile<128>::kStageBytes, ShiftTile<256>::kStageBytes};
+    const void *gemms[3] = {(const void *)k_shift_gemm<128, false>, (const void *)k_shift_gemm<256, false>,
+                            (const void *)k_shift_gemm<256, true>};
+    const int stage_bytes[3] = {ShiftTile<128>::kStageBytes, ShiftTile<256>::kStageBytes,
+                                ShiftTile<256, true>::kStageBytes};
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        int st = kSmemBudget / stage_bytes[i];
-        s->stages[i] = st > kMaxStages ? kMaxStages : st;
-        s->smem[i] = 1024 + (size_t)s->stages[i] * stage_bytes[i];
-        e = allow_max_smem(i == 0 ? (const void *)k_shift_gemm<128> : (const void *)k_shift_gemm<256>, s->smem[i]);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = allow_max_smem(gemms[i], 1024 + 2 * (size_t)stage_bytes[i]);
+    if (e == cudaSuccess) {
+        // how many CTA pairs fit at once with the largest launch's shared memory
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * (unsigned)sm_count);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = 1024 + (size_t)kSmemBudget;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_shift_gemm<256, true>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            clusters = 0;
+        }
+        s->pair_clusters = clusters;
     }
     // rescore: per warp the residual and two P-row buffers; as many warps per
     // block (up to kRescanWarps) as fit
@@ -656,9 +765,12 @@ cudaError_t shift_tc_reserve(const ShiftTc *s, const ShiftPlan &sp, int B, Shift
     return cudaSuccess;
 }
 
-// Template tile width of a B-channel launch: 256 unless that leaves SMs
-// idle or leaves room for fewer than two stages beside the tile's scale rows.
-static int shift_tc_bn(const ShiftTc *s, const ShiftPlan &sp, const RowTiling &tl, int *stages, size_t *smem) {
+// GEMM form of a B-channel launch: the template tile width (256 unless that
+// leaves SMs idle or leaves room for fewer than two stages beside the tile's
+// scale rows) and whether CTA pairs share each MMA (256-wide tiles, at least
+// two row tiles, a work unit for every pair that fits, pairs allowed).
+static int shift_tc_bn(const ShiftTc *s, const ShiftPlan &sp, const RowTiling &tl, bool pairs_allowed, int *stages,
+                       size_t *smem, bool *pair) {
     auto smem_for = [&](int bn, int stage_bytes, int *stg_out) {
         const size_t sc = (size_t)tl.Jt * (bn + 4) * sizeof(float);
         int stg = (int)((kSmemBudget - (int64_t)sc) / stage_bytes);
@@ -666,9 +778,24 @@ static int shift_tc_bn(const ShiftTc *s, const ShiftPlan &sp, const RowTiling &t
         *stg_out = stg;
         return 1024 + (size_t)stg * stage_bytes + sc;
     };
+    *pair = false;
     int st256 = 0;
     const size_t sm256 = smem_for(256, ShiftTile<256>::kStageBytes, &st256);
     if ((int64_t)tl.m_tiles * (sp.T_pad / 256) >= s->sm_count && st256 >= 2) {
+        int stp = 0;
+        const size_t smp = smem_for(256, ShiftTile<256, true>::kStageBytes, &stp);
+        const int64_t units = (int64_t)((tl.m_tiles + 1) / 2) * (sp.T_pad / 256);
+        if (pairs_allowed && s->pair_clusters > 0 && tl.m_tiles >= 2 && units >= s->pair_clusters && stp >= 2) {
+            // the whole budget: every operand read of a stage's MMAs stays
+            // inside the allocation even at the last stage
+            static_assert((kMaxStages - 1) * ShiftTile<256, true>::kStageBytes + 48 * 1024 <= kSmemBudget,
+                          "paired stages beyond the shared-memory budget");
+            (void)smp;
+            *pair = true;
+            *stages = stp;
+            *smem = 1024 + (size_t)kSmemBudget;
+            return 256;
+        }
         *stages = st256;
         *smem = sm256;
         return 256;
@@ -677,9 +804,18 @@ static int shift_tc_bn(const ShiftTc *s, const ShiftPlan &sp, const RowTiling &t
     return 128;
 }
 
+bool shift_tc_uses_pairs(const ShiftTc *s, const ShiftPlan &sp, int B, bool pairs_allowed) {
+    if (!s || B < 1) return false;
+    int stages = 0;
+    size_t smem = 0;
+    bool pair = false;
+    shift_tc_bn(s, sp, make_tiling(sp, B), pairs_allowed, &stages, &smem, &pair);
+    return pair;
+}
+
 cudaError_t launch_shift_tc_gemm(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
                                  int Lp, int L, int B, long long *stats, int *status, cudaStream_t st, bool pdl,
-                                 unsigned long long wait_ns) {
+                                 unsigned long long wait_ns, bool pairs_allowed) {
     if (!s || B < 1 || B > x.B_cap) return cudaErrorInvalidValue;
     const RowTiling tl = make_tiling(sp, B);
     cudaError_t e = launch_kernel(k_shift_rows, dim3(tl.m_tiles * kBM), dim3(128), 0, st, pdl, tl, R, Lp, sp.tc0,
@@ -690,16 +826,25 @@ cudaError_t launch_shift_tc_gemm(const ShiftTc *s, const ShiftTcScratch &x, cons
     if (!make_map(&mapA, x.X, (uint64_t)sp.Kt, (uint64_t)m_tiles * kBM, kBM)) return cudaErrorInvalidValue;
     int stages = 0;
     size_t smem = 0;
-    const int bn = shift_tc_bn(s, sp, tl, &stages, &smem);
-    const int i = bn == 256 ? 1 : 0;
+    bool pair = false;
+    const int bn = shift_tc_bn(s, sp, tl, pairs_allowed, &stages, &smem, &pair);
     const int n_tiles = sp.T_pad / bn;
+    if (stages < 2) return cudaErrorInvalidValue;
+    if (pair) {
+        // clusters of 2: each CTA loads 128-template halves (box height 128)
+        const int64_t units = (int64_t)((m_tiles + 1) / 2) * n_tiles;
+        const int pairs = (int)(units < s->pair_clusters ? units : s->pair_clusters);
+        return launch_kernel_cluster(k_shift_gemm<256, true>, dim3(2 * pairs), dim3(kThreads), smem, st, true, 2, mapA,
+                                     s->mapB[0], tl, n_tiles, s->nkc, stages, sp.T_pad, sp.scaleT, x.tile_max,
+                                     x.blk_max, x.chmax, status, wait_ns);
+    }
+    const int i = bn == 256 ? 1 : 0;
     const int64_t items = (int64_t)m_tiles * n_tiles;
     const int grid = (int)(items < s->sm_count ? items : s->sm_count);
-    if (stages < 2) return cudaErrorInvalidValue;
     // a programmatic dependent of the shifted-row build (set-up overlaps it)
-    return launch_kernel(bn == 256 ? k_shift_gemm<256> : k_shift_gemm<128>, dim3(grid), dim3(kThreads), smem, st, true,
-                         mapA, s->mapB[i], tl, n_tiles, s->nkc, stages, sp.T_pad, sp.scaleT, x.tile_max, x.blk_max,
-                         x.chmax, status, wait_ns);
+    return launch_kernel(bn == 256 ? k_shift_gemm<256, false> : k_shift_gemm<128, false>, dim3(grid), dim3(kThreads),
+                         smem, st, true, mapA, s->mapB[i], tl, n_tiles, s->nkc, stages, sp.T_pad, sp.scaleT,
+                         x.tile_max, x.blk_max, x.chmax, status, wait_ns);
 }
 
 cudaError_t launch_shift_tc_resolve(const ShiftTc *s, const ShiftTcScratch &x, const ShiftPlan &sp, const float *R,
@@ -710,7 +855,8 @@ cudaError_t launch_shift_tc_resolve(const ShiftTc *s, const ShiftTcScratch &x, c
     const RowTiling tl = make_tiling(sp, B);
     int stages = 0;
     size_t smem = 0;
-    const int bn = shift_tc_bn(s, sp, tl, &stages, &smem);  // the GEMM's tile width for B channels
+    bool pair = false;
+    const int bn = shift_tc_bn(s, sp, tl, false, &stages, &smem, &pair);  // the GEMM's tile width for B channels
     const int n_tiles = sp.T_pad / bn;
     const int entries = sp.Ntc * n_tiles;
     int slices = (entries + 255) / 256;

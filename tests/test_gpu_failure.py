@@ -81,6 +81,33 @@ def test_wait_limit_zero_times_out_then_recovers(name, build, search, tuning, mu
         act.act_destroy(ref_h)
 
 
+def test_wait_limit_zero_paired_template_gemm():
+    """The paired-SM template GEMM (a cluster of two CTAs): both CTAs give up,
+    wait for each other, release their tensor memory and exit; the next call
+    is clean and equal to a fresh grid's."""
+    B, P = 16, 2
+    grid = synth.grid_eeg()
+    sig = np.stack([synth.eeg_like_signal(3, ch)[0] for ch in range(B)])
+    h = _grid(act.ACT_DICT_RECOMPUTE, act.ACT_SEARCH_SHIFT_BF16, grid)
+    ref_h = _grid(act.ACT_DICT_RECOMPUTE, act.ACT_SEARCH_SHIFT_BF16, grid)
+    try:
+        assert act.act_get_cta_pairs(h, B)
+        st_ref, ref = _run(ref_h, sig, P)
+        assert st_ref == act.ACT_OK
+        act.act_set_wait_limit(h, 0)
+        st, _ = _run(h, sig, P)
+        assert st == act.ACT_ERR_DEVICE_TIMEOUT, act.status_name(st)
+        assert act.act_grid_status(h) == act.ACT_OK
+        act.act_set_wait_limit(h, 2_000_000_000)
+        st, out = _run(h, sig, P)
+        assert st == act.ACT_OK, act.status_name(st)
+        for x, y in zip(out, ref):
+            assert np.array_equal(x, y)
+    finally:
+        act.act_destroy(h)
+        act.act_destroy(ref_h)
+
+
 def test_negative_wait_limit_rejected():
     h = act.act_grid_create(synth.grid_small_test(), 0)
     try:

@@ -87,6 +87,60 @@ def test_eeg_like_channels_full_grid():
     assert items < 64 * 4 * 16
 
 
+def odd_tiles():
+    """100 whole-sample time centres (step 4) over the EEG templates: at 32
+    channels the rows form 25 tiles of 32 channels x 4 time centres, an odd
+    count, so the last CTA pair has a second tile without rows."""
+    g = synth.grid_eeg()
+    return synth.Grid(g.n_samples, g.fs, synth.Axis(0.0, 4.0, 100), g.fc, g.logdt, g.c)
+
+
+@pytest.mark.parametrize("name,grid_fn,B", [
+    ("eeg_8ch", synth.grid_eeg, 8),            # pairs of tiles 16 time centres apart (one channel block)
+    ("eeg_64ch", synth.grid_eeg, 64),          # pairs of channel blocks at the same time centres
+    ("eeg_130ch", synth.grid_eeg, 130),        # 5 channel blocks, the last with 2 channels
+    ("odd_tiles_32ch", odd_tiles, 32),         # 25 row tiles: the last pair's second tile is empty
+])
+def test_cta_pairs_equal_single_sm(name, grid_fn, B):
+    """The paired-SM GEMM (cta_group::2, M = 256 over two CTAs' row tiles)
+    and the single-SM GEMM give the same decomposition bit for bit, and both
+    equal the FP32 template search's."""
+    grid = grid_fn()
+    sig = np.stack([synth.eeg_like_signal(4, 300 + b)[0] for b in range(B)]).astype(np.float32)
+    P = 3
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        act.act_set_search(h, act.ACT_SEARCH_SHIFT)
+        ref = gpu_decompose(h, sig, P)
+        act.act_set_search(h, act.ACT_SEARCH_SHIFT_BF16)
+        assert act.act_get_cta_pairs(h, B)
+        paired = gpu_decompose(h, sig, P)
+        act.act_set_cta_pairs(h, False)
+        assert not act.act_get_cta_pairs(h, B)
+        single = gpu_decompose(h, sig, P)
+        act.act_set_cta_pairs(h, True)
+        again = gpu_decompose(h, sig, P)
+    finally:
+        act.act_destroy(h)
+    assert_same(paired, single)
+    assert_same(paired, ref)
+    assert_same(again, paired)
+
+
+def test_cta_pairs_not_used_where_they_do_not_apply():
+    h = act.act_grid_create(synth.grid_eeg(), 0)
+    try:
+        assert not act.act_get_cta_pairs(h, 64)  # no template build yet
+        act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        assert not act.act_get_cta_pairs(h, 1)   # one row tile
+        assert act.act_get_cta_pairs(h, 64)
+        with pytest.raises(act.ActError):
+            act.act_get_cta_pairs(h, 0)
+    finally:
+        act.act_destroy(h)
+
+
 def test_lockstep_against_oracle():
     grid = eeg_small()
     s, _ = synth.eeg_like_signal(2, 7)
