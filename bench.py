@@ -698,6 +698,11 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks, peaks, 
         st0 = act.act_bf16_stats(h)
         t64 = _time_decompose(act, torch, h, sig64, P, max(3, steps // 4), stream, dev)
         st1 = act.act_bf16_stats(h)
+        pairs64 = act.act_get_cta_pairs(h, B)
+        # the same search with one SM per MMA (cta_group::1), for comparison
+        act.act_set_cta_pairs(h, False)
+        s64 = _time_decompose(act, torch, h, sig64, P, 2, stream, dev)
+        act.act_set_cta_pairs(h, True)
         act.act_set_search(h, act.ACT_SEARCH_SHIFT)
         f64 = _time_decompose(act, torch, h, sig64, P, 2, stream, dev)
         act.act_set_search(h, act.ACT_SEARCH_SHIFT_BF16)
@@ -707,7 +712,8 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks, peaks, 
     finally:
         act.act_destroy(h)
     same_fp32 = all(torch.equal(a, b) for a, b in zip(f1[5], t1[5])) and \
-        all(torch.equal(a, b) for a, b in zip(f64[5], t64[5]))
+        all(torch.equal(a, b) for a, b in zip(f64[5], t64[5])) and \
+        all(torch.equal(a, b) for a, b in zip(s64[5], t64[5]))
     same_gemv = bool(torch.equal(act.atom_indices(f1[5][0]), act.atom_indices(fp32_atoms)))
     T = grid.fc.count * grid.logdt.count * grid.c.count
     S, Ntc = int(grid.tc.step), grid.tc.count
@@ -750,6 +756,7 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks, peaks, 
                 "tensor_ms_per_step": t64[0], "tensor_value": B * K * P / (t64[0] / 1e3),
                 "fp32_template_ms_per_step": f64[0], "fp32_template_value": B * K * P / (f64[0] / 1e3),
                 "unit": UNIT, "search_ms_per_order": t64[1], "rows_gemm_ms_per_order": t64[2],
+                "cta_pairs": pairs64, "single_sm_rows_gemm_ms_per_order": s64[2],
                 "resolved_items_fallbacks": fb,
                 "roofline": {"bound": "tensor", "achieved": alg64, "peak": tc_peak, "unit": "TFLOP/s",
                              "frac": alg64 / tc_peak,
@@ -757,7 +764,8 @@ def bench_shift(args, dev, stream, fp32_ms_per_step, fp32_atoms, clocks, peaks, 
                                                          ["paper_2607_16629_gb300/csrc/act_shift_tc.cu",
                                                           "paper_2607_16629_gb300/csrc/act_tc.cuh",
                                                           "paper_2607_16629_gb300/csrc/act_device.cuh"]),
-                             "kernel": "k_shift_rows + k_shift_gemm<256> (BF16 tcgen05, scaled tile maxima)",
+                             "kernel": "k_shift_rows + k_shift_gemm<256, pair> (BF16 tcgen05 on CTA pairs, "
+                                       "scaled tile maxima)",
                              "algorithmic_flops_per_launch": 2.0 * B * K * L,
                              "mma_flops_per_launch": mma_flops, "mma_tflops": mma64,
                              "mma_frac": mma64 / tc_peak, "avg_launch_ms": t64[2],
