@@ -123,28 +123,37 @@ __host__ __device__ inline void unit_chunks(const RowTiling &t, bool pair, int u
     kc_hi = max(kc_hi, hi1);
 }
 
-// Shifted residual rows X[(b, j)][kk] = bf16(r_b[m_lo + kk + tc0 + S j]):
-// blockIdx.x = X row (tile mt, local row lr), each thread 8 consecutive kk as
-// one 16-byte store; padding rows (b >= B or j >= Ntc) are not written (the
-// GEMM's epilogue ignores them).  The block of (b, 0) also prepares channel
-// b's selection for this order: |r| and |bf16(r) - r| (for the error bound),
-// the channel maximum and item count cleared.
-__global__ void __launch_bounds__(128) k_shift_rows(RowTiling t, const float *__restrict__ R, int Lp, int tc0,
-                                                    int m_lo, int Kt, __nv_bfloat16 *__restrict__ X,
-                                                    double2 *__restrict__ chan_norm, unsigned int *__restrict__ chmax,
-                                                    int *__restrict__ chcount, long long *__restrict__ stats) {
+// Shifted residual rows X[(b, j)][kk] = bf16(r_b[m_lo + kk + tc0 + S j]),
+// zero where the index leaves [0, L).  Block (g * n_seg + seg, b) writes
+// channel b's rows for time centres j0 = g RJ .. j0 + RJ - 1 (those below
+// Ntc), lags kk in [k0, k1) = [seg KSEG, min(Kt, (seg + 1) KSEG)).  It stages
+// the samples those pieces cover, n_lo + i for i in [0, span) with
+// n_lo = m_lo + tc0 + S j0 + k0 and span = S (rows - 1) + k1 - k0, as BF16
+// in shared memory: once as read (global loads issued four at a time), then
+// in 8 copies shifted by 0..7 samples built from it (copy s holds sample
+// i + s at i): the 8 samples of any 16-byte output piece, at offset
+// o = S jj + kk - k0, are one aligned 16-byte load from copy o & 7.  Padding
+// rows (b >= B or j >= Ntc) are not written (the GEMM's epilogue ignores
+// them).  Block (0, b) also prepares channel b's selection for this order:
+// |r| and |bf16(r) - r| (for the error bound), the channel maximum and item
+// count cleared.
+__global__ void __launch_bounds__(256) k_shift_rows(RowTiling t, const float *__restrict__ R, int Lp, int tc0,
+                                                    int m_lo, int Kt, int RJ, int KSEG, int n_seg, int span_pad,
+                                                    __nv_bfloat16 *__restrict__ X, double2 *__restrict__ chan_norm,
+                                                    unsigned int *__restrict__ chmax, int *__restrict__ chcount,
+                                                    long long *__restrict__ stats) {
+    extern __shared__ __align__(16) uint8_t rows_raw[];
     __shared__ float sh[32];
     // a programmatic dependent of the previous kernel (the residual update):
     // wait for it in every block, then let the GEMM launch
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int row = blockIdx.x;
-    int b, j;
-    tile_row(t, row / kBM, row % kBM, b, j);
-    if (b >= t.B || j >= t.Ntc) return;
+    const int b = blockIdx.y, g = blockIdx.x / n_seg, seg = blockIdx.x - g * n_seg;
+    const int j0 = g * RJ, nj = min(RJ, t.Ntc - j0);
+    const int k0 = seg * KSEG, k1 = min(Kt, k0 + KSEG);
     const int L = t.L, S = t.S;
     const float *r = R + (size_t)b * Lp;
-    if (j == 0) {
+    if (blockIdx.x == 0) {
         // FP32 sums of at most 2048 squares are within 2048 * 2^-24 < 1.3e-4
         // (relative) of the exact ones: inflated by 1e-3 they bound them
         float e = 0.0f, de = 0.0f;
@@ -163,19 +172,52 @@ __global__ void __launch_bounds__(128) k_shift_rows(RowTiling t, const float *__
             atomicAdd((unsigned long long *)&stats[0], 1ull);
         }
     }
-    const int n0 = m_lo + tc0 + S * j;  // sample under kk = 0
-    uint4 *out = reinterpret_cast<uint4 *>(X + (size_t)row * Kt);
-    for (int c = threadIdx.x; c < (Kt >> 3); c += blockDim.x) {
-        uint32_t w[4];
+    if (nj <= 0 || k0 >= k1) return;
+    // the 8 shifted BF16 copies, span_pad (a multiple of 8, >= span) samples
+    // each, then the plain staged window of span_pad + 8 samples
+    __nv_bfloat16 *plain = reinterpret_cast<__nv_bfloat16 *>(rows_raw) + 8 * span_pad;
+    const int n_lo = m_lo + tc0 + S * j0 + k0;
+    const int total = span_pad + 8;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+        float x[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int n = n0 + 8 * c + 2 * h;
-            const float x0 = (n >= 0 && n < L) ? r[n] : 0.0f;
-            const float x1 = (n + 1 >= 0 && n + 1 < L) ? r[n + 1] : 0.0f;
-            __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
-            w[h] = *reinterpret_cast<uint32_t *>(&v);
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x, n = n_lo + i;
+            x[u] = (i < total && n >= 0 && n < L) ? r[n] : 0.0f;
         }
-        out[c] = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < total) plain[i] = __float2bfloat16_rn(x[u]);
+        }
+    }
+    __syncthreads();
+    // copy s, pair q = plain samples 2q + s and 2q + s + 1: as 32-bit words of
+    // the plain window, word q + s / 2, shifted by a half word when s is odd
+    const int half = span_pad >> 1;
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(plain);
+    uint32_t *cw = reinterpret_cast<uint32_t *>(rows_raw);
+    for (int q = threadIdx.x; q < half; q += blockDim.x) {
+        uint32_t w[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u) w[u] = pw[q + u];
+#pragma unroll
+        for (int sft = 0; sft < 8; ++sft)
+            cw[sft * half + q] = (sft & 1) ? __funnelshift_r(w[sft >> 1], w[(sft >> 1) + 1], 16) : w[sft >> 1];
+    }
+    __syncthreads();
+    const uint4 *cp16 = reinterpret_cast<const uint4 *>(rows_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = k0 >> 3, c1 = k1 >> 3;
+    const int cb = b / t.Bg, bl = b - cb * t.Bg;
+    for (int jj = warp; jj < nj; jj += blockDim.x >> 5) {
+        const int j = j0 + jj, gt = j / t.Jt, jl = j - gt * t.Jt;
+        const int row = (gt * t.n_cb + cb) * kBM + jl * t.Bg + bl;
+        uint4 *out = reinterpret_cast<uint4 *>(X + (size_t)row * Kt);
+        for (int c = c0 + lane; c < c1; c += 32) {
+            const int o = S * jj + 8 * c - k0, sft = o & 7;
+            out[c] = cp16[(sft * span_pad + (o - sft)) >> 3];
+        }
     }
 }
 
@@ -659,6 +701,7 @@ cudaError_t shift_tc_prepare(ShiftTc **out, const ShiftPlan &sp, int sm_count) {
                                 ShiftTile<256, true>::kStageBytes};
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = allow_max_smem(gemms[i], 1024 + 2 * (size_t)stage_bytes[i]);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_shift_rows, 0);
     if (e == cudaSuccess) {
         // how many CTA pairs fit at once with the largest launch's shared memory
         cudaLaunchConfig_t cfg = {};
@@ -818,8 +861,23 @@ cudaError_t launch_shift_tc_gemm(const ShiftTc *s, const ShiftTcScratch &x, cons
                                  unsigned long long wait_ns, bool pairs_allowed) {
     if (!s || B < 1 || B > x.B_cap) return cudaErrorInvalidValue;
     const RowTiling tl = make_tiling(sp, B);
-    cudaError_t e = launch_kernel(k_shift_rows, dim3(tl.m_tiles * kBM), dim3(128), 0, st, pdl, tl, R, Lp, sp.tc0,
-                                  sp.m_lo, sp.Kt, x.X, x.chan_norm, x.chmax, x.chcount, stats);
+    // rows per block: up to 16, fewer when that leaves SMs idle (at least 4);
+    // lag segments keep the 8 staged copies within 64 KB of shared memory
+    int RJ = (int)(((int64_t)B * sp.Ntc + 2 * s->sm_count - 1) / (2 * s->sm_count));
+    RJ = RJ < 4 ? 4 : (RJ > 16 ? 16 : RJ);
+    constexpr int kRowsSmemSamples = 65536 / 18;  // samples per copy in 64 KB of 8 BF16 copies + the plain one
+    while (RJ > 1 && sp.S * (RJ - 1) + 8 + 64 > kRowsSmemSamples) --RJ;
+    int KSEG = sp.Kt;
+    if (sp.S * (RJ - 1) + 8 + KSEG > kRowsSmemSamples) KSEG = (kRowsSmemSamples - 8 - sp.S * (RJ - 1)) / 64 * 64;
+    if (KSEG < 64) return cudaErrorInvalidValue;
+    const int n_seg = (sp.Kt + KSEG - 1) / KSEG;
+    const int span_pad = (sp.S * (RJ - 1) + KSEG + 7) & ~7;
+    const size_t rows_smem = ((size_t)9 * span_pad + 8) * sizeof(__nv_bfloat16);
+    const int64_t gx = (int64_t)((sp.Ntc + RJ - 1) / RJ) * n_seg;
+    if (gx >= ((int64_t)1 << 31) || B > 65535) return cudaErrorInvalidValue;
+    cudaError_t e = launch_kernel(k_shift_rows, dim3((unsigned)gx, B), dim3(256), rows_smem, st, pdl, tl, R, Lp,
+                                  sp.tc0, sp.m_lo, sp.Kt, RJ, KSEG, n_seg, span_pad, x.X, x.chan_norm, x.chmax,
+                                  x.chcount, stats);
     if (e != cudaSuccess) return e;
     const int m_tiles = tl.m_tiles;
     CUtensorMap mapA;
