@@ -193,31 +193,22 @@ constexpr int kRefineWarps = kBfgsThreads / 32;
 constexpr int kCandPerCta = 2;     // line-search step sizes each CTA evaluates per round
 constexpr int kCandWarps = kRefineWarps / kCandPerCta;  // warps per step size
 
-// Sum over each group of 4 lanes (lane i of a group holds parameter i).
-__device__ __forceinline__ double sum4(double v) {
+// Sum over each group of 4 lanes (lane i of a group holds parameter i); the
+// same bits in every lane of the group (FP32 addition commutes).
+__device__ __forceinline__ float sum4f(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     return v + __shfl_xor_sync(0xffffffffu, v, 2);
 }
 
-// 1 / sqrt(x) for a positive finite double: the FP32 reciprocal square root
-// as the seed, then two Newton-Raphson steps y <- y (3 - x y^2) / 2 in FP64
-// (each squares the relative error: 2^-22 -> 2^-43 -> below 2^-53 + rounding).
-// x below 2^-100 is scaled by 2^100 first (exact, so the seed stays a normal
-// FP32 number), without a branch.  On this GPU an FP64 square root followed
-// by a division costs about ten dependent FP64 operations more.
-__device__ __forceinline__ double rsqrt_newton(double x) {
-    const bool tiny = x < 0x1p-100;
-    const double xs = tiny ? x * 0x1p100 : x;
-    double y = (double)rsqrtf((float)xs);
-    const double h = 0.5 * xs;
-    y = y * fma(-h * y, y, 1.5);
-    y = y * fma(-h * y, y, 1.5);
-    return tiny ? y * 0x1p50 : y;
-}
+// 2^-j for 0 <= j < 126, exact (built from the exponent bits).
+__device__ __forceinline__ float pow2_negf(int j) { return __int_as_float((127 - j) << 23); }
 
-// 2^-j for 0 <= j < 1023, exact (built from the exponent bits).
-__device__ __forceinline__ double pow2_neg(int j) {
-    return __longlong_as_double((long long)(1023 - j) << 52);
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ bool ff_less(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+// a - b rounded to FP32 (a and b close: the pair difference is nearly exact)
+__device__ __forceinline__ float ff_diff(ff a, ff b) {
+    const ff d = ff_add(a, ff_neg(b));
+    return d.hi + d.lo;
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -235,43 +226,46 @@ __device__ __forceinline__ void cluster_sync_all() {
 // Stores v into the shared memory of CTA `rank` of this cluster, at the
 // offset of p in this CTA's (C == 1: this CTA's own).  Made visible to that
 // CTA by the next cluster barrier (release / acquire).
-__device__ __forceinline__ void st_cluster_f64(double *p, uint32_t rank, int C, double v) {
+__device__ __forceinline__ void st_cluster_f32(float *p, uint32_t rank, int C, float v) {
     if (C == 1) {
         *p = v;
         return;
     }
     uint32_t addr;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(addr) : "r"(smem_u32(p)), "r"(rank));
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
 // One line-search candidate's evaluation, published to the cluster:
-// f = -|s|, the scaled gradient, and the candidate in scaled and natural
-// coordinates.
+// f = -|s| (float pair), the scaled gradient (FP32) and the candidate in
+// scaled coordinates (float pairs).
 struct Candidate {
-    double f;
-    double valid;  // 1: a step size of this round (j < kLineSearch)
-    double g[4], z[4], th[4];
+    ff f;
+    float valid;  // 1: a step size of this round (j < kLineSearch)
+    float g[4];
+    ff z[4];
 };
 
 // The per-candidate constants of Eq. (1) for lane i = parameter i of warp 0,
-// formed in parallel: lane 0 tc, lane 1 fc, lane 2 1/dt = exp(-logDt),
-// lane 3 c (each a float pair; 1/fs is fixed).
-__device__ __forceinline__ void put_const(EvalConst *ec, int i, double v, double inv_fs) {
+// formed in parallel from the parameter v as a float pair: lane 0 tc, lane 1
+// fc, lane 2 1/dt = exp(-logDt), lane 3 c (1/fs is fixed).  1/dt only
+// scales the envelope argument, which is rounded to FP32, so the FP32
+// exponential gives it to the precision the sample uses.
+__device__ __forceinline__ void put_const(EvalConst *ec, int i, ff v, ff inv_fs) {
     if (i == 0) {
-        ec->k.tc = ff_from_double(v);
-        ec->k.inv_fs = ff_from_double(inv_fs);
-        ec->inv_fs = (float)inv_fs;
+        ec->k.tc = v;
+        ec->k.inv_fs = inv_fs;
+        ec->inv_fs = inv_fs.hi;
     } else if (i == 1) {
-        ec->k.fc = ff_from_double(v);
-        ec->fc = (float)v;
+        ec->k.fc = v;
+        ec->fc = v.hi;
     } else if (i == 2) {
-        const double inv_dt = exp(-v);
-        ec->k.inv_dt = ff_from_double(inv_dt);
-        ec->inv_dt = (float)inv_dt;
+        const float inv_dt = expf(-(v.hi + v.lo));
+        ec->k.inv_dt = ff{inv_dt, 0.0f};
+        ec->inv_dt = inv_dt;
     } else {
-        ec->k.c = ff_from_double(v);
-        ec->c = (float)v;
+        ec->k.c = v;
+        ec->c = v.hi;
     }
 }
 
@@ -310,7 +304,7 @@ __device__ __forceinline__ void eval_warp_scatter(const EvalAcc &a, int lane, fl
 // Returned in every lane of each group's first warp: the score s and
 // component (lane & 3) of its gradient (zeros elsewhere).
 __device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__restrict__ r, int L, float (*red)[12],
-                                           double *s_out, double *gi_out) {
+                                           ff *s_out, float *gi_out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = warp / kCandWarps, t = (int)threadIdx.x - h * kCandWarps * 32;
     EvalAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0, 0, 0, 0}, {0, 0, 0, 0}};
@@ -345,8 +339,8 @@ __device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__r
         }
     }
     __syncthreads();
-    *s_out = 0.0;
-    *gi_out = 0.0;
+    *s_out = ff{0.0f, 0.0f};
+    *gi_out = 0.0f;
     if (warp != h * kCandWarps) return;
     __syncwarp();  // the finish runs with the whole warp converged
     // lane 0: ru, lane 2: uu (float-float), lanes 4..11: the gradient sums,
@@ -381,8 +375,8 @@ __device__ __forceinline__ void eval_cands(const EvalConst *ec, const float *__r
     const ff y2 = ff_add_f(y1, 0.5f * y1.hi * e1);
     const ff sff = ff_mul(ru, y2);
     const float sf = sff.hi + sff.lo;
-    *s_out = ok ? ff_to_double(sff) : 0.0;
-    *gi_out = ok ? (double)fmaf(rdi, y2.hi, -sf * y2.hi * y2.hi * udi) : 0.0;
+    *s_out = ok ? sff : ff{0.0f, 0.0f};
+    *gi_out = ok ? fmaf(rdi, y2.hi, -sf * y2.hi * y2.hi * udi) : 0.0f;
 }
 
 // BFGS refinement of channel b's grid winner; theta_out[b][4].  A cluster of
@@ -403,8 +397,14 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
                                                           const unsigned long long *__restrict__ keys,
                                                           const double *__restrict__ theta_in, int theta_in_stride,
                                                           double *__restrict__ theta_out, int C) {
-    __shared__ double z[4], gz[4], H[16], Hn[16], p[4], th_cur[4], sv[4], yv[4], inv_w[4];
-    __shared__ double f, gp, alpha0;
+    // BFGS state: scaled coordinates z and objective f = -|s| as float pairs,
+    // the scaled gradient, inverse Hessian, direction and step sizes in FP32
+    // (FP64 runs at a small fraction of the FP32 rate on this GPU, and this
+    // bookkeeping is the serial part of every iteration)
+    __shared__ ff z[4], f, zlo[4], zhi[4], wff[4];
+    __shared__ float gz[4], H[16], Hn[16], p[4], sv[4], yv[4], wf[4];
+    __shared__ float gp, alpha0;
+    __shared__ double th0[4];  // the start, returned unchanged if no step is taken
     // the round's candidates of the whole cluster (q = rank kCandPerCta + h),
     // pushed here by their owners before the round's cluster barrier; by
     // round parity
@@ -414,15 +414,15 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
     // direction: slot s = round * kCandPerCta + h
     constexpr int kMaxSlots = kLineSearch * kCandPerCta;  // enough for C = 1
     __shared__ EvalConst slot_ec[kMaxSlots];
-    __shared__ double slot_z[kMaxSlots][4], slot_th[kMaxSlots][4];
-    __shared__ int done, slot0;
+    __shared__ ff slot_z[kMaxSlots][4];
+    __shared__ int done, slot0, moved;
     const int b = blockIdx.x / C;
     const uint32_t rank = C > 1 ? cluster_rank() : 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pi = lane & 3;  // the parameter of this lane in warp 0's bookkeeping
     const float *r = R + (size_t)b * Lp;
     const int L = ax.L;
-    const double inv_fs = 1.0 / ax.fs;
+    const ff inv_fs = ff_from_double(1.0 / ax.fs);
 
     if (warp == 0) {
         double p0 = 0.0;
@@ -434,22 +434,31 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             p0 = pi == 0 ? pp[0] : (pi == 1 ? pp[1] : (pi == 2 ? pp[2] : pp[3]));
         }
         if (lane < 4) {
-            inv_w[pi] = 1.0 / box.w[pi];
-            z[pi] = p0 * inv_w[pi];
-            th_cur[pi] = p0;  // the parameters themselves: returned unchanged if no step is taken
+            // the clamp box in scaled coordinates, once per launch
+            const double w = box.w[pi];
+            wff[pi] = ff_from_double(w);
+            wf[pi] = (float)w;
+            zlo[pi] = ff_from_double(box.lo[pi] / w);
+            zhi[pi] = ff_from_double(box.hi[pi] / w);
+            z[pi] = ff_from_double(p0 / w);
+            th0[pi] = p0;
         }
-        if (lane < 4 * kCandPerCta) put_const(&slot_ec[lane >> 2], pi, p0, inv_fs);
-        if (lane < 16) H[lane] = (lane % 5 == 0) ? 1.0 : 0.0;
-        if (lane == 0) done = steps > 0 ? 0 : 1;
+        if (lane < 4 * kCandPerCta) put_const(&slot_ec[lane >> 2], pi, ff_from_double(p0), inv_fs);
+        if (lane < 16) H[lane] = (lane % 5 == 0) ? 1.0f : 0.0f;
+        if (lane == 0) {
+            done = steps > 0 ? 0 : 1;
+            moved = 0;
+        }
     }
     __syncthreads();
     {  // the start point (every group of every CTA of the cluster evaluates it, with the same bits)
-        double s0, g0;
+        ff s0;
+        float g0;
         eval_cands(slot_ec, r, L, red, &s0, &g0);
         if (warp == 0 && lane < 4) {
-            const double sg = s0 < 0.0 ? -1.0 : 1.0;
-            gz[pi] = -sg * g0 * box.w[pi];
-            if (lane == 0) f = -fabs(s0);
+            const float sg = s0.hi < 0.0f ? -1.0f : 1.0f;
+            gz[pi] = -sg * g0 * wf[pi];
+            if (lane == 0) f = s0.hi < 0.0f ? s0 : ff_neg(s0);
         }
     }
     int it = 0, j0 = 0, par = 0, rr = 0;
@@ -460,43 +469,41 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
         if (warp == 0) {
             __syncwarp();
             if (!done && new_dir) {  // p = -H g (steepest descent, H reset, if not a descent direction)
-                double v = 0.0;
+                float v = 0.0f;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v = fma(-H[4 * pi + j], gz[j], v);
-                double g_p = sum4(gz[pi] * v);
-                const bool reset = !(g_p < 0.0);
+                for (int j = 0; j < 4; ++j) v = fmaf(-H[4 * pi + j], gz[j], v);
+                float g_p = sum4f(gz[pi] * v);
+                const bool reset = !(g_p < 0.0f);
                 if (reset) {
                     v = -gz[pi];
-                    g_p = sum4(gz[pi] * v);
+                    g_p = sum4f(gz[pi] * v);
                 }
-                const double pn2 = sum4(v * v);
+                const float pn2 = sum4f(v * v);
                 __syncwarp();
                 if (lane < 4) {
                     p[pi] = v;
                     if (reset)
-                        for (int k = 0; k < 4; ++k) H[4 * pi + k] = pi == k ? 1.0 : 0.0;
+                        for (int k = 0; k < 4; ++k) H[4 * pi + k] = pi == k ? 1.0f : 0.0f;
                 }
                 if (lane == 0) {
                     gp = g_p;
-                    alpha0 = pn2 > 0.25 ? 0.5 * rsqrt_newton(pn2) : 1.0;
-                    if (!(g_p < 0.0)) done = 1;
+                    alpha0 = pn2 > 0.25f ? 0.5f * rsqrtf(pn2) : 1.0f;
+                    if (!(g_p < 0.0f)) done = 1;
                 }
                 new_dir = false;
                 j0 = 0;
                 rr = 0;
                 __syncwarp();
                 // the steps alpha0 2^-j of every round for this CTA, one (slot,
-                // parameter) pair per lane: their set-up (an FP64 exp each for
-                // 1/dt) runs side by side once per iteration
+                // parameter) pair per lane, clamped to the box
                 for (int t = lane; t < 4 * n_slots; t += 32) {
                     const int sl = t >> 2, i = t & 3;
                     const int j = (sl / kCandPerCta) * per_round + (int)rank * kCandPerCta + sl % kCandPerCta;
-                    const double a = alpha0 * pow2_neg(j < kLineSearch ? j : 0);
-                    double v = fma(a, p[i], z[i]) * box.w[i];
-                    v = v < box.lo[i] ? box.lo[i] : (v > box.hi[i] ? box.hi[i] : v);
-                    slot_z[sl][i] = v * inv_w[i];
-                    slot_th[sl][i] = v;
-                    put_const(&slot_ec[sl], i, v, inv_fs);
+                    const float a = alpha0 * pow2_negf(j < kLineSearch ? j : 0);
+                    ff zc = ff_add_f(z[i], a * p[i]);
+                    zc = ff_less(zc, zlo[i]) ? zlo[i] : (ff_less(zhi[i], zc) ? zhi[i] : zc);
+                    slot_z[sl][i] = zc;
+                    put_const(&slot_ec[sl], i, ff_mul(zc, wff[i]), inv_fs);
                 }
                 __syncwarp();
             }
@@ -505,7 +512,8 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
         __syncthreads();
         if (done) break;
         const int s0 = slot0;
-        double sc, gi;
+        ff sc;
+        float gi;
         eval_cands(slot_ec + s0, r, L, red, &sc, &gi);
         if (warp % kCandWarps == 0 && lane < 4 * C) {
             // lane = (destination CTA, parameter): this candidate into every
@@ -513,14 +521,16 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             const int hh = warp / kCandWarps, sl = s0 + hh;
             const uint32_t dst = (uint32_t)(lane >> 2);
             Candidate &cd = res[par][(int)rank * kCandPerCta + hh];
-            const double sg = sc < 0.0 ? -1.0 : 1.0;
-            st_cluster_f64(&cd.g[pi], dst, C, -sg * gi * box.w[pi]);
-            st_cluster_f64(&cd.z[pi], dst, C, slot_z[sl][pi]);
-            st_cluster_f64(&cd.th[pi], dst, C, slot_th[sl][pi]);
+            const float sg = sc.hi < 0.0f ? -1.0f : 1.0f;
+            st_cluster_f32(&cd.g[pi], dst, C, -sg * gi * wf[pi]);
+            st_cluster_f32(&cd.z[pi].hi, dst, C, slot_z[sl][pi].hi);
+            st_cluster_f32(&cd.z[pi].lo, dst, C, slot_z[sl][pi].lo);
             if (pi == 0) {
                 const int j = (sl / kCandPerCta) * per_round + (int)rank * kCandPerCta + hh;
-                st_cluster_f64(&cd.f, dst, C, -fabs(sc));
-                st_cluster_f64(&cd.valid, dst, C, j < kLineSearch ? 1.0 : 0.0);
+                const ff fq = sc.hi < 0.0f ? sc : ff_neg(sc);
+                st_cluster_f32(&cd.f.hi, dst, C, fq.hi);
+                st_cluster_f32(&cd.f.lo, dst, C, fq.lo);
+                st_cluster_f32(&cd.valid, dst, C, j < kLineSearch ? 1.0f : 0.0f);
             }
         }
         // every CTA's candidate of this round is published
@@ -530,57 +540,57 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             __syncthreads();
         if (warp == 0) {
             // lane q < C kCandPerCta: candidate q of the round (slot q % kCandPerCta
-            // of CTA q / kCandPerCta, step alpha0 2^-(j0 + q)) and its Armijo test
+            // of CTA q / kCandPerCta, step alpha0 2^-(j0 + q)) and its Armijo
+            // test f_q - f <= 1e-4 a_q <g, p> (the pair difference, nearly exact)
             int ok = 0;
             if (lane < C * kCandPerCta) {
                 const Candidate &cq = res[par][lane];
-                const double aq = alpha0 * pow2_neg(j0 + lane < kLineSearch ? j0 + lane : 0);
-                ok = cq.valid != 0.0 && cq.f <= f + 1e-4 * aq * gp;
+                const float aq = alpha0 * pow2_negf(j0 + lane < kLineSearch ? j0 + lane : 0);
+                ok = cq.valid != 0.0f && ff_diff(cq.f, f) <= 1e-4f * aq * gp;
             }
             const unsigned acc = __ballot_sync(0xffffffffu, ok);
             if (acc) {
                 const int q = __ffs((int)acc) - 1;  // the largest accepted step
                 const Candidate &cq = res[par][q];
-                const double zq = cq.z[pi];
-                const double gq = cq.g[pi];
-                const double tq = cq.th[pi];
-                const double fq = cq.f;
+                const ff zq = cq.z[pi];
+                const float gq = cq.g[pi];
+                const ff fq = cq.f;
                 // BFGS inverse update H' = (I - rho s y^T) H (I - rho y s^T) + rho s s^T when <y, s> > 0
-                const double si = zq - z[pi], yi = gq - gz[pi];
-                const double ys = sum4(yi * si);
-                const double rho = ys > 1e-300 ? 1.0 / ys : 0.0;
+                const float si = ff_diff(zq, z[pi]), yi = gq - gz[pi];
+                const float ys = sum4f(yi * si);
+                const float rho = ys > 1e-30f ? 1.0f / ys : 0.0f;
                 if (lane < 4) {
                     sv[pi] = si;
                     yv[pi] = yi;
                 }
                 __syncwarp();
-                if (rho != 0.0) {
+                if (rho != 0.0f) {
                     if (lane < 16) {  // Hn = (I - rho s y^T) H
                         const int i = lane >> 2, j = lane & 3;
-                        const double rs = rho * sv[i];
-                        double t = 0.0;
+                        const float rs = rho * sv[i];
+                        float t = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) t = fma((i == k ? 1.0 : 0.0) - rs * yv[k], H[4 * k + j], t);
+                        for (int k = 0; k < 4; ++k) t = fmaf((i == k ? 1.0f : 0.0f) - rs * yv[k], H[4 * k + j], t);
                         Hn[lane] = t;
                     }
                     __syncwarp();
                     if (lane < 16) {  // H = Hn (I - rho y s^T) + rho s s^T
                         const int i = lane >> 2, j = lane & 3;
-                        const double rs = rho * sv[j];
-                        double t = 0.0;
+                        const float rs = rho * sv[j];
+                        float t = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) t = fma(Hn[4 * i + k], (j == k ? 1.0 : 0.0) - rs * yv[k], t);
-                        H[lane] = fma(rho * sv[i], sv[j], t);
+                        for (int k = 0; k < 4; ++k) t = fmaf(Hn[4 * i + k], (j == k ? 1.0f : 0.0f) - rs * yv[k], t);
+                        H[lane] = fmaf(rho * sv[i], sv[j], t);
                     }
                 }
                 __syncwarp();
                 if (lane < 4) {
                     z[pi] = zq;
-                    th_cur[pi] = tq;
                     gz[pi] = gq;
                 }
                 if (lane == 0) {
                     f = fq;
+                    moved = 1;
                     if (++it >= steps) done = 1;
                 }
                 new_dir = true;
@@ -594,7 +604,8 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
     }
     // no CTA leaves while another may still read its candidates
     if (C > 1) cluster_sync_all();
-    if (rank == 0 && threadIdx.x < 4) theta_out[4 * b + threadIdx.x] = th_cur[threadIdx.x];
+    if (rank == 0 && threadIdx.x < 4)
+        theta_out[4 * b + threadIdx.x] = moved ? ff_to_double(ff_mul(z[threadIdx.x], wff[threadIdx.x])) : th0[threadIdx.x];
 }
 
 // Coefficient and residual update with the refined atom g(theta*) generated
