@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_chirplet_score(int L, double
 
 struct RefineBox {
     double w[4], lo[4], hi[4];
+    double inv_w[4], zlo[4], zhi[4];  // 1 / w and the box in scaled coordinates (formed on the host)
 };
 
 // Sums of one evaluation: the objective's two in float-float, the eight of
@@ -438,9 +439,9 @@ __global__ void __launch_bounds__(kBfgsThreads) k_refine(GridAxes ax, RefineBox 
             const double w = box.w[pi];
             wff[pi] = ff_from_double(w);
             wf[pi] = (float)w;
-            zlo[pi] = ff_from_double(box.lo[pi] / w);
-            zhi[pi] = ff_from_double(box.hi[pi] / w);
-            z[pi] = ff_from_double(p0 / w);
+            zlo[pi] = ff_from_double(box.zlo[pi]);
+            zhi[pi] = ff_from_double(box.zhi[pi]);
+            z[pi] = ff_from_double(p0 * box.inv_w[pi]);
             th0[pi] = p0;
         }
         if (lane < 4 * kCandPerCta) put_const(&slot_ec[lane >> 2], pi, ff_from_double(p0), inv_fs);
@@ -711,6 +712,9 @@ cudaError_t launch_refine(const GridAxes &ax, int steps, int Lp, const float *R,
         box.w[i] = st_i > 0.0 ? st_i : 1.0;
         box.lo[i] = st_i > 0.0 ? fmin(first, last) - st_i : first;
         box.hi[i] = st_i > 0.0 ? fmax(first, last) + st_i : first;
+        box.inv_w[i] = 1.0 / box.w[i];
+        box.zlo[i] = box.lo[i] / box.w[i];
+        box.zhi[i] = box.hi[i] / box.w[i];
     }
     // a cluster of kRefineCluster CTAs per channel when the device can place
     // one, else one CTA per channel (the same search, one step size a round)
