@@ -429,12 +429,13 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
                                        g->stats, g->status, g->gemv_grid, st, g->wait_ns));
             kernels += 4;
         } else {
+            // programmatic dependents between kernel nodes only (not next to profiling events)
             if (g->gemv_stream)
                 ACT_CK(launch_gemv_stream_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
-                                                 g->sm_count, st, g->wait_ns));
+                                                 g->sm_count, st, g->wait_ns, !profiling));
             else
                 ACT_CK(launch_gemv_argmax(g->d32, g->K, g->Lp, w.R, B, nullptr, nullptr, w.keys, g->status,
-                                          g->gemv_grid, st, g->wait_ns));
+                                          g->gemv_grid, st, g->wait_ns, !profiling));
             if (profiling) ACT_CK(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
             kernels += 1;
         }
@@ -458,7 +459,7 @@ act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_searc
             ++kernels;
         } else {
             ACT_CK(launch_update(g->d32, g->Lp, g->L, w.R, R16, g->Lb, B, w.keys, g->ax, k, P, w.atoms, w.coefs,
-                                 w.energy, bf16 ? w.fb_count : nullptr, st));
+                                 w.energy, bf16 ? w.fb_count : nullptr, st, !profiling));
             ++kernels;
         }
     }

@@ -34,6 +34,12 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const float *__restrict__
     __shared__ float red_s[kGemvThreads / 32][NB];
     __shared__ uint32_t red_i[kGemvThreads / 32][NB];
 
+    // launched as a programmatic dependent of the kernel before it (the
+    // residual update, or the queue that count_dev counts): every block waits
+    // for it before reading the residuals, the count or the keys, then lets
+    // the next kernel launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kGemvThreads / 32;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
@@ -186,26 +192,25 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const float *__restrict__
 template <int NV, int NB, bool WS>
 static cudaError_t gemv_instance(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                  const int *count_dev, unsigned long long *keys, float *scores, int *status,
-                                 int grid_ctas, unsigned long long wait_ns, cudaStream_t st) {
+                                 int grid_ctas, unsigned long long wait_ns, cudaStream_t st, bool pdl) {
     const size_t smem = (size_t)NB * Lp * sizeof(float);
-    k_gemv<NV, NB, WS><<<grid_ctas, kGemvThreads, smem, st>>>(D, K, Lp, R, B, chlist, count_dev, keys, scores,
-                                                              status, wait_ns);
-    return cudaGetLastError();
+    return launch_kernel(k_gemv<NV, NB, WS>, dim3(grid_ctas), dim3(kGemvThreads), smem, st, pdl, D, K, Lp, R, B,
+                         chlist, count_dev, keys, scores, status, wait_ns);
 }
 
 template <bool WS>
 static cudaError_t gemv_dispatch(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                  const int *count_dev, unsigned long long *keys, float *scores, int *status,
-                                 int grid_ctas, unsigned long long wait_ns, cudaStream_t st) {
+                                 int grid_ctas, unsigned long long wait_ns, cudaStream_t st, bool pdl = false) {
     const int nv = Lp / 128;
     // Several channels per pass over D only when the count is known on the host.
     const bool multi = (count_dev == nullptr) && B >= 4 && nv <= 4;
 #define ACT_GEMV_CASE(NVV)                                                                                 \
     case NVV:                                                                                              \
         return multi ? gemv_instance<NVV, 4, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, \
-                                                 grid_ctas, wait_ns, st)                                   \
+                                                 grid_ctas, wait_ns, st, pdl)                              \
                      : gemv_instance<NVV, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, \
-                                                 grid_ctas, wait_ns, st);
+                                                 grid_ctas, wait_ns, st, pdl);
     switch (nv) {
         ACT_GEMV_CASE(1)
         ACT_GEMV_CASE(2)
@@ -213,10 +218,10 @@ static cudaError_t gemv_dispatch(const float *D, int64_t K, int Lp, const float 
         ACT_GEMV_CASE(4)
         case 8:
             return gemv_instance<8, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, grid_ctas,
-                                           wait_ns, st);
+                                           wait_ns, st, pdl);
         case 16:
             return gemv_instance<16, 1, WS>(D, K, Lp, R, B, chlist, count_dev, keys, scores, status, grid_ctas,
-                                            wait_ns, st);
+                                            wait_ns, st, pdl);
         default:
             return cudaErrorInvalidValue;
     }
@@ -246,8 +251,9 @@ int gemv_max_ctas_per_sm(int Lp) {
 
 cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                const int *count_dev, unsigned long long *keys, int *status, int grid_ctas,
-                               cudaStream_t st, unsigned long long wait_ns) {
-    return gemv_dispatch<false>(D, K, Lp, R, B, chlist, count_dev, keys, nullptr, status, grid_ctas, wait_ns, st);
+                               cudaStream_t st, unsigned long long wait_ns, bool pdl) {
+    return gemv_dispatch<false>(D, K, Lp, R, B, chlist, count_dev, keys, nullptr, status, grid_ctas, wait_ns, st,
+                                pdl);
 }
 
 cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, int B, float *scores, int *status,

@@ -53,6 +53,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     __shared__ uint32_t red_i[kConsumerWarps];
     __shared__ int abort_sh;
     __shared__ unsigned long long issued_sh;  // bulk copies issued by the producer so far (all channels)
+    // launched as a programmatic dependent of the kernel before it (the
+    // residual update, or the queue that count_dev counts): every block waits
+    // for it before reading the residuals, the count or the keys, then lets
+    // the next kernel launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int count = count_dev ? *count_dev : B;
     // this CTA's chunks: k-th is chunk blockIdx.x + k gridDim.x of the dictionary
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 template <int NV>
 cudaError_t stream_instance(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                             const int *count_dev, unsigned long long *keys, int *status, int sm_count,
-                            cudaStream_t st, unsigned long long wait_ns) {
+                            cudaStream_t st, unsigned long long wait_ns, bool pdl) {
     const StreamShape sh = stream_shape(Lp);
     if (sh.stages < 2) return cudaErrorInvalidValue;
     const size_t smem = (size_t)sh.stages * sh.rows_per_chunk * Lp * sizeof(float);
@@ -181,23 +187,22 @@ cudaError_t stream_instance(const float *D, int64_t K, int Lp, const float *R, i
     cudaError_t e =
         cudaFuncSetAttribute(k_gemv_stream<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
     if (e != cudaSuccess) return e;
-    k_gemv_stream<NV><<<sm_count, kStreamThreads, smem, st>>>(D, K, Lp, R, B, chlist, count_dev, keys,
-                                                              sh.rows_per_chunk, sh.stages, status, wait_ns);
-    return cudaGetLastError();
+    return launch_kernel(k_gemv_stream<NV>, dim3(sm_count), dim3(kStreamThreads), smem, st, pdl, D, K, Lp, R, B,
+                         chlist, count_dev, keys, sh.rows_per_chunk, sh.stages, status, wait_ns);
 }
 
 }  // namespace
 
 cudaError_t launch_gemv_stream_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                       const int *count_dev, unsigned long long *keys, int *status, int sm_count,
-                                      cudaStream_t st, unsigned long long wait_ns) {
+                                      cudaStream_t st, unsigned long long wait_ns, bool pdl) {
     switch (Lp / 128) {
-        case 1: return stream_instance<1>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
-        case 2: return stream_instance<2>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
-        case 3: return stream_instance<3>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
-        case 4: return stream_instance<4>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
-        case 8: return stream_instance<8>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
-        case 16: return stream_instance<16>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns);
+        case 1: return stream_instance<1>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns, pdl);
+        case 2: return stream_instance<2>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns, pdl);
+        case 3: return stream_instance<3>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns, pdl);
+        case 4: return stream_instance<4>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns, pdl);
+        case 8: return stream_instance<8>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns, pdl);
+        case 16: return stream_instance<16>(D, K, Lp, R, B, chlist, count_dev, keys, status, sm_count, st, wait_ns, pdl);
         default: return cudaErrorInvalidValue;
     }
 }

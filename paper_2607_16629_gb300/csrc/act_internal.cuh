@@ -126,12 +126,12 @@ cudaError_t launch_init(const float *sig, int B, int L, int Lp, float *R, __nv_b
 cudaError_t launch_gemv_argmax(const float *D, int64_t K, int Lp, const float *R, int B,
                                const int *chlist, const int *count_dev, unsigned long long *keys,
                                int *status, int grid_ctas, cudaStream_t st,
-                               unsigned long long wait_ns = kWaitLimitNs);
+                               unsigned long long wait_ns = kWaitLimitNs, bool pdl = false);
 cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, int B, float *scores,
                            int *status, int grid_ctas, cudaStream_t st, unsigned long long wait_ns = kWaitLimitNs);
 cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
-                          float *coefs, double *energy, int *fb_count, cudaStream_t st);
+                          float *coefs, double *energy, int *fb_count, cudaStream_t st, bool pdl = false);
 cudaError_t launch_ragged_gather(const float *src, const int64_t *src_off, int B, int L, float *dst, cudaStream_t st);
 cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, const int64_t *dst_off,
                                   const act_atom *atoms, const float *coefs, const double *energy, const float *R,
@@ -141,7 +141,7 @@ cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, 
 // shared memory, one CTA per SM (act_gemv_stream.cu); same scores, same keys.
 cudaError_t launch_gemv_stream_argmax(const float *D, int64_t K, int Lp, const float *R, int B, const int *chlist,
                                       const int *count_dev, unsigned long long *keys, int *status, int sm_count,
-                                      cudaStream_t st, unsigned long long wait_ns = kWaitLimitNs);
+                                      cudaStream_t st, unsigned long long wait_ns = kWaitLimitNs, bool pdl = false);
 int gemv_ctas(int sm_count, int Lp);          // occupancy-limited, at most 4 CTAs per SM
 int gemv_max_ctas_per_sm(int Lp);
 

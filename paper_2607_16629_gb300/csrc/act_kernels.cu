@@ -9,6 +9,7 @@
 #include "act_device.cuh"
 #include "act_ff.cuh"
 #include "act_internal.cuh"
+#include "act_update.cuh"
 
 namespace act {
 
@@ -134,6 +135,8 @@ __global__ void __launch_bounds__(kUpdateThreads) k_init(const float *__restrict
                                                          int Lb, unsigned long long *__restrict__ keys,
                                                          double *__restrict__ energy, int P1, int *status) {
     __shared__ double sh[32];
+    // the first search may launch now (it waits for this kernel's completion)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int b = blockIdx.x;
     double e = 0.0;
     int bad = 0;
@@ -160,9 +163,9 @@ cudaError_t launch_init(const float *sig, int B, int L, int Lp, float *R, __nv_b
 
 // ---------------------------------------------------------------------------
 // Coefficient and residual update (Eq. (4), Fig. 1): one block per channel.
-// c_k = <g*, r_k> in FP32, r_{k+1} = r_k - c_k g*, |r_{k+1}|^2 in FP64,
-// the selected atom's parameters decoded from its flat index, the key
-// cleared for the next order.
+// c_k = <g*, r_k> in FP32, r_{k+1} = r_k - c_k g*, |r_{k+1}|^2 summed as
+// float pairs and returned in FP64, the selected atom's parameters decoded
+// from its flat index, the key cleared for the next order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kUpdateThreads) k_update(const float *__restrict__ D32, int Lp, int L,
                                                            float *__restrict__ R, __nv_bfloat16 *__restrict__ R16,
@@ -171,7 +174,11 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const float *__restri
                                                            act_atom *__restrict__ atoms, float *__restrict__ coefs,
                                                            double *__restrict__ energy, int *fb_count) {
     __shared__ float shf[32];
-    __shared__ double shd[32];
+    __shared__ ff shp[32];
+    // launched as a programmatic dependent of the search: every block waits
+    // for its keys, then lets the next search launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int b = blockIdx.x;
     const unsigned long long key = keys[b];
     const uint32_t idx = key_index(key);
@@ -182,26 +189,18 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const float *__restri
     for (int n = threadIdx.x; n < L; n += blockDim.x) part = fmaf(g[n], r[n], part);
     const float c = block_sum(part, shf);
 
-    double e = 0.0;
+    ff e = {0.0f, 0.0f};  // |r_{k+1}|^2 as a float pair (about 2^-44 relative)
     for (int n = threadIdx.x; n < L; n += blockDim.x) {
         const float v = fmaf(-c, g[n], r[n]);
         r[n] = v;
-        e = fma((double)v, (double)v, e);
+        ff_add_square(e, v);
         if (R16) R16[(int64_t)b * Lb + n] = __float2bfloat16_rn(v);
     }
-    const double tot = block_sum(e, shd);
+    const ff tot = block_sum_ff(e, shp);
+    if (threadIdx.x < 32) write_atom_lanes(ax, idx, atoms + (int64_t)b * P + k);
     if (threadIdx.x == 0) {
-        double p[4];
-        decode_params(ax, (int64_t)idx, p);
-        act_atom a;
-        a.tc = p[0];
-        a.fc = p[1];
-        a.logdt = p[2];
-        a.c = p[3];
-        a.flat_index = (int64_t)idx;
-        atoms[(int64_t)b * P + k] = a;
         coefs[(int64_t)b * P + k] = c;
-        energy[(int64_t)b * (P + 1) + k + 1] = tot;
+        energy[(int64_t)b * (P + 1) + k + 1] = ff_to_double(tot);
         keys[b] = 0ull;
         if (fb_count && b == 0) {
             fb_count[0] = 0;  // channels queued for the FP32 full search
@@ -212,10 +211,9 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const float *__restri
 
 cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms, float *coefs,
-                          double *energy, int *fb_count, cudaStream_t st) {
-    k_update<<<B, kUpdateThreads, 0, st>>>(D32, Lp, L, R, R16, Lb, keys, ax, k, P, atoms, coefs, energy,
-                                           fb_count);
-    return cudaGetLastError();
+                          double *energy, int *fb_count, cudaStream_t st, bool pdl) {
+    return launch_kernel(k_update, dim3(B), dim3(kUpdateThreads), 0, st, pdl, D32, Lp, L, R, R16, Lb, keys, ax, k, P,
+                         atoms, coefs, energy, fb_count);
 }
 
 }  // namespace act

@@ -45,6 +45,7 @@
 #include "act_device.cuh"
 #include "act_ff.cuh"
 #include "act_internal.cuh"
+#include "act_update.cuh"
 
 namespace act {
 
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kShiftMaxThreads) k_shift_search(ShiftArgs A) 
 
 // One block per channel: the winner (j, t) of keys[b], g = scale * u_t
 // read back from the template rows the search used, c = <g, r> (FP32),
-// r -= c g, |r|^2 in FP64, the atom record, the key cleared.
+// r -= c g, |r|^2 as a float-pair sum (returned in FP64), the atom record, the key cleared.
 __global__ void __launch_bounds__(kShiftUpdateThreads) k_shift_update(const float *__restrict__ tpl,
                                                                      const float *__restrict__ scale,
                                                      int S, int Sa, int rows, int NtcP, int T, GridAxes ax, int Lp,
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kShiftUpdateThreads) k_shift_update(const floa
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ float shf[32];
-    __shared__ double shd[32];
+    __shared__ ff shp[32];
     const int b = blockIdx.x;
     const int L = ax.L;
     const uint32_t flat = key_index(keys[b]);
@@ -391,29 +392,21 @@ __global__ void __launch_bounds__(kShiftUpdateThreads) k_shift_update(const floa
         }
     }
     const float c = block_sum(part, shf);
-    double e2 = 0.0;
+    ff e2 = {0.0f, 0.0f};  // |r_{k+1}|^2 as a float pair (about 2^-44 relative)
 #pragma unroll
     for (int i = 0; i < kUpdatePerThread; ++i) {
         const int n = threadIdx.x + i * kShiftUpdateThreads;
         if (n < L) {
             const float v = fmaf(-c, gv[i], r[n]);
             r[n] = v;
-            e2 = fma((double)v, (double)v, e2);
+            ff_add_square(e2, v);
         }
     }
-    const double tot = block_sum(e2, shd);
+    const ff tot = block_sum_ff(e2, shp);
+    if (threadIdx.x < 32) write_atom_lanes(ax, flat, atoms + (size_t)b * P + k);
     if (threadIdx.x == 0) {
-        double p[4];
-        decode_params(ax, (int64_t)flat, p);
-        act_atom a;
-        a.tc = p[0];
-        a.fc = p[1];
-        a.logdt = p[2];
-        a.c = p[3];
-        a.flat_index = (int64_t)flat;
-        atoms[(size_t)b * P + k] = a;
         coefs[(size_t)b * P + k] = c;
-        energy[(size_t)b * (P + 1) + k + 1] = tot;
+        energy[(size_t)b * (P + 1) + k + 1] = ff_to_double(tot);
         keys[b] = 0ull;
         if (counters && b == 0) {
             counters[0] = 0;
