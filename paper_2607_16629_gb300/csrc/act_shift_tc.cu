@@ -39,6 +39,7 @@ constexpr int kUmmaK = 16;
 constexpr int kThreads = 256;
 constexpr int kAChunkBytes = kBM * kBK * 2;  // 16 KB
 constexpr int kMaxStages = 6;
+constexpr int kUnitTab = 1024;  // row units whose lag-chunk range is tabulated in shared memory
 
 // Tile of BN templates (128 or 256, MMA N).  PAIR: a CTA pair shares each
 // MMA (M = 256: the two CTAs' row tiles), each CTA loading BN / 2 of the
@@ -63,6 +64,10 @@ struct Smem {
     uint32_t tmem_base;
     int abort;
     unsigned int chan_max[2][kBM];  // per item parity: the tile's channel maxima (float bits)
+    // the lag-chunk range [x, y] of row units 0 .. kUnitTab - 1, formed
+    // during set-up: the single thread that issues the MMAs reads it at
+    // every item instead of dividing (units past the table: computed there)
+    short2 unit_chunk[kUnitTab];
 };
 
 // Named barrier 1 over the 128 epilogue threads, returning whether any of
@@ -269,6 +274,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_mbar_init();
     }
     if (threadIdx.x < 2 * kBM) sm.chan_max[threadIdx.x / kBM][threadIdx.x % kBM] = 0u;
+    for (int u = threadIdx.x; u < m_units && u < kUnitTab; u += blockDim.x) {
+        int lo, hi;
+        unit_chunks(tl, PAIR, u, lo, hi);
+        sm.unit_chunk[u] = make_short2((short)lo, (short)hi);
+    }
     if (warp == 2) {
         if constexpr (PAIR) {  // the same columns in both CTAs, allocated by one warp of each
             asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -307,7 +317,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             // this CTA's row tile (PAIR: past the last tile, load the last one again)
             const int mt = PAIR ? min(2 * u + (int)rank, tl.m_tiles - 1) : u;
             int kc_lo, kc_hi;
-            unit_chunks(tl, PAIR, u, kc_lo, kc_hi);
+            if (u < kUnitTab) {
+                kc_lo = sm.unit_chunk[u].x;
+                kc_hi = sm.unit_chunk[u].y;
+            } else {
+                unit_chunks(tl, PAIR, u, kc_lo, kc_hi);
+            }
             for (int kc = kc_lo; kc <= kc_hi; ++kc) {
                 const bool ok = PAIR ? mbar_wait_cluster(&sm.bar_empty[s], ph ^ 1u, wait_ns)
                                      : mbar_wait(&sm.bar_empty[s], ph ^ 1u, wait_ns);
@@ -354,7 +369,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t d_tmem = tmem + acc * BN;
             int kc_lo, kc_hi;
-            unit_chunks(tl, PAIR, (int)(w / n_tiles), kc_lo, kc_hi);
+            const int u = (int)(w / n_tiles);
+            if (u < kUnitTab) {
+                kc_lo = sm.unit_chunk[u].x;
+                kc_hi = sm.unit_chunk[u].y;
+            } else {
+                unit_chunks(tl, PAIR, u, kc_lo, kc_hi);
+            }
             for (int kc = kc_lo; kc <= kc_hi; ++kc) {
                 const bool full = PAIR ? mbar_wait_cluster(&sm.bar_full[s], ph, wait_ns)
                                        : mbar_wait(&sm.bar_full[s], ph, wait_ns);
@@ -667,7 +688,7 @@ __global__ void __launch_bounds__(kRescanWarps * 32) k_shift_rescan(
 }
 
 // static shared memory of the kernels here (the GEMM's Smem is the largest)
-constexpr int kStaticReserve = 2048;
+constexpr int kStaticReserve = 6144;
 static_assert(sizeof(Smem) + 256 <= kStaticReserve, "static shared memory above its reserve");
 constexpr int kSmemBudget = 232448 - kStaticReserve - 1024;
 
