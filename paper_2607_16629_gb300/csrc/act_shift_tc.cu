@@ -33,6 +33,19 @@ namespace {
 
 using namespace tc;
 
+// (a0 b0, a1 b1) by one packed FP32 multiply, each product rounded to
+// nearest as a scalar multiply would be: the epilogue shares its warp
+// scheduler with the MMA-issuing warp, so its instruction count matters.
+__device__ __forceinline__ float2 mul_f32x2(float a0, float a1, float b0, float b1) {
+    unsigned long long x, y, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b0), "f"(b1));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+
 constexpr int kBM = 128;          // shifted residual rows per tile (MMA M)
 constexpr int kBlockRows = 256;   // templates per block of the tile-major BF16 layout
 constexpr int kUmmaK = 16;
@@ -458,10 +471,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const float4 s = valid ? sc4[c * 8 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    m0 = fmaxf(m0, fabsf(v[4 * e] * s.x));
-                    m1 = fmaxf(m1, fabsf(v[4 * e + 1] * s.y));
-                    m0 = fmaxf(m0, fabsf(v[4 * e + 2] * s.z));
-                    m1 = fmaxf(m1, fabsf(v[4 * e + 3] * s.w));
+                    const float2 p01 = mul_f32x2(v[4 * e], v[4 * e + 1], s.x, s.y);
+                    const float2 p23 = mul_f32x2(v[4 * e + 2], v[4 * e + 3], s.z, s.w);
+                    m0 = fmaxf(m0, fabsf(p01.x));
+                    m1 = fmaxf(m1, fabsf(p01.y));
+                    m0 = fmaxf(m0, fabsf(p23.x));
+                    m1 = fmaxf(m1, fabsf(p23.y));
                 }
                 bmv[c] = fmaxf(m0, m1);
                 mx = fmaxf(mx, bmv[c]);
