@@ -46,6 +46,25 @@ __device__ __forceinline__ float2 mul_f32x2(float a0, float a1, float b0, float 
     return o;
 }
 
+// Bounded wait on a phase by polling test_wait (never suspending the
+// thread), with an optional pause between polls; PAIR: cluster-scope
+// acquire.  The MMA-issuing thread polls without pausing, so it resumes the
+// moment a stage lands; the epilogue pauses, taking fewer issue slots from
+// the MMA-issuing warp that shares its scheduler.  Limit 0: one test.
+template <bool PAIR>
+__device__ __forceinline__ bool mbar_poll(uint64_t *bar, uint32_t parity, unsigned long long limit_ns,
+                                          unsigned pause_ns) {
+    auto test = [&]() { return PAIR ? mbar_test_wait_cluster(bar, parity) : mbar_test_wait(bar, parity); };
+    if (test()) return true;
+    if (limit_ns == 0) return false;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!test()) {
+        if (globaltimer_ns() - t0 >= limit_ns) return false;
+        if (pause_ns) __nanosleep(pause_ns);
+    }
+    return true;
+}
+
 constexpr int kBM = 128;          // shifted residual rows per tile (MMA M)
 constexpr int kBlockRows = 256;   // templates per block of the tile-major BF16 layout
 constexpr int kUmmaK = 16;
@@ -390,8 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unit_chunks(tl, PAIR, u, kc_lo, kc_hi);
             }
             for (int kc = kc_lo; kc <= kc_hi; ++kc) {
-                const bool full = PAIR ? mbar_wait_cluster(&sm.bar_full[s], ph, wait_ns)
-                                       : mbar_wait(&sm.bar_full[s], ph, wait_ns);
+                const bool full = mbar_poll<PAIR>(&sm.bar_full[s], ph, wait_ns, 0);
                 if (!full) {
                     *abort_flag = 1;
                     break;
@@ -446,8 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
             const uint32_t acc = local & 1u, aph = (local >> 1) & 1u;
-            const bool landed = PAIR ? mbar_wait_cluster(&sm.bar_acc_full[acc], aph, wait_ns)
-                                     : mbar_wait(&sm.bar_acc_full[acc], aph, wait_ns);
+            const bool landed = mbar_poll<PAIR>(&sm.bar_acc_full[acc], aph, wait_ns, 256);
             const int failed = (*abort_flag || !landed) ? 1 : 0;
             if (epilogue_bar_or(failed)) {  // the epilogue warps leave together
                 *abort_flag = 1;
