@@ -1096,27 +1096,36 @@ def bench_small_check(args, dev, stream):
                torch.empty((B, P), dtype=torch.float32, device=dev),
                torch.empty((B, L), dtype=torch.float32, device=dev),
                torch.empty((B, P + 1), dtype=torch.float64, device=dev)]
-        for _ in range(5):
-            act.act_decompose(h, sig, B, P, *out, stream)
         reps = 200
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            act.act_decompose(h, sig, B, P, *out, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / reps
-        st = act.act_grid_status(h, stream)
-        if st != act.ACT_OK:
-            raise RuntimeError(act.status_name(st))
+
+        def timed():
+            for _ in range(5):
+                act.act_decompose(h, sig, B, P, *out, stream)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                act.act_decompose(h, sig, B, P, *out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            st = act.act_grid_status(h, stream)
+            if st != act.ACT_OK:
+                raise RuntimeError(act.status_name(st))
+            return e0.elapsed_time(e1) / reps
+
+        fused_ctas = act.act_get_fused(h, B)
+        ms = timed()  # the default: one cooperative launch per decomposition
+        act.act_set_fused(h, 0)
+        ms_kernels = timed()  # the GEMV and update kernels of every order, in the grid's graph
         gemv = act.act_get_tuning(h)[0]
     finally:
         act.act_destroy(h)
     return {"workload": "plain_fp32_1ch_n256_fs128_grid32x16x4x8_k16384_p5", "value": B * K * P / (ms / 1e3),
             "unit": UNIT, "ms_per_step": ms, "us_per_order": 1e3 * ms / P, "steps": reps,
             "bound": "latency (the 16.8 MB dictionary is L2-resident)",
-            "gemv": "bulk-copy stream" if gemv == -1 else f"load-streaming, {gemv} CTAs",
+            "form": f"single cooperative launch per decomposition, {fused_ctas} CTAs (act_set_fused)",
+            "per_order_kernels": {"us_per_order": 1e3 * ms_kernels / P,
+                                  "gemv": "bulk-copy stream" if gemv == -1 else f"load-streaming, {gemv} CTAs"},
             "l2": "dictionary smaller than L2: every step after the first reads it from L2"}
 
 

@@ -241,6 +241,32 @@ ACT_API act_status act_set_cta_pairs(act_grid *grid, int32_t enable);
  * channels < 1 or a null pointer. */
 ACT_API act_status act_get_cta_pairs(const act_grid *grid, int32_t channels, int32_t *used);
 
+/* Single-launch decomposition (Fig. 1's loop: search, selection and the
+ * Eq. (4) update for every order) over a small stored FP32 dictionary.
+ * Where it applies (the FP32 search over an ACT_DICT_FP32 dictionary of at
+ * most 32 MiB, which stays in L2; 1 to 8 channels; no refinement; the
+ * grid not profiling; a device that runs cooperative launches) every
+ * act_decompose is one cooperative kernel: each CTA scores its share of
+ * the rows against its own shared-memory copy of the residuals, a bounded
+ * grid barrier per order makes the winners known, and every CTA applies
+ * the update to its copy.  The results are bit for bit those of the
+ * per-order GEMV and update kernels; the launch latency of 2P dependent
+ * kernels is what it saves.  With every buffer in device memory the call
+ * is one memset and that launch (no graph, no copies); with host buffers
+ * the launch runs inside the grid's graph, between the copies.  ctas_per_sm: CTAs per SM of that launch
+ * (capped by how many fit), 0 = never use it; the default is 2.  Errors:
+ * ACT_ERR_INVALID_ARG for values outside 0..32.  Changing it re-records
+ * the grid's graphs.  A barrier wait that runs past the grid's wait limit
+ * (act_set_wait_limit) makes the launch give up: the next synchronising
+ * call returns ACT_ERR_DEVICE_TIMEOUT. */
+ACT_API act_status act_set_fused(act_grid *grid, int32_t ctas_per_sm);
+
+/* *ctas = the number of CTAs of the single-launch decomposition a
+ * `channels`-channel act_decompose on this grid (as built and set now)
+ * launches, or 0 when it takes the per-order kernels.  Errors:
+ * ACT_ERR_INVALID_ARG for channels < 1 or a null pointer. */
+ACT_API act_status act_get_fused(const act_grid *grid, int32_t channels, int32_t *ctas);
+
 /* Test aid for out-of-memory handling: the nth device allocation made by
  * this library from now on (any grid, any thread; nth >= 1) fails once, as
  * if the device were out of memory.  The call that makes it returns

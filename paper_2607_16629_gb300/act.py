@@ -37,7 +37,7 @@ EXPORTS = (
     "act_ragged_plan_create", "act_ragged_decompose", "act_ragged_plan_info", "act_ragged_plan_destroy",
     "act_set_refinement", "act_chirplet_score", "act_set_lem", "act_set_shift_tuning", "act_get_shift_tuning",
     "act_dictionary_mode", "act_set_memory_budget", "act_set_wait_limit", "act_inject_alloc_failure",
-    "act_set_cta_pairs", "act_get_cta_pairs",
+    "act_set_cta_pairs", "act_get_cta_pairs", "act_set_fused", "act_get_fused",
 )
 
 
@@ -129,6 +129,8 @@ def load_library(path: str = LIB_PATH):
         lib.act_inject_alloc_failure.argtypes = [ctypes.c_int32]
         lib.act_set_cta_pairs.argtypes = [_P, ctypes.c_int32]
         lib.act_get_cta_pairs.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        lib.act_set_fused.argtypes = [_P, ctypes.c_int32]
+        lib.act_get_fused.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         lib.act_destroy.argtypes = [_P]
         lib.act_destroy.restype = None
         for name in EXPORTS:
@@ -395,6 +397,18 @@ def act_get_cta_pairs(grid: int, channels: int) -> bool:
     used = ctypes.c_int32(0)
     _check(load_library().act_get_cta_pairs(grid, int(channels), ctypes.byref(used)), "act_get_cta_pairs")
     return bool(used.value)
+
+
+def act_set_fused(grid: int, ctas_per_sm: int) -> None:
+    """CTAs per SM of the single-launch decomposition of small FP32 dictionaries (0: never)."""
+    _check(load_library().act_set_fused(grid, int(ctas_per_sm)), "act_set_fused")
+
+
+def act_get_fused(grid: int, channels: int) -> int:
+    """CTAs of the single launch a `channels`-channel decomposition takes (0: per-order kernels)."""
+    ctas = ctypes.c_int32(0)
+    _check(load_library().act_get_fused(grid, int(channels), ctypes.byref(ctas)), "act_get_fused")
+    return int(ctas.value)
 
 
 def act_inject_alloc_failure(nth: int) -> None:

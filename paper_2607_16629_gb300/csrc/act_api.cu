@@ -119,6 +119,7 @@ struct WorkBuffers {
     int *fb_list = nullptr;           // [B] channels queued for the FP32 full search
     int *fb_count = nullptr;          // [2] full-search and rescan queue lengths
     double *theta = nullptr;          // [B][4] refined parameters of the current order
+    unsigned long long *fsync = nullptr;  // [1 + 3B] single-launch decomposition: barrier words, key slots
     LemBuffers lem;                   // hierarchical-search candidates (allocated on first use)
     int lem_B = 0;
     Bf16Scratch b16;                  // dense tensor-core search maxima and rescan lists (on first use)
@@ -149,6 +150,8 @@ struct act_grid {
     int refine_steps = 0;  // BFGS iterations per order (0: grid-only search)
     unsigned long long wait_ns = kWaitLimitNs;  // limit of each bounded device-side wait
     bool cta_pairs = true;  // the tensor-core template GEMM may pair SMs (cta_group::2)
+    int fused_ctas_per_sm = 2;  // single-launch decomposition of small FP32 dictionaries (0: off)
+    bool coop = false;          // the device runs cooperative launches
     uint64_t mem_budget = 0;  // bytes ACT_DICT_AUTO may give the dictionary (0: free device memory)
     LemConfig lem;         // hierarchical search settings
     cudaStream_t cap = nullptr;
@@ -192,6 +195,7 @@ void free_base(WorkBuffers &w) {
     free_dev(w.fb_list);
     free_dev(w.fb_count);
     free_dev(w.theta);
+    free_dev(w.fsync);
     w.cap_B = w.cap_P = 0;
 }
 
@@ -249,6 +253,7 @@ act_status alloc_base(const act_grid *g, WorkBuffers &w, int B, int P) {
     ACT_AL(w.fb_count, 2 * sizeof(int));
     ACT_CK(cudaMemset(w.fb_count, 0, 2 * sizeof(int)));
     ACT_AL(w.theta, sizeof(double) * 4 * (size_t)B);
+    ACT_AL(w.fsync, sizeof(unsigned long long) * (1 + 3 * (size_t)B));
     w.cap_B = B;
     w.cap_P = P;
     return ACT_OK;
@@ -385,12 +390,32 @@ bool search_available(const act_grid *g, act_search_mode mode) {
     }
 }
 
+// CTAs of the single-launch decomposition of B channels, or 0 where it does
+// not apply: the FP32 search over a stored dictionary small enough to stay
+// in L2, grid-only (no refinement), at most kFusedMaxB channels, no
+// per-order profiling events, a device that runs cooperative launches.
+int fused_ctas(const act_grid *g, int B, act_search_mode mode, bool profiling) {
+    if (g->fused_ctas_per_sm <= 0 || !g->coop || profiling || mode != ACT_SEARCH_FP32 || !g->d32) return 0;
+    if (g->refine_steps > 0 || B < 1 || B > kFusedMaxB) return 0;
+    if (g->K * (int64_t)g->Lp * (int64_t)sizeof(float) > kFusedMaxDictBytes) return 0;
+    const int most = fused_max_ctas(g->sm_count, B, g->Lp);
+    const int want = g->sm_count * g->fused_ctas_per_sm;
+    return want < most ? want : most;
+}
+
 // Records the whole decomposition (init + P orders) on stream st (being captured).
 act_status record_decompose(act_grid *g, WorkBuffers &w, int B, int P, act_search_mode mode, GraphEntry &ge,
-                            cudaStream_t st, bool profiling) {
+                            cudaStream_t st, bool profiling, bool allow_fused) {
     const bool bf16 = mode == ACT_SEARCH_BF16;
     __nv_bfloat16 *R16 = bf16 ? w.R16 : nullptr;
     int kernels = 0;
+    const int fctas = allow_fused ? fused_ctas(g, B, mode, profiling) : 0;
+    if (fctas > 0) {  // the single-launch form (it also initialises the residuals)
+        ACT_CK(launch_mp_fused(g->d32, g->K, g->Lp, g->L, w.sig, B, P, g->ax, w.fsync, w.atoms, w.coefs, w.energy,
+                               w.R, g->Lp, g->status, fctas, g->wait_ns, st));
+        ge.kernels = 1;
+        return ACT_OK;
+    }
     ACT_CK(launch_init(w.sig, B, g->L, g->Lp, w.R, R16, g->Lb, w.keys, w.energy, P + 1, g->status, st));
     ++kernels;
     for (int k = 0; k < P; ++k) {
@@ -476,7 +501,7 @@ act_status get_graph(act_grid *g, int B, int P, act_search_mode mode, GraphEntry
     }
     GraphEntry ge;
     ACT_CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
-    act_status s = record_decompose(g, g->w, B, P, mode, ge, g->cap, g->profiling);
+    act_status s = record_decompose(g, g->w, B, P, mode, ge, g->cap, g->profiling, true);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
     if (s != ACT_OK) {
@@ -593,6 +618,9 @@ act_status act_grid_create(const act_grid_desc *desc, int32_t device, act_grid *
     g->ax.fs = desc->fs;
     g->ax.L = g->L;
     cudaError_t e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    g->coop = coop != 0;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = dev_alloc((void **)&g->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
@@ -792,6 +820,17 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
     act_status s = ensure_work(g, channels, n_atoms, mode);
     if (s != ACT_OK) return s;
     bool host_seen = !is_device_ptr(signals);
+    // all buffers in device memory and the single-launch form applies: the
+    // kernel reads the signals and writes the outputs itself (no graph, no copies)
+    const int fctas = fused_ctas(g, channels, mode, g->profiling);
+    if (fctas > 0 && !host_seen && (!atoms_out || is_device_ptr(atoms_out)) &&
+        (!coeffs_out || is_device_ptr(coeffs_out)) && (!residuals_out || is_device_ptr(residuals_out)) &&
+        (!energy_out || is_device_ptr(energy_out))) {
+        ACT_CK(launch_mp_fused(g->d32, g->K, g->Lp, g->L, signals, channels, n_atoms, g->ax, g->w.fsync, atoms_out,
+                               coeffs_out, energy_out, residuals_out, g->L, g->status, fctas, g->wait_ns, st));
+        g->last = nullptr;
+        return ACT_OK;
+    }
     ACT_CK(cudaMemcpyAsync(g->w.sig, signals, sizeof(float) * (size_t)channels * g->L, cudaMemcpyDefault, st));
     GraphEntry *ge = nullptr;
     s = get_graph(g, channels, n_atoms, mode, &ge);
@@ -1263,7 +1302,7 @@ static act_status ragged_build(act_ragged_plan *p, act_grid *const *grids, int32
         e = cudaStreamWaitEvent(gr.st, p->fork, 0);
         if (e == cudaSuccess) e = launch_ragged_gather(p->d_sig, gr.src_off, B, g->L, gr.w.sig, gr.st);
         GraphEntry ge;
-        if (e == cudaSuccess) s = record_decompose(g, gr.w, B, p->P, gr.mode, ge, gr.st, false);
+        if (e == cudaSuccess) s = record_decompose(g, gr.w, B, p->P, gr.mode, ge, gr.st, false, false);
         p->kernels += ge.kernels + 2;
         if (e == cudaSuccess && s == ACT_OK)
             e = launch_ragged_scatter(B, p->P, g->L, g->Lp, gr.d_chan, gr.src_off, gr.w.atoms, gr.w.coefs,
@@ -1371,6 +1410,22 @@ act_status act_set_cta_pairs(act_grid *g, int32_t enable) {
         g->cta_pairs = enable != 0;  // the recorded graphs hold the other kernel
         drop_graphs(g);
     }
+    return ACT_OK;
+}
+
+act_status act_set_fused(act_grid *g, int32_t ctas_per_sm) {
+    if (!g || ctas_per_sm < 0 || ctas_per_sm > 32) return ACT_ERR_INVALID_ARG;
+    if (ctas_per_sm != g->fused_ctas_per_sm) {
+        g->fused_ctas_per_sm = ctas_per_sm;  // the recorded graphs hold the other launch form
+        drop_graphs(g);
+    }
+    return ACT_OK;
+}
+
+act_status act_get_fused(const act_grid *g, int32_t channels, int32_t *ctas) {
+    if (!g || !ctas || channels < 1) return ACT_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    *ctas = fused_ctas(g, channels, effective_search(g), g->profiling);
     return ACT_OK;
 }
 

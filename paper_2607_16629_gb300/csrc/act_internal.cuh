@@ -132,6 +132,21 @@ cudaError_t launch_project(const float *D, int64_t K, int Lp, const float *R, in
 cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat16 *R16, int Lb, int B,
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
                           float *coefs, double *energy, int *fb_count, cudaStream_t st, bool pdl = false);
+// The whole decomposition over a small stored FP32 dictionary in one
+// cooperative launch (act_fused.cu): up to kFusedMaxB channels, results
+// equal to the initialisation, GEMV and update kernels'.  sync holds
+// 1 + 3B words (the barrier's count and abort flag, the key slots), cleared
+// by the launcher; outputs may be null; resid rows are resid_stride apart.
+constexpr int kFusedMaxB = 8;
+// Dictionaries up to this size: the single launch measured faster than the
+// per-order kernels at 16.8 MB (7.0 vs 9.8 us per order) and slower at
+// 95 MB, where the stream of rows, not launch latency, sets the time.
+constexpr int64_t kFusedMaxDictBytes = 32ll << 20;
+int fused_max_ctas(int sm_count, int B, int Lp);  // co-resident CTAs of the launch (0: no launch form)
+cudaError_t launch_mp_fused(const float *D, int64_t K, int Lp, int L, const float *sig, int B, int P,
+                            const GridAxes &ax, unsigned long long *sync, act_atom *atoms, float *coefs,
+                            double *energy, float *resid, int resid_stride, int *status, int ctas,
+                            unsigned long long wait_ns, cudaStream_t st);
 cudaError_t launch_ragged_gather(const float *src, const int64_t *src_off, int B, int L, float *dst, cudaStream_t st);
 cudaError_t launch_ragged_scatter(int B, int P, int L, int Lp, const int *chan, const int64_t *dst_off,
                                   const act_atom *atoms, const float *coefs, const double *energy, const float *R,

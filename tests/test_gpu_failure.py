@@ -226,3 +226,31 @@ def test_auto_dictionary_choice():
         assert act.act_dictionary_mode(h) == act.ACT_DICT_FP32
     finally:
         act.act_destroy(h)
+
+
+def test_wait_limit_zero_single_launch():
+    """The single-launch decomposition of a small FP32 dictionary: with the
+    wait limit at 0 every CTA but the last to arrive gives up at the first
+    grid barrier and raises the abort flag, which ends the others' waits;
+    the next call is clean and equal to a fresh grid's."""
+    w = synth.workload_c1()
+    B, P = 2, 4
+    sig = np.stack([w.signals[0], w.signals[0][::-1]]).astype(np.float32)
+    h = _grid(act.ACT_DICT_FP32, act.ACT_SEARCH_FP32, w.grid)
+    ref_h = _grid(act.ACT_DICT_FP32, act.ACT_SEARCH_FP32, w.grid)
+    try:
+        assert act.act_get_fused(h, B) > 1
+        st_ref, ref = _run(ref_h, sig, P)
+        assert st_ref == act.ACT_OK
+        act.act_set_wait_limit(h, 0)
+        st, _ = _run(h, sig, P)
+        assert st == act.ACT_ERR_DEVICE_TIMEOUT, act.status_name(st)
+        assert act.act_grid_status(h) == act.ACT_OK
+        act.act_set_wait_limit(h, 2_000_000_000)
+        st, out = _run(h, sig, P)
+        assert st == act.ACT_OK, act.status_name(st)
+        for x, y in zip(out, ref):
+            assert np.array_equal(x, y)
+    finally:
+        act.act_destroy(h)
+        act.act_destroy(ref_h)

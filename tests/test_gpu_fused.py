@@ -1,0 +1,149 @@
+"""The single-launch decomposition of small FP32 dictionaries (Fig. 1's
+loop, Eq. (4)) against the per-order GEMV and update kernels (bit for bit)
+and against the FP64 oracle (lock-step), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2607_16629_gb300 import act, synth
+from parity_helpers import check_lockstep, full_dictionary, gpu_decompose, gpu_residual_chain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    act.load_library()
+
+
+def _both_forms(grid, signals, P, ctas_per_sm=(2,)):
+    """Outputs with the per-order kernels, then with the single launch at
+    each CTAs-per-SM setting (asserting that it is the one taken)."""
+    B = signals.shape[0]
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        act.act_set_fused(h, 0)
+        assert act.act_get_fused(h, B) == 0
+        ref = gpu_decompose(h, signals, P)
+        outs = []
+        for c in ctas_per_sm:
+            act.act_set_fused(h, c)
+            assert act.act_get_fused(h, B) > 0
+            outs.append(gpu_decompose(h, signals, P))  # device buffers: the kernel alone
+            # host buffers: the same kernel inside the grid's graph, then copies
+            outs.append(gpu_decompose(h, signals, P, host=True))
+    finally:
+        act.act_destroy(h)
+    return ref, outs
+
+
+def _assert_same(ref, out):
+    for a, b, name in zip(ref, out, ("index", "params", "coef", "residual", "energy")):
+        assert np.array_equal(a, b), f"{name} differs"
+
+
+def _signals(grid, B, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((B, grid.n_samples)).astype(np.float32)
+
+
+@pytest.mark.parametrize("B,P", [(1, 5), (1, 1), (3, 12), (8, 40)])
+def test_single_launch_equals_per_order_kernels_c1(B, P):
+    """16,384 atoms, N = 256: the outputs of both forms are identical."""
+    w = synth.workload_c1()
+    grid = w.grid
+    sig = w.signals[:B] if B <= w.signals.shape[0] else _signals(grid, B, 11)
+    ref, outs = _both_forms(grid, np.asarray(sig, dtype=np.float32), P, ctas_per_sm=(1, 2, 4))
+    for out in outs:
+        _assert_same(ref, out)
+
+
+@pytest.mark.parametrize("name,grid", [
+    # N = 200: the padded row (256) is longer than the window
+    ("n200", synth.scaled_grid(synth.Grid(200, 2000.0, synth.Axis(0, 32, 7), synth.Axis(20, 10, 43),
+                                          synth.Axis(-4, 0.3, 14), synth.Axis(-10, 0.75, 27)), fc_count=11)),
+    # 12,288 atoms (25 MB; not a multiple of the rows one pass of the grid covers), N = 512
+    ("eeg12k", synth.scaled_grid(synth.grid_eeg(), tc_count=12, fc_count=4, c_count=32)),
+])
+def test_single_launch_equals_per_order_kernels(name, grid):
+    sig = _signals(grid, 2, 7)
+    ref, outs = _both_forms(grid, sig, 9)
+    _assert_same(ref, outs[0])
+
+
+def test_single_launch_paper_epoch_setting():
+    """The paper's EEG ranges (Table 2) at a coarser time-centre step:
+    tc 0..256 step 128, 23,200 atoms (23.8 MB), N = 256, 10 orders."""
+    desc = act.act_grid_from_ranges(256, 256.0, (0, 256, 128), (0.5, 15, 0.5), (-4, 1, 0.5), (-10, 10, 0.5))
+    sig = synth.eeg_like_signal(6, 0, n_samples=256, fs=256.0)[0][None, :].astype(np.float32)
+    h = act.act_grid_create(desc, 0)
+    try:
+        K, _ = act.act_grid_size(h)
+        assert K == 23200
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        act.act_set_fused(h, 0)
+        ref = gpu_decompose(h, sig, 10)
+        act.act_set_fused(h, 2)
+        assert act.act_get_fused(h, 1) > 0
+        out = gpu_decompose(h, sig, 10)
+    finally:
+        act.act_destroy(h)
+    _assert_same(ref, out)
+
+
+def test_single_launch_lockstep_against_oracle():
+    """Order by order against the FP64 oracle on the 16,384-atom grid: the
+    residual entering each order comes from chained one-order calls (each a
+    single launch of one order)."""
+    w = synth.workload_c1()
+    grid, P = w.grid, 12
+    sig = np.asarray(w.signals[:1], dtype=np.float32)
+    D = full_dictionary(grid)
+    h = act.act_grid_create(grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        assert act.act_get_fused(h, 1) > 0
+        idx, _, coef, resid, energy = gpu_decompose(h, sig, P)
+        rs, idx_c, coef_c = gpu_residual_chain(h, sig[0], P)
+    finally:
+        act.act_destroy(h)
+    assert np.array_equal(idx[0], idx_c) and np.array_equal(coef[0], coef_c)
+    ties = check_lockstep(lambda r: D @ r, rs, idx[0], coef[0], energy[0], lambda i: D[i])
+    assert ties <= 1
+    # the returned residual is the last one of the chain
+    assert np.array_equal(resid[0], rs[P])
+
+
+def test_single_launch_not_used_where_it_does_not_apply():
+    w = synth.workload_c1()
+    h = act.act_grid_create(w.grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        assert act.act_get_fused(h, 1) > 0
+        assert act.act_get_fused(h, 8) > 0
+        assert act.act_get_fused(h, 9) == 0          # more channels than the form holds
+        act.act_set_refinement(h, 4)
+        assert act.act_get_fused(h, 1) == 0          # refinement runs its own kernels
+        act.act_set_refinement(h, 0)
+        act.act_set_profiling(h, True)
+        assert act.act_get_fused(h, 1) == 0          # per-order events need per-order kernels
+        act.act_set_profiling(h, False)
+        act.act_set_search(h, act.ACT_SEARCH_LEM)
+        assert act.act_get_fused(h, 1) == 0
+        act.act_set_search(h, act.ACT_SEARCH_AUTO)
+        assert act.act_get_fused(h, 1) > 0
+        with pytest.raises(RuntimeError):
+            act.act_set_fused(h, -1)
+    finally:
+        act.act_destroy(h)
+    # a larger dictionary (268 MB) takes the per-order kernels
+    big = synth.scaled_grid(synth.grid_eeg(), tc_count=32, fc_count=16)
+    h = act.act_grid_create(big, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        assert act.act_get_fused(h, 1) == 0
+    finally:
+        act.act_destroy(h)
