@@ -133,11 +133,13 @@ cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat
                           unsigned long long *keys, const GridAxes &ax, int k, int P, act_atom *atoms,
                           float *coefs, double *energy, int *fb_count, cudaStream_t st, bool pdl = false);
 // The whole decomposition over a small stored FP32 dictionary in one
-// cooperative launch (act_fused.cu): up to kFusedMaxB channels, results
-// equal to the initialisation, GEMV and update kernels'.  sync holds
-// 1 + 3B words (the barrier's count and abort flag, the key slots), cleared
-// by the launcher; outputs may be null; resid rows are resid_stride apart.
-constexpr int kFusedMaxB = 8;
+// cooperative launch (act_fused.cu), results equal to the initialisation,
+// GEMV and update kernels'.  sync holds 1 + 3B words (the barrier's count
+// and abort flag, the key slots), cleared by the launcher; outputs may be
+// null; resid rows are resid_stride apart.  One channel: from two channels
+// on the per-order kernels measured as fast or faster (their GEMV scores
+// four channels per pass over the rows, the single launch one).
+constexpr int kFusedMaxB = 1;
 // Dictionaries up to this size: the single launch measured faster than the
 // per-order kernels at 16.8 MB (7.0 vs 9.8 us per order) and slower at
 // 95 MB, where the stream of rows, not launch latency, sets the time.
