@@ -27,7 +27,10 @@
  *   - calls that take a cuda_stream (a cudaStream_t, NULL = legacy default
  *     stream) enqueue their GPU work on it and return without waiting,
  *     except where a host buffer forces a copy back (then they wait);
- *   - a grid may be used by one host thread at a time.
+ *   - a grid may be used by one host thread at a time, and its calls share
+ *     the grid's work buffers: calls on different streams must be ordered
+ *     (an event or a synchronisation between them), or they overwrite each
+ *     other's residuals and results.
  */
 #ifndef ACT_H
 #define ACT_H
