@@ -82,10 +82,64 @@ __device__ bool grid_barrier(unsigned int *arrived, int *abort, unsigned int tar
 }
 
 // Rows a warp scores per pass (its loads are all issued before the first
-// product), as many as keep the operands of a pass in registers.
+// product), as many as keep the operands of two passes in registers.
 template <int NV>
 __host__ __device__ constexpr int fused_rows_per_pass() {
-    return NV <= 4 ? 4 : (NV <= 8 ? 2 : 1);
+    return NV <= 2 ? 4 : (NV <= 4 ? 2 : 1);
+}
+
+// One pass: rows row + u nw (u < U, those below K) of the dictionary, lane
+// l holding float4 l + 32 j of each.
+template <int NV, int U>
+__device__ __forceinline__ void fused_load_pass(const float4 *__restrict__ D4, int64_t K, int Lp4, int64_t row,
+                                                int64_t nw, int lane, float4 (&a)[U][NV]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t ru = row + u * nw;
+        if (ru < K) {
+            const float4 *pa = D4 + ru * Lp4 + lane;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) a[u][j] = ldg_stream(pa + 32 * j);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) a[u][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+// Scores of one pass's rows in the FP32 GEMV's arithmetic (two FMA chains
+// per lane, a butterfly sum), folded into the warp's best |score| with the
+// lowest row winning a tie (rows arrive in increasing order).
+template <int NV, int U>
+__device__ __forceinline__ void fused_score_pass(const float4 (&a)[U][NV], const float4 (&rv)[NV], int64_t K,
+                                                 int64_t row, int64_t nw, float &best, uint32_t &bidx) {
+    float sc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            x0 = fmaf(a[u][j].x, rv[j].x, x0);
+            x1 = fmaf(a[u][j].y, rv[j].y, x1);
+            x0 = fmaf(a[u][j].z, rv[j].z, x0);
+            x1 = fmaf(a[u][j].w, rv[j].w, x1);
+        }
+        sc[u] = x0 + x1;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) sc[u] += __shfl_xor_sync(0xffffffffu, sc[u], off);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t ru = row + u * nw;
+        const float x = fabsf(sc[u]);
+        if (ru < K && x > best) {
+            best = x;
+            bidx = (uint32_t)ru;
+        }
+    }
 }
 
 // sig: the B signals, [B][L]; outputs (each may be null): atoms and coefs
@@ -146,48 +200,19 @@ __global__ void __launch_bounds__(kFusedThreads) k_mp_fused(const float *__restr
             for (int j = 0; j < NV; ++j) rv[j] = r4[lane + 32 * j];
             float best = -1.0f;
             uint32_t bidx = 0u;
-            for (int64_t row = gw; row < K; row += U * nw) {
-                float4 a[U][NV];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t ru = row + u * nw;
-                    if (ru < K) {
-                        const float4 *pa = D4 + ru * Lp4 + lane;
-#pragma unroll
-                        for (int j = 0; j < NV; ++j) a[u][j] = ldg_stream(pa + 32 * j);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < NV; ++j) a[u][j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-                float sc[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    float x0 = 0.f, x1 = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NV; ++j) {
-                        x0 = fmaf(a[u][j].x, rv[j].x, x0);
-                        x1 = fmaf(a[u][j].y, rv[j].y, x1);
-                        x0 = fmaf(a[u][j].z, rv[j].z, x0);
-                        x1 = fmaf(a[u][j].w, rv[j].w, x1);
-                    }
-                    sc[u] = x0 + x1;
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                    for (int u = 0; u < U; ++u) sc[u] += __shfl_xor_sync(0xffffffffu, sc[u], off);
-                }
-                // rows in increasing order: the lowest wins a tie
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t ru = row + u * nw;
-                    const float x = fabsf(sc[u]);
-                    if (ru < K && x > best) {
-                        best = x;
-                        bidx = (uint32_t)ru;
-                    }
-                }
+            // two passes in flight: the next pass's rows load while this one's are scored
+            float4 a[U][NV], c[U][NV];
+            int64_t row = gw;
+            fused_load_pass<NV, U>(D4, K, Lp4, row, nw, lane, a);
+            while (row < K) {
+                const int64_t row2 = row + U * nw;
+                if (row2 < K) fused_load_pass<NV, U>(D4, K, Lp4, row2, nw, lane, c);
+                fused_score_pass<NV, U>(a, rv, K, row, nw, best, bidx);
+                if (row2 >= K) break;
+                const int64_t row3 = row2 + U * nw;
+                if (row3 < K) fused_load_pass<NV, U>(D4, K, Lp4, row3, nw, lane, a);
+                fused_score_pass<NV, U>(c, rv, K, row2, nw, best, bidx);
+                row = row3;
             }
             if (lane == 0) {
                 red_s[wid] = best;

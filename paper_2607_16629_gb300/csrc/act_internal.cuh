@@ -140,10 +140,10 @@ cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat
 // on the per-order kernels measured as fast or faster (their GEMV scores
 // four channels per pass over the rows, the single launch one).
 constexpr int kFusedMaxB = 1;
-// Dictionaries up to this size: the single launch measured faster than the
-// per-order kernels at 16.8 MB (7.0 vs 9.8 us per order) and slower at
-// 95 MB, where the stream of rows, not launch latency, sets the time.
-constexpr int64_t kFusedMaxDictBytes = 32ll << 20;
+// Dictionaries up to this size: there the single launch measured at least
+// 5 % faster than the per-order kernels (1.4x at 16.8 MB); from 1 GB on the
+// two are within 1.5 %, and larger dictionaries keep the TMA-fed GEMV.
+constexpr int64_t kFusedMaxDictBytes = 512ll << 20;
 int fused_max_ctas(int sm_count, int B, int Lp);  // co-resident CTAs of the launch (0: no launch form)
 cudaError_t launch_mp_fused(const float *D, int64_t K, int Lp, int L, const float *sig, int B, int P,
                             const GridAxes &ax, unsigned long long *sync, act_atom *atoms, float *coefs,

@@ -314,6 +314,7 @@ def test_streaming_gemv_gives_the_same_bits(name, grid):
         grid = eeg_small()
     sig = synth.random_signals(61, 3, grid.n_samples)
     with Grid(grid) as h:
+        act.act_set_fused(h, 0)  # one channel too: the per-order GEMV kernels
         ref1 = gpu_decompose(h, sig[:1], 6)
         ref3 = gpu_decompose(h, sig, 6)
         act.act_set_tuning(h, -1)

@@ -139,8 +139,8 @@ def test_single_launch_not_used_where_it_does_not_apply():
             act.act_set_fused(h, -1)
     finally:
         act.act_destroy(h)
-    # a larger dictionary (268 MB) takes the per-order kernels
-    big = synth.scaled_grid(synth.grid_eeg(), tc_count=32, fc_count=16)
+    # a larger dictionary (1 GiB) takes the per-order kernels
+    big = synth.scaled_grid(synth.grid_eeg(), tc_count=64, fc_count=32)
     h = act.act_grid_create(big, 0)
     try:
         act.act_dictionary_build(h, act.ACT_DICT_FP32)
