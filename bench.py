@@ -1353,10 +1353,31 @@ def run_profile_case(args):
     """Small, self-checking cases for ncu captures: a few launches of one
     search kernel on a dictionary larger than L2 but a few GB at most.
       gemv_small: FP32 GEMV over 1,048,576 EEG-grid atoms (2.1 GB), 1 channel.
-      bf16_small: BF16 GEMM search over the same atoms, 64 channels."""
+      bf16_small: BF16 GEMM search over the same atoms, 64 channels.
+      fused_check: the 16,384-atom check workload (5 orders), one cooperative
+        launch per decomposition."""
     import torch
 
     from paper_2607_16629_gb300 import act, synth
+    if args.case == "fused_check":
+        w = synth.workload_c1()
+        sig = torch.tensor(w.signals[:1], dtype=torch.float32, device="cuda")
+        h = act.act_grid_create(w.grid, 0)
+        try:
+            act.act_dictionary_build(h, act.ACT_DICT_FP32)
+            ctas = act.act_get_fused(h, 1)
+            assert ctas > 0
+            for _ in range(args.steps):
+                atoms, _, _, energy = act.decompose(h, sig, w.n_atoms)
+            torch.cuda.synchronize()
+            st = act.act_grid_status(h)
+            if st != act.ACT_OK:
+                raise RuntimeError(act.status_name(st))
+            assert np.all(np.diff(energy.cpu().numpy(), axis=1) <= 0.0)
+        finally:
+            act.act_destroy(h)
+        print(json.dumps({"case": args.case, "atoms": w.grid.n_atoms, "channels": 1, "ctas": ctas, "ok": True}))
+        return
     if args.case in ("shift_eeg", "shift_tc_eeg"):
         return run_shift_case(args)
     if args.case in ("lem_eeg", "refine_radar"):
@@ -1475,8 +1496,8 @@ def main():
                     help="FP32 GEMV of the gemv_small case: bulk-copy streaming or load-streaming")
     ap.add_argument("--shift-tuning", default="", help="JxW, JxWxS or JxWxSxC for --case shift_eeg (default: the build's)")
     ap.add_argument("--case", default="default",
-                    choices=["default", "gemv_small", "bf16_small", "shift_eeg", "shift_tc_eeg", "lem_eeg",
-                             "refine_radar"],
+                    choices=["default", "gemv_small", "bf16_small", "fused_check", "shift_eeg", "shift_tc_eeg",
+                             "lem_eeg", "refine_radar"],
                     help="small single-kernel cases for profiler captures (not bench lines)")
     args = ap.parse_args()
     if args.case != "default":
