@@ -1,9 +1,11 @@
 // The whole greedy loop of Fig. 1 (search, selection, Eq. (4) update) over
-// a small stored FP32 dictionary in one cooperative launch.
+// a stored FP32 dictionary in one cooperative launch.
 //
-// When the dictionary fits in L2 a decomposition is bound by the latency of
-// its P x 2 dependent launches, not by HBM.  Here every CTA of a grid that
-// is resident as a whole runs all P orders:
+// A one-channel decomposition over a dictionary that fits in L2 is bound by
+// the latency of its P x 2 dependent launches, not by HBM; over a larger one
+// by the stream of rows, which two passes of rows in flight per warp keep as
+// busy as the per-order GEMV does.  Every CTA of a grid that is resident as
+// a whole runs all P orders:
 //  1. it scores its share of the rows against its own shared-memory copy of
 //     each channel's residual (the FP32 GEMV's arithmetic: two FMA chains per
 //     lane over float4 l + 32 j, a butterfly sum, the lowest row on ties) and
