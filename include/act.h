@@ -247,10 +247,10 @@ ACT_API act_status act_get_cta_pairs(const act_grid *grid, int32_t channels, int
 /* Single-launch decomposition (Fig. 1's loop: search, selection and the
  * Eq. (4) update for every order) over a small stored FP32 dictionary.
  * Where it applies (the FP32 search over an ACT_DICT_FP32 dictionary of at
- * most 512 MiB; one channel; no refinement; the
+ * most 512 MiB; one or two channels; no refinement; the
  * grid not profiling; a device that runs cooperative launches) every
  * act_decompose is one cooperative kernel: each CTA scores its share of
- * the rows against its own shared-memory copy of the residual, a bounded
+ * the rows against its own shared-memory copy of the residuals, a bounded
  * grid barrier per order makes the winners known, and every CTA applies
  * the update to its copy.  The results are bit for bit those of the
  * per-order GEMV and update kernels; the launch latency of 2P dependent

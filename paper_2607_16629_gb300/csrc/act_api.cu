@@ -392,7 +392,7 @@ bool search_available(const act_grid *g, act_search_mode mode) {
 
 // CTAs of the single-launch decomposition of B channels, or 0 where it does
 // not apply: the FP32 search over a stored dictionary small enough to stay
-// in L2, grid-only (no refinement), at most kFusedMaxB channel, no
+// in L2, grid-only (no refinement), at most kFusedMaxB channels, no
 // per-order profiling events, a device that runs cooperative launches.
 int fused_ctas(const act_grid *g, int B, act_search_mode mode, bool profiling) {
     if (g->fused_ctas_per_sm <= 0 || !g->coop || profiling || mode != ACT_SEARCH_FP32 || !g->d32) return 0;

@@ -136,10 +136,10 @@ cudaError_t launch_update(const float *D32, int Lp, int L, float *R, __nv_bfloat
 // cooperative launch (act_fused.cu), results equal to the initialisation,
 // GEMV and update kernels'.  sync holds 1 + 3B words (the barrier's count
 // and abort flag, the key slots), cleared by the launcher; outputs may be
-// null; resid rows are resid_stride apart.  One channel: from two channels
-// on the per-order kernels measured as fast or faster (their GEMV scores
-// four channels per pass over the rows, the single launch one).
-constexpr int kFusedMaxB = 1;
+// null; resid rows are resid_stride apart.  One or two channels: from four
+// channels on the per-order kernels measured faster (their GEMV scores four
+// channels per pass over the rows, the single launch one).
+constexpr int kFusedMaxB = 2;
 // Dictionaries up to this size: there the single launch measured at least
 // 5 % faster than the per-order kernels (1.4x at 16.8 MB); from 1 GB on the
 // two are within 1.5 %, and larger dictionaries keep the TMA-fed GEMV.

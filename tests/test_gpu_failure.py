@@ -234,8 +234,8 @@ def test_wait_limit_zero_single_launch():
     grid barrier and raises the abort flag, which ends the others' waits;
     the next call is clean and equal to a fresh grid's."""
     w = synth.workload_c1()
-    B, P = 1, 4
-    sig = np.asarray(w.signals[:1], dtype=np.float32)
+    B, P = 2, 4
+    sig = np.stack([w.signals[0], w.signals[0][::-1]]).astype(np.float32)
     h = _grid(act.ACT_DICT_FP32, act.ACT_SEARCH_FP32, w.grid)
     ref_h = _grid(act.ACT_DICT_FP32, act.ACT_SEARCH_FP32, w.grid)
     try:

@@ -50,13 +50,13 @@ def _signals(grid, B, seed):
     return rng.standard_normal((B, grid.n_samples)).astype(np.float32)
 
 
-@pytest.mark.parametrize("seed,P", [(None, 5), (None, 1), (3, 12), (4, 40)])
-def test_single_launch_equals_per_order_kernels_c1(seed, P):
+@pytest.mark.parametrize("seed,B,P", [(None, 1, 5), (None, 1, 1), (3, 1, 12), (4, 1, 40), (5, 2, 7), (6, 2, 1)])
+def test_single_launch_equals_per_order_kernels_c1(seed, B, P):
     """16,384 atoms, N = 256: the outputs of both forms are identical (the
     check workload's signal, and white-noise signals)."""
     w = synth.workload_c1()
     grid = w.grid
-    sig = w.signals[:1] if seed is None else _signals(grid, 1, seed)
+    sig = w.signals[:1] if seed is None else _signals(grid, B, seed)
     ref, outs = _both_forms(grid, np.asarray(sig, dtype=np.float32), P, ctas_per_sm=(1, 2, 4))
     for out in outs:
         _assert_same(ref, out)
@@ -70,7 +70,7 @@ def test_single_launch_equals_per_order_kernels_c1(seed, P):
     ("eeg12k", synth.scaled_grid(synth.grid_eeg(), tc_count=12, fc_count=4, c_count=32)),
 ])
 def test_single_launch_equals_per_order_kernels(name, grid):
-    sig = _signals(grid, 1, 7)
+    sig = _signals(grid, 2, 7)
     ref, outs = _both_forms(grid, sig, 9)
     _assert_same(ref, outs[0])
 
@@ -124,7 +124,8 @@ def test_single_launch_not_used_where_it_does_not_apply():
     try:
         act.act_dictionary_build(h, act.ACT_DICT_FP32)
         assert act.act_get_fused(h, 1) > 0
-        assert act.act_get_fused(h, 2) == 0          # several channels: the per-order kernels
+        assert act.act_get_fused(h, 2) > 0
+        assert act.act_get_fused(h, 3) == 0          # more channels: the per-order kernels
         act.act_set_refinement(h, 4)
         assert act.act_get_fused(h, 1) == 0          # refinement runs its own kernels
         act.act_set_refinement(h, 0)
