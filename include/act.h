@@ -458,11 +458,10 @@ ACT_API void act_ragged_plan_destroy(act_ragged_plan *plan);
 
 /* act_search_noalloc -- the FP32 search (one projection + argmax step) for
  * callers that cannot allocate device memory.  The paper has no counterpart:
- * it exists because some callers may not call cudaMalloc -- code inside a
- * CUDA stream capture in global mode (an allocation there is illegal), a
- * latency-bound streaming loop that cannot take the device synchronisation
- * an allocation implies, or a process whose device memory is fully reserved
- * by another allocator.  It allocates nothing and uses no grid object.
+ * it exists because some callers may not call cudaMalloc -- a latency-bound
+ * streaming loop that cannot take the device synchronisation an allocation
+ * implies, or a process whose device memory is fully reserved by another
+ * allocator.  It allocates nothing and uses no grid object.
  *
  * For each channel b it returns the atom i maximising |<D_i, r_b>| (lowest
  * index on ties) and that |score|, computed exactly as act_decompose's FP32
@@ -478,10 +477,9 @@ ACT_API void act_ragged_plan_destroy(act_ragged_plan *plan);
  * Scratch: a fixed 2056-byte device array inside the library (one key per
  * channel plus a status word), held by every GPU that loads the library
  * until exit.  The first call on a device looks up that array's address with
- * cudaGetSymbolAddress while the device is current; make that first call
- * before any stream capture.  The first call with each row stride, and with
- * one and with several channels, also loads that kernel's code on the
- * device; make those first calls before any stream capture as well.  Every call clears and reuses the same array,
+ * cudaGetSymbolAddress while the device is current, and the first call with
+ * each row stride, and with one and with several channels, loads that
+ * kernel's code on the device.  Every call clears and reuses the same array,
  * so calls whose GPU work overlaps (different streams, or different host
  * threads on one device) race and must be serialised by the caller.
  * Enqueued on cuda_stream; nothing is waited for. */

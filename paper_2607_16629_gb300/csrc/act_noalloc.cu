@@ -1,13 +1,11 @@
 // act_search_noalloc: the FP32 search (GEMV with the argmax fused) for callers
 // that must not allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc is not allowed or not
-// acceptable -- inside a CUDA stream capture in global mode (an allocation
-// there is illegal and invalidates the capture), in a latency-bound streaming
-// loop where the implicit device synchronisation of an allocation would stall
-// the pipeline, or in a host process whose device memory is entirely
-// reserved up front by another allocator (a framework's caching allocator
-// holding the whole HBM).  Such callers own every buffer they pass; the only
+// Who needs it: code that runs where cudaMalloc is not acceptable -- a
+// latency-bound streaming loop where the implicit device synchronisation of
+// an allocation would stall the pipeline, or a host process whose device
+// memory is entirely reserved up front by another allocator (a framework's
+// caching allocator holding the whole HBM).  Such callers own every buffer they pass; the only
 // extra memory this path touches is the fixed scratch array below.
 #include <cuda_runtime.h>
 #include <stdint.h>

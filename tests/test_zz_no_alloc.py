@@ -1,6 +1,6 @@
 """act_search_noalloc, the search entry point for callers that cannot
-allocate device memory (inside a stream capture in global mode, in a
-latency-bound loop, or with all device memory reserved elsewhere).
+allocate device memory (in a latency-bound loop, or with all device memory
+reserved elsewhere).
 
 Its selections and scores must equal those of the allocating entry points
 (act_decompose's one-order FP32 search for the index, act_project for the
