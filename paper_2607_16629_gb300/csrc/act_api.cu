@@ -61,6 +61,17 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Memory the kernels of device `dev` may read and write directly: that
+// device's own allocations, or managed memory.
+bool is_local_device_ptr(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
 int round_up(int x, int g) { return (x + g - 1) / g * g; }
 
 // FP32 row stride: the smallest instantiated GEMV width that holds L.
@@ -820,12 +831,15 @@ act_status act_decompose(act_grid *g, const float *signals, int32_t channels, in
     act_status s = ensure_work(g, channels, n_atoms, mode);
     if (s != ACT_OK) return s;
     bool host_seen = !is_device_ptr(signals);
-    // all buffers in device memory and the single-launch form applies: the
-    // kernel reads the signals and writes the outputs itself (no graph, no copies)
+    // all buffers in the grid device's memory and the single-launch form
+    // applies: the kernel reads the signals and writes the outputs itself
+    // (no graph, no copies)
     const int fctas = fused_ctas(g, channels, mode, g->profiling);
-    if (fctas > 0 && !host_seen && (!atoms_out || is_device_ptr(atoms_out)) &&
-        (!coeffs_out || is_device_ptr(coeffs_out)) && (!residuals_out || is_device_ptr(residuals_out)) &&
-        (!energy_out || is_device_ptr(energy_out))) {
+    const int dev = g->device;
+    if (fctas > 0 && is_local_device_ptr(signals, dev) && (!atoms_out || is_local_device_ptr(atoms_out, dev)) &&
+        (!coeffs_out || is_local_device_ptr(coeffs_out, dev)) &&
+        (!residuals_out || is_local_device_ptr(residuals_out, dev)) &&
+        (!energy_out || is_local_device_ptr(energy_out, dev))) {
         ACT_CK(launch_mp_fused(g->d32, g->K, g->Lp, g->L, signals, channels, n_atoms, g->ax, g->w.fsync, atoms_out,
                                coeffs_out, energy_out, residuals_out, g->L, g->status, fctas, g->wait_ns, st));
         g->last = nullptr;
