@@ -148,3 +148,45 @@ def test_single_launch_not_used_where_it_does_not_apply():
         assert act.act_get_fused(h, 1) == 0
     finally:
         act.act_destroy(h)
+
+
+def test_single_launch_optional_outputs():
+    """Outputs the caller leaves out (null pointers) are not written; the
+    ones it asks for equal those of a call that asks for everything."""
+    w = synth.workload_c1()
+    P = 6
+    sig = torch.tensor(np.asarray(w.signals[:1], dtype=np.float32), device="cuda")
+    h = act.act_grid_create(w.grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        assert act.act_get_fused(h, 1) > 0
+        atoms, coef, resid, energy = act.decompose(h, sig, P)
+        for keep in ("atoms", "coef", "resid", "energy"):
+            out = {"atoms": torch.zeros_like(atoms), "coef": torch.zeros_like(coef),
+                   "resid": torch.zeros_like(resid), "energy": torch.zeros_like(energy)}
+            args = [out[k] if k == keep else None for k in ("atoms", "coef", "resid", "energy")]
+            act.act_decompose(h, sig, 1, P, *args)
+            torch.cuda.synchronize()
+            assert act.act_grid_status(h) == act.ACT_OK
+            ref = {"atoms": atoms, "coef": coef, "resid": resid, "energy": energy}[keep]
+            assert torch.equal(out[keep], ref), keep
+    finally:
+        act.act_destroy(h)
+
+
+def test_single_launch_reports_nonfinite_input():
+    w = synth.workload_c1()
+    s = np.asarray(w.signals[:1], dtype=np.float32).copy()
+    s[0, 17] = np.inf
+    h = act.act_grid_create(w.grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_FP32)
+        assert act.act_get_fused(h, 1) > 0
+        act.decompose(h, torch.tensor(s, device="cuda"), 3)
+        assert act.act_grid_status(h) == act.ACT_ERR_NONFINITE
+        assert act.act_grid_status(h) == act.ACT_OK  # read and cleared
+        # the next clean call is clean
+        act.decompose(h, torch.tensor(np.asarray(w.signals[:1], dtype=np.float32), device="cuda"), 3)
+        assert act.act_grid_status(h) == act.ACT_OK
+    finally:
+        act.act_destroy(h)
