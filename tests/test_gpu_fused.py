@@ -190,3 +190,18 @@ def test_single_launch_reports_nonfinite_input():
         assert act.act_grid_status(h) == act.ACT_OK
     finally:
         act.act_destroy(h)
+
+
+def test_single_launch_many_orders():
+    """300 orders (the key slots rotate 100 times; the per-order graph has
+    600 kernels): both forms equal bit for bit, the energy never rises and
+    the energy identity holds."""
+    w = synth.workload_c1()
+    sig = _signals(w.grid, 1, 21)
+    ref, outs = _both_forms(w.grid, sig, 300)
+    for out in outs:
+        _assert_same(ref, out)
+    _, _, coef, _, energy = ref
+    e0 = energy[0, 0]
+    assert np.all(np.diff(energy[0]) <= 1e-7 * e0)
+    assert abs(e0 - (np.sum(coef[0].astype(np.float64) ** 2) + energy[0, -1])) <= 1e-5 * e0
