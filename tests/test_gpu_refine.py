@@ -226,3 +226,25 @@ def test_autograd_function_drives_a_refinement():
         # the optimum is flat along some axes (logDt): parameters within 0.05 grid steps
         assert np.max(np.abs(th[b] - kern[b]) / wgt) <= 5e-2, (b, th[b], kern[b])
         assert abs(abs(c1.cpu().numpy()[b, 0]) - abs(s_kern)) <= 1e-5 * abs(s_kern)
+
+
+def test_refinement_does_not_depend_on_the_cluster_size():
+    """64 channels refine on clusters of 2 CTAs (every channel's cluster
+    resident at once), one channel on a cluster of 4: each line search takes
+    the first step that satisfies the Armijo condition either way, so a
+    channel's refined decomposition is the same bit for bit."""
+    w = synth.workload_c3()
+    P = 3
+    sig = torch.tensor(w.signals, dtype=torch.float32, device="cuda")
+    h = act.act_grid_create(w.grid, 0)
+    try:
+        act.act_dictionary_build(h, act.ACT_DICT_RECOMPUTE)
+        act.act_set_refinement(h, 20)
+        full = [t.cpu().numpy() for t in act.decompose(h, sig, P)]
+        for ch in (0, 37, 63):
+            one = [t.cpu().numpy() for t in act.decompose(h, sig[ch:ch + 1], P)]
+            for a, b in zip(one, full):
+                assert np.array_equal(a[0], b[ch]), ch
+        assert act.act_grid_status(h) == act.ACT_OK
+    finally:
+        act.act_destroy(h)
